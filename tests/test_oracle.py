@@ -1,0 +1,314 @@
+"""The FP64 oracle against what the paper and the mathematics fix (no GPU).
+
+Pins: the 2^N statevector (brute force), closed forms at gamma = 0 and beta = 0,
+normalisation, the closed-form p=1 MaxCut edge energy (Wang et al.), numpy's
+own einsum over the whole network, hand-worked greedy and slicing examples
+(tests/golden), the slice-sum invariant (Eq. 2), brute-force minimum width on
+tiny graphs, and numbers printed in the paper for the ledger's conventions.
+"""
+
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import contract, energy, ledger, network, ordering, slicing, statevector
+from paper_2012_02430_gb300.inputs import qaoa_instance, random_regular_graph
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def load(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def adj_of(n, edges):
+    a = np.zeros((n, n), dtype=bool)
+    for u, v in edges:
+        a[u, v] = a[v, u] = True
+    return a
+
+
+def problem(n, p, seed):
+    edges, g, b, z = qaoa_instance(n, p, seed)
+    t, nv, norm = network.build_network(n, edges, p, g, b, z)
+    adj = ordering.adjacency_matrix(network.line_graph(t, nv), nv)
+    return edges, g, b, z, t, nv, norm, adj
+
+
+# ----------------------------- network & statevector ------------------------
+
+def test_gate_matrices_match_matrix_exponentials():
+    from scipy.linalg import expm
+    x = np.array([[0, 1], [1, 0]], dtype=complex)
+    for beta in (0.0, 0.37, 1.9, 3.0):
+        u = expm(-1j * beta * x)  # exp(-i beta X), rows a', columns a
+        m = network.mixer_matrix(beta)  # M[a, a'] = <a'|U|a>
+        assert np.allclose(m, u.T, atol=1e-14)
+    zz = np.diag([1, -1, -1, 1]).astype(complex)
+    for gamma in (0.0, 0.5, 2.2):
+        cost = expm(-1j * gamma * 0.5 * (np.eye(4) - zz))
+        d = network.phase_matrix(gamma)
+        assert np.allclose(np.diag(cost).reshape(2, 2), d, atol=1e-14)
+
+
+def test_network_counts():
+    n, p = 10, 3
+    edges, g, b, z = qaoa_instance(n, p, 4)
+    t, nv, norm = network.build_network(n, edges, p, g, b, z)
+    assert nv == n * p
+    assert len(t) == n + p * len(edges) + n * (p - 1) + n
+    assert norm == 2.0 ** (-n / 2)
+
+
+def test_random_regular_graph_is_simple_and_regular():
+    for n, seed in [(10, 1), (80, 1002), (210, 1005)]:
+        e = random_regular_graph(n, 3, seed)
+        assert len(e) == 3 * n // 2 and len(set(e)) == len(e)
+        deg = [0] * n
+        for u, v in e:
+            assert u < v
+            deg[u] += 1
+            deg[v] += 1
+        assert deg == [3] * n
+
+
+@pytest.mark.parametrize("n,p,seed", [(6, 1, 1), (8, 2, 2), (10, 3, 3)])
+def test_statevector_normalised(n, p, seed):
+    edges, g, b, z = qaoa_instance(n, p, seed)
+    psi = statevector.qaoa_state(n, edges, g, b)
+    assert abs(np.vdot(psi, psi) - 1) < 1e-12
+
+
+def test_statevector_mixer_matches_full_exponential():
+    """The per-qubit mixer equals exp(-i beta sum_v X_v) built as one 2^N matrix."""
+    from scipy.linalg import expm
+    n = 4
+    edges = [(0, 1), (1, 2), (2, 3), (0, 3)]
+    g, b = [0.8], [0.45]
+    x = np.array([[0, 1], [1, 0]], dtype=complex)
+    bsum = np.zeros((1 << n, 1 << n), dtype=complex)
+    for q in range(n):
+        ops = [np.eye(2)] * n
+        ops[n - 1 - q] = x  # kron order: qubit q is bit q of the index
+        m = ops[0]
+        for o in ops[1:]:
+            m = np.kron(m, o)
+        bsum += m
+    cut = statevector.cut_values(n, edges)
+    psi0 = np.full(1 << n, 2 ** (-n / 2), dtype=complex)
+    ref = expm(-1j * b[0] * bsum) @ (np.exp(-1j * g[0] * cut) * psi0)
+    assert np.allclose(statevector.qaoa_state(n, edges, g, b), ref, atol=1e-13)
+
+
+@pytest.mark.parametrize("n,p,seed", [(8, 1, 11), (10, 2, 12), (12, 3, 13)])
+def test_closed_forms_gamma_zero_beta_zero(n, p, seed):
+    edges, g, b, z = qaoa_instance(n, p, seed)
+    t, nv, norm = network.build_network(n, edges, p, [0.0] * p, b, z)
+    adj = ordering.adjacency_matrix(network.line_graph(t, nv), nv)
+    o, _ = ordering.greedy_order(adj)
+    a, _ = contract.contract_amplitude(t, o)
+    assert abs(a * norm - 2 ** (-n / 2) * np.exp(-1j * n * sum(b))) < 1e-13
+    t, nv, norm = network.build_network(n, edges, p, g, [0.0] * p, z)
+    a, _ = contract.contract_amplitude(t, o)
+    cut = sum(z[u] != z[v] for u, v in edges)
+    assert abs(a * norm - 2 ** (-n / 2) * np.exp(-1j * sum(g) * cut)) < 1e-13
+
+
+# ----------------------------- bucket elimination ---------------------------
+
+@pytest.mark.parametrize("n,p,seed,algo", [(6, 1, 21, 0), (10, 2, 22, 1), (12, 3, 23, 0),
+                                           (14, 2, 24, 1), (20, 1, 1001, 0)])
+def test_bucket_elimination_equals_statevector(n, p, seed, algo):
+    edges, g, b, z, t, nv, norm, adj = problem(n, p, seed)
+    o, _ = ordering.greedy_order(adj, None, algo)
+    a, _ = contract.contract_amplitude(t, o)
+    sv = statevector.amplitude(n, edges, g, b, z)
+    assert abs(a * norm - sv) <= 1e-12 * abs(sv)
+
+
+def test_bucket_elimination_equals_whole_network_einsum():
+    """numpy's einsum over the whole network, its own path: an independent contraction."""
+    n, p = 6, 2
+    edges, g, b, z, t, nv, norm, adj = problem(n, p, 31)
+    args = []
+    for labels, data in t:
+        args += [data, list(labels)]
+    whole = np.einsum(*args, [], optimize="greedy")
+    o, _ = ordering.greedy_order(adj)
+    a, _ = contract.contract_amplitude(t, o)
+    assert abs(a - whole) < 1e-12 * abs(whole)
+
+
+@pytest.mark.parametrize("n,p,seed,algo,drop,r", [(10, 2, 2, 0, 2, 1), (12, 3, 3, 1, 3, 2),
+                                                  (16, 2, 41, 0, 3, 1), (14, 3, 42, 1, 4, 1)])
+def test_slicing_sum_invariant(n, p, seed, algo, drop, r):
+    """Eq. 2: the sum over all slices equals the unsliced contraction."""
+    edges, g, b, z, t, nv, norm, adj = problem(n, p, seed)
+    o, w = ordering.greedy_order(adj, None, algo)
+    full, _ = contract.contract_amplitude(t, o)
+    plan = slicing.step_dependent_slicing(adj, algo, max(w) - drop, 4, r)
+    assert plan["sliced"], "the plan must slice"
+    tot, per = contract.contract_amplitude(t, plan["order"], plan["sliced"], plan["slice_step"])
+    assert len(per) == 1 << len(plan["sliced"])
+    assert abs(tot - full) < 1e-12 * abs(full)
+    sv = statevector.amplitude(n, edges, g, b, z)
+    assert abs(tot * norm - sv) < 1e-12 * abs(sv)
+
+
+# ----------------------------- orders and widths ----------------------------
+
+def test_greedy_hand_examples():
+    for c in load("greedy_hand.json")["cases"]:
+        a = adj_of(c["n"], c["edges"])
+        for algo, key in ((ordering.MIN_DEGREE, "mindeg"), (ordering.MIN_FILL, "minfill")):
+            o, w = ordering.greedy_order(a, None, algo)
+            assert o == c[key]["order"] and w == c[key]["widths"], (c["name"], key)
+
+
+def brute_min_width(a):
+    n = a.shape[0]
+    best = n
+    for perm in itertools.permutations(range(n)):
+        best = min(best, max(ordering.replay_widths(a, perm)))
+    return best
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_width_at_least_brute_force_minimum(seed):
+    """No order beats the minimum over all orders (the treewidth, Sec. IV.B)."""
+    rng = np.random.default_rng(seed)
+    n = 7
+    a = rng.random((n, n)) < 0.45
+    a = np.triu(a, 1)
+    a = a | a.T
+    tw = brute_min_width(a)
+    for algo in (ordering.MIN_FILL, ordering.MIN_DEGREE):
+        _, w = ordering.greedy_order(a, None, algo)
+        assert max(w) >= tw
+
+
+def test_widths_of_known_graphs():
+    """Trees have treewidth 1, cycles 2, K_n n-1; greedy reaches them."""
+    tree = [(0, 1), (0, 2), (1, 3), (1, 4), (2, 5), (5, 6)]
+    cyc = [(i, (i + 1) % 9) for i in range(9)]
+    kn = list(itertools.combinations(range(6), 2))
+    for edges, n, want in ((tree, 7, 1), (cyc, 9, 2), (kn, 6, 5)):
+        for algo in (ordering.MIN_FILL, ordering.MIN_DEGREE):
+            _, w = ordering.greedy_order(adj_of(n, edges), None, algo)
+            assert max(w) == want
+
+
+def test_replay_matches_greedy_profile():
+    edges, g, b, z, t, nv, norm, adj = problem(30, 2, 5)
+    o, w = ordering.greedy_order(adj)
+    assert ordering.replay_widths(adj, o) == w
+
+
+# ----------------------------- slicing ---------------------------------------
+
+def test_slicing_hand_examples():
+    for c in load("slicing_hand.json")["cases"]:
+        a = adj_of(c["n"], c["edges"])
+        plan = slicing.step_dependent_slicing(a, ordering.MIN_DEGREE, c["width_limit"],
+                                              c["max_vars"], 1)
+        e = c["expect"]
+        assert plan["sliced"] == e["sliced"], c["name"]
+        assert plan["slice_step"] == e["slice_step"], c["name"]
+        assert plan["order"] == e["order"], c["name"]
+        assert plan["width"] == e["width"], c["name"]
+
+
+def test_slicing_plan_widths_replay():
+    """The plan's width profile is what eliminating its order on the graph gives
+    (slice vertices removed at their round's step; later rounds' vertices still present
+    during earlier segments)."""
+    edges, g, b, z, t, nv, norm, adj = problem(24, 2, 8)
+    plan = slicing.step_dependent_slicing(adj, ordering.MIN_FILL, 8, 4, 1)
+    a = adj.copy()
+    np.fill_diagonal(a, False)
+    alive = np.ones(nv, dtype=bool)
+    widths = []
+    rounds = list(plan["rounds"])
+    done = 0
+    for i, v in enumerate(plan["order"]):
+        while rounds and rounds[0][0] == i:
+            for x in rounds.pop(0)[1]:
+                ordering.remove_vertex(a, alive, x)
+        nb = np.flatnonzero(a[v])
+        widths.append(len(nb))
+        ordering.eliminate(a, alive, v, nb)
+        done += 1
+    assert widths == plan["widths"]
+    assert max(widths) == plan["width"]
+    assert plan["width"] <= 8 or len(plan["sliced"]) == 4
+
+
+# ----------------------------- ledger ----------------------------------------
+
+def test_ledger_hand_example():
+    """Path network A(x0) B(x0,x1) C(x1): step x0: m=2, u=2, c=1; step x1: m=2, u=1, c=0."""
+    labels = [(0,), (0, 1), (1,)]
+    tot, steps = ledger.ledger(labels, [0, 1])
+    assert [(s["m"], s["u"], s["c"]) for s in steps] == [(2, 2, 1), (2, 1, 0)]
+    # step 0: 6*(2-1)*4 + 2*(4-2) = 28 flops; bytes 8*(2+4+2) = 64
+    # step 1: 6*(2-1)*2 + 2*(2-1) = 14 flops; bytes 8*(2+2+1) = 40
+    assert [s["flops"] for s in steps] == [28, 14]
+    assert [s["bytes"] for s in steps] == [64, 40]
+
+
+def test_ledger_paper_numbers():
+    pn = load("paper_numbers.json")
+    # a rank-44 result in complex128
+    b = ledger.step_bytes([], 44, elem_bytes=16)
+    assert round(b / 1e12) == pn["width44_bytes_TB"]["value"]
+    assert round(4 * 2 ** 44 / 1e12) == pn["width44_flops_T"]["value"]
+    s = pn["slicing_speedup_64_nodes"]
+    assert 2 ** (s["width_before"] - s["width_after"]) == s["value"]
+    assert 2 ** pn["one_index_width_drop"]["value"] == pn["one_index_width_drop"]["speedup"]
+
+
+def test_ledger_slicing_counts():
+    """Per-slice steps drop sliced indices from every operand; prefix steps keep them."""
+    edges, g, b, z, t, nv, norm, adj = problem(16, 2, 41)
+    plan = slicing.step_dependent_slicing(adj, ordering.MIN_FILL, 5, 3, 1)
+    tot, steps = ledger.ledger([l for l, _ in t], plan["order"], plan["sliced"], plan["slice_step"])
+    k = len(plan["sliced"])
+    assert tot["total_flops"] == tot["prefix_flops"] + tot["slice_flops"] * 2 ** k
+    assert tot["slice_width"] <= plan["width"]
+    assert all(s["c"] == s["u"] - 1 for s in steps)
+    assert sum(1 for s in steps if s["region"] == "prefix") == tot["n_prefix_steps"]
+
+
+# ----------------------------- energy ----------------------------------------
+
+@pytest.mark.parametrize("n,p,seed", [(10, 1, 5), (12, 2, 6), (10, 3, 7)])
+def test_lightcone_energy_equals_statevector(n, p, seed):
+    edges, g, b, z = qaoa_instance(n, p, seed)
+    e_sv = statevector.maxcut_energy(n, edges, g, b)
+    e_lc, zz = energy.energy_lightcone(n, edges, p, g, b)
+    assert abs(e_sv - e_lc) < 1e-11
+    assert all(abs(x.imag if isinstance(x, complex) else 0.0) < 1e-12 for x in zz)
+
+
+def test_p1_closed_form_energy_with_triangles():
+    """Closed form with the triangle term, on graphs with triangles and mixed degrees."""
+    graphs = [(4, list(itertools.combinations(range(4), 2))),
+              (6, [(0, 1), (1, 2), (0, 2), (2, 3), (3, 4), (4, 5), (3, 5), (0, 5)])]
+    for n, edges in graphs:
+        for g, b in [(0.4, 0.3), (1.3, 2.1), (2.9, 0.7)]:
+            zz = statevector.zz_expectations(n, edges, [g], [b])
+            for (u, v), x in zip(edges, zz):
+                cf = energy.edge_energy_p1_closed_form(n, edges, g, b, u, v)
+                assert abs(cf - 0.5 * (1 - x)) < 1e-12
+
+
+def test_p1_closed_form_on_3_regular():
+    n = 12
+    edges, g, b, z = qaoa_instance(n, 1, 9)
+    e = sum(energy.edge_energy_p1_closed_form(n, edges, g[0], b[0], u, v) for u, v in edges)
+    assert abs(e - statevector.maxcut_energy(n, edges, g, b)) < 1e-11
