@@ -1,0 +1,344 @@
+"""Benchmark: slices/s of the sliced bucket-elimination amplitude on one GB300.
+
+Workload (one "step" = one pass of the whole hot path): the amplitude of p=2
+QAOA MaxCut on a seeded random 3-regular graph with N=80 vertices (seed 1002),
+greedy min-fill order, step-dependent slicing to contraction width <= 26, all
+2^k slices contracted on the GPU (complex64 steps, FP64 slice sum) and summed
+into one amplitude. Synthetic data: the paper's workload is itself synthetic
+(random 3-regular graphs), drawn here from a fixed seed.
+
+Printed: one JSON line (rank 0). `value` is device-resident throughput (gate
+tensors already in HBM); `e2e` goes through qt_contract with host inputs
+(new angles every step: host network rebuild, upload, contraction, download).
+`roofline` is the dominant kernel's algorithmic bytes over its live
+CUDA-event launch times. `cpu_baseline` is the FP64 oracle on a bounded sample.
+`--impl reference` times the oracle alone as the reference arm.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "slices/s & complex TFLOP/s vs plain FP32 greedy GPU path at rel.err<=1e-5"
+WORKLOAD = dict(n=80, p=2, seed=1002, width_limit=26, max_vars=20, r=1, algo="greedy-minfill")
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-slices", type=int, default=1)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def instance(rank):
+    from paper_2012_02430_gb300.inputs import qaoa_instance, random_bitstring
+    edges, gammas, betas, z = qaoa_instance(WORKLOAD["n"], WORKLOAD["p"], WORKLOAD["seed"])
+    if rank:  # weak scaling: every rank its own bitstring of the same circuit
+        z = random_bitstring(WORKLOAD["n"], WORKLOAD["seed"] + 7919 * rank)
+    return edges, gammas, betas, z
+
+
+# ------------------------------- CPU oracle ---------------------------------
+
+def oracle_sample(n_slices, rank=0):
+    """Times the FP64 oracle on `n_slices` slices of the workload (plan built first)."""
+    from oracle import contract, network, ordering, slicing
+    edges, gammas, betas, z = instance(rank)
+    tensors, nv, norm = network.build_network(WORKLOAD["n"], edges, WORKLOAD["p"], gammas, betas, z)
+    adj = ordering.adjacency_matrix(network.line_graph(tensors, nv), nv)
+    plan = slicing.step_dependent_slicing(adj, ordering.MIN_FILL, WORKLOAD["width_limit"],
+                                          WORKLOAD["max_vars"], WORKLOAD["r"])
+    k = len(plan["sliced"])
+    ids = list(range(min(n_slices, 1 << k)))
+    t0 = time.perf_counter()
+    contract.contract_amplitude(tensors, plan["order"], plan["sliced"], plan["slice_step"], ids)
+    dt = time.perf_counter() - t0
+    return len(ids), dt, k
+
+
+def cpu_threads_used():
+    # numpy.einsum (the oracle's contraction primitive) runs on one thread
+    return 1
+
+
+def reference_arm(args):
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            dist.destroy_process_group()
+            return
+    per_step = max(1, args.cpu_sample_slices)
+    for _ in range(args.warmup):
+        oracle_sample(per_step)
+    total_slices, total_t, k = 0, 0.0, 0
+    for _ in range(args.steps):
+        ns, dt, k = oracle_sample(per_step)
+        total_slices += ns
+        total_t += dt
+    v = total_slices / total_t
+    sample = (f"{per_step} of the 2^{k} slices per step (prefix + per-slice bucket elimination, "
+              f"complex128 numpy.einsum), plan built outside the timed region")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "slices/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": "qaoa-maxcut-amplitude N=80 p=2 3-regular seed=1002 "
+                               "min-fill sliced to width<=26", **WORKLOAD},
+        "cpu_baseline": {"value": v, "unit": "slices/s", "cores": cpu_threads_used(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "slices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ------------------------------- clocks --------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------- GPU arm -------------------------------------
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def ours(args):
+    import torch
+
+    from paper_2012_02430_gb300 import qtensor as Q
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    prec = Q.QT_FP64 if args.precision == "fp64" else Q.QT_FP32_SIMT
+    edges, gammas, betas, z = instance(rank)
+    net = Q.Network(edges, WORKLOAD["n"], WORKLOAD["p"], gammas, betas, z)
+    t_plan = time.perf_counter()
+    width = net.order(Q.QT_GREEDY_MINFILL)
+    k, sliced_width = net.slice(WORKLOAD["width_limit"], WORKLOAD["max_vars"], WORKLOAD["r"])
+    t_plan = time.perf_counter() - t_plan
+    nslices = 1 << k
+    net.prepare(prec, batch=nslices)
+    st = net.stats()
+    net.upload()
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        net.run(0, nslices, out)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: K steps, L2 flushed between steps (outside the event pairs)
+    launches0 = net.stats()["launches"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = net.stats()["launches"] - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * nslices * args.steps / (total_ms / 1e3)
+    amp = complex(out[0].item(), out[1].item())
+    flops_per_step = st["prefix_flops"] + st["slice_flops"] * nslices
+    bytes_per_step = (st["prefix_bytes"] + st["slice_bytes"] * nslices) * (st["elem_bytes"] // 8)
+    tflops = world * flops_per_step * args.steps / (total_ms / 1e3) / 1e12
+
+    # per-launch times of the same workload (events around every launch)
+    Q.qt_profile(net.handle, 1)
+    for i in range(max(1, min(args.steps, 5))):
+        flush.fill_(i & 0xFF)
+        step()
+    recs = Q.qt_profile_read(net.handle)
+    Q.qt_profile(net.handle, 0)
+    by_kind = {}
+    for r in recs:
+        d = by_kind.setdefault(r["kernel"], {"ms": 0.0, "bytes": 0, "flops": 0, "n": 0})
+        d["ms"] += r["ms"]
+        d["bytes"] += r["bytes"]
+        d["flops"] += r["flops"]
+        d["n"] += 1
+    kind_names = {0: "k_bucket_flat", 1: "k_bucket_tiled", 2: "k_finalize+k_reduce"}
+    tot_ms = sum(d["ms"] for d in by_kind.values()) or 1.0
+    dom = max(by_kind, key=lambda kk: by_kind[kk]["ms"])
+    d = by_kind[dom]
+    peak, peak_src = measured_peaks()
+    achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": kind_names[dom], "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs",
+                "traffic": None, "launches": d["n"],
+                "share": {kind_names[kk]: by_kind[kk]["ms"] / tot_ms for kk in by_kind}}
+
+    # end to end: host inputs -> amplitude on the host, through qt_contract
+    from paper_2012_02430_gb300.inputs import random_angles
+    e2e_steps = max(3, min(args.steps, 10))
+    gstage = st.get("workspace_bytes", 0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        g2, b2 = random_angles(WORKLOAD["p"], 5000 + i)
+        Q.qt_set_angles(net.handle, g2, b2)
+        net.contract(prec)
+    t_e2e = time.perf_counter() - t0
+    h2d = gate_upload_bytes(st)
+    e2e = {"value": world * nslices * e2e_steps / t_e2e, "unit": "slices/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16,
+           "ms_per_step": 1e3 * t_e2e / e2e_steps,
+           "includes": "qt_set_angles (host tensors) + qt_contract (H2D gates, all slices, D2H amplitude, stream sync)"}
+    del gstage
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64" if prec == Q.QT_FP32_SIMT else "c128", "data": "synthetic",
+        "config": {"workload": "qaoa-maxcut-amplitude N=80 p=2 3-regular seed=1002 "
+                               "min-fill sliced to width<=26",
+                   **WORKLOAD, "k": k, "slices": nslices, "width": width,
+                   "sliced_width": sliced_width, "precision": args.precision,
+                   "l2": "flushed between steps (512 MiB write outside the timed events)",
+                   "plan_seconds": t_plan},
+        "complex_tflops": tflops, "ledger_flops_per_step": flops_per_step,
+        "ledger_bytes_per_step": bytes_per_step,
+        "amplitude": [amp.real, amp.imag],
+        "gpu_launches": launches,
+        "roofline": roofline, "clocks": clk, "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ns, dt, _ = oracle_sample(args.cpu_sample_slices)
+        line["cpu_baseline"] = {"value": ns / dt, "unit": "slices/s", "cores": cpu_threads_used(),
+                                "kind": "oracle",
+                                "sample": f"{ns} slice(s) of the same workload, FP64 oracle "
+                                          f"(numpy.einsum bucket elimination), {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def gate_upload_bytes(st):
+    """Bytes of the host-to-device copies of one qt_contract (gates, gate meta, scalar table)."""
+    return int(st.get("upload_bytes", 0))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * qtensor.h -- C ABI of the GB300 sliced bucket-elimination QAOA simulator.
+ *
+ * The library computes the amplitude <z| psi_p(gamma, beta) > of the QAOA
+ * MaxCut ansatz (Sec. III.A of "Tensor Network Quantum Simulator With
+ * Step-Dependent Parallelization", arXiv:2012.02430) by bucket elimination of
+ * its line-graph tensor network (Sec. IV, Alg. 1) under step-dependent slicing
+ * (Sec. VI.C-D, Eq. 2). Every slice is an independent contraction on the GPU;
+ * the slice results are summed in FP64.
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns a qt_status and never throws or aborts. On failure the
+ *     message of the calling thread's last error is available from
+ *     qt_last_error(); a failed call leaves the network as it was unless its
+ *     comment says otherwise.
+ *   - The library copies every input array; outputs go into caller buffers.
+ *   - The library allocates no device memory. Device work runs in a caller
+ *     workspace (a device pointer and its size in bytes; size from
+ *     qt_prepare, base aligned to 256 bytes) on the caller's CUDA stream
+ *     (a cudaStream_t passed as void*, NULL for the legacy default stream).
+ *   - A network is not thread-safe: calls on one qt_net must not overlap.
+ *     Distinct networks are independent.
+ *   - Calls that need a GPU return QT_ECUDA when the CUDA runtime reports an
+ *     error; host-only calls (build, order, slice, schedule queries) need none.
+ */
+#ifndef QTENSOR_H
+#define QTENSOR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qt_net qt_net; /* opaque, owned by the library, freed by qt_free */
+
+typedef enum {
+  QT_OK = 0,
+  QT_EINVAL = 1,   /* bad argument: null pointer, out-of-range value, non-simple graph */
+  QT_ENOMEM = 2,   /* host allocation failed, or the workspace is too small */
+  QT_ECUDA = 3,    /* the CUDA runtime reported an error */
+  QT_ETIMEOUT = 4, /* a bounded device-side wait ran out */
+  QT_ESTATE = 5,   /* call made in the wrong order (e.g. contract before order) */
+  QT_ERANGE = 6    /* a tensor rank exceeds what the kernels address (32) */
+} qt_status;
+
+/* Ordering rules (Sec. V.A.1). Ties always go to the smaller vertex id. */
+enum {
+  QT_GREEDY_MINFILL = 0, /* key (fill-in, degree, id) */
+  QT_GREEDY_MINDEG = 1   /* key (degree, id): the paper's "lowest-degree vertex" */
+};
+
+/* Arithmetic of the bucket steps. Slice accumulation is FP64 in every mode. */
+enum {
+  QT_FP32_SIMT = 0, /* complex64 tensors, FP32 CUDA-core arithmetic */
+  QT_FP64 = 4       /* complex128 tensors, FP64 CUDA-core arithmetic */
+};
+
+/*
+ * Builds the tensor network of <z| U(gamma, beta) |+>^N (Sec. III.A; Sec. IV.A,
+ * Table I; line graph with diagonal gates, Sec. IV.B, Fig. 2).
+ *   edges       n_edges pairs (u, v), int32, row-major [n_edges][2]; the graph
+ *               must be simple (no loops, no repeated edge), ids in [0, n_vertices)
+ *   p           QAOA depth >= 1; gammas, betas: p doubles each (layer 1 first)
+ *   bitstring   n_vertices bytes, each 0 or 1 (bit v is qubit v)
+ *   out         receives the new network; free it with qt_free
+ * Variables are (v, k), k = 0..p-1, with id k*N + v. Tensors, in order: |+> on
+ * (v,0) for each v; then per layer k the phase exp(-i gamma_k [a != b]) on each
+ * edge's (u,k-1),(v,k-1), then the mixer <a'|exp(-i beta_k X)|a> on
+ * (v,k-1),(v,k) (k < p) or its row a' = z_v on (v,p-1) (k = p). The factor
+ * 2^(-N/2) of |+>^N is applied once to the final FP64 sum.
+ * Errors: QT_EINVAL for a null pointer, n_vertices < 1, p < 1, an edge id out
+ * of range, a loop or repeated edge, a bit that is not 0/1, more than 2^20
+ * variables; QT_ENOMEM on host allocation failure.
+ */
+qt_status qt_build_network(const int32_t* edges, int32_t n_vertices, int32_t n_edges, int32_t p,
+                           const double* gammas, const double* betas, const uint8_t* bitstring,
+                           qt_net** out);
+
+/* Replaces the angles of a built network (order, slices and schedule are kept:
+ * they depend only on the structure, Sec. VIII conclusion / Fig. 7 caption).
+ * A later qt_upload is needed before device-resident runs see the new data. */
+qt_status qt_set_angles(qt_net* net, const double* gammas, const double* betas);
+
+/* Replaces the target bitstring (n_vertices bytes, 0/1); as qt_set_angles. */
+qt_status qt_set_bitstring(qt_net* net, const uint8_t* bitstring);
+
+/*
+ * Greedy elimination order of the line graph (Sec. V.A.1) and its contraction
+ * width c = max over steps of the eliminated vertex's neighbour count
+ * (Sec. IV.B). seed is reserved for randomised rules and ignored by the greedy
+ * ones. Discards any earlier slicing. width_out may be NULL.
+ * Errors: QT_EINVAL for an unknown algo; QT_ESTATE never (any built network).
+ */
+qt_status qt_order(qt_net* net, int32_t algo, uint64_t seed, int32_t* width_out);
+
+/*
+ * Step-dependent slicing (Sec. VI.C-D, Fig. 8, Alg. 1). Rounds repeat while the
+ * plan's width exceeds width_limit and fewer than max_vars vertices are sliced.
+ * A round orders the current graph greedily (rule of qt_order), and for every
+ * step s up to the first peak eliminates the first s vertices, removes the r
+ * vertices with most neighbours one at a time (ties: smaller id), re-orders the
+ * rest and keeps the s with the smallest (width, sum of 2^w, s).
+ * Execution: steps before the first round's s run once unsliced; all k sliced
+ * indices are fixed from there on, one independent contraction per slice id
+ * (bit j of the id = value of the j-th sliced vertex).
+ * k_out (number of sliced vertices) and width_out (plan width) may be NULL.
+ * Errors: QT_ESTATE before qt_order; QT_EINVAL for width_limit < 1, r < 1,
+ * max_vars < 0 or max_vars > 30.
+ */
+qt_status qt_slice(qt_net* net, int32_t width_limit, int32_t max_vars, int32_t r, int32_t* k_out,
+                   int32_t* width_out);
+
+/* Copies of the integer plan, for bit-exact checks. Each writes at most `cap`
+ * entries and stores the full length in *len. Errors: QT_ESTATE before
+ * qt_order (qt_get_slices: before qt_order), QT_EINVAL for a null len. */
+qt_status qt_get_order(const qt_net* net, int32_t* order, int32_t cap, int32_t* len);
+qt_status qt_get_widths(const qt_net* net, int32_t* widths, int32_t cap, int32_t* len);
+/* sliced vertices in slice-bit order, and the first round's step s_1 */
+qt_status qt_get_slices(const qt_net* net, int32_t* vars, int32_t cap, int32_t* len,
+                        int32_t* slice_step);
+
+/*
+ * Number of tensors and their labels (variable ids, in the gate's own axis
+ * order) and FP64 data (interleaved re, im; axis t of the labels is bit t of
+ * the element index). labels/data may be NULL to query sizes only.
+ */
+qt_status qt_get_tensor(const qt_net* net, int32_t t, int32_t* labels, int32_t* rank,
+                        double* data);
+qt_status qt_num_tensors(const qt_net* net, int32_t* count, int32_t* n_vars);
+
+/*
+ * Compiles the execution schedule for `precision` with `batch` slices per
+ * device pass (batch >= 1; clamped to the number of slices) and returns the
+ * workspace it needs. The schedule follows Alg. 1 with the slicing above:
+ * canonical layouts (indices ordered by elimination position, earliest = least
+ * significant bit; sliced indices above all others), one fused product +
+ * sum-out kernel per bucket. Errors: QT_ESTATE before qt_order; QT_EINVAL for
+ * an unknown precision or batch < 1; QT_ERANGE if a tensor rank exceeds 32.
+ */
+qt_status qt_prepare(qt_net* net, int32_t precision, int32_t batch, size_t* workspace_bytes);
+
+/*
+ * Integer ledger of the prepared schedule (per-step FLOPs/bytes as in
+ * Alg. 1; see the DESIGN notes for the formulas), written as one JSON object
+ * into buf (NUL-terminated, truncated to cap). *needed receives the full length
+ * + 1. Errors: QT_ESTATE before qt_prepare.
+ */
+qt_status qt_stats(const qt_net* net, char* buf, size_t cap, size_t* needed);
+
+/*
+ * Copies the gate tensors (in the prepared precision and canonical layout) into
+ * the workspace, asynchronously on `stream`. The host source is a staging
+ * buffer owned by the network: it must not be modified (qt_set_angles) before
+ * the stream has passed this copy. Errors: QT_ESTATE before qt_prepare;
+ * QT_ENOMEM if workspace_bytes is below the prepared size; QT_EINVAL for a
+ * workspace not aligned to 256 bytes; QT_ECUDA.
+ */
+qt_status qt_upload(qt_net* net, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Device-resident run: contracts slices [first, first + count) of the uploaded
+ * network and writes their FP64 sum (times 2^(-N/2)) as two doubles (re, im)
+ * to the DEVICE pointer d_out, asynchronously on `stream`; no host copy, no
+ * synchronisation. The unsliced prefix (contract_first) is recomputed by every
+ * call. Errors: QT_ESTATE before qt_prepare; QT_EINVAL for a range outside
+ * [0, 2^k) or a null d_out; QT_ENOMEM for a small workspace; QT_ECUDA.
+ */
+qt_status qt_run(qt_net* net, int64_t first, int64_t count, void* workspace, size_t workspace_bytes,
+                 void* stream, double* d_out);
+
+/*
+ * End-to-end amplitude: prepares (if the precision differs from the prepared
+ * one; batch = all slices that fit the workspace), uploads the gates, runs all
+ * 2^k slices and copies the result to the HOST doubles amp_re, amp_im, then
+ * synchronises `stream`. Errors: as qt_prepare, qt_upload and qt_run.
+ */
+qt_status qt_contract(qt_net* net, int32_t precision, void* workspace, size_t workspace_bytes,
+                      void* stream, double* amp_re, double* amp_im);
+
+/*
+ * Tracing. qt_profile(net, 1) makes later qt_run / qt_contract calls record a
+ * CUDA event pair around every kernel launch on the caller's stream (a small
+ * cost per launch); qt_profile(net, 0) stops. Either call drops the records.
+ * qt_profile_read waits for the recorded events and writes a JSON array, one
+ * object per launch: {"step", "kernel" (0 flat bucket, 1 tiled bucket,
+ * 2 slice finalize + reduce), "slices", "bytes", "flops" (the ledger's
+ * algorithmic counts for that launch), "ms"} into buf (as qt_stats).
+ * Errors: QT_EINVAL for a null network; QT_ECUDA if an event fails.
+ */
+qt_status qt_profile(qt_net* net, int32_t enable);
+qt_status qt_profile_read(qt_net* net, char* buf, size_t cap, size_t* needed);
+
+/* Frees a network (NULL is a no-op). */
+void qt_free(qt_net* net);
+
+/* Message of the calling thread's last error ("" if none). Valid until the
+ * next call on that thread. */
+const char* qt_last_error(void);
+
+/* Library version string. */
+const char* qt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QTENSOR_H */

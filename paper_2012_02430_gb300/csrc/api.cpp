@@ -1,0 +1,366 @@
+// The C ABI (include/qtensor.h): argument checks, state checks, error strings,
+// and the network builder of Sec. III.A / Sec. IV.A-B.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <set>
+#include <string>
+#include <utility>
+
+#include "qt_internal.h"
+
+namespace qt {
+// engine.cu
+void build_stage(qt_net* net);
+qt_status upload(qt_net* net, void* ws, size_t bytes, void* stream, std::string& err);
+qt_status run(qt_net* net, long long first, long long count, void* ws, void* stream,
+              double* d_out, std::string& err);
+qt_status download_result(const double* d_out, double* host, void* stream, std::string& err);
+void prof_clear(qt_net* net);
+qt_status prof_read(qt_net* net, std::string& out, std::string& err);
+}  // namespace qt
+
+namespace {
+
+thread_local std::string g_err;
+
+qt_status fail(qt_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+qt_status ok() {
+  g_err.clear();
+  return QT_OK;
+}
+
+// Gate tensors of the ansatz, FP64, axis t of the labels = bit t of the index.
+void make_tensors(qt_net* net) {
+  const int n = net->n, p = net->p;
+  auto var = [n](int v, int k) { return k * n + v; };
+  std::vector<qt::Tensor>& T = net->tensors;
+  T.clear();
+  for (int v = 0; v < n; ++v) T.push_back({{var(v, 0)}, {1.0, 0.0, 1.0, 0.0}});
+  for (int k = 1; k <= p; ++k) {
+    const double g = net->gammas[k - 1], b = net->betas[k - 1];
+    // D(a, b) = exp(-i gamma [a != b]); M(a, a') = cos(beta) or -i sin(beta)
+    const double er = std::cos(g), ei = -std::sin(g);
+    const double c = std::cos(b), s = std::sin(b);
+    for (int e = 0; e < net->n_edges; ++e) {
+      const int u = net->edges[2 * e], w = net->edges[2 * e + 1];
+      T.push_back({{var(u, k - 1), var(w, k - 1)}, {1.0, 0.0, er, ei, er, ei, 1.0, 0.0}});
+    }
+    for (int v = 0; v < n; ++v) {
+      if (k < p) {
+        T.push_back({{var(v, k - 1), var(v, k)}, {c, 0.0, 0.0, -s, 0.0, -s, c, 0.0}});
+      } else {
+        // row a' = z_v of M, as a function of a
+        if (net->z[v] == 0) T.push_back({{var(v, p - 1)}, {c, 0.0, 0.0, -s}});
+        else T.push_back({{var(v, p - 1)}, {0.0, -s, c, 0.0}});
+      }
+    }
+  }
+}
+
+bool check_net(const qt_net* net) { return net != nullptr; }
+
+}  // namespace
+
+extern "C" {
+
+const char* qt_last_error(void) { return g_err.c_str(); }
+
+const char* qt_version(void) { return "qtensor-gb300 0.1 (sm_103a)"; }
+
+qt_status qt_build_network(const int32_t* edges, int32_t n_vertices, int32_t n_edges, int32_t p,
+                           const double* gammas, const double* betas, const uint8_t* bitstring,
+                           qt_net** out) {
+  if (!out) return fail(QT_EINVAL, "qt_build_network: out is NULL");
+  *out = nullptr;
+  if (!gammas || !betas || !bitstring || (n_edges > 0 && !edges))
+    return fail(QT_EINVAL, "qt_build_network: null input array");
+  if (n_vertices < 1 || p < 1 || n_edges < 0)
+    return fail(QT_EINVAL, "qt_build_network: need n_vertices >= 1, p >= 1, n_edges >= 0");
+  if ((int64_t)n_vertices * p > (1 << 20))
+    return fail(QT_EINVAL, "qt_build_network: more than 2^20 variables");
+  std::set<std::pair<int, int>> seen;
+  for (int e = 0; e < n_edges; ++e) {
+    int a = edges[2 * e], b = edges[2 * e + 1];
+    if (a < 0 || b < 0 || a >= n_vertices || b >= n_vertices)
+      return fail(QT_EINVAL, "qt_build_network: edge id out of range");
+    if (a == b) return fail(QT_EINVAL, "qt_build_network: self-loop");
+    if (!seen.insert({std::min(a, b), std::max(a, b)}).second)
+      return fail(QT_EINVAL, "qt_build_network: repeated edge");
+  }
+  for (int v = 0; v < n_vertices; ++v)
+    if (bitstring[v] > 1) return fail(QT_EINVAL, "qt_build_network: bit not 0/1");
+  for (int k = 0; k < p; ++k)
+    if (!std::isfinite(gammas[k]) || !std::isfinite(betas[k]))
+      return fail(QT_EINVAL, "qt_build_network: angle not finite");
+  qt_net* net = new (std::nothrow) qt_net();
+  if (!net) return fail(QT_ENOMEM, "qt_build_network: out of host memory");
+  try {
+    net->n = n_vertices;
+    net->p = p;
+    net->n_edges = n_edges;
+    net->n_vars = n_vertices * p;
+    net->edges.assign(edges, edges + 2 * (size_t)n_edges);
+    net->gammas.assign(gammas, gammas + p);
+    net->betas.assign(betas, betas + p);
+    net->z.assign(bitstring, bitstring + n_vertices);
+    make_tensors(net);
+  } catch (const std::bad_alloc&) {
+    delete net;
+    return fail(QT_ENOMEM, "qt_build_network: out of host memory");
+  }
+  *out = net;
+  return ok();
+}
+
+qt_status qt_set_angles(qt_net* net, const double* gammas, const double* betas) {
+  if (!check_net(net) || !gammas || !betas) return fail(QT_EINVAL, "qt_set_angles: null argument");
+  for (int k = 0; k < net->p; ++k)
+    if (!std::isfinite(gammas[k]) || !std::isfinite(betas[k]))
+      return fail(QT_EINVAL, "qt_set_angles: angle not finite");
+  net->gammas.assign(gammas, gammas + net->p);
+  net->betas.assign(betas, betas + net->p);
+  make_tensors(net);
+  net->stage_dirty = true;
+  return ok();
+}
+
+qt_status qt_set_bitstring(qt_net* net, const uint8_t* bitstring) {
+  if (!check_net(net) || !bitstring) return fail(QT_EINVAL, "qt_set_bitstring: null argument");
+  for (int v = 0; v < net->n; ++v)
+    if (bitstring[v] > 1) return fail(QT_EINVAL, "qt_set_bitstring: bit not 0/1");
+  net->z.assign(bitstring, bitstring + net->n);
+  make_tensors(net);
+  net->stage_dirty = true;
+  return ok();
+}
+
+qt_status qt_order(qt_net* net, int32_t algo, uint64_t seed, int32_t* width_out) {
+  (void)seed;
+  if (!check_net(net)) return fail(QT_EINVAL, "qt_order: null network");
+  if (algo != QT_GREEDY_MINFILL && algo != QT_GREEDY_MINDEG)
+    return fail(QT_EINVAL, "qt_order: unknown ordering rule");
+  try {
+    qt::BitGraph g = qt::line_graph(net->tensors, net->n_vars);
+    qt::OrderResult r = qt::greedy_order(g, algo);
+    net->plan = qt::SlicePlan();
+    net->plan.order = r.order;
+    net->plan.widths = r.widths;
+    int w = 0;
+    for (int x : r.widths) w = std::max(w, x);
+    net->plan.width = w;
+    net->algo = algo;
+    net->ordered = true;
+    net->sched = qt::Schedule();
+    net->stage_dirty = true;
+    if (width_out) *width_out = w;
+  } catch (const std::bad_alloc&) {
+    return fail(QT_ENOMEM, "qt_order: out of host memory");
+  }
+  return ok();
+}
+
+qt_status qt_slice(qt_net* net, int32_t width_limit, int32_t max_vars, int32_t r, int32_t* k_out,
+                   int32_t* width_out) {
+  if (!check_net(net)) return fail(QT_EINVAL, "qt_slice: null network");
+  if (!net->ordered) return fail(QT_ESTATE, "qt_slice: call qt_order first");
+  if (width_limit < 1 || r < 1 || max_vars < 0 || max_vars > 30)
+    return fail(QT_EINVAL, "qt_slice: need width_limit >= 1, r >= 1, 0 <= max_vars <= 30");
+  try {
+    qt::BitGraph g = qt::line_graph(net->tensors, net->n_vars);
+    net->plan = qt::step_dependent_slicing(g, net->algo, width_limit, max_vars, r);
+    net->sched = qt::Schedule();
+    net->stage_dirty = true;
+    if (k_out) *k_out = (int32_t)net->plan.sliced.size();
+    if (width_out) *width_out = net->plan.width;
+  } catch (const std::bad_alloc&) {
+    return fail(QT_ENOMEM, "qt_slice: out of host memory");
+  }
+  return ok();
+}
+
+static qt_status copy_out(const std::vector<int32_t>& v, int32_t* dst, int32_t cap, int32_t* len) {
+  if (!len) return fail(QT_EINVAL, "null length pointer");
+  *len = (int32_t)v.size();
+  if (dst)
+    for (int32_t i = 0; i < cap && i < (int32_t)v.size(); ++i) dst[i] = v[i];
+  return ok();
+}
+
+qt_status qt_get_order(const qt_net* net, int32_t* order, int32_t cap, int32_t* len) {
+  if (!check_net(net)) return fail(QT_EINVAL, "qt_get_order: null network");
+  if (!net->ordered) return fail(QT_ESTATE, "qt_get_order: call qt_order first");
+  return copy_out(net->plan.order, order, cap, len);
+}
+
+qt_status qt_get_widths(const qt_net* net, int32_t* widths, int32_t cap, int32_t* len) {
+  if (!check_net(net)) return fail(QT_EINVAL, "qt_get_widths: null network");
+  if (!net->ordered) return fail(QT_ESTATE, "qt_get_widths: call qt_order first");
+  return copy_out(net->plan.widths, widths, cap, len);
+}
+
+qt_status qt_get_slices(const qt_net* net, int32_t* vars, int32_t cap, int32_t* len,
+                        int32_t* slice_step) {
+  if (!check_net(net)) return fail(QT_EINVAL, "qt_get_slices: null network");
+  if (!net->ordered) return fail(QT_ESTATE, "qt_get_slices: call qt_order first");
+  if (slice_step) *slice_step = net->plan.slice_step;
+  return copy_out(net->plan.sliced, vars, cap, len);
+}
+
+qt_status qt_num_tensors(const qt_net* net, int32_t* count, int32_t* n_vars) {
+  if (!check_net(net) || !count) return fail(QT_EINVAL, "qt_num_tensors: null argument");
+  *count = (int32_t)net->tensors.size();
+  if (n_vars) *n_vars = net->n_vars;
+  return ok();
+}
+
+qt_status qt_get_tensor(const qt_net* net, int32_t t, int32_t* labels, int32_t* rank,
+                        double* data) {
+  if (!check_net(net) || !rank) return fail(QT_EINVAL, "qt_get_tensor: null argument");
+  if (t < 0 || t >= (int32_t)net->tensors.size())
+    return fail(QT_EINVAL, "qt_get_tensor: tensor index out of range");
+  const qt::Tensor& T = net->tensors[t];
+  *rank = (int32_t)T.labels.size();
+  if (labels)
+    for (size_t i = 0; i < T.labels.size(); ++i) labels[i] = T.labels[i];
+  if (data) std::memcpy(data, T.data.data(), T.data.size() * sizeof(double));
+  return ok();
+}
+
+qt_status qt_prepare(qt_net* net, int32_t precision, int32_t batch, size_t* workspace_bytes) {
+  if (!check_net(net)) return fail(QT_EINVAL, "qt_prepare: null network");
+  if (!net->ordered) return fail(QT_ESTATE, "qt_prepare: call qt_order first");
+  if (precision != QT_FP32_SIMT && precision != QT_FP64)
+    return fail(QT_EINVAL, "qt_prepare: unknown precision");
+  if (batch < 1) return fail(QT_EINVAL, "qt_prepare: batch must be >= 1");
+  std::string err;
+  try {
+    if (!qt::compile_schedule(net->tensors, net->n_vars, net->plan, precision, batch, net->sched,
+                              err)) {
+      net->sched = qt::Schedule();
+      return fail(err.find("rank") != std::string::npos ? QT_ERANGE : QT_EINVAL,
+                  "qt_prepare: " + err);
+    }
+  } catch (const std::bad_alloc&) {
+    net->sched = qt::Schedule();
+    return fail(QT_ENOMEM, "qt_prepare: out of host memory");
+  }
+  net->stage_dirty = true;
+  if (workspace_bytes) *workspace_bytes = net->sched.total_bytes;
+  return ok();
+}
+
+qt_status qt_stats(const qt_net* net, char* buf, size_t cap, size_t* needed) {
+  if (!check_net(net)) return fail(QT_EINVAL, "qt_stats: null network");
+  if (!net->sched.valid) return fail(QT_ESTATE, "qt_stats: call qt_prepare first");
+  std::string s = qt::schedule_json(net->sched, net->plan);
+  s.pop_back();
+  s += ",\"launches\":" + std::to_string(net->launches) + "}";
+  if (needed) *needed = s.size() + 1;
+  if (buf && cap > 0) {
+    size_t n = std::min(cap - 1, s.size());
+    std::memcpy(buf, s.data(), n);
+    buf[n] = '\0';
+  }
+  return ok();
+}
+
+static qt_status check_ws(const qt_net* net, void* ws, size_t bytes, const char* who) {
+  if (!ws) return fail(QT_EINVAL, std::string(who) + ": null workspace");
+  if (((uintptr_t)ws) % 256 != 0)
+    return fail(QT_EINVAL, std::string(who) + ": workspace not 256-byte aligned");
+  if (bytes < net->sched.total_bytes)
+    return fail(QT_ENOMEM, std::string(who) + ": workspace smaller than qt_prepare's size");
+  return QT_OK;
+}
+
+qt_status qt_upload(qt_net* net, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!check_net(net)) return fail(QT_EINVAL, "qt_upload: null network");
+  if (!net->sched.valid) return fail(QT_ESTATE, "qt_upload: call qt_prepare first");
+  qt_status s = check_ws(net, workspace, workspace_bytes, "qt_upload");
+  if (s != QT_OK) return s;
+  std::string err;
+  s = qt::upload(net, workspace, workspace_bytes, stream, err);
+  if (s != QT_OK) return fail(s, "qt_upload: " + err);
+  return ok();
+}
+
+qt_status qt_run(qt_net* net, int64_t first, int64_t count, void* workspace, size_t workspace_bytes,
+                 void* stream, double* d_out) {
+  if (!check_net(net)) return fail(QT_EINVAL, "qt_run: null network");
+  if (!net->sched.valid) return fail(QT_ESTATE, "qt_run: call qt_prepare first");
+  if (!d_out) return fail(QT_EINVAL, "qt_run: null output pointer");
+  if (first < 0 || count < 1 || first + count > net->sched.nslices)
+    return fail(QT_EINVAL, "qt_run: slice range outside [0, 2^k)");
+  qt_status s = check_ws(net, workspace, workspace_bytes, "qt_run");
+  if (s != QT_OK) return s;
+  std::string err;
+  s = qt::run(net, first, count, workspace, stream, d_out, err);
+  if (s != QT_OK) return fail(s, "qt_run: " + err);
+  return ok();
+}
+
+qt_status qt_contract(qt_net* net, int32_t precision, void* workspace, size_t workspace_bytes,
+                      void* stream, double* amp_re, double* amp_im) {
+  if (!check_net(net) || !amp_re || !amp_im) return fail(QT_EINVAL, "qt_contract: null argument");
+  if (!net->ordered) return fail(QT_ESTATE, "qt_contract: call qt_order first");
+  if (!net->sched.valid || net->sched.precision != precision) {
+    // the largest batch whose workspace fits
+    size_t need = 0;
+    qt_status s = qt_prepare(net, precision, 1, &need);
+    if (s != QT_OK) return s;
+    int64_t lo = 1, hi = net->sched.nslices;
+    while (lo < hi) {
+      int64_t mid = (lo + hi + 1) / 2;
+      s = qt_prepare(net, precision, (int32_t)std::min<int64_t>(mid, 1 << 30), &need);
+      if (s != QT_OK) return s;
+      if (need <= workspace_bytes) lo = mid;
+      else hi = mid - 1;
+    }
+    s = qt_prepare(net, precision, (int32_t)lo, &need);
+    if (s != QT_OK) return s;
+  }
+  qt_status s = check_ws(net, workspace, workspace_bytes, "qt_contract");
+  if (s != QT_OK) return s;
+  std::string err;
+  s = qt::upload(net, workspace, workspace_bytes, stream, err);
+  if (s != QT_OK) return fail(s, "qt_contract: " + err);
+  double* d_out = reinterpret_cast<double*>((char*)workspace + net->sched.off_acc + 16);
+  s = qt::run(net, 0, net->sched.nslices, workspace, stream, d_out, err);
+  if (s != QT_OK) return fail(s, "qt_contract: " + err);
+  double h[2];
+  s = qt::download_result(d_out, h, stream, err);
+  if (s != QT_OK) return fail(s, "qt_contract: " + err);
+  *amp_re = h[0];
+  *amp_im = h[1];
+  return ok();
+}
+
+qt_status qt_profile(qt_net* net, int32_t enable) {
+  if (!check_net(net)) return fail(QT_EINVAL, "qt_profile: null network");
+  qt::prof_clear(net);
+  net->prof = enable != 0;
+  return ok();
+}
+
+qt_status qt_profile_read(qt_net* net, char* buf, size_t cap, size_t* needed) {
+  if (!check_net(net)) return fail(QT_EINVAL, "qt_profile_read: null network");
+  std::string out, err;
+  qt_status s = qt::prof_read(net, out, err);
+  if (s != QT_OK) return fail(s, "qt_profile_read: " + err);
+  if (needed) *needed = out.size() + 1;
+  if (buf && cap > 0) {
+    size_t n = std::min(cap - 1, out.size());
+    std::memcpy(buf, out.data(), n);
+    buf[n] = '\0';
+  }
+  return ok();
+}
+
+void qt_free(qt_net* net) { delete net; }
+
+}  // extern "C"

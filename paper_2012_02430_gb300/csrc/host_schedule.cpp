@@ -1,0 +1,295 @@
+// Schedule compiler: turns (network, order, slices) into the list of bucket
+// steps the GPU executes, with canonical tensor layouts, memory offsets and
+// the integer FLOP/byte ledger.
+//
+// Bucket elimination follows Alg. 1: bucket i holds the tensors whose earliest
+// index (by elimination position) is the i-th vertex of the order; its tensors
+// are multiplied over the union of their indices and that vertex is summed
+// out; the result goes to the bucket of its own earliest index, or multiplies
+// the result when it is a scalar. Slicing follows Alg. 1 and Eq. 2: steps
+// before the first slice step run once on the unsliced network, later steps
+// run once per slice with every sliced index fixed.
+//
+// Canonical layout: a tensor's indices are ordered by elimination position,
+// earliest = least significant bit of the element index; sliced vertices get
+// positions above every eliminated one (in slice-bit order), so fixing them
+// selects one contiguous block of a shared tensor. In bucket i every operand
+// has the bucket vertex as bit 0, so the two values that are summed are
+// adjacent in memory.
+#include <algorithm>
+#include <cstdio>
+#include <map>
+#include <sstream>
+
+#include "qt_internal.h"
+
+namespace qt {
+
+std::vector<double> canonical_data(const Tensor& t, const std::vector<int32_t>& canon) {
+  const int r = (int)t.labels.size();
+  std::vector<int> axis_of(r);  // canonical bit b -> axis of the gate data
+  for (int b = 0; b < r; ++b)
+    for (int a = 0; a < r; ++a)
+      if (t.labels[a] == canon[b]) axis_of[b] = a;
+  const size_t n = (size_t)1 << r;
+  std::vector<double> out(2 * n);
+  for (size_t e = 0; e < n; ++e) {
+    size_t src = 0;
+    for (int b = 0; b < r; ++b)
+      if ((e >> b) & 1u) src |= (size_t)1 << axis_of[b];
+    out[2 * e] = t.data[2 * src];
+    out[2 * e + 1] = t.data[2 * src + 1];
+  }
+  return out;
+}
+
+namespace {
+
+// First-fit allocator over an element range, for liveness-based reuse.
+struct Arena {
+  std::map<int64_t, int64_t> free_blocks;  // offset -> size
+  int64_t top = 0;
+  static int64_t align(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+  int64_t alloc(int64_t n, int64_t a) {
+    n = align(n, a);
+    for (auto it = free_blocks.begin(); it != free_blocks.end(); ++it) {
+      if (it->second >= n) {
+        int64_t off = it->first;
+        int64_t rest = it->second - n;
+        free_blocks.erase(it);
+        if (rest > 0) free_blocks[off + n] = rest;
+        return off;
+      }
+    }
+    int64_t off = top;
+    top += n;
+    return off;
+  }
+  void release(int64_t off, int64_t n, int64_t a) {
+    n = align(n, a);
+    auto it = free_blocks.emplace(off, n).first;
+    auto nx = std::next(it);
+    if (nx != free_blocks.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_blocks.erase(nx);
+    }
+    if (it != free_blocks.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_blocks.erase(it);
+      }
+    }
+  }
+};
+
+constexpr int64_t kArenaAlign = 64;  // elements (512 B for complex64)
+constexpr int64_t kGateAlign = 2;    // elements: keeps every value pair 16-byte aligned
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePlan& plan,
+                      int precision, int64_t batch, Schedule& S, std::string& err) {
+  S = Schedule();
+  S.precision = precision;
+  S.elem_bytes = precision == QT_FP64 ? 16 : 8;
+  const int n_order = (int)plan.order.size();
+  S.k = (int)plan.sliced.size();
+  S.nslices = (int64_t)1 << S.k;
+  S.batch = std::max<int64_t>(1, std::min<int64_t>(batch, S.nslices));
+  S.pos.assign(n_vars, -1);
+  std::vector<int> slice_bit(n_vars, -1);
+  for (int i = 0; i < n_order; ++i) S.pos[plan.order[i]] = i;
+  for (int j = 0; j < S.k; ++j) {
+    S.pos[plan.sliced[j]] = n_order + j;
+    slice_bit[plan.sliced[j]] = j;
+  }
+  for (int v = 0; v < n_vars; ++v)
+    if (S.pos[v] < 0) {
+      err = "plan does not cover every variable";
+      return false;
+    }
+  const int boundary = S.k > 0 ? plan.slice_step : 0;
+  auto by_pos = [&](int32_t a, int32_t b) { return S.pos[a] < S.pos[b]; };
+
+  std::vector<std::vector<int32_t>> buckets(n_order);
+  auto place = [&](int32_t tid, int region_of_creation) {
+    STensor& t = S.tensors[tid];
+    int e = -1;
+    for (int32_t l : t.labels)
+      if (slice_bit[l] < 0 && (e < 0 || S.pos[l] < e)) e = S.pos[l];
+    (void)region_of_creation;
+    if (e < 0) {
+      S.scalars.push_back(tid);  // rank 0, or only sliced indices: a per-slice factor
+    } else {
+      buckets[e].push_back(tid);
+    }
+  };
+  auto make_tensor = [&](int kind, std::vector<int32_t> labels) {
+    STensor t;
+    t.kind = kind;
+    std::sort(labels.begin(), labels.end(), by_pos);
+    t.labels = labels;
+    t.rank = (int)labels.size();
+    for (int32_t l : labels)
+      if (slice_bit[l] >= 0) {
+        t.nsliced++;
+        t.smask |= 1u << slice_bit[l];
+      }
+    S.tensors.push_back(t);
+    return (int32_t)S.tensors.size() - 1;
+  };
+  for (size_t g = 0; g < net.size(); ++g) {
+    int32_t tid = make_tensor(TK_GATE, net[g].labels);
+    S.tensors[tid].gate = (int)g;
+    place(tid, 0);
+  }
+  for (int i = 0; i < n_order; ++i) {
+    std::vector<int32_t> bucket = buckets[i];
+    if (bucket.empty()) continue;
+    SStep st;
+    st.region = i < boundary ? 0 : 1;
+    st.var = plan.order[i];
+    st.ops = bucket;
+    std::vector<int32_t> uni;
+    for (int32_t tid : bucket)
+      for (int32_t l : S.tensors[tid].labels) {
+        if (st.region == 1 && slice_bit[l] >= 0) continue;
+        if (std::find(uni.begin(), uni.end(), l) == uni.end()) uni.push_back(l);
+      }
+    std::sort(uni.begin(), uni.end(), by_pos);
+    if (uni.empty() || uni[0] != st.var) {
+      err = "internal: bucket vertex is not the earliest index";
+      return false;
+    }
+    st.ulabels = uni;
+    st.u = (int)uni.size();
+    st.c = st.u - 1;
+    st.nsum = 1;
+    if (st.c > 32 || st.u > 33) {
+      err = "tensor rank above 32";
+      return false;
+    }
+    std::vector<int32_t> out(uni.begin() + 1, uni.end());
+    int32_t oid = make_tensor(st.region == 0 ? TK_PREFIX : TK_SLICE, out);
+    S.tensors[oid].producer = (int)S.steps.size();
+    st.out = oid;
+    // ledger (Alg. 1 step, complex arithmetic)
+    int64_t m = (int64_t)bucket.size();
+    st.flops = 6 * (m - 1) * ((int64_t)1 << st.u) + 2 * (((int64_t)1 << st.u) - ((int64_t)1 << st.c));
+    int64_t elems = (int64_t)1 << st.c;
+    for (int32_t tid : bucket) {
+      const STensor& t = S.tensors[tid];
+      int rk = st.region == 1 ? t.rank - t.nsliced : t.rank;
+      elems += (int64_t)1 << rk;
+    }
+    st.bytes = 8 * elems;
+    for (int32_t tid : bucket) S.tensors[tid].last_use = (int)S.steps.size();
+    S.steps.push_back(st);
+    place(oid, st.region);
+  }
+  for (const SStep& st : S.steps) {
+    if (st.region == 0) {
+      S.n_prefix_steps++;
+      S.prefix_flops += st.flops;
+      S.prefix_bytes += st.bytes;
+      S.prefix_width = std::max(S.prefix_width, st.c);
+    } else {
+      S.slice_flops += st.flops;
+      S.slice_bytes += st.bytes;
+      S.slice_width = std::max(S.slice_width, st.c);
+    }
+  }
+  // scalars live to the end
+  const int end_step = (int)S.steps.size();
+  for (int32_t tid : S.scalars) S.tensors[tid].last_use = end_step;
+  // prefix results read by slice steps live to the end of the run
+  for (STensor& t : S.tensors)
+    if (t.kind == TK_PREFIX && t.last_use >= 0 && t.last_use < end_step &&
+        S.steps[t.last_use].region == 1)
+      t.last_use = end_step;
+
+  // memory: gates packed, prefix and slice arenas by liveness
+  int64_t goff = 0;
+  for (STensor& t : S.tensors)
+    if (t.kind == TK_GATE) {
+      t.offset = goff;
+      goff += Arena::align((int64_t)1 << t.rank, kGateAlign);
+    }
+  S.gate_elems = goff;
+  Arena pre, sl;
+  for (int s = 0; s < (int)S.steps.size(); ++s) {
+    STensor& o = S.tensors[S.steps[s].out];
+    Arena& ar = o.kind == TK_PREFIX ? pre : sl;
+    o.offset = ar.alloc((int64_t)1 << o.rank, kArenaAlign);
+    if (o.last_use < 0) o.last_use = s;  // never read (cannot happen: results are placed)
+    for (int32_t tid : S.steps[s].ops) {
+      STensor& t = S.tensors[tid];
+      if (t.kind != TK_GATE && t.last_use == s)
+        (t.kind == TK_PREFIX ? pre : sl).release(t.offset, (int64_t)1 << t.rank, kArenaAlign);
+    }
+  }
+  S.prefix_elems = std::max<int64_t>(pre.top, kArenaAlign);
+  S.slice_elems = std::max<int64_t>(sl.top, kArenaAlign);
+  // meta slots
+  int64_t shared = 0, per_slice = 0;
+  for (STensor& t : S.tensors) {
+    if (t.kind == TK_SLICE) t.meta = per_slice++;
+    else t.meta = shared++;
+  }
+  S.n_shared_meta = shared;
+  S.n_slice_meta_tensors = per_slice;
+  for (STensor& t : S.tensors)
+    if (t.kind == TK_SLICE) t.meta = shared + t.meta * S.batch;
+  // workspace layout
+  const size_t eb = (size_t)S.elem_bytes;
+  size_t off = 0;
+  S.off_gates = off;
+  off = align256(off + (size_t)S.gate_elems * eb);
+  S.off_prefix = off;
+  off = align256(off + (size_t)S.prefix_elems * eb);
+  S.off_slices = off;
+  off = align256(off + (size_t)S.slice_elems * eb * (size_t)S.batch);
+  S.off_meta = off;
+  off = align256(off + (size_t)(shared + per_slice * S.batch) * 16);
+  S.off_partials = off;
+  off = align256(off + (size_t)S.batch * 16);
+  S.off_acc = off;
+  off = align256(off + 64);
+  S.off_terms = off;
+  off = align256(off + S.scalars.size() * kScalarTermBytes);
+  S.total_bytes = off;
+  S.valid = true;
+  return true;
+}
+
+std::string schedule_json(const Schedule& S, const SlicePlan& plan) {
+  std::ostringstream o;
+  o << "{\"k\":" << S.k << ",\"nslices\":" << S.nslices << ",\"batch\":" << S.batch
+    << ",\"precision\":" << S.precision << ",\"elem_bytes\":" << S.elem_bytes
+    << ",\"plan_width\":" << plan.width << ",\"slice_step\":" << plan.slice_step
+    << ",\"prefix_flops\":" << S.prefix_flops << ",\"prefix_bytes\":" << S.prefix_bytes
+    << ",\"slice_flops\":" << S.slice_flops << ",\"slice_bytes\":" << S.slice_bytes
+    << ",\"prefix_width\":" << S.prefix_width << ",\"slice_width\":" << S.slice_width
+    << ",\"n_prefix_steps\":" << S.n_prefix_steps
+    << ",\"n_slice_steps\":" << (int)S.steps.size() - S.n_prefix_steps
+    << ",\"n_scalars\":" << S.scalars.size() << ",\"workspace_bytes\":" << S.total_bytes
+    << ",\"prefix_arena_bytes\":" << S.prefix_elems * S.elem_bytes
+    << ",\"slice_arena_bytes\":" << S.slice_elems * S.elem_bytes
+    << ",\"upload_bytes\":"
+    << S.gate_elems * S.elem_bytes + S.n_shared_meta * 8 +
+           (int64_t)S.scalars.size() * (int64_t)kScalarTermBytes
+    << ",\"steps\":[";
+  for (size_t i = 0; i < S.steps.size(); ++i) {
+    const SStep& st = S.steps[i];
+    if (i) o << ",";
+    o << "[" << st.region << "," << st.var << "," << st.ops.size() << "," << st.u << "," << st.c
+      << "," << st.nsum << "," << st.flops << "," << st.bytes << "]";
+  }
+  o << "]}";
+  return o.str();
+}
+
+}  // namespace qt

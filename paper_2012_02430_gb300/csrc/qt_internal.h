@@ -1,0 +1,157 @@
+// Internal structures of the qtensor library (host side and launch descriptors).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qtensor.h"
+
+namespace qt {
+
+// ---------------------------------------------------------------------------
+// Network (Sec. IV.A-B): tensors over binary indices, FP64 data.
+// ---------------------------------------------------------------------------
+struct Tensor {
+  std::vector<int32_t> labels;  // axis t of the data is labels[t] (bit t of the element index)
+  std::vector<double> data;     // interleaved (re, im), 2 * 2^rank doubles
+};
+
+// ---------------------------------------------------------------------------
+// Line graph as dense bitset rows (Sec. IV.B) and greedy ordering (Sec. V.A.1).
+// ---------------------------------------------------------------------------
+struct BitGraph {
+  int n = 0;  // vertices
+  int W = 0;  // 64-bit words per row
+  std::vector<uint64_t> rows;
+  std::vector<uint8_t> alive;
+
+  void init(int nv);
+  uint64_t* row(int v) { return rows.data() + (size_t)v * W; }
+  const uint64_t* row(int v) const { return rows.data() + (size_t)v * W; }
+  bool has(int a, int b) const { return (row(a)[b >> 6] >> (b & 63)) & 1u; }
+  void add_edge(int a, int b);
+  int degree(int v) const;
+  // joins v's neighbours into a clique and deletes v; returns v's neighbour count
+  int eliminate(int v);
+  // deletes v without joining its neighbours (slicing)
+  void remove(int v);
+};
+
+struct OrderResult {
+  std::vector<int32_t> order;
+  std::vector<int32_t> widths;
+};
+
+OrderResult greedy_order(const BitGraph& g, int algo);
+
+struct SlicePlan {
+  std::vector<int32_t> order;   // every non-sliced vertex, elimination order
+  std::vector<int32_t> widths;  // neighbour count of each step of `order` as planned
+  std::vector<int32_t> sliced;  // sliced vertices, slice-bit order
+  int32_t slice_step = 0;       // first round's step s_1 (0 without slicing)
+  int32_t width = 0;
+};
+
+SlicePlan step_dependent_slicing(const BitGraph& g, int algo, int width_limit, int max_vars,
+                                 int r);
+
+BitGraph line_graph(const std::vector<Tensor>& tensors, int n_vars);
+
+// ---------------------------------------------------------------------------
+// Compiled schedule.
+// ---------------------------------------------------------------------------
+enum TensorKind { TK_GATE = 0, TK_PREFIX = 1, TK_SLICE = 2 };
+
+struct STensor {
+  int kind = TK_GATE;
+  int gate = -1;                // index into the network's tensors for TK_GATE
+  std::vector<int32_t> labels;  // canonical: ascending position (sliced labels on top)
+  int rank = 0;                 // number of labels (sliced included)
+  int nsliced = 0;              // labels that are sliced vertices
+  uint32_t smask = 0;           // slice-id bits present (bit j: j-th sliced vertex)
+  int64_t offset = 0;           // element offset inside its region
+  int64_t meta = 0;             // meta slot (shared) or first slot (per slice)
+  int producer = -1;            // step that writes it (-1 for gates)
+  int last_use = -1;            // last step that reads it
+};
+
+struct SStep {
+  int region = 1;               // 0 prefix (once, unsliced), 1 per slice
+  int var = -1;                 // bucket variable
+  std::vector<int32_t> ops;     // schedule tensor ids
+  std::vector<int32_t> ulabels; // union labels as the step sees them (canonical order)
+  int out = -1;                 // schedule tensor id of the result
+  int u = 0, c = 0, nsum = 1;
+  int64_t flops = 0, bytes = 0;
+};
+
+struct Schedule {
+  bool valid = false;
+  int precision = QT_FP32_SIMT;
+  int elem_bytes = 8;
+  int k = 0;
+  int64_t nslices = 1;
+  int64_t batch = 1;
+  std::vector<int32_t> pos;     // variable -> canonical position
+  std::vector<STensor> tensors;
+  std::vector<SStep> steps;
+  int n_prefix_steps = 0;
+  std::vector<int32_t> scalars; // tensors whose value multiplies the slice result
+  // region sizes in elements
+  int64_t gate_elems = 0, prefix_elems = 0, slice_elems = 0;
+  int64_t n_shared_meta = 0, n_slice_meta_tensors = 0;
+  // workspace layout (bytes)
+  size_t off_gates = 0, off_prefix = 0, off_slices = 0, off_meta = 0, off_partials = 0,
+         off_acc = 0, off_terms = 0, total_bytes = 0;
+  // ledger
+  int64_t prefix_flops = 0, prefix_bytes = 0, slice_flops = 0, slice_bytes = 0;
+  int prefix_width = 0, slice_width = 0;
+};
+
+bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePlan& plan,
+                      int precision, int64_t batch, Schedule& out, std::string& err);
+
+std::string schedule_json(const Schedule& s, const SlicePlan& plan);
+
+constexpr size_t kScalarTermBytes = 32;  // device ScalarTerm record
+
+// Canonical-layout copy of a gate tensor's data (FP64 interleaved).
+std::vector<double> canonical_data(const Tensor& t, const std::vector<int32_t>& canon_labels);
+
+// One profiled kernel launch (events recorded around it on the caller's stream).
+struct ProfRec {
+  int step;         // schedule step (-1: finalize/reduce)
+  int kernel;       // 0 flat bucket, 1 tiled bucket, 2 finalize + reduce
+  int64_t slices;   // slices processed by the launch
+  int64_t bytes;    // algorithmic bytes of the launch (ledger bytes x slices)
+  int64_t flops;    // ledger flops of the launch
+  void* ev0;
+  void* ev1;
+};
+
+}  // namespace qt
+
+// The opaque network handle.
+struct qt_net {
+  int32_t n = 0, p = 0, n_edges = 0, n_vars = 0;
+  std::vector<int32_t> edges;
+  std::vector<double> gammas, betas;
+  std::vector<uint8_t> z;
+  std::vector<qt::Tensor> tensors;
+  bool ordered = false;
+  int algo = QT_GREEDY_MINFILL;
+  qt::SlicePlan plan;
+  qt::Schedule sched;
+  // host staging of the canonical gate data for the prepared precision
+  std::vector<unsigned char> gate_stage;
+  std::vector<unsigned char> meta_stage;
+  bool stage_dirty = true;
+  // tracing: CUDA events around every launch when enabled
+  bool prof = false;
+  std::vector<qt::ProfRec> prof_recs;
+  std::vector<void*> prof_pool;  // recycled cudaEvent_t
+  int64_t launches = 0;          // kernel launches issued by this network
+  ~qt_net();
+};

@@ -1,0 +1,250 @@
+"""Python binding of the C ABI in include/qtensor.h (argument marshalling only).
+
+The functions below carry the C names and forward to libqtensor.so through
+ctypes; every step of the contraction runs in the library's CUDA kernels.
+PyTorch is used only for device memory (the caller-owned workspace) and for the
+current CUDA stream. Importing this module loads the in-tree library and
+raises ImportError when it is missing: there is no fallback path.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import json
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libqtensor.so")
+
+QT_OK, QT_EINVAL, QT_ENOMEM, QT_ECUDA, QT_ETIMEOUT, QT_ESTATE, QT_ERANGE = range(7)
+QT_GREEDY_MINFILL, QT_GREEDY_MINDEG = 0, 1
+QT_FP32_SIMT, QT_FP64 = 0, 4
+
+STATUS_NAMES = {0: "QT_OK", 1: "QT_EINVAL", 2: "QT_ENOMEM", 3: "QT_ECUDA",
+                4: "QT_ETIMEOUT", 5: "QT_ESTATE", 6: "QT_ERANGE"}
+
+
+class QtError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libqtensor.so not built ({LIB_PATH}); run __graft_entry__.build()")
+lib = C.CDLL(LIB_PATH)
+
+_i32p = C.POINTER(C.c_int32)
+_f64p = C.POINTER(C.c_double)
+_u8p = C.POINTER(C.c_uint8)
+_vp = C.c_void_p
+
+_SIGS = {
+    "qt_build_network": [_i32p, C.c_int32, C.c_int32, C.c_int32, _f64p, _f64p, _u8p,
+                         C.POINTER(_vp)],
+    "qt_set_angles": [_vp, _f64p, _f64p],
+    "qt_set_bitstring": [_vp, _u8p],
+    "qt_order": [_vp, C.c_int32, C.c_uint64, _i32p],
+    "qt_slice": [_vp, C.c_int32, C.c_int32, C.c_int32, _i32p, _i32p],
+    "qt_get_order": [_vp, _i32p, C.c_int32, _i32p],
+    "qt_get_widths": [_vp, _i32p, C.c_int32, _i32p],
+    "qt_get_slices": [_vp, _i32p, C.c_int32, _i32p, _i32p],
+    "qt_get_tensor": [_vp, C.c_int32, _i32p, _i32p, _f64p],
+    "qt_num_tensors": [_vp, _i32p, _i32p],
+    "qt_prepare": [_vp, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)],
+    "qt_stats": [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)],
+    "qt_upload": [_vp, _vp, C.c_size_t, _vp],
+    "qt_run": [_vp, C.c_int64, C.c_int64, _vp, C.c_size_t, _vp, _vp],
+    "qt_contract": [_vp, C.c_int32, _vp, C.c_size_t, _vp, _f64p, _f64p],
+    "qt_profile": [_vp, C.c_int32],
+    "qt_profile_read": [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)],
+}
+for _name, _args in _SIGS.items():
+    _fn = getattr(lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = C.c_int
+lib.qt_free.argtypes = [_vp]
+lib.qt_free.restype = None
+lib.qt_last_error.argtypes = []
+lib.qt_last_error.restype = C.c_char_p
+lib.qt_version.argtypes = []
+lib.qt_version.restype = C.c_char_p
+
+
+def _check(status: int):
+    if status != QT_OK:
+        raise QtError(status, lib.qt_last_error().decode())
+
+
+def _arr(ctype, values):
+    values = list(values)
+    return (ctype * max(1, len(values)))(*values)
+
+
+# ----------------------------- C-named functions -----------------------------
+
+def qt_build_network(edges, n_vertices, p, gammas, betas, bitstring):
+    flat = [int(x) for e in edges for x in e]
+    out = _vp()
+    _check(lib.qt_build_network(_arr(C.c_int32, flat), int(n_vertices), len(edges), int(p),
+                                _arr(C.c_double, gammas), _arr(C.c_double, betas),
+                                _arr(C.c_uint8, bitstring), C.byref(out)))
+    return out
+
+
+def qt_set_angles(net, gammas, betas):
+    _check(lib.qt_set_angles(net, _arr(C.c_double, gammas), _arr(C.c_double, betas)))
+
+
+def qt_set_bitstring(net, bitstring):
+    _check(lib.qt_set_bitstring(net, _arr(C.c_uint8, bitstring)))
+
+
+def qt_order(net, algo=QT_GREEDY_MINFILL, seed=0):
+    w = C.c_int32()
+    _check(lib.qt_order(net, int(algo), int(seed), C.byref(w)))
+    return w.value
+
+
+def qt_slice(net, width_limit, max_vars, r=1):
+    k, w = C.c_int32(), C.c_int32()
+    _check(lib.qt_slice(net, int(width_limit), int(max_vars), int(r), C.byref(k), C.byref(w)))
+    return k.value, w.value
+
+
+def _get_list(fn, net, *extra):
+    n = C.c_int32()
+    _check(fn(net, None, 0, C.byref(n), *extra))
+    buf = (C.c_int32 * max(1, n.value))()
+    _check(fn(net, buf, n.value, C.byref(n), *extra))
+    return list(buf[: n.value])
+
+
+def qt_get_order(net):
+    return _get_list(lib.qt_get_order, net)
+
+
+def qt_get_widths(net):
+    return _get_list(lib.qt_get_widths, net)
+
+
+def qt_get_slices(net):
+    step = C.c_int32()
+    vars_ = _get_list(lib.qt_get_slices, net, C.byref(step))
+    return vars_, step.value
+
+
+def qt_num_tensors(net):
+    c, nv = C.c_int32(), C.c_int32()
+    _check(lib.qt_num_tensors(net, C.byref(c), C.byref(nv)))
+    return c.value, nv.value
+
+
+def qt_get_tensor(net, t):
+    rank = C.c_int32()
+    _check(lib.qt_get_tensor(net, int(t), None, C.byref(rank), None))
+    labels = (C.c_int32 * max(1, rank.value))()
+    data = (C.c_double * (2 << rank.value))()
+    _check(lib.qt_get_tensor(net, int(t), labels, C.byref(rank), data))
+    return list(labels[: rank.value]), list(data)
+
+
+def qt_prepare(net, precision=QT_FP32_SIMT, batch=1):
+    n = C.c_size_t()
+    _check(lib.qt_prepare(net, int(precision), int(batch), C.byref(n)))
+    return n.value
+
+
+def qt_stats(net):
+    n = C.c_size_t()
+    _check(lib.qt_stats(net, None, 0, C.byref(n)))
+    buf = C.create_string_buffer(n.value)
+    _check(lib.qt_stats(net, buf, n.value, C.byref(n)))
+    return json.loads(buf.value.decode())
+
+
+def qt_upload(net, workspace_ptr, workspace_bytes, stream_ptr):
+    _check(lib.qt_upload(net, _vp(workspace_ptr), int(workspace_bytes), _vp(stream_ptr)))
+
+
+def qt_run(net, first, count, workspace_ptr, workspace_bytes, stream_ptr, d_out_ptr):
+    _check(lib.qt_run(net, int(first), int(count), _vp(workspace_ptr), int(workspace_bytes),
+                      _vp(stream_ptr), _vp(d_out_ptr)))
+
+
+def qt_contract(net, precision, workspace_ptr, workspace_bytes, stream_ptr):
+    re, im = C.c_double(), C.c_double()
+    _check(lib.qt_contract(net, int(precision), _vp(workspace_ptr), int(workspace_bytes),
+                           _vp(stream_ptr), C.byref(re), C.byref(im)))
+    return complex(re.value, im.value)
+
+
+def qt_profile(net, enable):
+    _check(lib.qt_profile(net, 1 if enable else 0))
+
+
+def qt_profile_read(net):
+    n = C.c_size_t()
+    _check(lib.qt_profile_read(net, None, 0, C.byref(n)))
+    buf = C.create_string_buffer(n.value)
+    _check(lib.qt_profile_read(net, buf, n.value, C.byref(n)))
+    return json.loads(buf.value.decode())
+
+
+def qt_free(net):
+    lib.qt_free(net)
+
+
+def qt_version():
+    return lib.qt_version().decode()
+
+
+# ------------------------ convenience wrapper (torch) ------------------------
+
+class Network:
+    """Owns a qt_net handle and, once prepared, a torch-allocated device workspace."""
+
+    def __init__(self, edges, n_vertices, p, gammas, betas, bitstring):
+        self.n, self.p = int(n_vertices), int(p)
+        self.handle = qt_build_network(edges, n_vertices, p, gammas, betas, bitstring)
+        self.workspace = None
+        self.ws_bytes = 0
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            qt_free(h)
+            self.handle = None
+
+    def order(self, algo=QT_GREEDY_MINFILL):
+        return qt_order(self.handle, algo)
+
+    def slice(self, width_limit, max_vars, r=1):
+        return qt_slice(self.handle, width_limit, max_vars, r)
+
+    def prepare(self, precision=QT_FP32_SIMT, batch=1, device="cuda"):
+        import torch
+        self.ws_bytes = qt_prepare(self.handle, precision, batch)
+        if self.workspace is None or self.workspace.numel() < self.ws_bytes:
+            self.workspace = None
+            self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)
+        return self.ws_bytes
+
+    def stats(self):
+        return qt_stats(self.handle)
+
+    def _stream(self):
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+
+    def upload(self):
+        qt_upload(self.handle, self.workspace.data_ptr(), self.workspace.numel(), self._stream())
+
+    def run(self, first, count, out):
+        """Device-resident run; out is a float64 CUDA tensor with >= 2 elements."""
+        qt_run(self.handle, first, count, self.workspace.data_ptr(), self.workspace.numel(),
+               self._stream(), out.data_ptr())
+
+    def contract(self, precision=QT_FP32_SIMT):
+        return qt_contract(self.handle, precision, self.workspace.data_ptr(),
+                           self.workspace.numel(), self._stream())

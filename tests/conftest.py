@@ -10,7 +10,7 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (runs the sm_103a kernels)")
-    config.addinivalue_line("markers", "slow: a long CPU test (oracle at full size)")
+    config.addinivalue_line("markers", "slow: a CPU test of the full-size workload (tens of seconds)")
 
 
 def gpu_available():

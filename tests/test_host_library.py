@@ -1,0 +1,173 @@
+"""The C-ABI library on the CPU: exported symbols, bit-exact integer plans against the
+oracle (network, orders, widths, slices, ledger), and argument/state error handling."""
+
+import math
+import re
+import os
+
+import pytest
+
+from helpers import oracle_plan, oracle_problem
+from oracle import ledger
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_symbols():
+    with open(os.path.join(ROOT, "include", "qtensor.h")) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^(?:qt_status|void|const char\*)\s+(qt_\w+)\(", text, re.M)))
+
+
+def test_library_exports_every_header_symbol(qt):
+    names = header_symbols()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(qt.lib, name), name
+    assert "sm_103a" in qt.qt_version()
+
+
+def test_network_tensors_match_oracle(qt):
+    n, p, seed = 10, 3, 4
+    edges, gammas, betas, z, tensors, nv, norm, adj = oracle_problem(n, p, seed)
+    h = qt.qt_build_network(edges, n, p, gammas, betas, z)
+    try:
+        cnt, nvars = qt.qt_num_tensors(h)
+        assert cnt == len(tensors) and nvars == nv
+        for t, (labels, data) in enumerate(tensors):
+            lab, flat = qt.qt_get_tensor(h, t)
+            assert tuple(lab) == tuple(labels)
+            r = len(lab)
+            for e in range(1 << r):
+                idx = tuple((e >> a) & 1 for a in range(r))  # axis a = bit a of e
+                want = data[idx]
+                assert abs(complex(flat[2 * e], flat[2 * e + 1]) - want) < 1e-15
+    finally:
+        qt.qt_free(h)
+
+
+CASES = [(8, 1, 1, 3, 4, 1), (12, 3, 3, 8, 4, 1), (12, 3, 3, 8, 4, 2), (20, 1, 1001, 3, 4, 1),
+         (30, 2, 11, 12, 6, 1), (24, 3, 15, 14, 6, 2), (44, 2, 14, 17, 6, 1)]
+
+
+@pytest.mark.parametrize("algo", [0, 1])
+@pytest.mark.parametrize("case", CASES)
+def test_plan_bit_exact(qt, case, algo):
+    n, p, seed, lim, mv, r = case
+    edges, gammas, betas, z, tensors, nv, norm, adj = oracle_problem(n, p, seed)
+    h = qt.qt_build_network(edges, n, p, gammas, betas, z)
+    try:
+        from oracle import ordering
+        o, w = ordering.greedy_order(adj, None, {0: ordering.MIN_FILL, 1: ordering.MIN_DEGREE}[algo])
+        assert qt.qt_order(h, algo) == max(w)
+        assert qt.qt_get_order(h) == o and qt.qt_get_widths(h) == w
+        plan = oracle_plan(adj, algo, lim, mv, r)
+        k, width = qt.qt_slice(h, lim, mv, r)
+        sliced, step = qt.qt_get_slices(h)
+        assert sliced == plan["sliced"] and step == plan["slice_step"]
+        assert qt.qt_get_order(h) == plan["order"] and qt.qt_get_widths(h) == plan["widths"]
+        assert width == plan["width"] and k == len(plan["sliced"])
+        for prec, eb in ((0, 8), (4, 16)):
+            qt.qt_prepare(h, prec, 3)
+            st = qt.qt_stats(h)
+            tot, steps = ledger.ledger([l for l, _ in tensors], plan["order"], plan["sliced"],
+                                       plan["slice_step"])
+            for key in ("prefix_flops", "prefix_bytes", "slice_flops", "slice_bytes",
+                        "prefix_width", "slice_width", "n_prefix_steps", "n_slice_steps"):
+                assert st[key] == tot[key], key
+            assert [s[2:5] for s in st["steps"]] == [[s["m"], s["u"], s["c"]] for s in steps]
+            assert st["nslices"] == 1 << k and st["batch"] == min(3, 1 << k)
+            assert st["elem_bytes"] == eb
+    finally:
+        qt.qt_free(h)
+
+
+@pytest.mark.slow
+def test_bench_workload_plan_bit_exact(qt):
+    """The benchmark workload's plan (N=80, p=2, seed 1002, width <= 26): order, slices, ledger."""
+    n, p, seed = 80, 2, 1002
+    edges, gammas, betas, z, tensors, nv, norm, adj = oracle_problem(n, p, seed)
+    h = qt.qt_build_network(edges, n, p, gammas, betas, z)
+    try:
+        qt.qt_order(h, 0)
+        k, width = qt.qt_slice(h, 26, 20, 1)
+        plan = oracle_plan(adj, 0, 26, 20, 1)
+        assert qt.qt_get_slices(h) == (plan["sliced"], plan["slice_step"])
+        assert qt.qt_get_order(h) == plan["order"] and width == plan["width"] <= 26
+        qt.qt_prepare(h, 0, 1 << k)
+        st = qt.qt_stats(h)
+        tot, _ = ledger.ledger([l for l, _ in tensors], plan["order"], plan["sliced"],
+                               plan["slice_step"])
+        assert st["slice_flops"] == tot["slice_flops"] and st["slice_bytes"] == tot["slice_bytes"]
+    finally:
+        qt.qt_free(h)
+
+
+def test_errors(qt):
+    QtError = qt.QtError
+    g, b = [0.1], [0.2]
+    with pytest.raises(QtError) as e:
+        qt.qt_build_network([(0, 0)], 2, 1, g, b, [0, 0])
+    assert e.value.status == qt.QT_EINVAL
+    with pytest.raises(QtError) as e:
+        qt.qt_build_network([(0, 1), (1, 0)], 2, 1, g, b, [0, 0])
+    assert e.value.status == qt.QT_EINVAL
+    with pytest.raises(QtError) as e:
+        qt.qt_build_network([(0, 5)], 2, 1, g, b, [0, 0])
+    assert e.value.status == qt.QT_EINVAL
+    with pytest.raises(QtError) as e:
+        qt.qt_build_network([(0, 1)], 2, 1, g, b, [0, 2])
+    assert e.value.status == qt.QT_EINVAL
+    with pytest.raises(QtError) as e:
+        qt.qt_build_network([(0, 1)], 2, 1, [math.nan], b, [0, 1])
+    assert e.value.status == qt.QT_EINVAL
+    h = qt.qt_build_network([(0, 1), (1, 2)], 3, 1, g, b, [0, 1, 0])
+    try:
+        for call in (lambda: qt.qt_slice(h, 2, 1), lambda: qt.qt_prepare(h, 0, 1),
+                     lambda: qt.qt_get_order(h), lambda: qt.qt_stats(h)):
+            with pytest.raises(QtError) as e:
+                call()
+            assert e.value.status == qt.QT_ESTATE
+        qt.qt_order(h, 0)
+        with pytest.raises(QtError) as e:
+            qt.qt_order(h, 7)
+        assert e.value.status == qt.QT_EINVAL
+        with pytest.raises(QtError) as e:
+            qt.qt_slice(h, 0, 1)
+        assert e.value.status == qt.QT_EINVAL
+        with pytest.raises(QtError) as e:
+            qt.qt_prepare(h, 3, 1)
+        assert e.value.status == qt.QT_EINVAL
+        need = qt.qt_prepare(h, 0, 1)
+        assert need > 0
+        # workspace checks happen before any CUDA call
+        with pytest.raises(QtError) as e:
+            qt.qt_run(h, 0, 1, 0, need, 0, 0)
+        assert e.value.status == qt.QT_EINVAL
+        with pytest.raises(QtError) as e:
+            qt.qt_run(h, 0, 2, 256, need, 0, 256)
+        assert e.value.status == qt.QT_EINVAL
+        with pytest.raises(QtError) as e:
+            qt.qt_run(h, 0, 1, 256 * 3 + 8, need, 0, 256)
+        assert e.value.status == qt.QT_EINVAL
+        with pytest.raises(QtError) as e:
+            qt.qt_run(h, 0, 1, 256, need - 1, 0, 256)
+        assert e.value.status == qt.QT_ENOMEM
+    finally:
+        qt.qt_free(h)
+
+
+def test_set_angles_keeps_plan(qt):
+    n, p, seed = 12, 2, 3
+    edges, gammas, betas, z, tensors, nv, norm, adj = oracle_problem(n, p, seed)
+    h = qt.qt_build_network(edges, n, p, gammas, betas, z)
+    try:
+        qt.qt_order(h, 0)
+        qt.qt_slice(h, 6, 3, 1)
+        before = (qt.qt_get_order(h), qt.qt_get_slices(h))
+        qt.qt_prepare(h, 0, 2)
+        qt.qt_set_angles(h, [0.5, 0.6], [0.7, 0.8])
+        assert (qt.qt_get_order(h), qt.qt_get_slices(h)) == before
+        qt.qt_stats(h)  # schedule still valid
+    finally:
+        qt.qt_free(h)
