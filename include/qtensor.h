@@ -192,6 +192,31 @@ qt_status qt_contract(qt_net* net, int32_t precision, void* workspace, size_t wo
 qt_status qt_profile(qt_net* net, int32_t enable);
 qt_status qt_profile_read(qt_net* net, char* buf, size_t cap, size_t* needed);
 
+/*
+ * qt_contract_static -- as qt_contract, with no caller workspace and no device
+ * allocation. The paper has no counterpart: this entry point exists for callers
+ * that cannot allocate device memory (a plugin inside a host application that
+ * owns the CUDA allocator, or a path that must not allocate), so they pass only
+ * their inputs (the network) and outputs (amp_re, amp_im, host doubles).
+ * All device scratch (gate copies, intermediate tensors, bookkeeping) lives in
+ * one static device array of 64 MiB inside the library; every GPU on which the
+ * library's module is loaded holds it until the process exits. The largest
+ * slice batch whose schedule fits the array is used (a schedule the caller had
+ * prepared with qt_prepare is restored before the call returns); a network whose schedule
+ * needs more than 64 MiB even one slice at a time is rejected with QT_ENOMEM
+ * and a message giving both sizes. It calls no cudaMalloc/cudaFree and creates
+ * no CUDA objects (tracing is skipped on this path).
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture. All calls
+ * on a device share the array, which keeps the last call's contents (the call
+ * re-uploads and re-zeroes everything it reads): calls that may overlap on the
+ * GPU (different streams or threads) race and must be serialised by the caller.
+ * The call synchronises `stream`. Errors: QT_EINVAL for a null argument;
+ * QT_ESTATE before qt_order; QT_ENOMEM as above; QT_ECUDA; others as qt_prepare.
+ */
+qt_status qt_contract_static(qt_net* net, int32_t precision, void* stream, double* amp_re,
+                             double* amp_im);
+
 /* Frees a network (NULL is a no-op). */
 void qt_free(qt_net* net);
 

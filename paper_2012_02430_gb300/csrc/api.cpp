@@ -66,6 +66,10 @@ bool check_net(const qt_net* net) { return net != nullptr; }
 
 }  // namespace
 
+namespace qt {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace qt
+
 extern "C" {
 
 const char* qt_last_error(void) { return g_err.c_str(); }

@@ -57,6 +57,7 @@ _SIGS = {
     "qt_run": [_vp, C.c_int64, C.c_int64, _vp, C.c_size_t, _vp, _vp],
     "qt_contract": [_vp, C.c_int32, _vp, C.c_size_t, _vp, _f64p, _f64p],
     "qt_profile": [_vp, C.c_int32],
+    "qt_contract_static": [_vp, C.c_int32, _vp, _f64p, _f64p],
     "qt_profile_read": [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)],
 }
 for _name, _args in _SIGS.items():
@@ -176,6 +177,12 @@ def qt_contract(net, precision, workspace_ptr, workspace_bytes, stream_ptr):
     re, im = C.c_double(), C.c_double()
     _check(lib.qt_contract(net, int(precision), _vp(workspace_ptr), int(workspace_bytes),
                            _vp(stream_ptr), C.byref(re), C.byref(im)))
+    return complex(re.value, im.value)
+
+
+def qt_contract_static(net, precision, stream_ptr):
+    re, im = C.c_double(), C.c_double()
+    _check(lib.qt_contract_static(net, int(precision), _vp(stream_ptr), C.byref(re), C.byref(im)))
     return complex(re.value, im.value)
 
 
