@@ -214,6 +214,7 @@ def ours(args):
     net.prepare(prec, batch=nslices)
     st = net.stats()
     net.upload()
+    tuned = net.autotune()
     out = torch.zeros(2, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -307,6 +308,7 @@ def ours(args):
                    **WORKLOAD, "k": k, "slices": nslices, "width": width,
                    "sliced_width": sliced_width, "precision": args.precision,
                    "l2": "flushed between steps (512 MiB write outside the timed events)",
+                   "autotuned_variants": {str(t["step"]): t["variant"] for t in tuned},
                    "plan_seconds": t_plan},
         "complex_tflops": tflops, "ledger_flops_per_step": flops_per_step,
         "ledger_bytes_per_step": bytes_per_step,

@@ -180,6 +180,20 @@ qt_status qt_contract(qt_net* net, int32_t precision, void* workspace, size_t wo
                       void* stream, double* amp_re, double* amp_im);
 
 /*
+ * Autotuner for the tile kernels. Runs the uploaded network's unsliced prefix
+ * and first slice batch once (the results are those of a normal run), launching
+ * every large step with each kernel variant (loads in flight per thread versus
+ * resident blocks per SM) timed by CUDA events, and keeps the fastest variant
+ * per step for later qt_run / qt_contract calls until the next qt_prepare.
+ * Synchronises `stream`. The choice per step is written as a JSON array
+ * [{"step", "variant", "ms": [per variant]}] into buf (as qt_stats; buf may be
+ * NULL). Errors: QT_ESTATE before qt_prepare; workspace errors as qt_run;
+ * QT_ECUDA.
+ */
+qt_status qt_autotune(qt_net* net, void* workspace, size_t workspace_bytes, void* stream, char* buf,
+                      size_t cap, size_t* needed);
+
+/*
  * Tracing. qt_profile(net, 1) makes later qt_run / qt_contract calls record a
  * CUDA event pair around every kernel launch on the caller's stream (a small
  * cost per launch); qt_profile(net, 0) stops. Either call drops the records.

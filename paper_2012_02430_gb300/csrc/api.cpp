@@ -17,6 +17,7 @@ qt_status run(qt_net* net, long long first, long long count, void* ws, void* str
               double* d_out, std::string& err);
 qt_status download_result(const double* d_out, double* host, void* stream, std::string& err);
 void prof_clear(qt_net* net);
+qt_status autotune(qt_net* net, void* ws, void* stream, std::string& report, std::string& err);
 qt_status prof_read(qt_net* net, std::string& out, std::string& err);
 }  // namespace qt
 
@@ -360,6 +361,24 @@ qt_status qt_profile_read(qt_net* net, char* buf, size_t cap, size_t* needed) {
   if (buf && cap > 0) {
     size_t n = std::min(cap - 1, out.size());
     std::memcpy(buf, out.data(), n);
+    buf[n] = '\0';
+  }
+  return ok();
+}
+
+qt_status qt_autotune(qt_net* net, void* workspace, size_t workspace_bytes, void* stream, char* buf,
+                      size_t cap, size_t* needed) {
+  if (!check_net(net)) return fail(QT_EINVAL, "qt_autotune: null network");
+  if (!net->sched.valid) return fail(QT_ESTATE, "qt_autotune: call qt_prepare first");
+  qt_status s = check_ws(net, workspace, workspace_bytes, "qt_autotune");
+  if (s != QT_OK) return s;
+  std::string report, err;
+  s = qt::autotune(net, workspace, stream, report, err);
+  if (s != QT_OK) return fail(s, "qt_autotune: " + err);
+  if (needed) *needed = report.size() + 1;
+  if (buf && cap > 0) {
+    size_t n = std::min(cap - 1, report.size());
+    std::memcpy(buf, report.data(), n);
     buf[n] = '\0';
   }
   return ok();

@@ -31,10 +31,6 @@
 namespace qt {
 
 constexpr int MAXOP = 12;
-constexpr int TILED_MAXOP = 6;
-constexpr int PAIR_TILE_BITS = 13;  // pairs per tile of the tiled kernel: 8192
-constexpr int TILE_THREADS = 256;
-constexpr int Q_PER_THREAD = (1 << PAIR_TILE_BITS) / TILE_THREADS;  // 32
 
 struct KOp {
   long long base;          // element offset from the workspace base
@@ -194,109 +190,230 @@ __global__ void __launch_bounds__(256) k_bucket_flat(const KStep st, R* data, Me
   }
 }
 
-// Tiled kernel: a tile is 2^PAIR_TILE_BITS pairs of one slice; a thread owns
-// 32 of them (thread bits = U bits 1..8, loop bits = U bits 9..13). Operand
-// offsets = tile part (one warp, per tile) + thread part (registers) + loop
-// part (shared-memory table), so the inner loop is loads and complex FMAs.
-template <typename R, int M>
-__global__ void __launch_bounds__(TILE_THREADS) k_bucket_tiled(const KStep st, R* data,
-                                                               Meta* meta) {
-  __shared__ int qoff[M][Q_PER_THREAD];
-  __shared__ long long toff[M];
-  __shared__ R tsc[M];
-  __shared__ long long tout;
+// Tiled kernel. Per slice, the U index space is cut into tiles of 2^TILE_UBITS
+// elements; a block owns a contiguous range of tiles. Inside a tile a thread
+// owns 4 consecutive U elements (U bits 0-1), the 256 threads cover U bits
+// 2-9 and a loop of Q_ITERS iterations covers U bits 10-13. An operand's
+// element offset is tile part (computed per warp) + thread part (registers) +
+// loop part (shared-memory table); whether the operand holds U bit 0 / bit 1
+// decides its load shape (32, 16 or 8 bytes), uniformly per warp. Loads of
+// UNR loop iterations are issued before their products are formed. Operands
+// whose exponents are moderate are multiplied unscaled (the result exponent is
+// then sum E_j); a slice with an extreme operand exponent takes the scaled path
+// (operand j times 2^-s_j, result exponent sum (E_j + s_j)). The decision depends
+// only on the slice's operand metadata, so every tile of a slice agrees.
+constexpr int TILE_THREADS = 256;
+constexpr int TILE_UBITS = 14;
+constexpr int Q_BITS = TILE_UBITS - 10;
+constexpr int Q_ITERS = 1 << Q_BITS;
+constexpr int TILED_MAXOP = 6;
+constexpr int SCALE_FREE_EXP = 30;  // |s_j| above this takes the scaled path
+
+template <typename R> struct V4 { R r[4], i[4]; };
+
+// loads the 4 values (U elements 0..3 of the thread) of one operand
+template <typename R>
+__device__ __forceinline__ void load4(const R* __restrict__ p, bool b0, bool b1, V4<R>& v) {
+  using C2 = typename CT<R>::c2;
+  if constexpr (sizeof(R) == 4) {
+    if (b0 && b1) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+      const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+      v.r[0] = a.x; v.i[0] = a.y; v.r[1] = a.z; v.i[1] = a.w;
+      v.r[2] = b.x; v.i[2] = b.y; v.r[3] = b.z; v.i[3] = b.w;
+    } else if (b0 || b1) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+      if (b0) {
+        v.r[0] = v.r[2] = a.x; v.i[0] = v.i[2] = a.y; v.r[1] = v.r[3] = a.z; v.i[1] = v.i[3] = a.w;
+      } else {
+        v.r[0] = v.r[1] = a.x; v.i[0] = v.i[1] = a.y; v.r[2] = v.r[3] = a.z; v.i[2] = v.i[3] = a.w;
+      }
+    } else {
+      const float2 a = __ldg(reinterpret_cast<const float2*>(p));
+      v.r[0] = v.r[1] = v.r[2] = v.r[3] = a.x;
+      v.i[0] = v.i[1] = v.i[2] = v.i[3] = a.y;
+    }
+  } else {
+    const C2* q = reinterpret_cast<const C2*>(p);
+    if (b0 && b1) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const C2 a = __ldg(q + e);
+        v.r[e] = a.x; v.i[e] = a.y;
+      }
+    } else if (b0 || b1) {
+      const C2 a = __ldg(q), b = __ldg(q + 1);
+      if (b0) {
+        v.r[0] = v.r[2] = a.x; v.i[0] = v.i[2] = a.y; v.r[1] = v.r[3] = b.x; v.i[1] = v.i[3] = b.y;
+      } else {
+        v.r[0] = v.r[1] = a.x; v.i[0] = v.i[1] = a.y; v.r[2] = v.r[3] = b.x; v.i[2] = v.i[3] = b.y;
+      }
+    } else {
+      const C2 a = __ldg(q);
+      v.r[0] = v.r[1] = v.r[2] = v.r[3] = a.x;
+      v.i[0] = v.i[1] = v.i[2] = v.i[3] = a.y;
+    }
+  }
+}
+
+// Variants of the tiled kernel (picked per step by the autotuner): loop
+// iterations whose loads are in flight together, and the minimum resident
+// blocks per SM the register allocation must allow.
+constexpr int N_VARIANTS = 3;
+__host__ __device__ constexpr int variant_unr(int v, int m) {
+  return v == 0 ? (m <= 2 ? 4 : (m <= 4 ? 2 : 1)) : (v == 1 ? (m <= 2 ? 2 : 1) : 1);
+}
+__host__ __device__ constexpr int variant_minb(int v) { return v == 0 ? 1 : (v == 1 ? 3 : 4); }
+
+template <typename R, int M, bool SCALE, int UNR>
+__device__ __forceinline__ void tile_body(const KStep& st, const R* const (&base)[M],
+                                          const int (&thr)[M], const bool (&b0)[M],
+                                          const bool (&b1)[M], const R (&sc)[M],
+                                          const int (*qoff)[Q_ITERS], R* __restrict__ out,
+                                          int tid, int lane, float& mx) {
+  const int nsum = st.nsum;
+#pragma unroll 1
+  for (int q0 = 0; q0 < Q_ITERS; q0 += UNR) {
+    V4<R> v[UNR][M];
+#pragma unroll
+    for (int uu = 0; uu < UNR; ++uu)
+#pragma unroll
+      for (int j = 0; j < M; ++j)
+        load4<R>(base[j] + 2 * (thr[j] + qoff[j][q0 + uu]), b0[j], b1[j], v[uu][j]);
+#pragma unroll
+    for (int uu = 0; uu < UNR; ++uu) {
+      R pr[4], pi[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        pr[e] = v[uu][0].r[e];
+        pi[e] = v[uu][0].i[e];
+        if constexpr (SCALE) {
+          pr[e] *= sc[0];
+          pi[e] *= sc[0];
+        }
+      }
+#pragma unroll
+      for (int j = 1; j < M; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          R br = v[uu][j].r[e], bi = v[uu][j].i[e];
+          if constexpr (SCALE) {
+            br *= sc[j];
+            bi *= sc[j];
+          }
+          cmul<R>(pr[e], pi[e], br, bi);
+        }
+      // sum over U bit 0, then (fused groups) bit 1 and lane bits
+      R s0r = pr[0] + pr[1], s0i = pi[0] + pi[1];
+      R s1r = pr[2] + pr[3], s1i = pi[2] + pi[3];
+      const unsigned long long ubase = ((unsigned long long)(q0 + uu) << 10) | ((unsigned)tid << 2);
+      if (nsum == 1) {
+        using C2 = typename CT<R>::c2;
+        const long long o = (long long)(ubase >> 1);
+        if constexpr (sizeof(R) == 4) {
+          *reinterpret_cast<float4*>(out + 2 * o) = make_float4(s0r, s0i, s1r, s1i);
+        } else {
+          C2* w = reinterpret_cast<C2*>(out + 2 * o);
+          w[0] = C2{s0r, s0i};
+          w[1] = C2{s1r, s1i};
+        }
+        mx = fmaxf(mx, fmaxf(absmax(s0r, s0i), absmax(s1r, s1i)));
+      } else {
+        R sr = s0r + s1r, si = s0i + s1i;
+        const int grp = 1 << (nsum - 2);
+        for (int w = 1; w < grp; w <<= 1) {
+          sr += __shfl_xor_sync(0xffffffffu, sr, w);
+          si += __shfl_xor_sync(0xffffffffu, si, w);
+        }
+        if ((lane & (grp - 1)) == 0) {
+          store_out<R>(out, (long long)(ubase >> nsum), sr, si);
+          mx = fmaxf(mx, absmax(sr, si));
+        }
+      }
+    }
+  }
+}
+
+template <typename R, int M, int V>
+__global__ void __launch_bounds__(TILE_THREADS, variant_minb(V))
+    k_bucket_tiled(const KStep st, R* data, Meta* meta) {
+  constexpr int UNR = variant_unr(V, M);
+  __shared__ int qoff[M][Q_ITERS];
   __shared__ unsigned int blkmax;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  const int grp = 1 << (st.nsum - 1);
-  for (int e = tid; e < M * Q_PER_THREAD; e += TILE_THREADS) {
-    const int j = e / Q_PER_THREAD, q = e % Q_PER_THREAD;
-    qoff[j][q] = (int)pext64((unsigned long long)q << 9, st.op[j].umask);
+  for (int e = tid; e < M * Q_ITERS; e += TILE_THREADS) {
+    const int j = e / Q_ITERS, q = e % Q_ITERS;
+    qoff[j][q] = (int)pext64((unsigned long long)q << 10, st.op[j].umask);
   }
   if (tid == 0) blkmax = 0u;
+  __syncthreads();
   int thr[M];
-  bool has0[M];
+  bool b0[M], b1[M];
 #pragma unroll
   for (int j = 0; j < M; ++j) {
-    thr[j] = (int)pext64((unsigned long long)tid << 1, st.op[j].umask);
-    has0[j] = st.op[j].umask & 1u;
+    thr[j] = (int)pext64((unsigned long long)tid << 2, st.op[j].umask);
+    b0[j] = st.op[j].umask & 1u;
+    b1[j] = (st.op[j].umask >> 1) & 1u;
   }
-  const long long tiles_per_slice = 1ll << (st.u - 1 - PAIR_TILE_BITS);
+  const long long tiles_per_slice = 1ll << (st.u - TILE_UBITS);
   const long long ntiles = st.nslices * tiles_per_slice;
-  long long cur_slice = -1;
+  const long long T0 = ntiles * blockIdx.x / gridDim.x;
+  const long long T1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+  long long cur_slice = T0 < T1 ? T0 / tiles_per_slice : -1;
   float mx = 0.f;
-  for (long long T = blockIdx.x; T < ntiles; T += gridDim.x) {
+  for (long long T = T0; T < T1; ++T) {
     const long long i = T / tiles_per_slice;
     const long long Tl = T - i * tiles_per_slice;
-    __syncthreads();  // previous tile done with toff/tsc; qoff/blkmax initialised
-    if (i != cur_slice) {
-      if (cur_slice >= 0) {  // flush the running max of the previous slice
-        unsigned int v = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
-        if (lane == 0) atomicMax(&blkmax, v);
-        __syncthreads();
-        if (tid == 0 && blkmax)
+    if (i != cur_slice) {  // block-uniform: flush the previous slice's max
+      unsigned int v = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+      if (lane == 0 && v) atomicMax(&blkmax, v);
+      __syncthreads();
+      if (tid == 0) {
+        if (blkmax)
           atomicMax(&meta[st.out_meta + (st.out_meta_per_slice ? cur_slice : 0)].maxabs, blkmax);
-        __syncthreads();
-        if (tid == 0) blkmax = 0u;
+        blkmax = 0u;
       }
+      __syncthreads();
       cur_slice = i;
       mx = 0.f;
     }
-    if (tid < 32) {
-      const unsigned long long sid = (unsigned long long)(st.slice_first + i);
-      const unsigned long long Ihi = (unsigned long long)Tl << (PAIR_TILE_BITS + 1);
-      int Eout = 0;
-      if (lane < M) {
-        const KOp& o = st.op[lane];
-        long long off = o.base + i * o.slice_stride + (long long)pext64(Ihi, o.umask);
-        if (o.smask) off += (long long)(pext64(sid, o.smask) << o.sshift);
-        toff[lane] = off;
-        const Meta mt = meta[o.meta + (o.meta_per_slice ? i : 0)];
-        const int s = scale_exp(mt.maxabs);
-        tsc[lane] = pow2_neg<R>(s);
-        Eout = mt.E + s;
-      }
-      Eout = __reduce_add_sync(0xffffffffu, Eout);
-      if (lane == 0) {
-        tout = st.out_base + i * st.out_slice_stride + (long long)(Ihi >> st.nsum);
-        if (Tl == 0) meta[st.out_meta + (st.out_meta_per_slice ? i : 0)].E = Eout;
-      }
+    // tile part of every operand's offset, computed by each warp (lane j: operand j)
+    const unsigned long long sid = (unsigned long long)(st.slice_first + i);
+    const unsigned long long Uhi = (unsigned long long)Tl << TILE_UBITS;
+    long long myoff = 0;
+    int mys = 0, myE = 0;
+    if (lane < M) {
+      const KOp& o = st.op[lane];
+      myoff = o.base + i * o.slice_stride + (long long)pext64(Uhi, o.umask);
+      if (o.smask) myoff += (long long)(pext64(sid, o.smask) << o.sshift);
+      const Meta mt = meta[o.meta + (o.meta_per_slice ? i : 0)];
+      mys = scale_exp(mt.maxabs);
+      myE = mt.E;
     }
-    __syncthreads();
-    long long base[M];
+    const bool extreme = __any_sync(0xffffffffu, lane < M && (mys > SCALE_FREE_EXP || mys < -SCALE_FREE_EXP));
+    const int ssum = __reduce_add_sync(0xffffffffu, mys);
+    const int Esum = __reduce_add_sync(0xffffffffu, myE);
+    const bool scaled = extreme || ssum > 2 * SCALE_FREE_EXP || ssum < -2 * SCALE_FREE_EXP;
+    if (Tl == 0 && tid == 0)
+      meta[st.out_meta + (st.out_meta_per_slice ? i : 0)].E = Esum + (scaled ? ssum : 0);
+    const R* base[M];
     R sc[M];
 #pragma unroll
     for (int j = 0; j < M; ++j) {
-      base[j] = toff[j] + thr[j];
-      sc[j] = tsc[j];
+      const long long off = __shfl_sync(0xffffffffu, myoff, j);
+      base[j] = data + 2 * off;
+      sc[j] = pow2_neg<R>(__shfl_sync(0xffffffffu, mys, j));
     }
-    const long long obase = tout;
-#pragma unroll 4
-    for (int q = 0; q < Q_PER_THREAD; ++q) {
-      R p0r = 1, p0i = 0, p1r = 1, p1i = 0;
-#pragma unroll
-      for (int j = 0; j < M; ++j) {
-        R r0, i0, r1, i1;
-        load_pair<R>(data, base[j] + qoff[j][q], has0[j], r0, i0, r1, i1);
-        cmul<R>(p0r, p0i, r0 * sc[j], i0 * sc[j]);
-        cmul<R>(p1r, p1i, r1 * sc[j], i1 * sc[j]);
-      }
-      R sr = p0r + p1r, si = p0i + p1i;
-      for (int w = 1; w < grp; w <<= 1) {
-        sr += __shfl_xor_sync(0xffffffffu, sr, w);
-        si += __shfl_xor_sync(0xffffffffu, si, w);
-      }
-      if ((lane & (grp - 1)) == 0) {
-        const unsigned long long pl = ((unsigned long long)q << 8) | (unsigned)tid;
-        store_out<R>(data, obase + (long long)((pl << 1) >> st.nsum), sr, si);
-        mx = fmaxf(mx, absmax(sr, si));
-      }
-    }
+    R* out = data + 2 * (st.out_base + i * st.out_slice_stride + (long long)(Uhi >> st.nsum));
+    if (scaled)
+      tile_body<R, M, true, UNR>(st, base, thr, b0, b1, sc, qoff, out, tid, lane, mx);
+    else
+      tile_body<R, M, false, UNR>(st, base, thr, b0, b1, sc, qoff, out, tid, lane, mx);
   }
   // final flush
-  __syncthreads();
   unsigned int v = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
-  if (lane == 0) atomicMax(&blkmax, v);
+  if (lane == 0 && v) atomicMax(&blkmax, v);
   __syncthreads();
   if (tid == 0 && cur_slice >= 0 && blkmax)
     atomicMax(&meta[st.out_meta + (st.out_meta_per_slice ? cur_slice : 0)].maxabs, blkmax);
@@ -437,6 +554,16 @@ qt_status prof_read(qt_net* net, std::string& out, std::string& err) {
   return QT_OK;
 }
 
+// resident blocks per SM of a kernel launched with TILE_THREADS threads (cached)
+template <typename K>
+static int resident_blocks(K kernel) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, TILE_THREADS, 0) != cudaSuccess ||
+      n < 1)
+    n = 2;
+  return n;
+}
+
 // builds the host copies uploaded by qt_upload: gate data, gate meta, scalar table
 void build_stage(qt_net* net) {
   const Schedule& S = net->sched;
@@ -541,17 +668,70 @@ static void fill_op(const Schedule& S, const SStep& st, int j, KOp& o) {
   }
 }
 
+// A step ready to launch: its kernel arguments (slice_first patched per batch),
+// the kernel chosen for it and the grid.
+struct LaunchDesc {
+  KStep k;
+  int step;
+  int kind;     // 0 flat, 1 tiled
+  int variant;  // tiled kernel variant
+  unsigned grid;
+  int64_t bytes, flops;  // ledger counts per slice
+};
+
+struct EngineCache {
+  uint64_t generation = 0;
+  std::vector<LaunchDesc> prefix, slice;
+  // captured run
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t capture = nullptr;
+  long long first = -1, count = -1;
+  void* ws = nullptr;
+  double* d_out = nullptr;
+  ~EngineCache() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (capture) cudaStreamDestroy(capture);
+  }
+};
+
 template <typename R>
-static qt_status launch_step(qt_net* net, int step_index, const SStep& st, long long nslices,
-                             long long slice_first, char* base, cudaStream_t s,
-                             std::string& err) {
-  const Schedule& S = net->sched;
-  KStep k{};
+using TiledFn = void (*)(const KStep, R*, Meta*);
+
+template <typename R, int V>
+static TiledFn<R> tiled_fn_v(int m) {
+  switch (m) {
+    case 1: return k_bucket_tiled<R, 1, V>;
+    case 2: return k_bucket_tiled<R, 2, V>;
+    case 3: return k_bucket_tiled<R, 3, V>;
+    case 4: return k_bucket_tiled<R, 4, V>;
+    case 5: return k_bucket_tiled<R, 5, V>;
+    case 6: return k_bucket_tiled<R, 6, V>;
+    default: return nullptr;
+  }
+}
+
+template <typename R>
+static TiledFn<R> tiled_fn(int v, int m) {
+  return v == 0 ? tiled_fn_v<R, 0>(m) : (v == 1 ? tiled_fn_v<R, 1>(m) : tiled_fn_v<R, 2>(m));
+}
+
+template <typename R>
+static int tiled_grid_cap(int v, int m) {
+  static int cap[N_VARIANTS][TILED_MAXOP + 1] = {};
+  if (cap[v][m] == 0) cap[v][m] = num_sms() * resident_blocks(tiled_fn<R>(v, m));
+  return cap[v][m];
+}
+
+template <typename R>
+static bool make_desc(const Schedule& S, int si, long long nslices, LaunchDesc& d,
+                      std::string& err, int variant = 1) {
+  const SStep& st = S.steps[si];
+  KStep& k = d.k;
+  k = KStep{};
   k.m = (int)st.ops.size();
   k.u = st.u;
   k.nsum = st.nsum;
   k.nslices = nslices;
-  k.slice_first = slice_first;
   const STensor& out = S.tensors[st.out];
   const long long eb = S.elem_bytes;
   if (out.kind == TK_SLICE) {
@@ -566,42 +746,74 @@ static qt_status launch_step(qt_net* net, int step_index, const SStep& st, long 
   k.out_meta = out.meta;
   if (k.m > MAXOP) {
     err = "bucket with more operands than the kernels take";
-    return QT_ERANGE;
+    return false;
   }
   for (int j = 0; j < k.m; ++j) fill_op(S, st, j, k.op[j]);
-  R* data = reinterpret_cast<R*>(base);
-  Meta* meta = reinterpret_cast<Meta*>(base + S.off_meta);
-  const bool tiled = st.u - 1 >= PAIR_TILE_BITS + 1 && k.m <= TILED_MAXOP;
-  ProfRec pr{step_index, tiled ? 1 : 0, nslices, st.bytes * (S.elem_bytes / 8) * nslices,
-             st.flops * nslices, nullptr, nullptr};
-  if (net->prof) prof_begin(net, s, pr);
-  net->launches++;
+  d.step = si;
+  d.bytes = st.bytes * (S.elem_bytes / 8);
+  d.flops = st.flops;
+  const bool tiled = st.u >= TILE_UBITS && k.m <= TILED_MAXOP && st.nsum <= 7;
+  d.kind = tiled ? 1 : 0;
+  d.variant = variant;
   if (tiled) {
-    const long long ntiles = nslices << (st.u - 1 - PAIR_TILE_BITS);
-    const long long grid = std::min<long long>(ntiles, (long long)num_sms() * 4);
-    switch (k.m) {
-#define QT_CASE(MM)                                                                  \
-  case MM:                                                                           \
-    k_bucket_tiled<R, MM><<<(unsigned)grid, TILE_THREADS, 0, s>>>(k, data, meta);    \
-    break;
-      QT_CASE(1) QT_CASE(2) QT_CASE(3) QT_CASE(4) QT_CASE(5) QT_CASE(6)
-#undef QT_CASE
-      default: break;
-    }
+    const long long ntiles = nslices << (st.u - TILE_UBITS);
+    d.grid = (unsigned)std::min<long long>(ntiles, tiled_grid_cap<R>(variant, k.m));
   } else {
     const long long total = nslices << (st.u - 1);
     const long long blocks = (total + 255) / 256;
-    const long long grid = std::max<long long>(1, std::min<long long>(blocks, (long long)num_sms() * 16));
-    k_bucket_flat<R><<<(unsigned)grid, 256, 0, s>>>(k, data, meta);
+    d.grid = (unsigned)std::max<long long>(1, std::min<long long>(blocks, (long long)num_sms() * 16));
   }
-  if (net->prof) prof_end(net, s, pr);
-  if (!cuda_ok(cudaGetLastError(), "bucket kernel launch", err)) return QT_ECUDA;
-  return QT_OK;
+  return true;
 }
 
 template <typename R>
-static qt_status run_impl(qt_net* net, long long first, long long count, char* base,
-                          cudaStream_t s, double* d_out, std::string& err) {
+static bool build_cache(qt_net* net, EngineCache& c, std::string& err) {
+  const Schedule& S = net->sched;
+  c.prefix.clear();
+  c.slice.clear();
+  for (int si = 0; si < (int)S.steps.size(); ++si) {
+    LaunchDesc d;
+    const bool pre = S.steps[si].region == 0;
+    if (!make_desc<R>(S, si, pre ? 1 : S.batch, d, err)) return false;
+    (pre ? c.prefix : c.slice).push_back(d);
+  }
+  if (c.exec) cudaGraphExecDestroy(c.exec);
+  c.exec = nullptr;
+  c.first = c.count = -1;
+  c.generation = S.generation;
+  return true;
+}
+
+template <typename R>
+static void launch_desc(qt_net* net, const LaunchDesc& d0, long long nslices, long long slice_first,
+                        char* base, cudaStream_t s) {
+  const Schedule& S = net->sched;
+  KStep k = d0.k;
+  k.nslices = nslices;
+  k.slice_first = slice_first;
+  unsigned grid = d0.grid;
+  if (nslices != d0.k.nslices) {  // a short last batch
+    LaunchDesc d;
+    std::string e;
+    make_desc<R>(S, d0.step, nslices, d, e, d0.variant);
+    grid = d.grid;
+  }
+  R* data = reinterpret_cast<R*>(base);
+  Meta* meta = reinterpret_cast<Meta*>(base + S.off_meta);
+  ProfRec pr{d0.step, d0.kind, nslices, d0.bytes * nslices, d0.flops * nslices, nullptr, nullptr};
+  if (net->prof) prof_begin(net, s, pr);
+  net->launches++;
+  if (d0.kind == 1) {
+    tiled_fn<R>(d0.variant, k.m)<<<grid, TILE_THREADS, 0, s>>>(k, data, meta);
+  } else {
+    k_bucket_flat<R><<<grid, 256, 0, s>>>(k, data, meta);
+  }
+  if (net->prof) prof_end(net, s, pr);
+}
+
+template <typename R>
+static qt_status enqueue_run(qt_net* net, EngineCache& c, long long first, long long count,
+                             char* base, cudaStream_t s, double* d_out, std::string& err) {
   const Schedule& S = net->sched;
   const size_t ngm = n_gate_meta(S);
   Meta* meta = reinterpret_cast<Meta*>(base + S.off_meta);
@@ -610,12 +822,7 @@ static qt_status run_impl(qt_net* net, long long first, long long count, char* b
       !cuda_ok(cudaMemsetAsync(meta + ngm, 0, (S.n_shared_meta - ngm) * sizeof(Meta), s),
                "reset prefix meta", err))
     return QT_ECUDA;
-  for (size_t si = 0; si < S.steps.size(); ++si) {
-    const SStep& st = S.steps[si];
-    if (st.region != 0) continue;
-    qt_status r = launch_step<R>(net, (int)si, st, 1, 0, base, s, err);
-    if (r != QT_OK) return r;
-  }
+  for (const LaunchDesc& d : c.prefix) launch_desc<R>(net, d, 1, 0, base, s);
   const ScalarTerm* terms = reinterpret_cast<const ScalarTerm*>(base + S.off_terms);
   const int nterms = (int)S.scalars.size();
   double2* partials = reinterpret_cast<double2*>(base + S.off_partials);
@@ -628,12 +835,7 @@ static qt_status run_impl(qt_net* net, long long first, long long count, char* b
                                  (size_t)(S.n_slice_meta_tensors * S.batch) * sizeof(Meta), s),
                  "reset slice meta", err))
       return QT_ECUDA;
-    for (size_t si = 0; si < S.steps.size(); ++si) {
-      const SStep& st = S.steps[si];
-      if (st.region != 1) continue;
-      qt_status r = launch_step<R>(net, (int)si, st, nb, b0, base, s, err);
-      if (r != QT_OK) return r;
-    }
+    for (const LaunchDesc& d : c.slice) launch_desc<R>(net, d, nb, b0, base, s);
     ProfRec pr{-1, 2, nb, 0, 0, nullptr, nullptr};
     if (net->prof) prof_begin(net, s, pr);
     net->launches += 2;
@@ -641,12 +843,169 @@ static qt_status run_impl(qt_net* net, long long first, long long count, char* b
         terms, nterms, reinterpret_cast<const R*>(base), meta, nb, b0, partials);
     k_reduce<<<1, 1024, 0, s>>>(partials, nb, acc, first_batch ? 1 : 0);
     if (net->prof) prof_end(net, s, pr);
-    if (!cuda_ok(cudaGetLastError(), "finalize/reduce launch", err)) return QT_ECUDA;
     first_batch = false;
   }
   net->launches++;
   k_write_out<<<1, 1, 0, s>>>(acc, std::pow(2.0, -0.5 * net->n), d_out);
-  if (!cuda_ok(cudaGetLastError(), "write_out launch", err)) return QT_ECUDA;
+  if (!cuda_ok(cudaGetLastError(), "kernel launch", err)) return QT_ECUDA;
+  return QT_OK;
+}
+
+// Autotuner: runs the schedule's first batch once, launching every tiled step
+// with each kernel variant (forward then backward over the variants, so warm
+// caches favour none), and keeps the fastest variant per step.
+template <typename R>
+static qt_status autotune_impl(qt_net* net, char* base, cudaStream_t s, std::string& report,
+                               std::string& err) {
+  if (!net->engine) net->engine = new EngineCache();
+  EngineCache& c = *static_cast<EngineCache*>(net->engine);
+  const Schedule& S = net->sched;
+  if (c.generation != S.generation && !build_cache<R>(net, c, err)) return QT_ERANGE;
+  const bool prof = net->prof;
+  net->prof = false;
+  struct Trial {
+    std::vector<LaunchDesc>* list;
+    size_t idx;
+    int variant;
+    cudaEvent_t a, b;
+  };
+  std::vector<Trial> trials;
+  auto ev = [&]() {
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  };
+  auto run_list = [&](std::vector<LaunchDesc>& list, long long nb, long long b0) {
+    for (size_t i = 0; i < list.size(); ++i) {
+      LaunchDesc& d = list[i];
+      if (d.kind != 1) {
+        launch_desc<R>(net, d, nb, b0, base, s);
+        continue;
+      }
+      for (int pass = 0; pass < 2; ++pass)
+        for (int t = 0; t < N_VARIANTS; ++t) {
+          const int v = pass == 0 ? t : N_VARIANTS - 1 - t;
+          LaunchDesc dv = d;
+          std::string e2;
+          make_desc<R>(S, d.step, d.k.nslices, dv, e2, v);
+          Trial tr{&list, i, v, ev(), ev()};
+          cudaEventRecord(tr.a, s);
+          launch_desc<R>(net, dv, nb, b0, base, s);
+          cudaEventRecord(tr.b, s);
+          trials.push_back(tr);
+        }
+    }
+  };
+  const size_t ngm = n_gate_meta(S);
+  Meta* meta = reinterpret_cast<Meta*>(base + S.off_meta);
+  if (S.n_shared_meta > (int64_t)ngm)
+    cudaMemsetAsync(meta + ngm, 0, (S.n_shared_meta - ngm) * sizeof(Meta), s);
+  run_list(c.prefix, 1, 0);
+  const long long nb = std::min<long long>(S.batch, S.nslices);
+  if (S.n_slice_meta_tensors)
+    cudaMemsetAsync(meta + S.n_shared_meta, 0,
+                    (size_t)(S.n_slice_meta_tensors * S.batch) * sizeof(Meta), s);
+  run_list(c.slice, nb, 0);
+  qt_status st = QT_OK;
+  if (!cuda_ok(cudaStreamSynchronize(s), "autotune run", err)) st = QT_ECUDA;
+  std::vector<std::vector<float>> best;  // per (list, idx): ms per variant
+  report = "[";
+  if (st == QT_OK) {
+    // accumulate times per step and variant
+    struct Key { std::vector<LaunchDesc>* list; size_t idx; };
+    std::vector<std::pair<Key, std::vector<float>>> acc;
+    for (const Trial& tr : trials) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, tr.a, tr.b);
+      if (acc.empty() || acc.back().first.list != tr.list || acc.back().first.idx != tr.idx)
+        acc.push_back({Key{tr.list, tr.idx}, std::vector<float>(N_VARIANTS, 0.f)});
+      acc.back().second[tr.variant] += ms;
+    }
+    bool first = true;
+    for (auto& kv : acc) {
+      LaunchDesc& d = (*kv.first.list)[kv.first.idx];
+      int bv = 0;
+      for (int v = 1; v < N_VARIANTS; ++v)
+        if (kv.second[v] < kv.second[bv]) bv = v;
+      std::string e2;
+      make_desc<R>(S, d.step, d.k.nslices, d, e2, bv);
+      char buf[160];
+      std::snprintf(buf, sizeof buf, "%s{\"step\":%d,\"variant\":%d,\"ms\":[%.4f,%.4f,%.4f]}",
+                    first ? "" : ",", d.step, bv, kv.second[0] / 2, kv.second[1] / 2,
+                    kv.second[2] / 2);
+      report += buf;
+      first = false;
+    }
+  }
+  report += "]";
+  for (const Trial& tr : trials) {
+    cudaEventDestroy(tr.a);
+    cudaEventDestroy(tr.b);
+  }
+  if (c.exec) {
+    cudaGraphExecDestroy(c.exec);
+    c.exec = nullptr;
+  }
+  c.first = c.count = -1;
+  net->prof = prof;
+  return st;
+}
+
+qt_status autotune(qt_net* net, void* ws, void* stream, std::string& report, std::string& err) {
+  char* base = (char*)ws;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (net->sched.precision == QT_FP64) return autotune_impl<double>(net, base, s, report, err);
+  return autotune_impl<float>(net, base, s, report, err);
+}
+
+constexpr long long kMaxGraphLaunches = 8192;
+
+template <typename R>
+static qt_status run_impl(qt_net* net, long long first, long long count, char* base,
+                          cudaStream_t s, double* d_out, std::string& err) {
+  if (!net->engine) net->engine = new EngineCache();
+  EngineCache& c = *static_cast<EngineCache*>(net->engine);
+  const Schedule& S = net->sched;
+  if (c.generation != S.generation && !build_cache<R>(net, c, err)) return QT_ERANGE;
+  const long long batches = (count + S.batch - 1) / S.batch;
+  const long long nlaunch = (long long)c.prefix.size() + batches * ((long long)c.slice.size() + 2) + 1;
+  if (!net->graphs || net->prof || nlaunch > kMaxGraphLaunches)
+    return enqueue_run<R>(net, c, first, count, base, s, d_out, err);
+  // captured once per (range, workspace, output, schedule), replayed afterwards
+  if (!(c.exec && c.first == first && c.count == count && c.ws == (void*)base && c.d_out == d_out)) {
+    if (c.exec) {
+      cudaGraphExecDestroy(c.exec);
+      c.exec = nullptr;
+    }
+    if (!c.capture &&
+        !cuda_ok(cudaStreamCreateWithFlags(&c.capture, cudaStreamNonBlocking), "capture stream", err))
+      return QT_ECUDA;
+    if (!cuda_ok(cudaStreamBeginCapture(c.capture, cudaStreamCaptureModeThreadLocal),
+                 "begin capture", err))
+      return QT_ECUDA;
+    const int64_t launches0 = net->launches;
+    qt_status r = enqueue_run<R>(net, c, first, count, base, c.capture, d_out, err);
+    net->launches = launches0;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c.capture, &g);
+    if (r != QT_OK) {
+      if (g) cudaGraphDestroy(g);
+      return r;
+    }
+    if (!cuda_ok(e, "end capture", err)) return QT_ECUDA;
+    e = cudaGraphInstantiate(&c.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (!cuda_ok(e, "graph instantiate", err)) {
+      c.exec = nullptr;
+      return QT_ECUDA;
+    }
+    c.first = first;
+    c.count = count;
+    c.ws = base;
+    c.d_out = d_out;
+  }
+  net->launches += nlaunch;
+  if (!cuda_ok(cudaGraphLaunch(c.exec, s), "graph launch", err)) return QT_ECUDA;
   return QT_OK;
 }
 
@@ -670,6 +1029,7 @@ qt_status download_result(const double* d_out, double* host, void* stream, std::
 }  // namespace qt
 
 qt_net::~qt_net() {
+  delete static_cast<qt::EngineCache*>(engine);
   qt::prof_clear(this);
   for (void* e : prof_pool) cudaEventDestroy((cudaEvent_t)e);
 }

@@ -92,7 +92,9 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePlan& plan,
                       int precision, int64_t batch, Schedule& S, std::string& err) {
+  static uint64_t next_generation = 1;
   S = Schedule();
+  S.generation = next_generation++;
   S.precision = precision;
   S.elem_bytes = precision == QT_FP64 ? 16 : 8;
   const int n_order = (int)plan.order.size();

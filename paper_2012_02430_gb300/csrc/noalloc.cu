@@ -116,9 +116,10 @@ qt_status qt_contract_static(qt_net* net, int32_t precision, void* stream, doubl
     restore();
     return fail(s, m);
   }
-  // no tracing events on this path: it creates no CUDA objects
-  const bool prof = net->prof;
+  // no tracing events and no graph capture on this path: it creates no CUDA objects
+  const bool prof = net->prof, graphs = net->graphs;
   net->prof = false;
+  net->graphs = false;
   std::string err;
   s = qt::upload(net, ws, kStaticWorkspaceBytes, stream, err);
   double* d_out = reinterpret_cast<double*>((char*)ws + net->sched.off_acc + 16);
@@ -126,6 +127,7 @@ qt_status qt_contract_static(qt_net* net, int32_t precision, void* stream, doubl
   double h[2] = {0.0, 0.0};
   if (s == QT_OK) s = qt::download_result(d_out, h, stream, err);
   net->prof = prof;
+  net->graphs = graphs;
   restore();
   if (s != QT_OK) return fail(s, "qt_contract_static: " + err);
   *amp_re = h[0];

@@ -89,6 +89,7 @@ struct SStep {
 
 struct Schedule {
   bool valid = false;
+  uint64_t generation = 0;      // changes with every compile
   int precision = QT_FP32_SIMT;
   int elem_bytes = 8;
   int k = 0;
@@ -153,5 +154,7 @@ struct qt_net {
   std::vector<qt::ProfRec> prof_recs;
   std::vector<void*> prof_pool;  // recycled cudaEvent_t
   int64_t launches = 0;          // kernel launches issued by this network
+  bool graphs = true;            // replay runs as captured CUDA graphs
+  void* engine = nullptr;        // engine.cu: launch descriptors and graph cache
   ~qt_net();
 };

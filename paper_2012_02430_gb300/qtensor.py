@@ -58,6 +58,7 @@ _SIGS = {
     "qt_contract": [_vp, C.c_int32, _vp, C.c_size_t, _vp, _f64p, _f64p],
     "qt_profile": [_vp, C.c_int32],
     "qt_contract_static": [_vp, C.c_int32, _vp, _f64p, _f64p],
+    "qt_autotune": [_vp, _vp, C.c_size_t, _vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)],
     "qt_profile_read": [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)],
 }
 for _name, _args in _SIGS.items():
@@ -186,6 +187,14 @@ def qt_contract_static(net, precision, stream_ptr):
     return complex(re.value, im.value)
 
 
+def qt_autotune(net, workspace_ptr, workspace_bytes, stream_ptr):
+    n = C.c_size_t()
+    buf = C.create_string_buffer(1 << 16)
+    _check(lib.qt_autotune(net, _vp(workspace_ptr), int(workspace_bytes), _vp(stream_ptr), buf,
+                           len(buf), C.byref(n)))
+    return json.loads(buf.value.decode())
+
+
 def qt_profile(net, enable):
     _check(lib.qt_profile(net, 1 if enable else 0))
 
@@ -243,6 +252,10 @@ class Network:
     def _stream(self):
         import torch
         return torch.cuda.current_stream().cuda_stream
+
+    def autotune(self):
+        return qt_autotune(self.handle, self.workspace.data_ptr(), self.workspace.numel(),
+                           self._stream())
 
     def upload(self):
         qt_upload(self.handle, self.workspace.data_ptr(), self.workspace.numel(), self._stream())

@@ -118,6 +118,24 @@ def test_slice_sum_equals_unsliced_gpu(qt):
     assert rel_err(sliced, unsliced) <= 1e-10
 
 
+@pytest.mark.parametrize("prec", [0, 4])
+def test_autotuned_schedule_parity(qt, prec):
+    """Every kernel variant the autotuner may pick gives the oracle's amplitude."""
+    n, p, seed = 60, 2, 18
+    edges, gammas, betas, z, tensors, nv, norm, adj = oracle_problem(n, p, seed)
+    net = qt.Network(edges, n, p, gammas, betas, z)
+    w = net.order(0)
+    net.slice(w - 4, 6, 1)
+    plan = oracle_plan(adj, 0, w - 4, 6, 1)
+    net.prepare(prec, batch=4)
+    net.upload()
+    report = net.autotune()
+    assert report and all(0 <= r["variant"] <= 2 for r in report)
+    ref, _ = oracle_amplitude(tensors, norm, plan)
+    amp = net.contract(prec)
+    assert rel_err(amp, ref) <= TOL[prec]
+
+
 def test_no_edges_and_single_qubit(qt):
     """Degenerate graphs: no cost gates (closed form), one qubit."""
     import math
