@@ -280,6 +280,34 @@ def ours(args):
                 "traffic": None, "launches": d["n"],
                 "share": {kind_names[kk]: by_kind[kk]["ms"] / tot_ms for kk in by_kind}}
 
+    # the plain FP32 greedy GPU path: one launch per bucket (no fused groups), default
+    # kernel variants, same slices; device-resident like `value`
+    plain = Q.Network(edges, WORKLOAD["n"], WORKLOAD["p"], gammas, betas, z)
+    Q.qt_set_option(plain.handle, Q.QT_OPT_FUSION, 0)
+    plain.order(Q.QT_GREEDY_MINFILL)
+    plain.slice(WORKLOAD["width_limit"], WORKLOAD["max_vars"], WORKLOAD["r"])
+    plain.prepare(prec, batch=nslices)
+    plain.upload()
+    pout = torch.zeros(2, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        plain.run(0, nslices, pout)
+    pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        pev[i][0].record(stream)
+        plain.run(0, nslices, pout)
+        pev[i][1].record(stream)
+    torch.cuda.synchronize()
+    plain_ms = sum(a.elapsed_time(b) for a, b in pev)
+    plain_amp = complex(pout[0].item(), pout[1].item())
+    plain_line = {"value": nslices * args.steps / (plain_ms / 1e3), "unit": "slices/s",
+                  "ms_per_step": plain_ms / args.steps,
+                  "complex_tflops": flops_per_step * args.steps / (plain_ms / 1e3) / 1e12,
+                  "launch_bytes_per_step": plain.stats()["slice_launch_bytes"] * nslices,
+                  "rel_diff_vs_value": abs(plain_amp - amp) / abs(plain_amp)}
+    del plain
+
     # end to end: host inputs -> amplitude on the host, through qt_contract
     from paper_2012_02430_gb300.inputs import random_angles
     e2e_steps = max(3, min(args.steps, 10))
@@ -312,6 +340,9 @@ def ours(args):
                    "plan_seconds": t_plan},
         "complex_tflops": tflops, "ledger_flops_per_step": flops_per_step,
         "ledger_bytes_per_step": bytes_per_step,
+        "launch_bytes_per_step": (st["prefix_launch_bytes"] + st["slice_launch_bytes"] * nslices)
+        * (st["elem_bytes"] // 8),
+        "plain_fp32_greedy_path": plain_line,
         "amplitude": [amp.real, amp.imag],
         "gpu_launches": launches,
         "roofline": roofline, "clocks": clk, "e2e": e2e,

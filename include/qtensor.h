@@ -179,6 +179,20 @@ qt_status qt_run(qt_net* net, int64_t first, int64_t count, void* workspace, siz
 qt_status qt_contract(qt_net* net, int32_t precision, void* workspace, size_t workspace_bytes,
                       void* stream, double* amp_re, double* amp_im);
 
+/* Options of a network (qt_set_option):
+ *   QT_OPT_FUSION  1 (default): consecutive bucket steps whose summed indices
+ *                  die together run as one launch that sums several indices,
+ *                  multiplying each step's own operands in at its level of the
+ *                  nested sum (the arithmetic of Alg. 1, without storing the
+ *                  intermediate results); 0: one launch per bucket (Alg. 1 as
+ *                  printed). Changing it discards the prepared schedule.
+ *   QT_OPT_GRAPHS  1 (default): qt_run captures its launches once per
+ *                  (slice range, workspace, output) and replays the CUDA
+ *                  graph; 0: direct launches.
+ * Errors: QT_EINVAL for a null network or an unknown option. */
+enum { QT_OPT_FUSION = 1, QT_OPT_GRAPHS = 2 };
+qt_status qt_set_option(qt_net* net, int32_t option, int64_t value);
+
 /*
  * Autotuner for the tile kernels. Runs the uploaded network's unsliced prefix
  * and first slice batch once (the results are those of a normal run), launching

@@ -244,8 +244,8 @@ qt_status qt_prepare(qt_net* net, int32_t precision, int32_t batch, size_t* work
   if (batch < 1) return fail(QT_EINVAL, "qt_prepare: batch must be >= 1");
   std::string err;
   try {
-    if (!qt::compile_schedule(net->tensors, net->n_vars, net->plan, precision, batch, net->sched,
-                              err)) {
+    if (!qt::compile_schedule(net->tensors, net->n_vars, net->plan, precision, batch, net->fuse,
+                              net->sched, err)) {
       net->sched = qt::Schedule();
       return fail(err.find("rank") != std::string::npos ? QT_ERANGE : QT_EINVAL,
                   "qt_prepare: " + err);
@@ -362,6 +362,22 @@ qt_status qt_profile_read(qt_net* net, char* buf, size_t cap, size_t* needed) {
     size_t n = std::min(cap - 1, out.size());
     std::memcpy(buf, out.data(), n);
     buf[n] = '\0';
+  }
+  return ok();
+}
+
+qt_status qt_set_option(qt_net* net, int32_t option, int64_t value) {
+  if (!check_net(net)) return fail(QT_EINVAL, "qt_set_option: null network");
+  switch (option) {
+    case QT_OPT_FUSION:
+      net->fuse = value != 0;
+      net->sched = qt::Schedule();  // prepare again
+      break;
+    case QT_OPT_GRAPHS:
+      net->graphs = value != 0;
+      break;
+    default:
+      return fail(QT_EINVAL, "qt_set_option: unknown option");
   }
   return ok();
 }

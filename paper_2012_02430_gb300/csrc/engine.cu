@@ -40,10 +40,12 @@ struct KOp {
   unsigned int smask;      // slice-id bits fixed into the operand
   int sshift;              // position of the slice block (unsliced rank)
   int meta_per_slice;
+  int level;               // nested-sum level at which the operand is multiplied in
+  int pad;
 };
 
 struct KStep {
-  int m, u, nsum, pad0;
+  int m, u, nsum, ms;  // ms: streaming operands (tiled kernel), placed first
   long long nslices, slice_first;
   long long out_base, out_slice_stride, out_meta;
   int out_meta_per_slice, pad1;
@@ -137,8 +139,11 @@ __device__ __forceinline__ void store_out(R* data, long long off, R re, R im) {
   *reinterpret_cast<C2*>(data + 2 * off) = v;
 }
 
-// Flat kernel: one U-element pair per thread, offsets from bit extracts.
-// For steps whose per-slice U space is small (the common case).
+// Flat kernel: one U-element pair (U bit 0) per thread, lanes cover U bits 1-5;
+// offsets from bit extracts. For launches whose per-slice U space is small.
+// Level-0 operands multiply both values of the pair, the pair is summed, then
+// for level l = 1 .. nsum-1 the level-l operands multiply each lane's partial
+// sum before the lanes that differ in U bit l are added (a shuffle).
 template <typename R>
 __global__ void __launch_bounds__(256) k_bucket_flat(const KStep st, R* data, Meta* meta) {
   const long long npairs = 1ll << (st.u - 1);
@@ -151,17 +156,18 @@ __global__ void __launch_bounds__(256) k_bucket_flat(const KStep st, R* data, Me
     const bool active = g < total;
     long long i = active ? g >> (st.u - 1) : 0;
     const unsigned long long I = (unsigned long long)(g & (npairs - 1)) << 1;
+    const unsigned long long sid = (unsigned long long)(st.slice_first + i);
     R p0r = 1, p0i = 0, p1r = 1, p1i = 0;
     int Eout = 0;
     if (active) {
-      const unsigned long long sid = (unsigned long long)(st.slice_first + i);
       for (int j = 0; j < st.m; ++j) {
         const KOp& o = st.op[j];
-        long long off = o.base + i * o.slice_stride + (long long)pext64(I, o.umask);
-        if (o.smask) off += (long long)(pext64(sid, o.smask) << o.sshift);
         const Meta mt = meta[o.meta + (o.meta_per_slice ? i : 0)];
         const int s = scale_exp(mt.maxabs);
         Eout += mt.E + s;
+        if (o.level != 0) continue;
+        long long off = o.base + i * o.slice_stride + (long long)pext64(I, o.umask);
+        if (o.smask) off += (long long)(pext64(sid, o.smask) << o.sshift);
         const R sc = pow2_neg<R>(s);
         R r0, i0, r1, i1;
         load_pair<R>(data, off, o.umask & 1u, r0, i0, r1, i1);
@@ -170,9 +176,21 @@ __global__ void __launch_bounds__(256) k_bucket_flat(const KStep st, R* data, Me
       }
     }
     R sr = active ? p0r + p1r : R(0), si = active ? p0i + p1i : R(0);
-    for (int w = 1; w < grp; w <<= 1) {
-      sr += __shfl_xor_sync(0xffffffffu, sr, w);
-      si += __shfl_xor_sync(0xffffffffu, si, w);
+    for (int l = 1; l < st.nsum; ++l) {
+      if (active) {
+        for (int j = 0; j < st.m; ++j) {
+          const KOp& o = st.op[j];
+          if (o.level != l) continue;
+          long long off = o.base + i * o.slice_stride + (long long)pext64(I, o.umask);
+          if (o.smask) off += (long long)(pext64(sid, o.smask) << o.sshift);
+          const R sc = pow2_neg<R>(scale_exp(meta[o.meta + (o.meta_per_slice ? i : 0)].maxabs));
+          using C2 = typename CT<R>::c2;
+          const C2 a = __ldg(reinterpret_cast<const C2*>(data + 2 * off));
+          cmul<R>(sr, si, a.x * sc, a.y * sc);
+        }
+      }
+      sr += __shfl_xor_sync(0xffffffffu, sr, 1 << (l - 1));
+      si += __shfl_xor_sync(0xffffffffu, si, 1 << (l - 1));
     }
     const bool writer = active && (lane & (grp - 1)) == 0;
     float mx = 0.f;
@@ -193,20 +211,34 @@ __global__ void __launch_bounds__(256) k_bucket_flat(const KStep st, R* data, Me
 // Tiled kernel. Per slice, the U index space is cut into tiles of 2^TILE_UBITS
 // elements; a block owns a contiguous range of tiles. Inside a tile a thread
 // owns 4 consecutive U elements (U bits 0-1), the 256 threads cover U bits
-// 2-9 and a loop of Q_ITERS iterations covers U bits 10-13. An operand's
-// element offset is tile part (computed per warp) + thread part (registers) +
-// loop part (shared-memory table); whether the operand holds U bit 0 / bit 1
-// decides its load shape (32, 16 or 8 bytes), uniformly per warp. Loads of
-// UNR loop iterations are issued before their products are formed. Operands
-// whose exponents are moderate are multiplied unscaled (the result exponent is
-// then sum E_j); a slice with an extreme operand exponent takes the scaled path
-// (operand j times 2^-s_j, result exponent sum (E_j + s_j)). The decision depends
-// only on the slice's operand metadata, so every tile of a slice agrees.
+// 2-9 and a loop of Q_ITERS iterations covers U bits 10-13.
+//
+// Operands come in two kinds. A "streaming" operand has indices among the loop
+// or tile bits: its offset is tile part (computed per warp) + thread part
+// (registers) + loop part (shared-memory table) and it is loaded every loop
+// iteration, UNR iterations at a time; whether it holds U bit 0 / bit 1
+// decides the load shape (32, 16 or 8 bytes). A "thread-constant" operand has
+// indices among U bits 0-9 only: its values at a thread's four elements are the
+// same for the whole tile, so the constant operands of each level are
+// multiplied once per tile into per-level factors F.
+//
+// Levels (fused launches): level-0 operands multiply all four elements; the
+// pair over U bit 0 is summed; level-1 operands multiply the two half sums,
+// which are added (U bit 1); level l >= 2 operands multiply each lane's partial
+// sum before the lanes that differ in U bit l are added (a shuffle).
+//
+// Scaling: operands whose exponents are moderate are multiplied unscaled (the
+// result exponent is then sum E_j); a slice with an extreme operand exponent
+// takes the scaled path (operand j times 2^-s_j, exponent sum (E_j + s_j)). The
+// decision depends only on the slice's operand metadata, so all tiles agree.
 constexpr int TILE_THREADS = 256;
 constexpr int TILE_UBITS = 14;
-constexpr int Q_BITS = TILE_UBITS - 10;
+constexpr int TILE_LOCAL_BITS = 10;  // U bits fixed by the thread inside a tile
+constexpr int Q_BITS = TILE_UBITS - TILE_LOCAL_BITS;
 constexpr int Q_ITERS = 1 << Q_BITS;
-constexpr int TILED_MAXOP = 6;
+constexpr int TILED_MAXSTREAM = 6;
+constexpr int MAX_LEVELS = 8;
+constexpr int MAX_FUSED_SUM = kMaxFusedSum;  // levels 0 .. MAX_FUSED_SUM-1
 constexpr int SCALE_FREE_EXP = 30;  // |s_j| above this takes the scaled path
 
 template <typename R> struct V4 { R r[4], i[4]; };
@@ -256,7 +288,15 @@ __device__ __forceinline__ void load4(const R* __restrict__ p, bool b0, bool b1,
   }
 }
 
-// Variants of the tiled kernel (picked per step by the autotuner): loop
+// per-thread products of the thread-constant operands, by level
+template <typename R> struct ConstF {
+  R f0r[4], f0i[4];   // level 0, at the four elements
+  R f1r[2], f1i[2];   // level 1, at U bit 1 = 0 / 1
+  R flr[MAX_LEVELS], fli[MAX_LEVELS];  // levels >= 2
+  unsigned int levels;  // bit l: some constant operand at level l
+};
+
+// Variants of the tiled kernel (picked per launch by the autotuner): loop
 // iterations whose loads are in flight together, and the minimum resident
 // blocks per SM the register allocation must allow.
 constexpr int N_VARIANTS = 3;
@@ -265,35 +305,33 @@ __host__ __device__ constexpr int variant_unr(int v, int m) {
 }
 __host__ __device__ constexpr int variant_minb(int v) { return v == 0 ? 1 : (v == 1 ? 3 : 4); }
 
-template <typename R, int M, bool SCALE, int UNR>
-__device__ __forceinline__ void tile_body(const KStep& st, const R* const (&base)[M],
-                                          const int (&thr)[M], const bool (&b0)[M],
-                                          const bool (&b1)[M], const R (&sc)[M],
+template <typename R, int MS, bool SCALE, int UNR>
+__device__ __forceinline__ void tile_body(const KStep& st, const R* const (&base)[MS],
+                                          const int (&thr)[MS], const bool (&b0)[MS],
+                                          const bool (&b1)[MS], const int (&lev)[MS],
+                                          const R (&sc)[MS], const ConstF<R>& F,
                                           const int (*qoff)[Q_ITERS], R* __restrict__ out,
                                           int tid, int lane, float& mx) {
   const int nsum = st.nsum;
 #pragma unroll 1
   for (int q0 = 0; q0 < Q_ITERS; q0 += UNR) {
-    V4<R> v[UNR][M];
+    V4<R> v[UNR][MS];
 #pragma unroll
     for (int uu = 0; uu < UNR; ++uu)
 #pragma unroll
-      for (int j = 0; j < M; ++j)
+      for (int j = 0; j < MS; ++j)
         load4<R>(base[j] + 2 * (thr[j] + qoff[j][q0 + uu]), b0[j], b1[j], v[uu][j]);
 #pragma unroll
     for (int uu = 0; uu < UNR; ++uu) {
       R pr[4], pi[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        pr[e] = v[uu][0].r[e];
-        pi[e] = v[uu][0].i[e];
-        if constexpr (SCALE) {
-          pr[e] *= sc[0];
-          pi[e] *= sc[0];
-        }
+        pr[e] = F.f0r[e];
+        pi[e] = F.f0i[e];
       }
 #pragma unroll
-      for (int j = 1; j < M; ++j)
+      for (int j = 0; j < MS; ++j) {
+        if (lev[j] != 0) continue;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           R br = v[uu][j].r[e], bi = v[uu][j].i[e];
@@ -303,29 +341,56 @@ __device__ __forceinline__ void tile_body(const KStep& st, const R* const (&base
           }
           cmul<R>(pr[e], pi[e], br, bi);
         }
-      // sum over U bit 0, then (fused groups) bit 1 and lane bits
-      R s0r = pr[0] + pr[1], s0i = pi[0] + pi[1];
-      R s1r = pr[2] + pr[3], s1i = pi[2] + pi[3];
-      const unsigned long long ubase = ((unsigned long long)(q0 + uu) << 10) | ((unsigned)tid << 2);
+      }
+      R h0r = pr[0] + pr[1], h0i = pi[0] + pi[1];
+      R h1r = pr[2] + pr[3], h1i = pi[2] + pi[3];
+      const unsigned long long ubase = ((unsigned long long)(q0 + uu) << TILE_LOCAL_BITS) |
+                                       ((unsigned)tid << 2);
       if (nsum == 1) {
         using C2 = typename CT<R>::c2;
         const long long o = (long long)(ubase >> 1);
         if constexpr (sizeof(R) == 4) {
-          *reinterpret_cast<float4*>(out + 2 * o) = make_float4(s0r, s0i, s1r, s1i);
+          *reinterpret_cast<float4*>(out + 2 * o) = make_float4(h0r, h0i, h1r, h1i);
         } else {
           C2* w = reinterpret_cast<C2*>(out + 2 * o);
-          w[0] = C2{s0r, s0i};
-          w[1] = C2{s1r, s1i};
+          w[0] = C2{h0r, h0i};
+          w[1] = C2{h1r, h1i};
         }
-        mx = fmaxf(mx, fmaxf(absmax(s0r, s0i), absmax(s1r, s1i)));
+        mx = fmaxf(mx, fmaxf(absmax(h0r, h0i), absmax(h1r, h1i)));
       } else {
-        R sr = s0r + s1r, si = s0i + s1i;
-        const int grp = 1 << (nsum - 2);
-        for (int w = 1; w < grp; w <<= 1) {
-          sr += __shfl_xor_sync(0xffffffffu, sr, w);
-          si += __shfl_xor_sync(0xffffffffu, si, w);
+        if (F.levels & 2u) {
+          cmul<R>(h0r, h0i, F.f1r[0], F.f1i[0]);
+          cmul<R>(h1r, h1i, F.f1r[1], F.f1i[1]);
         }
-        if ((lane & (grp - 1)) == 0) {
+#pragma unroll
+        for (int j = 0; j < MS; ++j) {
+          if (lev[j] != 1) continue;
+          R ar = v[uu][j].r[0], ai = v[uu][j].i[0], br = v[uu][j].r[2], bi = v[uu][j].i[2];
+          if constexpr (SCALE) {
+            ar *= sc[j]; ai *= sc[j]; br *= sc[j]; bi *= sc[j];
+          }
+          cmul<R>(h0r, h0i, ar, ai);
+          cmul<R>(h1r, h1i, br, bi);
+        }
+        R sr = h0r + h1r, si = h0i + h1i;
+#pragma unroll
+        for (int l = 2; l < MAX_FUSED_SUM; ++l) {
+          if (l >= nsum) break;
+          if (F.levels & (1u << l)) cmul<R>(sr, si, F.flr[l], F.fli[l]);
+#pragma unroll
+          for (int j = 0; j < MS; ++j) {
+            if (lev[j] != l) continue;
+            R ar = v[uu][j].r[0], ai = v[uu][j].i[0];
+            if constexpr (SCALE) {
+              ar *= sc[j];
+              ai *= sc[j];
+            }
+            cmul<R>(sr, si, ar, ai);
+          }
+          sr += __shfl_xor_sync(0xffffffffu, sr, 1 << (l - 2));
+          si += __shfl_xor_sync(0xffffffffu, si, 1 << (l - 2));
+        }
+        if ((lane & ((1 << (nsum - 2)) - 1)) == 0) {
           store_out<R>(out, (long long)(ubase >> nsum), sr, si);
           mx = fmaxf(mx, absmax(sr, si));
         }
@@ -334,28 +399,32 @@ __device__ __forceinline__ void tile_body(const KStep& st, const R* const (&base
   }
 }
 
-template <typename R, int M, int V>
+// Operands 0..ms-1 of the launch are streaming (template MS == ms), operands
+// ms..m-1 thread-constant.
+template <typename R, int MS, int V>
 __global__ void __launch_bounds__(TILE_THREADS, variant_minb(V))
     k_bucket_tiled(const KStep st, R* data, Meta* meta) {
-  constexpr int UNR = variant_unr(V, M);
-  __shared__ int qoff[M][Q_ITERS];
+  constexpr int UNR = variant_unr(V, MS);
+  __shared__ int qoff[MS][Q_ITERS];
   __shared__ unsigned int blkmax;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  for (int e = tid; e < M * Q_ITERS; e += TILE_THREADS) {
+  for (int e = tid; e < MS * Q_ITERS; e += TILE_THREADS) {
     const int j = e / Q_ITERS, q = e % Q_ITERS;
-    qoff[j][q] = (int)pext64((unsigned long long)q << 10, st.op[j].umask);
+    qoff[j][q] = (int)pext64((unsigned long long)q << TILE_LOCAL_BITS, st.op[j].umask);
   }
   if (tid == 0) blkmax = 0u;
   __syncthreads();
-  int thr[M];
-  bool b0[M], b1[M];
+  int thr[MS], lev[MS];
+  bool b0[MS], b1[MS];
 #pragma unroll
-  for (int j = 0; j < M; ++j) {
+  for (int j = 0; j < MS; ++j) {
     thr[j] = (int)pext64((unsigned long long)tid << 2, st.op[j].umask);
     b0[j] = st.op[j].umask & 1u;
     b1[j] = (st.op[j].umask >> 1) & 1u;
+    lev[j] = st.op[j].level;
   }
+  const int m = st.m;
   const long long tiles_per_slice = 1ll << (st.u - TILE_UBITS);
   const long long ntiles = st.nslices * tiles_per_slice;
   const long long T0 = ntiles * blockIdx.x / gridDim.x;
@@ -383,7 +452,7 @@ __global__ void __launch_bounds__(TILE_THREADS, variant_minb(V))
     const unsigned long long Uhi = (unsigned long long)Tl << TILE_UBITS;
     long long myoff = 0;
     int mys = 0, myE = 0;
-    if (lane < M) {
+    if (lane < m) {
       const KOp& o = st.op[lane];
       myoff = o.base + i * o.slice_stride + (long long)pext64(Uhi, o.umask);
       if (o.smask) myoff += (long long)(pext64(sid, o.smask) << o.sshift);
@@ -391,25 +460,63 @@ __global__ void __launch_bounds__(TILE_THREADS, variant_minb(V))
       mys = scale_exp(mt.maxabs);
       myE = mt.E;
     }
-    const bool extreme = __any_sync(0xffffffffu, lane < M && (mys > SCALE_FREE_EXP || mys < -SCALE_FREE_EXP));
+    const bool extreme =
+        __any_sync(0xffffffffu, lane < m && (mys > SCALE_FREE_EXP || mys < -SCALE_FREE_EXP));
     const int ssum = __reduce_add_sync(0xffffffffu, mys);
     const int Esum = __reduce_add_sync(0xffffffffu, myE);
     const bool scaled = extreme || ssum > 2 * SCALE_FREE_EXP || ssum < -2 * SCALE_FREE_EXP;
     if (Tl == 0 && tid == 0)
       meta[st.out_meta + (st.out_meta_per_slice ? i : 0)].E = Esum + (scaled ? ssum : 0);
-    const R* base[M];
-    R sc[M];
+    const R* base[MS];
+    R sc[MS];
 #pragma unroll
-    for (int j = 0; j < M; ++j) {
+    for (int j = 0; j < MS; ++j) {
       const long long off = __shfl_sync(0xffffffffu, myoff, j);
       base[j] = data + 2 * off;
       sc[j] = pow2_neg<R>(__shfl_sync(0xffffffffu, mys, j));
     }
+    // thread-constant operands folded into per-level factors
+    ConstF<R> F;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      F.f0r[e] = 1;
+      F.f0i[e] = 0;
+    }
+    F.f1r[0] = F.f1r[1] = 1;
+    F.f1i[0] = F.f1i[1] = 0;
+#pragma unroll
+    for (int l = 0; l < MAX_LEVELS; ++l) {
+      F.flr[l] = 1;
+      F.fli[l] = 0;
+    }
+    F.levels = 0u;
+    for (int j = MS; j < m; ++j) {
+      const long long off0 = __shfl_sync(0xffffffffu, myoff, j);
+      const int sj = __shfl_sync(0xffffffffu, mys, j);
+      const KOp& o = st.op[j];
+      V4<R> c;
+      load4<R>(data + 2 * (off0 + (long long)pext64((unsigned long long)tid << 2, o.umask)),
+               o.umask & 1u, (o.umask >> 1) & 1u, c);
+      const R scj = scaled ? pow2_neg<R>(sj) : R(1);
+      const int l = o.level;
+      F.levels |= 1u << l;
+      if (l == 0) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) cmul<R>(F.f0r[e], F.f0i[e], c.r[e] * scj, c.i[e] * scj);
+      } else if (l == 1) {
+        cmul<R>(F.f1r[0], F.f1i[0], c.r[0] * scj, c.i[0] * scj);
+        cmul<R>(F.f1r[1], F.f1i[1], c.r[2] * scj, c.i[2] * scj);
+      } else {
+#pragma unroll
+        for (int ll = 2; ll < MAX_LEVELS; ++ll)
+          if (ll == l) cmul<R>(F.flr[ll], F.fli[ll], c.r[0] * scj, c.i[0] * scj);
+      }
+    }
     R* out = data + 2 * (st.out_base + i * st.out_slice_stride + (long long)(Uhi >> st.nsum));
     if (scaled)
-      tile_body<R, M, true, UNR>(st, base, thr, b0, b1, sc, qoff, out, tid, lane, mx);
+      tile_body<R, MS, true, UNR>(st, base, thr, b0, b1, lev, sc, F, qoff, out, tid, lane, mx);
     else
-      tile_body<R, M, false, UNR>(st, base, thr, b0, b1, sc, qoff, out, tid, lane, mx);
+      tile_body<R, MS, false, UNR>(st, base, thr, b0, b1, lev, sc, F, qoff, out, tid, lane, mx);
   }
   // final flush
   unsigned int v = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
@@ -642,15 +749,16 @@ qt_status upload(qt_net* net, void* ws, size_t bytes, void* stream, std::string&
   return QT_OK;
 }
 
-static void fill_op(const Schedule& S, const SStep& st, int j, KOp& o) {
-  const STensor& t = S.tensors[st.ops[j]];
+static void fill_op(const Schedule& S, const SGroup& g, int j, KOp& o) {
+  const STensor& t = S.tensors[g.ops[j]];
   const long long eb = S.elem_bytes;
   o = KOp{};
   unsigned int um = 0;
-  for (int b = 0; b < st.u; ++b)
-    if (std::find(t.labels.begin(), t.labels.end(), st.ulabels[b]) != t.labels.end())
+  for (int b = 0; b < g.u; ++b)
+    if (std::find(t.labels.begin(), t.labels.end(), g.ulabels[b]) != t.labels.end())
       um |= 1u << b;
   o.umask = um;
+  o.level = g.levels[j];
   if (t.kind == TK_SLICE) {
     o.base = (long long)S.off_slices / eb + t.offset;
     o.slice_stride = S.slice_elems;
@@ -661,7 +769,7 @@ static void fill_op(const Schedule& S, const SStep& st, int j, KOp& o) {
     o.slice_stride = 0;
     o.meta = t.meta;
     o.meta_per_slice = 0;
-    if (st.region == 1 && t.nsliced) {
+    if (g.region == 1 && t.nsliced) {
       o.smask = t.smask;
       o.sshift = t.rank - t.nsliced;
     }
@@ -672,7 +780,7 @@ static void fill_op(const Schedule& S, const SStep& st, int j, KOp& o) {
 // the kernel chosen for it and the grid.
 struct LaunchDesc {
   KStep k;
-  int step;
+  int group;    // schedule launch group
   int kind;     // 0 flat, 1 tiled
   int variant;  // tiled kernel variant
   unsigned grid;
@@ -717,15 +825,15 @@ static TiledFn<R> tiled_fn(int v, int m) {
 
 template <typename R>
 static int tiled_grid_cap(int v, int m) {
-  static int cap[N_VARIANTS][TILED_MAXOP + 1] = {};
+  static int cap[N_VARIANTS][TILED_MAXSTREAM + 1] = {};
   if (cap[v][m] == 0) cap[v][m] = num_sms() * resident_blocks(tiled_fn<R>(v, m));
   return cap[v][m];
 }
 
 template <typename R>
-static bool make_desc(const Schedule& S, int si, long long nslices, LaunchDesc& d,
+static bool make_desc(const Schedule& S, int gi, long long nslices, LaunchDesc& d,
                       std::string& err, int variant = 1) {
-  const SStep& st = S.steps[si];
+  const SGroup& st = S.groups[gi];
   KStep& k = d.k;
   k = KStep{};
   k.m = (int)st.ops.size();
@@ -749,15 +857,19 @@ static bool make_desc(const Schedule& S, int si, long long nslices, LaunchDesc& 
     return false;
   }
   for (int j = 0; j < k.m; ++j) fill_op(S, st, j, k.op[j]);
-  d.step = si;
+  // streaming operands (indices among the tiled kernel's loop or tile bits) first
+  std::stable_partition(k.op, k.op + k.m, [](const KOp& o) { return (o.umask >> TILE_LOCAL_BITS) != 0u; });
+  k.ms = 0;
+  for (int j = 0; j < k.m; ++j) k.ms += (k.op[j].umask >> TILE_LOCAL_BITS) != 0u;
+  d.group = gi;
   d.bytes = st.bytes * (S.elem_bytes / 8);
   d.flops = st.flops;
-  const bool tiled = st.u >= TILE_UBITS && k.m <= TILED_MAXOP && st.nsum <= 7;
+  const bool tiled = st.u >= TILE_UBITS && k.ms >= 1 && k.ms <= TILED_MAXSTREAM && st.nsum <= 7;
   d.kind = tiled ? 1 : 0;
   d.variant = variant;
   if (tiled) {
     const long long ntiles = nslices << (st.u - TILE_UBITS);
-    d.grid = (unsigned)std::min<long long>(ntiles, tiled_grid_cap<R>(variant, k.m));
+    d.grid = (unsigned)std::min<long long>(ntiles, tiled_grid_cap<R>(variant, k.ms));
   } else {
     const long long total = nslices << (st.u - 1);
     const long long blocks = (total + 255) / 256;
@@ -771,10 +883,10 @@ static bool build_cache(qt_net* net, EngineCache& c, std::string& err) {
   const Schedule& S = net->sched;
   c.prefix.clear();
   c.slice.clear();
-  for (int si = 0; si < (int)S.steps.size(); ++si) {
+  for (int gi = 0; gi < (int)S.groups.size(); ++gi) {
     LaunchDesc d;
-    const bool pre = S.steps[si].region == 0;
-    if (!make_desc<R>(S, si, pre ? 1 : S.batch, d, err)) return false;
+    const bool pre = S.groups[gi].region == 0;
+    if (!make_desc<R>(S, gi, pre ? 1 : S.batch, d, err)) return false;
     (pre ? c.prefix : c.slice).push_back(d);
   }
   if (c.exec) cudaGraphExecDestroy(c.exec);
@@ -795,16 +907,17 @@ static void launch_desc(qt_net* net, const LaunchDesc& d0, long long nslices, lo
   if (nslices != d0.k.nslices) {  // a short last batch
     LaunchDesc d;
     std::string e;
-    make_desc<R>(S, d0.step, nslices, d, e, d0.variant);
+    make_desc<R>(S, d0.group, nslices, d, e, d0.variant);
     grid = d.grid;
   }
   R* data = reinterpret_cast<R*>(base);
   Meta* meta = reinterpret_cast<Meta*>(base + S.off_meta);
-  ProfRec pr{d0.step, d0.kind, nslices, d0.bytes * nslices, d0.flops * nslices, nullptr, nullptr};
+  ProfRec pr{S.groups[d0.group].first, d0.kind, nslices, d0.bytes * nslices, d0.flops * nslices,
+             nullptr, nullptr};
   if (net->prof) prof_begin(net, s, pr);
   net->launches++;
   if (d0.kind == 1) {
-    tiled_fn<R>(d0.variant, k.m)<<<grid, TILE_THREADS, 0, s>>>(k, data, meta);
+    tiled_fn<R>(d0.variant, k.ms)<<<grid, TILE_THREADS, 0, s>>>(k, data, meta);
   } else {
     k_bucket_flat<R><<<grid, 256, 0, s>>>(k, data, meta);
   }
@@ -887,7 +1000,7 @@ static qt_status autotune_impl(qt_net* net, char* base, cudaStream_t s, std::str
           const int v = pass == 0 ? t : N_VARIANTS - 1 - t;
           LaunchDesc dv = d;
           std::string e2;
-          make_desc<R>(S, d.step, d.k.nslices, dv, e2, v);
+          make_desc<R>(S, d.group, d.k.nslices, dv, e2, v);
           Trial tr{&list, i, v, ev(), ev()};
           cudaEventRecord(tr.a, s);
           launch_desc<R>(net, dv, nb, b0, base, s);
@@ -928,10 +1041,10 @@ static qt_status autotune_impl(qt_net* net, char* base, cudaStream_t s, std::str
       for (int v = 1; v < N_VARIANTS; ++v)
         if (kv.second[v] < kv.second[bv]) bv = v;
       std::string e2;
-      make_desc<R>(S, d.step, d.k.nslices, d, e2, bv);
+      make_desc<R>(S, d.group, d.k.nslices, d, e2, bv);
       char buf[160];
       std::snprintf(buf, sizeof buf, "%s{\"step\":%d,\"variant\":%d,\"ms\":[%.4f,%.4f,%.4f]}",
-                    first ? "" : ",", d.step, bv, kv.second[0] / 2, kv.second[1] / 2,
+                    first ? "" : ",", S.groups[d.group].first, bv, kv.second[0] / 2, kv.second[1] / 2,
                     kv.second[2] / 2);
       report += buf;
       first = false;

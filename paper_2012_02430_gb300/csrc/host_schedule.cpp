@@ -91,9 +91,10 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 }  // namespace
 
 bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePlan& plan,
-                      int precision, int64_t batch, Schedule& S, std::string& err) {
+                      int precision, int64_t batch, bool fuse, Schedule& S, std::string& err) {
   static uint64_t next_generation = 1;
   S = Schedule();
+  S.fused = fuse;
   S.generation = next_generation++;
   S.precision = precision;
   S.elem_bytes = precision == QT_FP64 ? 16 : 8;
@@ -204,14 +205,83 @@ bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePla
       S.slice_width = std::max(S.slice_width, st.c);
     }
   }
-  // scalars live to the end
-  const int end_step = (int)S.steps.size();
-  for (int32_t tid : S.scalars) S.tensors[tid].last_use = end_step;
-  // prefix results read by slice steps live to the end of the run
+  // launch groups: a step joins the previous group when its vertex is the next
+  // position, it consumes the group's running result, every other operand lies
+  // inside the group's U, and the limits on summed indices and operands hold
+  auto seen_labels = [&](int32_t tid, int region) {
+    std::vector<int32_t> out;
+    for (int32_t l : S.tensors[tid].labels)
+      if (region == 0 || slice_bit[l] < 0) out.push_back(l);
+    return out;
+  };
+  for (int si = 0; si < (int)S.steps.size(); ++si) {
+    const SStep& st = S.steps[si];
+    bool joined = false;
+    if (fuse && !S.groups.empty()) {
+      SGroup& g = S.groups.back();
+      const SStep& last = S.steps[g.first + g.nsteps - 1];
+      bool ok = st.region == g.region && S.pos[st.var] == S.pos[last.var] + 1 &&
+                g.nsum + 1 <= kMaxFusedSum;
+      int nothers = 0;
+      bool has_prev = false;
+      if (ok) {
+        for (int32_t tid : st.ops) {
+          if (tid == last.out) {
+            has_prev = true;
+            continue;
+          }
+          ++nothers;
+          for (int32_t l : seen_labels(tid, st.region))
+            if (std::find(g.ulabels.begin(), g.ulabels.end(), l) == g.ulabels.end()) ok = false;
+        }
+      }
+      ok = ok && has_prev && (int)g.ops.size() + nothers <= kMaxGroupOps;
+      if (ok) {
+        for (int32_t tid : st.ops)
+          if (tid != last.out) {
+            g.ops.push_back(tid);
+            g.levels.push_back(g.nsum);
+          }
+        S.tensors[last.out].virt = true;
+        g.nsteps++;
+        g.nsum++;
+        g.c = g.u - g.nsum;
+        g.out = st.out;
+        g.flops += st.flops;
+        joined = true;
+      }
+    }
+    if (!joined) {
+      SGroup g;
+      g.region = st.region;
+      g.first = si;
+      g.ops = st.ops;
+      g.levels.assign(st.ops.size(), 0);
+      g.ulabels = st.ulabels;
+      g.out = st.out;
+      g.u = st.u;
+      g.nsum = 1;
+      g.c = st.c;
+      g.flops = st.flops;
+      S.groups.push_back(g);
+    }
+  }
+  for (SGroup& g : S.groups) {
+    int64_t elems = (int64_t)1 << g.c;
+    for (int32_t tid : g.ops) elems += (int64_t)1 << seen_labels(tid, g.region).size();
+    g.bytes = 8 * elems;
+    (g.region == 0 ? S.prefix_launch_bytes : S.slice_launch_bytes) += g.bytes;
+  }
+  // liveness by group: a stored tensor lives from its group to the last group reading it
+  const int end_group = (int)S.groups.size();
+  for (STensor& t : S.tensors) t.last_use = -1;
+  for (int gi = 0; gi < end_group; ++gi)
+    for (int32_t tid : S.groups[gi].ops) S.tensors[tid].last_use = gi;
+  for (int32_t tid : S.scalars) S.tensors[tid].last_use = end_group;
   for (STensor& t : S.tensors)
-    if (t.kind == TK_PREFIX && t.last_use >= 0 && t.last_use < end_step &&
-        S.steps[t.last_use].region == 1)
-      t.last_use = end_step;
+    if (t.kind == TK_PREFIX && !t.virt && t.last_use >= 0 && t.last_use < end_group &&
+        S.groups[t.last_use].region == 1)
+      t.last_use = end_group;
 
   // memory: gates packed, prefix and slice arenas by liveness
   int64_t goff = 0;
@@ -222,14 +292,14 @@ bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePla
     }
   S.gate_elems = goff;
   Arena pre, sl;
-  for (int s = 0; s < (int)S.steps.size(); ++s) {
-    STensor& o = S.tensors[S.steps[s].out];
+  for (int gi = 0; gi < end_group; ++gi) {
+    STensor& o = S.tensors[S.groups[gi].out];
     Arena& ar = o.kind == TK_PREFIX ? pre : sl;
     o.offset = ar.alloc((int64_t)1 << o.rank, kArenaAlign);
-    if (o.last_use < 0) o.last_use = s;  // never read (cannot happen: results are placed)
-    for (int32_t tid : S.steps[s].ops) {
+    if (o.last_use < 0) o.last_use = gi;
+    for (int32_t tid : S.groups[gi].ops) {
       STensor& t = S.tensors[tid];
-      if (t.kind != TK_GATE && t.last_use == s)
+      if (t.kind != TK_GATE && !t.virt && t.last_use == gi)
         (t.kind == TK_PREFIX ? pre : sl).release(t.offset, (int64_t)1 << t.rank, kArenaAlign);
     }
   }
@@ -280,6 +350,9 @@ std::string schedule_json(const Schedule& S, const SlicePlan& plan) {
     << ",\"n_scalars\":" << S.scalars.size() << ",\"workspace_bytes\":" << S.total_bytes
     << ",\"prefix_arena_bytes\":" << S.prefix_elems * S.elem_bytes
     << ",\"slice_arena_bytes\":" << S.slice_elems * S.elem_bytes
+    << ",\"fused\":" << (S.fused ? 1 : 0) << ",\"n_groups\":" << S.groups.size()
+    << ",\"prefix_launch_bytes\":" << S.prefix_launch_bytes
+    << ",\"slice_launch_bytes\":" << S.slice_launch_bytes
     << ",\"upload_bytes\":"
     << S.gate_elems * S.elem_bytes + S.n_shared_meta * 8 +
            (int64_t)S.scalars.size() * (int64_t)kScalarTermBytes
@@ -289,6 +362,13 @@ std::string schedule_json(const Schedule& S, const SlicePlan& plan) {
     if (i) o << ",";
     o << "[" << st.region << "," << st.var << "," << st.ops.size() << "," << st.u << "," << st.c
       << "," << st.nsum << "," << st.flops << "," << st.bytes << "]";
+  }
+  o << "],\"groups\":[";
+  for (size_t i = 0; i < S.groups.size(); ++i) {
+    const SGroup& g = S.groups[i];
+    if (i) o << ",";
+    o << "[" << g.region << "," << g.first << "," << g.nsteps << "," << g.ops.size() << ","
+      << g.u << "," << g.nsum << "," << g.flops << "," << g.bytes << "]";
   }
   o << "]}";
   return o.str();

@@ -74,7 +74,8 @@ struct STensor {
   int64_t offset = 0;           // element offset inside its region
   int64_t meta = 0;             // meta slot (shared) or first slot (per slice)
   int producer = -1;            // step that writes it (-1 for gates)
-  int last_use = -1;            // last step that reads it
+  int last_use = -1;            // last step (then group) that reads it
+  bool virt = false;            // produced and consumed inside one fused group: never stored
 };
 
 struct SStep {
@@ -87,8 +88,25 @@ struct SStep {
   int64_t flops = 0, bytes = 0;
 };
 
+// A launch: consecutive bucket steps fused when the indices they sum out die
+// together. Step i+l of the group (l = 1..nsum-1) adds operands whose indices
+// all lie in the first step's union U; they enter at "level" l, i.e. after the
+// l lowest U bits have been summed, so the arithmetic is exactly that of the
+// separate steps while the intermediate results never reach memory.
+struct SGroup {
+  int region = 1;
+  int first = 0, nsteps = 1;     // steps first .. first + nsteps - 1
+  std::vector<int32_t> ops;      // tensor ids, level 0 first
+  std::vector<int32_t> levels;   // level of each operand
+  std::vector<int32_t> ulabels;  // U of the first step (canonical order)
+  int out = -1;                  // result of the last step
+  int u = 0, nsum = 1, c = 0;
+  int64_t flops = 0, bytes = 0;  // flops: sum over the steps; bytes: operands once + result
+};
+
 struct Schedule {
   bool valid = false;
+  bool fused = true;             // steps grouped into fused launches
   uint64_t generation = 0;      // changes with every compile
   int precision = QT_FP32_SIMT;
   int elem_bytes = 8;
@@ -98,6 +116,7 @@ struct Schedule {
   std::vector<int32_t> pos;     // variable -> canonical position
   std::vector<STensor> tensors;
   std::vector<SStep> steps;
+  std::vector<SGroup> groups;
   int n_prefix_steps = 0;
   std::vector<int32_t> scalars; // tensors whose value multiplies the slice result
   // region sizes in elements
@@ -108,11 +127,15 @@ struct Schedule {
          off_acc = 0, off_terms = 0, total_bytes = 0;
   // ledger
   int64_t prefix_flops = 0, prefix_bytes = 0, slice_flops = 0, slice_bytes = 0;
+  int64_t prefix_launch_bytes = 0, slice_launch_bytes = 0;  // bytes of the (fused) launches
   int prefix_width = 0, slice_width = 0;
 };
 
+constexpr int kMaxFusedSum = 6;   // indices summed by one launch
+constexpr int kMaxGroupOps = 12;  // operands of one launch
+
 bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePlan& plan,
-                      int precision, int64_t batch, Schedule& out, std::string& err);
+                      int precision, int64_t batch, bool fuse, Schedule& out, std::string& err);
 
 std::string schedule_json(const Schedule& s, const SlicePlan& plan);
 
@@ -155,6 +178,7 @@ struct qt_net {
   std::vector<void*> prof_pool;  // recycled cudaEvent_t
   int64_t launches = 0;          // kernel launches issued by this network
   bool graphs = true;            // replay runs as captured CUDA graphs
+  bool fuse = true;              // fuse bucket steps whose summed indices die together
   void* engine = nullptr;        // engine.cu: launch descriptors and graph cache
   ~qt_net();
 };

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libqtensor.so")
 QT_OK, QT_EINVAL, QT_ENOMEM, QT_ECUDA, QT_ETIMEOUT, QT_ESTATE, QT_ERANGE = range(7)
 QT_GREEDY_MINFILL, QT_GREEDY_MINDEG = 0, 1
 QT_FP32_SIMT, QT_FP64 = 0, 4
+QT_OPT_FUSION, QT_OPT_GRAPHS = 1, 2
 
 STATUS_NAMES = {0: "QT_OK", 1: "QT_EINVAL", 2: "QT_ENOMEM", 3: "QT_ECUDA",
                 4: "QT_ETIMEOUT", 5: "QT_ESTATE", 6: "QT_ERANGE"}
@@ -58,6 +59,7 @@ _SIGS = {
     "qt_contract": [_vp, C.c_int32, _vp, C.c_size_t, _vp, _f64p, _f64p],
     "qt_profile": [_vp, C.c_int32],
     "qt_contract_static": [_vp, C.c_int32, _vp, _f64p, _f64p],
+    "qt_set_option": [_vp, C.c_int32, C.c_int64],
     "qt_autotune": [_vp, _vp, C.c_size_t, _vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)],
     "qt_profile_read": [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)],
 }
@@ -185,6 +187,10 @@ def qt_contract_static(net, precision, stream_ptr):
     re, im = C.c_double(), C.c_double()
     _check(lib.qt_contract_static(net, int(precision), _vp(stream_ptr), C.byref(re), C.byref(im)))
     return complex(re.value, im.value)
+
+
+def qt_set_option(net, option, value):
+    _check(lib.qt_set_option(net, int(option), int(value)))
 
 
 def qt_autotune(net, workspace_ptr, workspace_bytes, stream_ptr):

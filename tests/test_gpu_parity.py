@@ -119,6 +119,31 @@ def test_slice_sum_equals_unsliced_gpu(qt):
 
 
 @pytest.mark.parametrize("prec", [0, 4])
+@pytest.mark.parametrize("case", [(24, 3, 15, -4), (44, 2, 14, -4), (60, 2, 18, -4)])
+def test_fused_and_unfused_launches(qt, case, prec):
+    """Fused launch groups (several indices summed per launch) and one launch per
+    bucket give the oracle's amplitude."""
+    n, p, seed, off = case
+    edges, gammas, betas, z, tensors, nv, norm, adj = oracle_problem(n, p, seed)
+    plan = None
+    amps = {}
+    for fuse in (0, 1):
+        net = qt.Network(edges, n, p, gammas, betas, z)
+        qt.qt_set_option(net.handle, qt.QT_OPT_FUSION, fuse)
+        w = net.order(0)
+        net.slice(w + off, 6, 1)
+        if plan is None:
+            plan = oracle_plan(adj, 0, w + off, 6, 1)
+        net.prepare(prec, batch=3)
+        st = net.stats()
+        assert st["fused"] == fuse
+        amps[fuse] = net.contract(prec)
+    ref, _ = oracle_amplitude(tensors, norm, plan)
+    for fuse in (0, 1):
+        assert rel_err(amps[fuse], ref) <= TOL[prec], (fuse, amps[fuse], ref)
+
+
+@pytest.mark.parametrize("prec", [0, 4])
 def test_autotuned_schedule_parity(qt, prec):
     """Every kernel variant the autotuner may pick gives the oracle's amplitude."""
     n, p, seed = 60, 2, 18

@@ -76,6 +76,10 @@ def test_plan_bit_exact(qt, case, algo):
                         "prefix_width", "slice_width", "n_prefix_steps", "n_slice_steps"):
                 assert st[key] == tot[key], key
             assert [s[2:5] for s in st["steps"]] == [[s["m"], s["u"], s["c"]] for s in steps]
+            groups = ledger.launch_groups([l for l, _ in tensors], plan["order"], plan["sliced"],
+                                          plan["slice_step"])
+            assert st["groups"] == groups
+            assert sum(g[6] for g in groups) == tot["prefix_flops"] + tot["slice_flops"]
             assert st["nslices"] == 1 << k and st["batch"] == min(3, 1 << k)
             assert st["elem_bytes"] == eb
     finally:
@@ -99,6 +103,9 @@ def test_bench_workload_plan_bit_exact(qt):
         tot, _ = ledger.ledger([l for l, _ in tensors], plan["order"], plan["sliced"],
                                plan["slice_step"])
         assert st["slice_flops"] == tot["slice_flops"] and st["slice_bytes"] == tot["slice_bytes"]
+        groups = ledger.launch_groups([l for l, _ in tensors], plan["order"], plan["sliced"],
+                                      plan["slice_step"])
+        assert st["groups"] == groups
     finally:
         qt.qt_free(h)
 
@@ -153,6 +160,33 @@ def test_errors(qt):
         with pytest.raises(QtError) as e:
             qt.qt_run(h, 0, 1, 256, need - 1, 0, 256)
         assert e.value.status == qt.QT_ENOMEM
+    finally:
+        qt.qt_free(h)
+
+
+def test_fusion_option(qt):
+    """Without fusion every bucket is its own launch; with it, launch bytes only drop."""
+    n, p, seed = 44, 2, 14
+    edges, gammas, betas, z, tensors, nv, norm, adj = oracle_problem(n, p, seed)
+    h = qt.qt_build_network(edges, n, p, gammas, betas, z)
+    try:
+        qt.qt_order(h, 0)
+        qt.qt_slice(h, 17, 6, 1)
+        qt.qt_prepare(h, 0, 2)
+        fused = qt.qt_stats(h)
+        qt.qt_set_option(h, qt.QT_OPT_FUSION, 0)
+        with pytest.raises(qt.QtError):
+            qt.qt_stats(h)  # the option discards the prepared schedule
+        qt.qt_prepare(h, 0, 2)
+        plain = qt.qt_stats(h)
+        assert plain["fused"] == 0 and fused["fused"] == 1
+        assert len(plain["groups"]) == len(plain["steps"])
+        assert all(g[2] == 1 and g[5] == 1 for g in plain["groups"])
+        assert plain["slice_launch_bytes"] == plain["slice_bytes"]
+        assert fused["slice_launch_bytes"] < plain["slice_launch_bytes"]
+        assert fused["slice_flops"] == plain["slice_flops"]
+        with pytest.raises(qt.QtError):
+            qt.qt_set_option(h, 99, 1)
     finally:
         qt.qt_free(h)
 
