@@ -308,6 +308,8 @@ def ours(args):
                   "rel_diff_vs_value": abs(plain_amp - amp) / abs(plain_amp)}
     del plain
 
+    energy_line = batched_energy(args, Q, torch, flush, stream)
+
     # end to end: host inputs -> amplitude on the host, through qt_contract
     from paper_2012_02430_gb300.inputs import random_angles
     e2e_steps = max(3, min(args.steps, 10))
@@ -343,6 +345,7 @@ def ours(args):
         "launch_bytes_per_step": (st["prefix_launch_bytes"] + st["slice_launch_bytes"] * nslices)
         * (st["elem_bytes"] // 8),
         "plain_fp32_greedy_path": plain_line,
+        "batched_energy": energy_line,
         "amplitude": [amp.real, amp.imag],
         "gpu_launches": launches,
         "roofline": roofline, "clocks": clk, "e2e": e2e,
@@ -358,6 +361,48 @@ def ours(args):
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+ENERGY_WORKLOAD = dict(n=1000, p=2, seed=1004)
+
+
+def batched_energy(args, Q, torch, flush, stream):
+    """Secondary measurement: the p=2 MaxCut energy of a random 3-regular graph with
+    N=1000 (1500 lightcone networks) as one persistent launch (CUDA-graph replay),
+    device-resident, autotuned block size; CUDA events, L2 flushed between evaluations."""
+    from paper_2012_02430_gb300.inputs import qaoa_instance
+    n, p, seed = ENERGY_WORKLOAD["n"], ENERGY_WORKLOAD["p"], ENERGY_WORKLOAD["seed"]
+    edges, g, b, _ = qaoa_instance(n, p, seed)
+    en = Q.Energy(edges, n, p, g, b)
+    en.prepare(Q.QT_FP32_SIMT)
+    en.upload()
+    threads = en.autotune()
+    zz = torch.zeros(len(edges), dtype=torch.float64, device="cuda")
+    E = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        en.run(zz, E)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        en.run(zz, E)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b2) for a, b2 in ev) / args.steps
+    st = en.stats()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        E_host, _ = en.compute(Q.QT_FP32_SIMT)
+    e2e_ms = 1e3 * (time.perf_counter() - t0) / 3
+    return {"workload": f"p={p} MaxCut energy, random 3-regular N={n} seed={seed}, "
+                        f"{len(edges)} lightcone networks, one persistent launch",
+            "edges_per_s": len(edges) / (ms / 1e3), "ms_per_energy": ms,
+            "energy": float(E.item()), "e2e_ms_per_energy": e2e_ms,
+            "e2e_includes": "upload of gates and step tables, launch, D2H of zz and energy",
+            "block_threads": threads, "blocks": st["blocks"], "lightcone_width_hist": st["width_hist"],
+            "ledger_flops": st["flops"], "launch_bytes": st["bytes"],
+            "upload_bytes": st["upload_bytes"]}
 
 
 def gate_upload_bytes(st):

@@ -245,6 +245,53 @@ qt_status qt_profile_read(qt_net* net, char* buf, size_t cap, size_t* needed);
 qt_status qt_contract_static(qt_net* net, int32_t precision, void* stream, double* amp_re,
                              double* amp_im);
 
+/* ---------------------------------------------------------------------------
+ * Batched energy: <C> = sum over edges of (1 - <Z_u Z_v>) / 2 for the same
+ * ansatz, every edge contracted as its own lightcone tensor network: the
+ * energy as a duplicated bra-ket expression (Sec. III.B) restricted to the
+ * backward lightcone of Z_u Z_v (Sec. III.A). Gates kept: the layer-k cost gate
+ * on (a, b) iff min(d(a), d(b)) <= p - k, the layer-k mixer on w iff
+ * d(w) <= p - k, |+> on d(w) <= p, with d the distance to {u, v}; ket and bra
+ * share each qubit's final index; Z = (1, -1) on the final indices of u and v.
+ * Each network is ordered greedily (rule `algo`) and compiled like an
+ * amplitude without slicing; all of them run in ONE persistent kernel launch
+ * (replayed from a captured CUDA graph) whose blocks take networks, largest
+ * first, from an atomic work counter.
+ * ------------------------------------------------------------------------- */
+typedef struct qt_energy qt_energy; /* opaque, owned by the library */
+
+/* Builds and orders every edge's lightcone network. edges/angles as in
+ * qt_build_network. Errors: QT_EINVAL (null pointer, n_vertices < 2, p < 1,
+ * no edge, bad edge, non-finite angle, unknown algo), QT_ENOMEM. */
+qt_status qt_energy_build(const int32_t* edges, int32_t n_vertices, int32_t n_edges, int32_t p,
+                          const double* gammas, const double* betas, int32_t algo,
+                          qt_energy** out);
+/* New angles, same structure (orders kept). A later qt_energy_upload is needed. */
+qt_status qt_energy_set_angles(qt_energy* e, const double* gammas, const double* betas);
+/* Compiles all networks for `precision` and returns the workspace size. */
+qt_status qt_energy_prepare(qt_energy* e, int32_t precision, size_t* workspace_bytes);
+/* Copies gates and step tables into the workspace (async on `stream`). */
+qt_status qt_energy_upload(qt_energy* e, void* workspace, size_t workspace_bytes, void* stream);
+/* Device-resident run: writes <Z_u Z_v> per edge (FP64, edge order of the
+ * input) to d_zz and the energy to d_energy (DEVICE pointers), async. */
+qt_status qt_energy_run(qt_energy* e, void* workspace, size_t workspace_bytes, void* stream,
+                        double* d_zz, double* d_energy);
+/* Times block sizes 32..256 of the persistent kernel on the uploaded networks and
+ * keeps the fastest (synchronises `stream`); threads_out may be NULL. */
+qt_status qt_energy_autotune(qt_energy* e, void* workspace, size_t workspace_bytes, void* stream,
+                             int32_t* threads_out);
+/* End to end: prepare (if needed), upload, run, copy zz (host, may be NULL) and
+ * the energy (host) back, synchronise `stream`. */
+qt_status qt_energy_compute(qt_energy* e, int32_t precision, void* workspace,
+                            size_t workspace_bytes, void* stream, double* zz_host,
+                            double* energy_host);
+/* One edge's network: greedy order (variable ids), variable count and width. */
+qt_status qt_energy_get_order(const qt_energy* e, int32_t edge, int32_t* order, int32_t cap,
+                              int32_t* len, int32_t* n_vars, int32_t* width);
+/* JSON: edges, steps, widths histogram, ledger flops/bytes, launch shape. */
+qt_status qt_energy_stats(const qt_energy* e, char* buf, size_t cap, size_t* needed);
+void qt_energy_free(qt_energy* e);
+
 /* Frees a network (NULL is a no-op). */
 void qt_free(qt_net* net);
 

@@ -19,7 +19,8 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libqtensor.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["api.cpp", "host_graph.cpp", "host_schedule.cpp", "engine.cu", "noalloc.cu"]
+SOURCES = ["api.cpp", "host_graph.cpp", "host_schedule.cpp", "engine.cu", "noalloc.cu",
+           "energy_host.cpp", "energy.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

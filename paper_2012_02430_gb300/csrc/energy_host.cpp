@@ -1,0 +1,208 @@
+// Host side of the batched energy: one lightcone tensor network per edge
+// (the energy as a duplicated bra-ket expression, Sec. III.B, restricted to the
+// backward lightcone of Z_u Z_v, Sec. III.A), each ordered greedily (Sec. V.A.1)
+// and compiled with the bucket-elimination schedule compiler (Alg. 1), then
+// packed into flat device tables for one persistent kernel launch.
+//
+// Lightcone reading: with d(w) the graph distance from w to {u, v}, the layer-k
+// cost gate on edge (a, b) stays iff min(d(a), d(b)) <= p - k, the layer-k
+// mixer on w stays iff d(w) <= p - k, and |+> stays on every w with d(w) <= p.
+// Qubit w with L(w) = max(0, p - d(w)) mixers has ket variables (w, 0..L-1),
+// bra variables likewise, and one final variable shared by ket and bra; the
+// observable is (1, -1) on the final variables of u and v; <Z_u Z_v> is
+// 2^(-|S|) times the contraction, S = {w : d(w) <= p}.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <string>
+#include <tuple>
+
+#include "energy_internal.h"
+
+namespace qt {
+
+static void lightcone(const qt_energy* E, int u, int v, std::vector<Tensor>& T, int& n_vars,
+                      double& norm) {
+  const int n = E->n, p = E->p;
+  // distances to {u, v}
+  std::vector<int> d(n, -1);
+  std::deque<int> q;
+  d[u] = d[v] = 0;
+  q.push_back(u);
+  q.push_back(v);
+  while (!q.empty()) {
+    int a = q.front();
+    q.pop_front();
+    for (int b : E->adj[a])
+      if (d[b] < 0) {
+        d[b] = d[a] + 1;
+        q.push_back(b);
+      }
+  }
+  std::vector<int> qubits;
+  for (int w = 0; w < n; ++w)
+    if (d[w] >= 0 && d[w] <= p) qubits.push_back(w);
+  std::vector<int> nmix(n, 0);
+  for (int w : qubits) nmix[w] = std::max(0, p - d[w]);
+  // variable ids in order of first use: kind 0 final, 1 ket, 2 bra
+  std::map<std::tuple<int, int, int>, int> ids;
+  auto var = [&](int kind, int w, int t) {
+    auto key = std::make_tuple(kind, w, t);
+    auto it = ids.find(key);
+    if (it != ids.end()) return it->second;
+    int id = (int)ids.size();
+    ids.emplace(key, id);
+    return id;
+  };
+  auto idx = [&](int side, int w, int t) {
+    return t >= nmix[w] ? var(0, w, 0) : var(side, w, t);
+  };
+  T.clear();
+  for (int side = 1; side <= 2; ++side) {
+    const double sgn = side == 1 ? 1.0 : -1.0;  // bra: complex conjugate
+    for (int w : qubits) T.push_back({{idx(side, w, 0)}, {1.0, 0.0, 1.0, 0.0}});
+    for (int k = 1; k <= p; ++k) {
+      const double g = E->gammas[k - 1], b = E->betas[k - 1];
+      const double er = std::cos(g), ei = -std::sin(g) * sgn;
+      const double c = std::cos(b), s = std::sin(b) * sgn;
+      for (size_t e = 0; e < E->edges.size() / 2; ++e) {
+        const int a = E->edges[2 * e], bb = E->edges[2 * e + 1];
+        if (d[a] >= 0 && d[bb] >= 0 && std::min(d[a], d[bb]) <= p - k)
+          T.push_back({{idx(side, a, k - 1), idx(side, bb, k - 1)},
+                       {1.0, 0.0, er, ei, er, ei, 1.0, 0.0}});
+      }
+      for (int w : qubits)
+        if (d[w] <= p - k)
+          T.push_back({{idx(side, w, k - 1), idx(side, w, k)}, {c, 0.0, 0.0, -s, 0.0, -s, c, 0.0}});
+    }
+  }
+  T.push_back({{var(0, u, 0)}, {1.0, 0.0, -1.0, 0.0}});
+  T.push_back({{var(0, v, 0)}, {1.0, 0.0, -1.0, 0.0}});
+  n_vars = (int)ids.size();
+  norm = std::ldexp(1.0, -(int)qubits.size());
+}
+
+bool energy_build_networks(qt_energy* E, std::string& err) {
+  const int ne = (int)E->edges.size() / 2;
+  E->nets.assign(ne, EnergyNet{});
+  for (int e = 0; e < ne; ++e) {
+    EnergyNet& N = E->nets[e];
+    lightcone(E, E->edges[2 * e], E->edges[2 * e + 1], N.tensors, N.n_vars, N.norm);
+    BitGraph g = line_graph(N.tensors, N.n_vars);
+    OrderResult o = greedy_order(g, E->algo);
+    N.plan = SlicePlan();
+    N.plan.order = o.order;
+    N.plan.widths = o.widths;
+    N.plan.width = 0;
+    for (int w : o.widths) N.plan.width = std::max(N.plan.width, w);
+  }
+  (void)err;
+  return true;
+}
+
+bool energy_compile(qt_energy* E, int precision, std::string& err) {
+  const int ne = (int)E->nets.size();
+  E->precision = precision;
+  E->elem_bytes = precision == QT_FP64 ? 16 : 8;
+  E->h_ops.clear();
+  E->h_steps.clear();
+  E->h_nets.assign(ne, ENet{});
+  E->h_scalars.clear();
+  E->gate_elems = 0;
+  E->arena_elems = 64;
+  E->total_flops = 0;
+  E->total_bytes = 0;
+  E->max_width = 0;
+  E->hist_width.assign(64, 0);
+  std::vector<int64_t> gate_base(ne, 0);
+  for (int e = 0; e < ne; ++e) {
+    EnergyNet& N = E->nets[e];
+    if (!compile_schedule(N.tensors, N.n_vars, N.plan, precision, 1, E->fuse, N.sched, err))
+      return false;
+    gate_base[e] = E->gate_elems;
+    E->gate_elems += N.sched.gate_elems;
+    E->arena_elems = std::max<int64_t>(E->arena_elems, N.sched.slice_elems);
+    E->max_width = std::max(E->max_width, N.plan.width);
+    E->hist_width[std::min(N.plan.width, 63)]++;
+  }
+  if (E->gate_elems >= (int64_t(1) << 31) || E->arena_elems >= (int64_t(1) << 31)) {
+    err = "energy tables exceed 2^31 elements";
+    return false;
+  }
+  // networks in descending cost for the work queue
+  std::vector<int> byc(ne);
+  for (int e = 0; e < ne; ++e) byc[e] = e;
+  auto cost = [&](int e) {
+    const Schedule& S = E->nets[e].sched;
+    return S.slice_flops + S.slice_bytes;
+  };
+  std::stable_sort(byc.begin(), byc.end(), [&](int a, int b) { return cost(a) > cost(b); });
+  for (int slot = 0; slot < ne; ++slot) {
+    const int e = byc[slot];
+    EnergyNet& N = E->nets[e];
+    const Schedule& S = N.sched;
+    ENet nd{};
+    nd.first_step = (uint32_t)E->h_steps.size();
+    nd.edge = (uint32_t)e;
+    nd.norm = N.norm;
+    for (const SGroup& g : S.groups) {
+      EStep sd{};
+      sd.m = (uint16_t)g.ops.size();
+      sd.u = (uint16_t)g.u;
+      sd.nsum = (uint16_t)g.nsum;
+      sd.first_op = (uint32_t)E->h_ops.size();
+      sd.out = (uint32_t)S.tensors[g.out].offset;
+      for (size_t j = 0; j < g.ops.size(); ++j) {
+        const STensor& t = S.tensors[g.ops[j]];
+        EOp od{};
+        unsigned int um = 0;
+        for (int b = 0; b < g.u; ++b)
+          if (std::find(t.labels.begin(), t.labels.end(), g.ulabels[b]) != t.labels.end())
+            um |= 1u << b;
+        od.umask = um;
+        od.level = (uint16_t)g.levels[j];
+        od.in_arena = t.kind == TK_GATE ? 0 : 1;
+        od.off = (uint32_t)(t.kind == TK_GATE ? gate_base[e] + t.offset : t.offset);
+        E->h_ops.push_back(od);
+      }
+      E->h_steps.push_back(sd);
+      if (g.u > 24) {
+        err = "a lightcone step exceeds rank 24";
+        return false;
+      }
+    }
+    nd.nsteps = (uint32_t)(E->h_steps.size() - nd.first_step);
+    nd.first_scalar = (uint32_t)E->h_scalars.size();
+    for (int32_t tid : S.scalars) E->h_scalars.push_back((uint32_t)S.tensors[tid].offset);
+    nd.nscalars = (uint32_t)(E->h_scalars.size() - nd.first_scalar);
+    E->h_nets[slot] = nd;
+    E->total_flops += S.slice_flops;
+    E->total_bytes += S.slice_launch_bytes;
+  }
+  // gate data in the precision, canonical layout per network
+  const size_t eb = (size_t)E->elem_bytes;
+  E->h_gates.assign((size_t)E->gate_elems * eb, 0);
+  for (int e = 0; e < ne; ++e) {
+    const Schedule& S = E->nets[e].sched;
+    for (const STensor& t : S.tensors) {
+      if (t.kind != TK_GATE) continue;
+      std::vector<double> dd = canonical_data(E->nets[e].tensors[t.gate], t.labels);
+      for (size_t k = 0; k < dd.size(); ++k) {
+        const size_t at = (size_t)(gate_base[e] + t.offset) * 2 + k;
+        if (precision == QT_FP64) {
+          double x = dd[k];
+          std::memcpy(E->h_gates.data() + at * sizeof(double), &x, sizeof(double));
+        } else {
+          float x = (float)dd[k];
+          std::memcpy(E->h_gates.data() + at * sizeof(float), &x, sizeof(float));
+        }
+      }
+    }
+  }
+  E->compiled = true;
+  return true;
+}
+
+}  // namespace qt

@@ -1,0 +1,72 @@
+// Internal structures of the batched lightcone energy.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "qt_internal.h"
+
+namespace qt {
+
+// one edge's lightcone network, its order and its compiled schedule
+struct EnergyNet {
+  std::vector<Tensor> tensors;
+  int n_vars = 0;
+  double norm = 1.0;  // 2^(-|S|)
+  SlicePlan plan;
+  Schedule sched;
+};
+
+// device tables (plain data, uploaded as is)
+struct EOp {
+  uint32_t off;       // element offset: in the gate region, or in the block's arena
+  uint32_t umask;     // U bits of the operand
+  uint16_t level;     // nested-sum level
+  uint16_t in_arena;  // 1: offset is in the block's arena
+};
+struct EStep {
+  uint16_t m, u, nsum, pad;
+  uint32_t first_op;  // index into the operand table
+  uint32_t out;       // arena offset of the result
+};
+struct ENet {
+  uint32_t first_step, nsteps, first_scalar, nscalars;
+  uint32_t edge, pad;
+  double norm;
+};
+
+}  // namespace qt
+
+struct qt_energy {
+  int32_t n = 0, p = 0, algo = 0;
+  std::vector<int32_t> edges;
+  std::vector<std::vector<int>> adj;
+  std::vector<double> gammas, betas;
+  std::vector<qt::EnergyNet> nets;
+  bool fuse = true;
+  bool compiled = false;
+  int precision = 0, elem_bytes = 8;
+  // packed tables
+  std::vector<qt::EOp> h_ops;
+  std::vector<qt::EStep> h_steps;
+  std::vector<qt::ENet> h_nets;
+  std::vector<uint32_t> h_scalars;
+  std::vector<unsigned char> h_gates;
+  int64_t gate_elems = 0, arena_elems = 0;
+  int64_t total_flops = 0, total_bytes = 0;
+  int max_width = 0;
+  std::vector<int> hist_width;
+  // launch shape (autotuned) and workspace layout
+  int block_threads = 128;
+  int blocks = 0;
+  size_t off_gates = 0, off_ops = 0, off_steps = 0, off_nets = 0, off_scalars = 0,
+         off_arenas = 0, off_zz = 0, off_counter = 0, total_bytes_ws = 0;
+  void* engine = nullptr;  // graph cache
+  ~qt_energy();
+};
+
+namespace qt {
+bool energy_build_networks(qt_energy* E, std::string& err);
+bool energy_compile(qt_energy* E, int precision, std::string& err);
+}  // namespace qt

@@ -60,6 +60,16 @@ _SIGS = {
     "qt_profile": [_vp, C.c_int32],
     "qt_contract_static": [_vp, C.c_int32, _vp, _f64p, _f64p],
     "qt_set_option": [_vp, C.c_int32, C.c_int64],
+    "qt_energy_build": [_i32p, C.c_int32, C.c_int32, C.c_int32, _f64p, _f64p, C.c_int32,
+                        C.POINTER(_vp)],
+    "qt_energy_set_angles": [_vp, _f64p, _f64p],
+    "qt_energy_prepare": [_vp, C.c_int32, C.POINTER(C.c_size_t)],
+    "qt_energy_upload": [_vp, _vp, C.c_size_t, _vp],
+    "qt_energy_run": [_vp, _vp, C.c_size_t, _vp, _vp, _vp],
+    "qt_energy_autotune": [_vp, _vp, C.c_size_t, _vp, _i32p],
+    "qt_energy_compute": [_vp, C.c_int32, _vp, C.c_size_t, _vp, _f64p, _f64p],
+    "qt_energy_get_order": [_vp, C.c_int32, _i32p, C.c_int32, _i32p, _i32p, _i32p],
+    "qt_energy_stats": [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)],
     "qt_autotune": [_vp, _vp, C.c_size_t, _vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)],
     "qt_profile_read": [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)],
 }
@@ -67,6 +77,8 @@ for _name, _args in _SIGS.items():
     _fn = getattr(lib, _name)
     _fn.argtypes = _args
     _fn.restype = C.c_int
+lib.qt_energy_free.argtypes = [_vp]
+lib.qt_energy_free.restype = None
 lib.qt_free.argtypes = [_vp]
 lib.qt_free.restype = None
 lib.qt_last_error.argtypes = []
@@ -219,6 +231,115 @@ def qt_free(net):
 
 def qt_version():
     return lib.qt_version().decode()
+
+
+def qt_energy_build(edges, n_vertices, p, gammas, betas, algo=QT_GREEDY_MINFILL):
+    flat = [int(x) for e in edges for x in e]
+    out = _vp()
+    _check(lib.qt_energy_build(_arr(C.c_int32, flat), int(n_vertices), len(edges), int(p),
+                               _arr(C.c_double, gammas), _arr(C.c_double, betas), int(algo),
+                               C.byref(out)))
+    return out
+
+
+def qt_energy_set_angles(h, gammas, betas):
+    _check(lib.qt_energy_set_angles(h, _arr(C.c_double, gammas), _arr(C.c_double, betas)))
+
+
+def qt_energy_prepare(h, precision=QT_FP32_SIMT):
+    n = C.c_size_t()
+    _check(lib.qt_energy_prepare(h, int(precision), C.byref(n)))
+    return n.value
+
+
+def qt_energy_upload(h, workspace_ptr, workspace_bytes, stream_ptr):
+    _check(lib.qt_energy_upload(h, _vp(workspace_ptr), int(workspace_bytes), _vp(stream_ptr)))
+
+
+def qt_energy_run(h, workspace_ptr, workspace_bytes, stream_ptr, d_zz_ptr, d_energy_ptr):
+    _check(lib.qt_energy_run(h, _vp(workspace_ptr), int(workspace_bytes), _vp(stream_ptr),
+                             _vp(d_zz_ptr), _vp(d_energy_ptr)))
+
+
+def qt_energy_autotune(h, workspace_ptr, workspace_bytes, stream_ptr):
+    t = C.c_int32()
+    _check(lib.qt_energy_autotune(h, _vp(workspace_ptr), int(workspace_bytes), _vp(stream_ptr),
+                                  C.byref(t)))
+    return t.value
+
+
+def qt_energy_compute(h, precision, workspace_ptr, workspace_bytes, stream_ptr, n_edges):
+    zz = (C.c_double * max(1, n_edges))()
+    en = C.c_double()
+    _check(lib.qt_energy_compute(h, int(precision), _vp(workspace_ptr), int(workspace_bytes),
+                                 _vp(stream_ptr), zz, C.byref(en)))
+    return en.value, list(zz[:n_edges])
+
+
+def qt_energy_get_order(h, edge):
+    n, nv, w = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib.qt_energy_get_order(h, int(edge), None, 0, C.byref(n), C.byref(nv), C.byref(w)))
+    buf = (C.c_int32 * max(1, n.value))()
+    _check(lib.qt_energy_get_order(h, int(edge), buf, n.value, C.byref(n), C.byref(nv), C.byref(w)))
+    return list(buf[: n.value]), nv.value, w.value
+
+
+def qt_energy_stats(h):
+    n = C.c_size_t()
+    _check(lib.qt_energy_stats(h, None, 0, C.byref(n)))
+    buf = C.create_string_buffer(n.value)
+    _check(lib.qt_energy_stats(h, buf, n.value, C.byref(n)))
+    return json.loads(buf.value.decode())
+
+
+def qt_energy_free(h):
+    lib.qt_energy_free(h)
+
+
+class Energy:
+    """Owns a qt_energy handle and a torch-allocated workspace."""
+
+    def __init__(self, edges, n_vertices, p, gammas, betas, algo=QT_GREEDY_MINFILL):
+        self.n_edges = len(edges)
+        self.handle = qt_energy_build(edges, n_vertices, p, gammas, betas, algo)
+        self.workspace = None
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            qt_energy_free(h)
+            self.handle = None
+
+    def _stream(self):
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+
+    def prepare(self, precision=QT_FP32_SIMT, device="cuda"):
+        import torch
+        need = qt_energy_prepare(self.handle, precision)
+        if self.workspace is None or self.workspace.numel() < need:
+            self.workspace = None
+            self.workspace = torch.empty(need, dtype=torch.uint8, device=device)
+        return need
+
+    def upload(self):
+        qt_energy_upload(self.handle, self.workspace.data_ptr(), self.workspace.numel(),
+                         self._stream())
+
+    def autotune(self):
+        return qt_energy_autotune(self.handle, self.workspace.data_ptr(), self.workspace.numel(),
+                                  self._stream())
+
+    def run(self, zz, energy):
+        qt_energy_run(self.handle, self.workspace.data_ptr(), self.workspace.numel(),
+                      self._stream(), zz.data_ptr(), energy.data_ptr())
+
+    def compute(self, precision=QT_FP32_SIMT):
+        return qt_energy_compute(self.handle, precision, self.workspace.data_ptr(),
+                                 self.workspace.numel(), self._stream(), self.n_edges)
+
+    def stats(self):
+        return qt_energy_stats(self.handle)
 
 
 # ------------------------ convenience wrapper (torch) ------------------------

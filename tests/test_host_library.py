@@ -205,3 +205,44 @@ def test_set_angles_keeps_plan(qt):
         qt.qt_stats(h)  # schedule still valid
     finally:
         qt.qt_free(h)
+
+
+@pytest.mark.parametrize("n,p,seed,algo", [(16, 1, 3, 0), (16, 2, 3, 1), (12, 3, 5, 0),
+                                           (40, 2, 9, 0)])
+def test_energy_lightcone_orders_bit_exact(qt, n, p, seed, algo):
+    """Every edge's lightcone network: variable count, greedy order and width equal the
+    oracle's (same gate set, same variable numbering, same greedy rule)."""
+    from oracle import energy, network, ordering
+    from paper_2012_02430_gb300.inputs import qaoa_instance
+    edges, g, b, z = qaoa_instance(n, p, seed)
+    h = qt.qt_energy_build(edges, n, p, g, b, algo)
+    try:
+        for e, (u, v) in enumerate(edges):
+            tensors, nv, norm = energy.lightcone_network(n, edges, p, g, b, u, v)
+            adj = ordering.adjacency_matrix(network.line_graph(tensors, nv), nv)
+            o, w = ordering.greedy_order(adj, None, {0: ordering.MIN_FILL, 1: ordering.MIN_DEGREE}[algo])
+            assert qt.qt_energy_get_order(h, e) == (o, nv, max(w)), e
+        qt.qt_energy_prepare(h, 0)
+        st = qt.qt_energy_stats(h)
+        assert st["edges"] == len(edges) and st["workspace_bytes"] > 0
+    finally:
+        qt.qt_energy_free(h)
+
+
+def test_energy_errors(qt):
+    with pytest.raises(qt.QtError) as e:
+        qt.qt_energy_build([(0, 1), (1, 1)], 3, 1, [0.1], [0.2])
+    assert e.value.status == qt.QT_EINVAL
+    with pytest.raises(qt.QtError) as e:
+        qt.qt_energy_build([(0, 1)], 2, 1, [0.1], [0.2], 5)
+    assert e.value.status == qt.QT_EINVAL
+    h = qt.qt_energy_build([(0, 1), (1, 2)], 3, 1, [0.1], [0.2])
+    try:
+        with pytest.raises(qt.QtError) as e:
+            qt.qt_energy_stats(h)
+        assert e.value.status == qt.QT_ESTATE
+        with pytest.raises(qt.QtError) as e:
+            qt.qt_energy_get_order(h, 7)
+        assert e.value.status == qt.QT_EINVAL
+    finally:
+        qt.qt_energy_free(h)
