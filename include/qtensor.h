@@ -179,6 +179,76 @@ qt_status qt_run(qt_net* net, int64_t first, int64_t count, void* workspace, siz
 qt_status qt_contract(qt_net* net, int32_t precision, void* workspace, size_t workspace_bytes,
                       void* stream, double* amp_re, double* amp_im);
 
+/* Plan bookkeeping: greedy ordering runs made by the last qt_order/qt_slice/
+ * qt_slice_learned and the plan's cost sum over its steps of 2^width. */
+qt_status qt_plan_info(const qt_net* net, int64_t* greedy_runs, double* plan_cost);
+
+/* ---------------------------------------------------------------------------
+ * Learned proposals for the slicing search (not in the paper: the search of
+ * Sec. VI.C-D re-orders the graph once per candidate step, Fig. 8). A candidate
+ * is (s, v): the step s of the current greedy order (s up to its first peak)
+ * and the first vertex v sliced there, v among the `topv` vertices of largest
+ * degree at step s (topv = 1 is the paper's max-degree rule; further vertices
+ * of a round with r > 1 are still taken by largest degree). Each candidate has
+ * QT_PROPOSAL_FEATURES features read off the graph at step s with no ordering
+ * run (positions, widths, degrees, fill-in and density, normalised by the
+ * current width). A 2-hidden-layer ReLU MLP scores them; only the `topm`
+ * best-scored candidates are ordered greedily and the best verified plan by
+ * (width, sum of 2^w, s, rank) is kept, so greedy stays the judge.
+ * ------------------------------------------------------------------------- */
+enum { QT_PROPOSAL_FEATURES = 16 };
+
+/* Training data from the network's first slicing round (a network ordered with
+ * qt_order): every candidate's features [count][QT_PROPOSAL_FEATURES], its label
+ * (the plan width after slicing it, divided by the current width) and meta
+ * [count][3] = (s, v, width). Writes at most cap rows; *count gets the total.
+ * Each candidate costs one greedy ordering run. */
+qt_status qt_slice_dataset(const qt_net* net, int32_t topv, float* features, float* labels,
+                           int32_t* meta, int32_t cap, int32_t* count);
+
+/* Slicing with learned proposals. Per round the verified (greedily ordered)
+ * candidates are: the `topm` best MLP scores (params: the MLP's parameters as
+ * laid out by the qt_mlp_* calls, `hidden` units; picked steps kept apart while
+ * enough candidates remain), plus `spread` candidates evenly spaced in
+ * (s, rank) order. NULL params: the spread set alone (the budget the model is
+ * compared with); spread >= the number of candidates verifies every candidate
+ * (a full scan over (s, v); with topv = 1 this is exactly qt_slice). Sets the
+ * network's plan like qt_slice. Errors as qt_slice, and QT_EINVAL for topv < 1,
+ * topm < 0, spread < 0, an empty verified set, or hidden out of [1, 1024]. */
+qt_status qt_slice_learned(qt_net* net, const float* params, int32_t hidden, int32_t width_limit,
+                           int32_t max_vars, int32_t r, int32_t topv, int32_t topm, int32_t spread,
+                           int32_t* k_out, int32_t* width_out);
+
+/* The MLP's forward pass on the host, as qt_slice_learned uses it: x [batch][F]
+ * -> y [batch]. Parameters: W1[H][F], b1[H], W2[H][H], b2[H], w3[H], b3. */
+qt_status qt_mlp_forward_host(const float* params, int32_t n_features, int32_t hidden,
+                              const float* x, int32_t batch, float* y);
+
+/* GPU training of the MLP (mean-squared error, Adam with beta1 0.9, beta2 0.999,
+ * eps 1e-8). The handle holds sizes and the Adam step count; parameters,
+ * moments, activations and gradients live in a caller workspace
+ * (qt_mlp_workspace_size). Device pointers: d_x [batch][F], d_t/d_y [batch],
+ * d_grad [n_params], d_loss [1]. Reductions run in a fixed order (reproducible).
+ * Errors: QT_EINVAL (null pointer, batch outside [1, max_batch], lr <= 0),
+ * QT_ENOMEM (workspace too small), QT_ECUDA. */
+typedef struct qt_mlp qt_mlp;
+qt_status qt_mlp_create(int32_t n_features, int32_t hidden, int32_t max_batch, qt_mlp** out);
+qt_status qt_mlp_workspace_size(const qt_mlp* mlp, size_t* bytes, int32_t* n_params);
+/* host parameters in; resets the Adam moments and step (synchronises) */
+qt_status qt_mlp_set_params(qt_mlp* mlp, void* workspace, size_t bytes, const float* params,
+                            void* stream);
+qt_status qt_mlp_get_params(const qt_mlp* mlp, void* workspace, size_t bytes, float* params,
+                            void* stream);
+qt_status qt_mlp_forward(qt_mlp* mlp, void* workspace, size_t bytes, const float* d_x,
+                         int32_t batch, float* d_y, void* stream);
+qt_status qt_mlp_gradients(qt_mlp* mlp, void* workspace, size_t bytes, const float* d_x,
+                           const float* d_t, int32_t batch, float* d_grad, float* d_loss,
+                           void* stream);
+qt_status qt_mlp_train_step(qt_mlp* mlp, void* workspace, size_t bytes, const float* d_x,
+                            const float* d_t, int32_t batch, float lr, float* d_loss,
+                            void* stream);
+void qt_mlp_free(qt_mlp* mlp);
+
 /* Options of a network (qt_set_option):
  *   QT_OPT_FUSION  1 (default): consecutive bucket steps whose summed indices
  *                  die together run as one launch that sums several indices,

@@ -69,6 +69,11 @@ bool check_net(const qt_net* net) { return net != nullptr; }
 
 namespace qt {
 void set_last_error(const std::string& msg) { g_err = msg; }
+bool slice_dataset(const qt_net* net, int topv, std::vector<float>& feats,
+                   std::vector<float>& labels, std::vector<int32_t>& meta);
+SlicePlan learned_slicing(const qt_net* net, const float* params, int hidden, int width_limit,
+                          int max_vars, int r, int topv, int topm, int spread,
+                          int64_t& greedy_runs);
 }  // namespace qt
 
 extern "C" {
@@ -363,6 +368,69 @@ qt_status qt_profile_read(qt_net* net, char* buf, size_t cap, size_t* needed) {
     std::memcpy(buf, out.data(), n);
     buf[n] = '\0';
   }
+  return ok();
+}
+
+qt_status qt_plan_info(const qt_net* net, int64_t* greedy_runs, double* plan_cost) {
+  if (!check_net(net)) return fail(QT_EINVAL, "qt_plan_info: null network");
+  if (!net->ordered) return fail(QT_ESTATE, "qt_plan_info: call qt_order first");
+  if (greedy_runs) *greedy_runs = net->plan.greedy_runs;
+  if (plan_cost) {
+    double c = 0.0;
+    for (int32_t w : net->plan.widths) c += std::ldexp(1.0, w);
+    *plan_cost = c;
+  }
+  return ok();
+}
+
+qt_status qt_slice_dataset(const qt_net* net, int32_t topv, float* features, float* labels,
+                           int32_t* meta, int32_t cap, int32_t* count) {
+  if (!check_net(net) || !count) return fail(QT_EINVAL, "qt_slice_dataset: null argument");
+  if (!net->ordered) return fail(QT_ESTATE, "qt_slice_dataset: call qt_order first");
+  if (topv < 1) return fail(QT_EINVAL, "qt_slice_dataset: topv must be >= 1");
+  std::vector<float> f, l;
+  std::vector<int32_t> m;
+  try {
+    qt::slice_dataset(net, topv, f, l, m);
+  } catch (const std::bad_alloc&) {
+    return fail(QT_ENOMEM, "qt_slice_dataset: out of host memory");
+  }
+  *count = (int32_t)l.size();
+  const int32_t n = std::min<int32_t>(cap, (int32_t)l.size());
+  if (features && n > 0) std::memcpy(features, f.data(), sizeof(float) * n * qt::kProposalFeatures);
+  if (labels && n > 0) std::memcpy(labels, l.data(), sizeof(float) * n);
+  if (meta && n > 0) std::memcpy(meta, m.data(), sizeof(int32_t) * n * 3);
+  return ok();
+}
+
+qt_status qt_slice_learned(qt_net* net, const float* params, int32_t hidden, int32_t width_limit,
+                           int32_t max_vars, int32_t r, int32_t topv, int32_t topm, int32_t spread,
+                           int32_t* k_out, int32_t* width_out) {
+  if (!check_net(net)) return fail(QT_EINVAL, "qt_slice_learned: null network");
+  if (!net->ordered) return fail(QT_ESTATE, "qt_slice_learned: call qt_order first");
+  if (width_limit < 1 || r < 1 || max_vars < 0 || max_vars > 30 || topv < 1 || topm < 0 ||
+      spread < 0 || (!params && spread < 1) ||
+      (params && (hidden < 1 || hidden > 1024)))
+    return fail(QT_EINVAL, "qt_slice_learned: argument out of range");
+  try {
+    int64_t runs = 0;
+    net->plan =
+        qt::learned_slicing(net, params, hidden, width_limit, max_vars, r, topv, topm, spread, runs);
+    net->sched = qt::Schedule();
+    net->stage_dirty = true;
+    if (k_out) *k_out = (int32_t)net->plan.sliced.size();
+    if (width_out) *width_out = net->plan.width;
+  } catch (const std::bad_alloc&) {
+    return fail(QT_ENOMEM, "qt_slice_learned: out of host memory");
+  }
+  return ok();
+}
+
+qt_status qt_mlp_forward_host(const float* params, int32_t n_features, int32_t hidden,
+                              const float* x, int32_t batch, float* y) {
+  if (!params || !x || !y || n_features < 1 || hidden < 1 || batch < 0)
+    return fail(QT_EINVAL, "qt_mlp_forward_host: bad argument");
+  qt::mlp_forward_host(params, n_features, hidden, x, batch, y);
   return ok();
 }
 

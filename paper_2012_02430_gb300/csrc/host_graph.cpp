@@ -176,6 +176,7 @@ SlicePlan step_dependent_slicing(const BitGraph& g0, int algo, int width_limit, 
                                  int r) {
   BitGraph g = g0;
   OrderResult cur = greedy_order(g, algo);
+  int64_t runs = 1;
   std::vector<int32_t> done_order, done_widths, sliced;
   int32_t first_step = -1;
   auto maxw = [](const std::vector<int32_t>& v, int32_t init) {
@@ -220,6 +221,7 @@ SlicePlan step_dependent_slicing(const BitGraph& g0, int algo, int width_limit, 
         removed.push_back(bestv);
       }
       OrderResult o2 = greedy_order(b, algo);
+      ++runs;
       int32_t w = std::max(std::max(done_max, prefix_max), maxw(o2.widths, 0));
       double cost = plan_cost(done_widths, cur.widths, s, o2.widths);
       bool better = !have || w < best_w || (w == best_w && cost < best_cost);
@@ -252,6 +254,7 @@ SlicePlan step_dependent_slicing(const BitGraph& g0, int algo, int width_limit, 
   plan.sliced = sliced;
   plan.slice_step = first_step < 0 ? 0 : first_step;
   plan.width = maxw(plan.widths, 0);
+  plan.greedy_runs = runs;
   return plan;
 }
 

@@ -52,6 +52,7 @@ struct SlicePlan {
   std::vector<int32_t> sliced;  // sliced vertices, slice-bit order
   int32_t slice_step = 0;       // first round's step s_1 (0 without slicing)
   int32_t width = 0;
+  int64_t greedy_runs = 0;      // ordering runs the search made
 };
 
 SlicePlan step_dependent_slicing(const BitGraph& g, int algo, int width_limit, int max_vars,
@@ -154,6 +155,11 @@ struct ProfRec {
   void* ev0;
   void* ev1;
 };
+
+// learned proposals (learn.cpp)
+constexpr int kProposalFeatures = 16;
+int mlp_param_count(int nf, int hidden);
+void mlp_forward_host(const float* params, int nf, int hidden, const float* x, int batch, float* y);
 
 }  // namespace qt
 

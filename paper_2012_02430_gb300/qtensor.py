@@ -20,6 +20,7 @@ QT_OK, QT_EINVAL, QT_ENOMEM, QT_ECUDA, QT_ETIMEOUT, QT_ESTATE, QT_ERANGE = range
 QT_GREEDY_MINFILL, QT_GREEDY_MINDEG = 0, 1
 QT_FP32_SIMT, QT_FP64 = 0, 4
 QT_OPT_FUSION, QT_OPT_GRAPHS = 1, 2
+QT_PROPOSAL_FEATURES = 16
 
 STATUS_NAMES = {0: "QT_OK", 1: "QT_EINVAL", 2: "QT_ENOMEM", 3: "QT_ECUDA",
                 4: "QT_ETIMEOUT", 5: "QT_ESTATE", 6: "QT_ERANGE"}
@@ -60,6 +61,20 @@ _SIGS = {
     "qt_profile": [_vp, C.c_int32],
     "qt_contract_static": [_vp, C.c_int32, _vp, _f64p, _f64p],
     "qt_set_option": [_vp, C.c_int32, C.c_int64],
+    "qt_plan_info": [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_double)],
+    "qt_slice_dataset": [_vp, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float), _i32p,
+                         C.c_int32, _i32p],
+    "qt_slice_learned": [_vp, C.POINTER(C.c_float), C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                         C.c_int32, C.c_int32, C.c_int32, _i32p, _i32p],
+    "qt_mlp_forward_host": [C.POINTER(C.c_float), C.c_int32, C.c_int32, C.POINTER(C.c_float),
+                            C.c_int32, C.POINTER(C.c_float)],
+    "qt_mlp_create": [C.c_int32, C.c_int32, C.c_int32, C.POINTER(_vp)],
+    "qt_mlp_workspace_size": [_vp, C.POINTER(C.c_size_t), _i32p],
+    "qt_mlp_set_params": [_vp, _vp, C.c_size_t, C.POINTER(C.c_float), _vp],
+    "qt_mlp_get_params": [_vp, _vp, C.c_size_t, C.POINTER(C.c_float), _vp],
+    "qt_mlp_forward": [_vp, _vp, C.c_size_t, _vp, C.c_int32, _vp, _vp],
+    "qt_mlp_gradients": [_vp, _vp, C.c_size_t, _vp, _vp, C.c_int32, _vp, _vp, _vp],
+    "qt_mlp_train_step": [_vp, _vp, C.c_size_t, _vp, _vp, C.c_int32, C.c_float, _vp, _vp],
     "qt_energy_build": [_i32p, C.c_int32, C.c_int32, C.c_int32, _f64p, _f64p, C.c_int32,
                         C.POINTER(_vp)],
     "qt_energy_set_angles": [_vp, _f64p, _f64p],
@@ -77,6 +92,8 @@ for _name, _args in _SIGS.items():
     _fn = getattr(lib, _name)
     _fn.argtypes = _args
     _fn.restype = C.c_int
+lib.qt_mlp_free.argtypes = [_vp]
+lib.qt_mlp_free.restype = None
 lib.qt_energy_free.argtypes = [_vp]
 lib.qt_energy_free.restype = None
 lib.qt_free.argtypes = [_vp]

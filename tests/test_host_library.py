@@ -246,3 +246,60 @@ def test_energy_errors(qt):
         assert e.value.status == qt.QT_EINVAL
     finally:
         qt.qt_energy_free(h)
+
+
+@pytest.mark.parametrize("n,p,seed", [(20, 2, 3), (40, 2, 9), (30, 3, 4)])
+def test_proposal_dataset_matches_oracle(qt, n, p, seed):
+    """Features (float tolerance), labels and (s, v, width) bit-exact against the oracle."""
+    import numpy as np
+    from oracle import proposal
+    from paper_2012_02430_gb300 import learn
+    edges, gammas, betas, z, tensors, nv, norm, adj = oracle_problem(n, p, seed)
+    X, Y, M = learn.dataset_of(edges, n, p, gammas, betas, z, topv=3)
+    F, L, meta = proposal.dataset(adj, 0, 3)
+    assert X.shape == F.shape
+    assert np.max(np.abs(X - F)) <= 1e-6
+    assert [tuple(r) for r in M] == [tuple(r) for r in meta]
+    assert np.max(np.abs(Y - L)) <= 1e-6
+
+
+@pytest.mark.parametrize("case", [(12, 3, 3, 8, 4, 1), (24, 3, 15, 14, 6, 2), (40, 2, 9, 11, 4, 1)])
+def test_learned_search_without_model_is_the_papers(qt, case):
+    """qt_slice_learned with no model, topv = 1 and an unlimited spread is qt_slice's search."""
+    import ctypes as C
+    n, p, seed, lim, mv, r = case
+    edges, gammas, betas, z, tensors, nv, norm, adj = oracle_problem(n, p, seed)
+    plan = oracle_plan(adj, 0, lim, mv, r)
+    h = qt.qt_build_network(edges, n, p, gammas, betas, z)
+    try:
+        qt.qt_order(h, 0)
+        k, w = C.c_int32(), C.c_int32()
+        qt._check(qt.lib.qt_slice_learned(h, None, 64, lim, mv, r, 1, 0, 1 << 30, C.byref(k),
+                                          C.byref(w)))
+        assert qt.qt_get_slices(h) == (plan["sliced"], plan["slice_step"])
+        assert qt.qt_get_order(h) == plan["order"] and w.value == plan["width"]
+        runs = C.c_int64()
+        qt._check(qt.lib.qt_plan_info(h, C.byref(runs), None))
+        qt.qt_order(h, 0)
+        qt.qt_slice(h, lim, mv, r)
+        runs2 = C.c_int64()
+        qt._check(qt.lib.qt_plan_info(h, C.byref(runs2), None))
+        assert runs.value == runs2.value
+    finally:
+        qt.qt_free(h)
+
+
+def test_mlp_forward_host_matches_oracle(qt):
+    import ctypes as C
+    import numpy as np
+    from oracle import mlp
+    nf, hidden, batch = 16, 24, 11
+    rng = np.random.default_rng(7)
+    p = rng.normal(0, 0.4, mlp.n_params(nf, hidden)).astype(np.float32)
+    x = rng.normal(0, 1, (batch, nf)).astype(np.float32)
+    y = np.zeros(batch, dtype=np.float32)
+    fp = C.POINTER(C.c_float)
+    qt._check(qt.lib.qt_mlp_forward_host(p.ctypes.data_as(fp), nf, hidden, x.ctypes.data_as(fp),
+                                         batch, y.ctypes.data_as(fp)))
+    ref, _ = mlp.forward(p.astype(np.float64), x.astype(np.float64), nf, hidden)
+    assert np.max(np.abs(y - ref)) <= 1e-5 * max(1.0, np.max(np.abs(ref)))

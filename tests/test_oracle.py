@@ -312,3 +312,52 @@ def test_p1_closed_form_on_3_regular():
     edges, g, b, z = qaoa_instance(n, 1, 9)
     e = sum(energy.edge_energy_p1_closed_form(n, edges, g[0], b[0], u, v) for u, v in edges)
     assert abs(e - statevector.maxcut_energy(n, edges, g, b)) < 1e-11
+
+
+# ----------------------------- proposal MLP ----------------------------------
+
+def _mlp_case(nf=5, hidden=7, batch=9, seed=4):
+    from oracle import mlp
+    rng = np.random.default_rng(seed)
+    p = rng.normal(0, 0.6, mlp.n_params(nf, hidden))
+    x = rng.normal(0, 1, (batch, nf))
+    t = rng.normal(0, 1, batch)
+    return p, x, t
+
+
+def test_mlp_gradients_match_finite_differences():
+    """The oracle's chain-rule gradients against central differences of its loss (FP64)."""
+    from oracle import mlp
+    nf, hidden = 5, 7
+    p, x, t = _mlp_case(nf, hidden)
+    g = mlp.gradients(p, x, t, nf, hidden)
+    h = 1e-6
+    fd = np.zeros_like(p)
+    for i in range(len(p)):
+        e = np.zeros_like(p)
+        e[i] = h
+        fd[i] = (mlp.loss(p + e, x, t, nf, hidden) - mlp.loss(p - e, x, t, nf, hidden)) / (2 * h)
+    assert np.max(np.abs(fd - g)) <= 1e-7 * max(1.0, np.max(np.abs(g)))
+
+
+def test_adam_first_step_is_signed_lr():
+    """Adam's first step (bias-corrected m = g, v = g^2) moves each parameter by lr*sign(g)."""
+    from oracle import mlp
+    p = np.array([0.5, -1.0, 2.0])
+    g = np.array([0.3, -2.0, 1e-3])
+    p1, m, v = mlp.adam_step(p, g, np.zeros(3), np.zeros(3), 1, lr=0.01)
+    assert np.allclose(p1, p - 0.01 * np.sign(g), atol=1e-7)
+
+
+def test_proposal_candidate_counts():
+    """One candidate per (step up to the first peak, top-degree vertex); labels never exceed 1
+    by more than the prefix allows and the paper's max-degree candidate is rank 0."""
+    from oracle import proposal
+    edges, g, b, z, t, nv, norm, adj = problem(20, 2, 3)
+    order, widths = ordering.greedy_order(adj)
+    peak = int(np.argmax(widths))
+    cands = proposal.round_candidates(adj, order, widths, nv, 3)
+    assert len(cands) == 3 * (peak + 1)
+    assert all(c[2] == i % 3 for i, c in enumerate(cands))
+    F, L, M = proposal.dataset(adj, ordering.MIN_FILL, 3)
+    assert F.shape == (3 * (peak + 1), 16) and np.all(L > 0) and np.all(L <= 1.0 + 1e-12)
