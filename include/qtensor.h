@@ -54,8 +54,19 @@ enum {
 /* Arithmetic of the bucket steps. Slice accumulation is FP64 in every mode. */
 enum {
   QT_FP32_SIMT = 0, /* complex64 tensors, FP32 CUDA-core arithmetic */
+  QT_TF32 = 1,      /* complex64; GEMM-form launches on the tensor cores in TF32 */
+  QT_BF16 = 2,      /* complex64; GEMM-form launches in BF16 with FP32 accumulation */
+  QT_3XTF32 = 3,    /* complex64; GEMM-form launches in split TF32 (hi*hi+hi*lo+lo*hi) */
   QT_FP64 = 4       /* complex128 tensors, FP64 CUDA-core arithmetic */
 };
+/* A launch is in GEMM form when its two largest tensors A, B hold every index of
+ * its union and every other tensor's indices lie inside A or inside B; then it
+ * is out[bt][m][n] = sum_k A'[bt][m][k] B'[bt][n][k] (k summed indices of both,
+ * m/n output indices of A/B only, bt of both; A' = A times the tensors folded
+ * into it, summed over indices only A sums), computed by pack kernels (planar
+ * re/im) and a batched complex GEMM: on the tensor cores (mma.sync m16n8k8 TF32,
+ * m16n8k16 BF16) in the TF32/BF16/3XTF32 modes when it has at least one full
+ * 16 x 8 tile, else on CUDA cores in FP32. Other launches use the FP32 kernels. */
 
 /*
  * Builds the tensor network of <z| U(gamma, beta) |+>^N (Sec. III.A; Sec. IV.A,
@@ -259,8 +270,11 @@ void qt_mlp_free(qt_mlp* mlp);
  *   QT_OPT_GRAPHS  1 (default): qt_run captures its launches once per
  *                  (slice range, workspace, output) and replays the CUDA
  *                  graph; 0: direct launches.
+ *   QT_OPT_GEMM    1: launches in GEMM form also use it in QT_FP32_SIMT mode
+ *                  (CUDA-core GEMM); 0 (default): there only the autotuner may
+ *                  pick it. Discards the prepared schedule.
  * Errors: QT_EINVAL for a null network or an unknown option. */
-enum { QT_OPT_FUSION = 1, QT_OPT_GRAPHS = 2 };
+enum { QT_OPT_FUSION = 1, QT_OPT_GRAPHS = 2, QT_OPT_GEMM = 3 };
 qt_status qt_set_option(qt_net* net, int32_t option, int64_t value);
 
 /*

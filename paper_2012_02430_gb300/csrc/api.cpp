@@ -244,7 +244,7 @@ qt_status qt_get_tensor(const qt_net* net, int32_t t, int32_t* labels, int32_t* 
 qt_status qt_prepare(qt_net* net, int32_t precision, int32_t batch, size_t* workspace_bytes) {
   if (!check_net(net)) return fail(QT_EINVAL, "qt_prepare: null network");
   if (!net->ordered) return fail(QT_ESTATE, "qt_prepare: call qt_order first");
-  if (precision != QT_FP32_SIMT && precision != QT_FP64)
+  if (precision < QT_FP32_SIMT || precision > QT_FP64)
     return fail(QT_EINVAL, "qt_prepare: unknown precision");
   if (batch < 1) return fail(QT_EINVAL, "qt_prepare: batch must be >= 1");
   std::string err;
@@ -255,6 +255,7 @@ qt_status qt_prepare(qt_net* net, int32_t precision, int32_t batch, size_t* work
       return fail(err.find("rank") != std::string::npos ? QT_ERANGE : QT_EINVAL,
                   "qt_prepare: " + err);
     }
+    net->sched.force_gemm = net->force_gemm;
   } catch (const std::bad_alloc&) {
     net->sched = qt::Schedule();
     return fail(QT_ENOMEM, "qt_prepare: out of host memory");
@@ -443,6 +444,10 @@ qt_status qt_set_option(qt_net* net, int32_t option, int64_t value) {
       break;
     case QT_OPT_GRAPHS:
       net->graphs = value != 0;
+      break;
+    case QT_OPT_GEMM:
+      net->force_gemm = value != 0;
+      net->sched = qt::Schedule();  // prepare again
       break;
     default:
       return fail(QT_EINVAL, "qt_set_option: unknown option");

@@ -26,6 +26,7 @@
 #include <cstring>
 #include <string>
 
+#include "gemm.h"
 #include "qt_internal.h"
 
 namespace qt {
@@ -780,12 +781,67 @@ static void fill_op(const Schedule& S, const SGroup& g, int j, KOp& o) {
 // the kernel chosen for it and the grid.
 struct LaunchDesc {
   KStep k;
+  GemmArgs ga;  // kind 3
   int group;    // schedule launch group
-  int kind;     // 0 flat, 1 tiled
-  int variant;  // tiled kernel variant
+  int kind;     // 0 flat, 1 tiled, 3 GEMM form (pack A', pack B', GEMM)
+  int variant;  // 0..2 tiled kernel variants, 3 GEMM form
+  int gemm_mode;
   unsigned grid;
   int64_t bytes, flops;  // ledger counts per slice
 };
+
+constexpr int VARIANT_GEMM = 3;
+
+// GEMM flavour of a GEMM-form launch in a precision mode
+static int gemm_mode_for(const Schedule& S, const SGroup& g) {
+  const int mb = __builtin_popcount(g.mM), nb = __builtin_popcount(g.mN);
+  const bool tc_shape = mb >= 4 && nb >= 3;  // at least one full 16 x 8 tile
+  switch (S.precision) {
+    case QT_TF32: return tc_shape ? GEMM_TC_TF32 : GEMM_SIMT;
+    case QT_BF16: return tc_shape ? GEMM_TC_BF16 : GEMM_SIMT;
+    case QT_3XTF32: return tc_shape ? GEMM_TC_3XTF32 : GEMM_SIMT;
+    default: return GEMM_SIMT;
+  }
+}
+
+static bool tc_precision(int p) { return p == QT_TF32 || p == QT_BF16 || p == QT_3XTF32; }
+
+static void fill_gemm(const Schedule& S, const SGroup& g, long long nslices, GemmArgs& a) {
+  a = GemmArgs{};
+  a.m = (int)g.ops.size();
+  a.nsum = g.nsum;
+  a.mK = g.mK;
+  a.mSA = g.mSA;
+  a.mSB = g.mSB;
+  a.mM = g.mM;
+  a.mN = g.mN;
+  a.mBt = g.mBt;
+  a.nslices = nslices;
+  const STensor& out = S.tensors[g.out];
+  const long long eb = S.elem_bytes;
+  const bool per_slice = out.kind == TK_SLICE;
+  const long long region = (long long)(per_slice ? S.off_slices : S.off_prefix) / eb;
+  a.out_base = region + out.offset;
+  a.out_slice_stride = per_slice ? S.slice_elems : 0;
+  a.out_meta_per_slice = per_slice ? 1 : 0;
+  a.out_meta = out.meta;
+  a.scratch_a = region + g.scratch_a;
+  a.scratch_b = region + g.scratch_b;
+  a.scratch_stride = per_slice ? S.slice_elems : 0;
+  for (int j = 0; j < a.m; ++j) {
+    KOp o;
+    fill_op(S, g, j, o);
+    GOp& q = a.op[j];
+    q.base = o.base;
+    q.slice_stride = o.slice_stride;
+    q.meta = o.meta;
+    q.umask = o.umask;
+    q.smask = o.smask;
+    q.sshift = o.sshift;
+    q.meta_per_slice = o.meta_per_slice;
+    q.side = g.side[j];
+  }
+}
 
 struct EngineCache {
   uint64_t generation = 0;
@@ -832,8 +888,10 @@ static int tiled_grid_cap(int v, int m) {
 
 template <typename R>
 static bool make_desc(const Schedule& S, int gi, long long nslices, LaunchDesc& d,
-                      std::string& err, int variant = 1) {
+                      std::string& err, int variant = -1) {
   const SGroup& st = S.groups[gi];
+  if (variant < 0)
+    variant = st.gemm && (tc_precision(S.precision) || S.force_gemm) ? VARIANT_GEMM : 1;
   KStep& k = d.k;
   k = KStep{};
   k.m = (int)st.ops.size();
@@ -867,6 +925,15 @@ static bool make_desc(const Schedule& S, int gi, long long nslices, LaunchDesc& 
   const bool tiled = st.u >= TILE_UBITS && k.ms >= 1 && k.ms <= TILED_MAXSTREAM && st.nsum <= 7;
   d.kind = tiled ? 1 : 0;
   d.variant = variant;
+  d.gemm_mode = -1;
+  if (variant == VARIANT_GEMM && st.gemm && sizeof(R) == 4) {
+    d.kind = 3;
+    d.gemm_mode = gemm_mode_for(S, st);
+    fill_gemm(S, st, nslices, d.ga);
+    d.grid = 0;
+    return true;
+  }
+  if (variant == VARIANT_GEMM) d.variant = variant = 1;
   if (tiled) {
     const long long ntiles = nslices << (st.u - TILE_UBITS);
     d.grid = (unsigned)std::min<long long>(ntiles, tiled_grid_cap<R>(variant, k.ms));
@@ -915,6 +982,15 @@ static void launch_desc(qt_net* net, const LaunchDesc& d0, long long nslices, lo
   ProfRec pr{S.groups[d0.group].first, d0.kind, nslices, d0.bytes * nslices, d0.flops * nslices,
              nullptr, nullptr};
   if (net->prof) prof_begin(net, s, pr);
+  if (d0.kind == 3) {
+    GemmArgs ga = d0.ga;
+    ga.nslices = nslices;
+    ga.slice_first = slice_first;
+    net->launches += gemm_launch(ga, d0.gemm_mode, reinterpret_cast<float*>(base),
+                                 reinterpret_cast<GMeta*>(meta), s, num_sms());
+    if (net->prof) prof_end(net, s, pr);
+    return;
+  }
   net->launches++;
   if (d0.kind == 1) {
     tiled_fn<R>(d0.variant, k.ms)<<<grid, TILE_THREADS, 0, s>>>(k, data, meta);
@@ -991,13 +1067,16 @@ static qt_status autotune_impl(qt_net* net, char* base, cudaStream_t s, std::str
   auto run_list = [&](std::vector<LaunchDesc>& list, long long nb, long long b0) {
     for (size_t i = 0; i < list.size(); ++i) {
       LaunchDesc& d = list[i];
-      if (d.kind != 1) {
+      const SGroup& grp = S.groups[d.group];
+      const bool can_gemm = grp.gemm && !tc_precision(S.precision) && sizeof(R) == 4;
+      if (d.kind == 0 || (d.kind == 3 && (tc_precision(S.precision) || S.force_gemm))) {
         launch_desc<R>(net, d, nb, b0, base, s);
         continue;
       }
+      const int nv = N_VARIANTS + (can_gemm ? 1 : 0);
       for (int pass = 0; pass < 2; ++pass)
-        for (int t = 0; t < N_VARIANTS; ++t) {
-          const int v = pass == 0 ? t : N_VARIANTS - 1 - t;
+        for (int t = 0; t < nv; ++t) {
+          const int v = pass == 0 ? t : nv - 1 - t;
           LaunchDesc dv = d;
           std::string e2;
           make_desc<R>(S, d.group, d.k.nslices, dv, e2, v);
@@ -1031,21 +1110,24 @@ static qt_status autotune_impl(qt_net* net, char* base, cudaStream_t s, std::str
       float ms = 0.f;
       cudaEventElapsedTime(&ms, tr.a, tr.b);
       if (acc.empty() || acc.back().first.list != tr.list || acc.back().first.idx != tr.idx)
-        acc.push_back({Key{tr.list, tr.idx}, std::vector<float>(N_VARIANTS, 0.f)});
-      acc.back().second[tr.variant] += ms;
+        acc.push_back({Key{tr.list, tr.idx}, std::vector<float>(N_VARIANTS + 1, 1e30f)});
+      float& slot = acc.back().second[tr.variant];
+      slot = slot >= 1e29f ? ms : slot + ms;
     }
     bool first = true;
     for (auto& kv : acc) {
       LaunchDesc& d = (*kv.first.list)[kv.first.idx];
       int bv = 0;
-      for (int v = 1; v < N_VARIANTS; ++v)
+      for (int v = 1; v <= N_VARIANTS; ++v)
         if (kv.second[v] < kv.second[bv]) bv = v;
       std::string e2;
       make_desc<R>(S, d.group, d.k.nslices, d, e2, bv);
-      char buf[160];
-      std::snprintf(buf, sizeof buf, "%s{\"step\":%d,\"variant\":%d,\"ms\":[%.4f,%.4f,%.4f]}",
-                    first ? "" : ",", S.groups[d.group].first, bv, kv.second[0] / 2, kv.second[1] / 2,
-                    kv.second[2] / 2);
+      char buf[200];
+      auto half = [](float x) { return x >= 1e29f ? -1.0 : x / 2.0; };
+      std::snprintf(buf, sizeof buf,
+                    "%s{\"step\":%d,\"variant\":%d,\"ms\":[%.4f,%.4f,%.4f,%.4f]}",
+                    first ? "" : ",", S.groups[d.group].first, bv, half(kv.second[0]),
+                    half(kv.second[1]), half(kv.second[2]), half(kv.second[3]));
       report += buf;
       first = false;
     }

@@ -1,0 +1,350 @@
+// GEMM form of a fused bucket launch (complex64 tensors).
+//
+// A launch whose two largest operands A, B hold every index of its union U
+// (all other operands lying inside A or inside B) is a batched complex GEMM:
+//   out[bt][m][n] = sum_k A'[bt][m][k] B'[bt][n][k],
+// k: summed indices both A and B have; m (n): output indices only A (B) has;
+// bt: output indices both have. A' is A times the operands folded into it (exact
+// by distributivity: each operand of the nested sum only multiplies terms it
+// is constant over), already summed over the summed indices only A has; B'
+// likewise. The pack kernels write A', B' planar (re plane, im plane); the
+// GEMM kernels multiply them on CUDA cores (FP32) or on the tensor cores
+// (mma.sync TF32 m16n8k8, BF16 m16n8k16 with FP32 accumulation, or 3xTF32:
+// a = a_hi + a_lo with a_hi = tf32(a), products a_hi b_hi + a_hi b_lo + a_lo b_hi),
+// and the epilogue scatters each result to its place in the canonical layout
+// of the output (index = the output's U bits, shifted down by the summed ones).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "gemm.h"
+
+namespace qt {
+
+namespace {
+
+__device__ __forceinline__ unsigned int pdep32(unsigned int x, unsigned int m) {
+  unsigned int r = 0;
+  int k = 0;
+  while (m) {
+    const int b = __ffs(m) - 1;
+    r |= ((x >> k) & 1u) << b;
+    ++k;
+    m &= m - 1;
+  }
+  return r;
+}
+
+__device__ __forceinline__ unsigned long long pext64g(unsigned long long x, unsigned int m) {
+  unsigned long long r = 0;
+  int k = 0;
+  while (m) {
+    const int b = __ffs(m) - 1;
+    r |= ((x >> b) & 1ull) << k;
+    ++k;
+    m &= m - 1;
+  }
+  return r;
+}
+
+__device__ __forceinline__ int scale_exp_g(unsigned int maxabs_bits) {
+  if (maxabs_bits == 0u) return 0;
+  const int s = (int)((maxabs_bits >> 23) & 0xffu) - 126;
+  return max(-125, min(125, s));
+}
+
+__device__ __forceinline__ float pow2_neg_g(int s) { return __int_as_float((127 - s) << 23); }
+
+// A' (side 0) or B' (side 1): one packed element per thread
+__global__ void k_gemm_pack(const GemmArgs a, int side, float* data, const GMeta* meta) {
+  const int kb = __popc(a.mK), xb = __popc(side ? a.mN : a.mM), bb = __popc(a.mBt);
+  const unsigned int mX = side ? a.mN : a.mM, mS = side ? a.mSB : a.mSA;
+  const int sb = __popc(mS);
+  const long long per = 1ll << (bb + xb + kb);
+  const long long total = a.nslices * per;
+  float* plane = data + 2 * (side ? a.scratch_b : a.scratch_a);
+  const long long sstride = 2 * a.scratch_stride;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / per;
+    const long long loc = e - i * per;
+    const unsigned int k = (unsigned int)(loc & ((1ll << kb) - 1));
+    const unsigned int x = (unsigned int)((loc >> kb) & ((1ll << xb) - 1));
+    const unsigned int bt = (unsigned int)(loc >> (kb + xb));
+    const unsigned int U0 = pdep32(k, a.mK) | pdep32(x, mX) | pdep32(bt, a.mBt);
+    const unsigned long long sid = (unsigned long long)(a.slice_first + i);
+    float accr = 0.f, acci = 0.f;
+    for (unsigned int t = 0; t < (1u << sb); ++t) {
+      const unsigned int U = U0 | pdep32(t, mS);
+      float pr = 1.f, pi = 0.f;
+      for (int j = 0; j < a.m; ++j) {
+        const GOp& o = a.op[j];
+        if (o.side != side) continue;
+        long long off = o.base + i * o.slice_stride + (long long)pext64g(U, o.umask);
+        if (o.smask) off += (long long)(pext64g(sid, o.smask) << o.sshift);
+        const float sc = pow2_neg_g(scale_exp_g(meta[o.meta + (o.meta_per_slice ? i : 0)].maxabs));
+        const float2 v = reinterpret_cast<const float2*>(data)[off];
+        const float vr = v.x * sc, vi = v.y * sc;
+        const float nr = pr * vr - pi * vi, ni = pr * vi + pi * vr;
+        pr = nr;
+        pi = ni;
+      }
+      accr += pr;
+      acci += pi;
+    }
+    float* pl = plane + i * sstride;
+    pl[loc] = accr;
+    pl[per + loc] = acci;
+  }
+}
+
+__device__ __forceinline__ long long out_index(const GemmArgs& a, unsigned int bt, unsigned int m,
+                                               unsigned int n) {
+  const unsigned int U = pdep32(bt, a.mBt) | pdep32(m, a.mM) | pdep32(n, a.mN);
+  return (long long)(U >> a.nsum);
+}
+
+__device__ __forceinline__ void write_meta_e(const GemmArgs& a, GMeta* meta, long long i) {
+  int E = 0;
+  for (int j = 0; j < a.m; ++j) {
+    const GOp& o = a.op[j];
+    const GMeta mt = meta[o.meta + (o.meta_per_slice ? i : 0)];
+    E += mt.E + scale_exp_g(mt.maxabs);
+  }
+  meta[a.out_meta + (a.out_meta_per_slice ? i : 0)].E = E;
+}
+
+__device__ __forceinline__ void flush_max(const GemmArgs& a, GMeta* meta, long long i, float mx) {
+  const unsigned int v = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+  if ((threadIdx.x & 31) == 0 && v)
+    atomicMax(&meta[a.out_meta + (a.out_meta_per_slice ? i : 0)].maxabs, v);
+}
+
+// CUDA-core GEMM: one output element per thread, k summed in order
+__global__ void k_gemm_simt(const GemmArgs a, float* data, GMeta* meta) {
+  const int kb = __popc(a.mK), mb = __popc(a.mM), nb = __popc(a.mN), bb = __popc(a.mBt);
+  const long long per = 1ll << (bb + mb + nb);
+  const long long total = a.nslices * per;
+  const int K = 1 << kb;
+  const long long pa = 1ll << (bb + mb + kb), pb = 1ll << (bb + nb + kb);
+  long long cur = -1;
+  float mx = 0.f;
+  const long long step = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += step) {
+    const long long e = base + threadIdx.x;
+    const bool active = e < total;
+    const long long i = active ? e / per : cur;
+    if (__any_sync(0xffffffffu, active && i != cur && cur >= 0)) {
+      flush_max(a, meta, cur, mx);
+      mx = 0.f;
+    }
+    cur = __shfl_sync(0xffffffffu, i, 0);
+    if (active) {
+      const long long loc = e - i * per;
+      const unsigned int n = (unsigned int)(loc & ((1ll << nb) - 1));
+      const unsigned int m = (unsigned int)((loc >> nb) & ((1ll << mb) - 1));
+      const unsigned int bt = (unsigned int)(loc >> (nb + mb));
+      const float* A = data + 2 * (a.scratch_a + i * a.scratch_stride);
+      const float* B = data + 2 * (a.scratch_b + i * a.scratch_stride);
+      const long long ra = ((long long)bt << (mb + kb)) | ((long long)m << kb);
+      const long long rb = ((long long)bt << (nb + kb)) | ((long long)n << kb);
+      float cr = 0.f, ci = 0.f;
+      for (int k = 0; k < K; ++k) {
+        const float ar = A[ra + k], ai = A[pa + ra + k], br = B[rb + k], bi = B[pb + rb + k];
+        cr += ar * br - ai * bi;
+        ci += ar * bi + ai * br;
+      }
+      const long long o = a.out_base + i * a.out_slice_stride + out_index(a, bt, m, n);
+      reinterpret_cast<float2*>(data)[o] = make_float2(cr, ci);
+      mx = fmaxf(mx, fmaxf(fabsf(cr), fabsf(ci)));
+      if (loc == 0) write_meta_e(a, meta, i);
+    }
+  }
+  if (cur >= 0) flush_max(a, meta, cur, mx);
+}
+
+__device__ __forceinline__ unsigned int to_tf32(float x) {
+  unsigned int r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned int (&a)[4],
+                                         const unsigned int (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ unsigned int pack_bf16(float lo, float hi) {
+  unsigned int r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned int (&a)[4],
+                                         const unsigned int (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Tensor-core GEMM: one warp per (slice, bt, 16-row m tile, 8-column n tile).
+// Fragment layouts of mma.m16n8k8 (tf32) / m16n8k16 (bf16), with g = lane / 4,
+// t = lane % 4: A row g (+8), columns t (+4) [tf32] or 2t, 2t+1 (+8) [bf16];
+// B column g, rows t (+4) [tf32] or 2t, 2t+1 (+8) [bf16]; C rows g (+8),
+// columns 2t, 2t+1. Out-of-range rows, columns and k read as 0.
+template <int MODE>
+__global__ void k_gemm_tc(const GemmArgs a, float* data, GMeta* meta) {
+  const int kb = __popc(a.mK), mb = __popc(a.mM), nb = __popc(a.mN), bb = __popc(a.mBt);
+  const int M = 1 << mb, N = 1 << nb, K = 1 << kb;
+  const int mt = (M + 15) / 16, nt = (N + 7) / 8;
+  const long long per = (long long)mt * nt << bb;
+  const long long items = a.nslices * per;
+  const long long pa = 1ll << (bb + mb + kb), pb = 1ll << (bb + nb + kb);
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const long long warps = (long long)gridDim.x * (blockDim.x / 32);
+  long long cur = -1;
+  float mx = 0.f;
+  for (long long w = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < items;
+       w += warps) {
+    const long long i = w / per;
+    const long long r = w - i * per;
+    const int ntile = (int)(r % nt);
+    const int mtile = (int)((r / nt) % mt);
+    const unsigned int bt = (unsigned int)(r / ((long long)nt * mt));
+    if (i != cur) {
+      if (cur >= 0) flush_max(a, meta, cur, mx);
+      cur = i;
+      mx = 0.f;
+    }
+    const float* Ar = data + 2 * (a.scratch_a + i * a.scratch_stride) + ((long long)bt << (mb + kb));
+    const float* Ai = Ar + pa;
+    const float* Br = data + 2 * (a.scratch_b + i * a.scratch_stride) + ((long long)bt << (nb + kb));
+    const float* Bi = Br + pb;
+    const int m0 = mtile * 16, n0 = ntile * 8;
+    auto ld = [&](const float* P, int row, int rows, int k) -> float {
+      return (row < rows && k < K) ? P[((long long)row << kb) + k] : 0.f;
+    };
+    float cr[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f};
+    if constexpr (MODE == GEMM_TC_BF16) {
+      for (int k0 = 0; k0 < K; k0 += 16) {
+        unsigned int ar_[4], ai_[4], nai_[4], br_[2], bi_[2];
+        const int ka = k0 + 2 * t;
+        ar_[0] = pack_bf16(ld(Ar, m0 + g, M, ka), ld(Ar, m0 + g, M, ka + 1));
+        ar_[1] = pack_bf16(ld(Ar, m0 + g + 8, M, ka), ld(Ar, m0 + g + 8, M, ka + 1));
+        ar_[2] = pack_bf16(ld(Ar, m0 + g, M, ka + 8), ld(Ar, m0 + g, M, ka + 9));
+        ar_[3] = pack_bf16(ld(Ar, m0 + g + 8, M, ka + 8), ld(Ar, m0 + g + 8, M, ka + 9));
+        ai_[0] = pack_bf16(ld(Ai, m0 + g, M, ka), ld(Ai, m0 + g, M, ka + 1));
+        ai_[1] = pack_bf16(ld(Ai, m0 + g + 8, M, ka), ld(Ai, m0 + g + 8, M, ka + 1));
+        ai_[2] = pack_bf16(ld(Ai, m0 + g, M, ka + 8), ld(Ai, m0 + g, M, ka + 9));
+        ai_[3] = pack_bf16(ld(Ai, m0 + g + 8, M, ka + 8), ld(Ai, m0 + g + 8, M, ka + 9));
+        nai_[0] = ai_[0] ^ 0x80008000u;
+        nai_[1] = ai_[1] ^ 0x80008000u;
+        nai_[2] = ai_[2] ^ 0x80008000u;
+        nai_[3] = ai_[3] ^ 0x80008000u;
+        br_[0] = pack_bf16(ld(Br, n0 + g, N, ka), ld(Br, n0 + g, N, ka + 1));
+        br_[1] = pack_bf16(ld(Br, n0 + g, N, ka + 8), ld(Br, n0 + g, N, ka + 9));
+        bi_[0] = pack_bf16(ld(Bi, n0 + g, N, ka), ld(Bi, n0 + g, N, ka + 1));
+        bi_[1] = pack_bf16(ld(Bi, n0 + g, N, ka + 8), ld(Bi, n0 + g, N, ka + 9));
+        mma_bf16(cr, ar_, br_);
+        mma_bf16(cr, nai_, bi_);
+        mma_bf16(ci, ar_, bi_);
+        mma_bf16(ci, ai_, br_);
+      }
+    } else {
+      for (int k0 = 0; k0 < K; k0 += 8) {
+        const float far[4] = {ld(Ar, m0 + g, M, k0 + t), ld(Ar, m0 + g + 8, M, k0 + t),
+                              ld(Ar, m0 + g, M, k0 + t + 4), ld(Ar, m0 + g + 8, M, k0 + t + 4)};
+        const float fai[4] = {ld(Ai, m0 + g, M, k0 + t), ld(Ai, m0 + g + 8, M, k0 + t),
+                              ld(Ai, m0 + g, M, k0 + t + 4), ld(Ai, m0 + g + 8, M, k0 + t + 4)};
+        const float fbr[2] = {ld(Br, n0 + g, N, k0 + t), ld(Br, n0 + g, N, k0 + t + 4)};
+        const float fbi[2] = {ld(Bi, n0 + g, N, k0 + t), ld(Bi, n0 + g, N, k0 + t + 4)};
+        unsigned int arh[4], aih[4], naih[4], brh[2], bih[2];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          arh[q] = to_tf32(far[q]);
+          aih[q] = to_tf32(fai[q]);
+          naih[q] = aih[q] ^ 0x80000000u;
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          brh[q] = to_tf32(fbr[q]);
+          bih[q] = to_tf32(fbi[q]);
+        }
+        mma_tf32(cr, arh, brh);
+        mma_tf32(cr, naih, bih);
+        mma_tf32(ci, arh, bih);
+        mma_tf32(ci, aih, brh);
+        if constexpr (MODE == GEMM_TC_3XTF32) {
+          unsigned int arl[4], ail[4], nail[4], brl[2], bil[2];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            arl[q] = to_tf32(far[q] - __uint_as_float(arh[q]));
+            ail[q] = to_tf32(fai[q] - __uint_as_float(aih[q]));
+            nail[q] = ail[q] ^ 0x80000000u;
+          }
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            brl[q] = to_tf32(fbr[q] - __uint_as_float(brh[q]));
+            bil[q] = to_tf32(fbi[q] - __uint_as_float(bih[q]));
+          }
+          // hi*lo and lo*hi terms
+          mma_tf32(cr, arh, brl);
+          mma_tf32(cr, naih, bil);
+          mma_tf32(ci, arh, bil);
+          mma_tf32(ci, aih, brl);
+          mma_tf32(cr, arl, brh);
+          mma_tf32(cr, nail, bih);
+          mma_tf32(ci, arl, bih);
+          mma_tf32(ci, ail, brh);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int m = m0 + g + (q >= 2 ? 8 : 0);
+      const int n = n0 + 2 * t + (q & 1);
+      if (m < M && n < N) {
+        const long long o = a.out_base + i * a.out_slice_stride + out_index(a, bt, m, n);
+        reinterpret_cast<float2*>(data)[o] = make_float2(cr[q], ci[q]);
+        mx = fmaxf(mx, fmaxf(fabsf(cr[q]), fabsf(ci[q])));
+      }
+    }
+    if (r == 0 && lane == 0) write_meta_e(a, meta, i);
+  }
+  if (cur >= 0) flush_max(a, meta, cur, mx);
+}
+
+}  // namespace
+
+int gemm_launch(const GemmArgs& a, int mode, float* data, GMeta* meta, cudaStream_t s, int sms) {
+  const int kb = __builtin_popcount(a.mK), bb = __builtin_popcount(a.mBt);
+  const long long pa = a.nslices << (bb + __builtin_popcount(a.mM) + kb);
+  const long long pb = a.nslices << (bb + __builtin_popcount(a.mN) + kb);
+  auto grid_for = [&](long long work, int threads) {
+    long long g = (work + threads - 1) / threads;
+    return (unsigned)std::max<long long>(1, std::min<long long>(g, (long long)sms * 16));
+  };
+  k_gemm_pack<<<grid_for(pa, 256), 256, 0, s>>>(a, 0, data, meta);
+  k_gemm_pack<<<grid_for(pb, 256), 256, 0, s>>>(a, 1, data, meta);
+  const int mb = __builtin_popcount(a.mM), nb = __builtin_popcount(a.mN);
+  if (mode == GEMM_SIMT) {
+    const long long outs = a.nslices << (bb + mb + nb);
+    k_gemm_simt<<<grid_for(outs, 256), 256, 0, s>>>(a, data, meta);
+  } else {
+    const long long items =
+        a.nslices * (long long)(((1 << mb) + 15) / 16) * (((1 << nb) + 7) / 8) << bb;
+    const unsigned grid = grid_for(items * 32, 128);
+    if (mode == GEMM_TC_TF32) k_gemm_tc<GEMM_TC_TF32><<<grid, 128, 0, s>>>(a, data, meta);
+    else if (mode == GEMM_TC_BF16) k_gemm_tc<GEMM_TC_BF16><<<grid, 128, 0, s>>>(a, data, meta);
+    else k_gemm_tc<GEMM_TC_3XTF32><<<grid, 128, 0, s>>>(a, data, meta);
+  }
+  return 3;
+}
+
+}  // namespace qt

@@ -272,6 +272,53 @@ bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePla
     g.bytes = 8 * elems;
     (g.region == 0 ? S.prefix_launch_bytes : S.slice_launch_bytes) += g.bytes;
   }
+  // GEMM form of large groups (complex64 precisions)
+  if (precision != QT_FP64) {
+    for (SGroup& g : S.groups) {
+      if (g.u < 14 || g.ops.size() < 2) continue;
+      std::vector<uint32_t> mask(g.ops.size(), 0u);
+      for (size_t j = 0; j < g.ops.size(); ++j)
+        for (int32_t l : seen_labels(g.ops[j], g.region))
+          for (int b = 0; b < g.u; ++b)
+            if (g.ulabels[b] == l) mask[j] |= 1u << b;
+      int a = -1, bb = -1;
+      for (int j = 0; j < (int)g.ops.size(); ++j) {
+        const int pj = __builtin_popcount(mask[j]);
+        if (a < 0 || pj > __builtin_popcount(mask[a])) {
+          bb = a;
+          a = j;
+        } else if (bb < 0 || pj > __builtin_popcount(mask[bb])) {
+          bb = j;
+        }
+      }
+      if (a < 0 || bb < 0 || __builtin_popcount(mask[a]) < 8 || __builtin_popcount(mask[bb]) < 2)
+        continue;
+      const uint32_t A = mask[a], B = mask[bb];
+      bool ok = true;
+      std::vector<int8_t> side(g.ops.size(), 0);
+      for (size_t j = 0; j < g.ops.size(); ++j) {
+        if ((int)j == a) side[j] = 0;
+        else if ((int)j == bb) side[j] = 1;
+        else if ((mask[j] & ~A) == 0u) side[j] = 0;
+        else if ((mask[j] & ~B) == 0u) side[j] = 1;
+        else ok = false;
+      }
+      const uint32_t all = g.u >= 32 ? 0xffffffffu : ((1u << g.u) - 1u);
+      if (!ok || (A | B) != all) continue;
+      const uint32_t Sm = (1u << g.nsum) - 1u, O = all & ~Sm;
+      g.mK = Sm & A & B;
+      g.mSA = Sm & A & ~B;
+      g.mSB = Sm & B & ~A;
+      g.mM = O & A & ~B;
+      g.mN = O & B & ~A;
+      g.mBt = O & A & B;
+      if (__builtin_popcount(g.mK) > 7) continue;
+      g.gemm = true;
+      g.gA = a;
+      g.gB = bb;
+      g.side = side;
+    }
+  }
   // liveness by group: a stored tensor lives from its group to the last group reading it
   const int end_group = (int)S.groups.size();
   for (STensor& t : S.tensors) t.last_use = -1;
@@ -293,10 +340,20 @@ bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePla
   S.gate_elems = goff;
   Arena pre, sl;
   for (int gi = 0; gi < end_group; ++gi) {
-    STensor& o = S.tensors[S.groups[gi].out];
+    SGroup& g = S.groups[gi];
+    STensor& o = S.tensors[g.out];
     Arena& ar = o.kind == TK_PREFIX ? pre : sl;
     o.offset = ar.alloc((int64_t)1 << o.rank, kArenaAlign);
     if (o.last_use < 0) o.last_use = gi;
+    if (g.gemm) {  // A', B' live only during the group
+      const int kb = __builtin_popcount(g.mK), bt = __builtin_popcount(g.mBt);
+      const int64_t na = (int64_t)1 << (bt + __builtin_popcount(g.mM) + kb);
+      const int64_t nb = (int64_t)1 << (bt + __builtin_popcount(g.mN) + kb);
+      g.scratch_a = ar.alloc(na, kArenaAlign);
+      g.scratch_b = ar.alloc(nb, kArenaAlign);
+      ar.release(g.scratch_a, na, kArenaAlign);
+      ar.release(g.scratch_b, nb, kArenaAlign);
+    }
     for (int32_t tid : S.groups[gi].ops) {
       STensor& t = S.tensors[tid];
       if (t.kind != TK_GATE && !t.virt && t.last_use == gi)
@@ -339,6 +396,17 @@ bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePla
 
 std::string schedule_json(const Schedule& S, const SlicePlan& plan) {
   std::ostringstream o;
+  int64_t gemm_flops = 0, tc_flops = 0, k32_flops = 0, total_flops = 0;
+  int n_gemm = 0;
+  for (const SGroup& g : S.groups) {
+    const int64_t f = g.flops * (g.region == 1 ? S.nslices : 1);
+    total_flops += f;
+    if (!g.gemm) continue;
+    ++n_gemm;
+    gemm_flops += f;
+    if (__builtin_popcount(g.mM) >= 4 && __builtin_popcount(g.mN) >= 3) tc_flops += f;
+    if (__builtin_popcount(g.mK) >= 5) k32_flops += f;
+  }
   o << "{\"k\":" << S.k << ",\"nslices\":" << S.nslices << ",\"batch\":" << S.batch
     << ",\"precision\":" << S.precision << ",\"elem_bytes\":" << S.elem_bytes
     << ",\"plan_width\":" << plan.width << ",\"slice_step\":" << plan.slice_step
@@ -351,6 +419,9 @@ std::string schedule_json(const Schedule& S, const SlicePlan& plan) {
     << ",\"prefix_arena_bytes\":" << S.prefix_elems * S.elem_bytes
     << ",\"slice_arena_bytes\":" << S.slice_elems * S.elem_bytes
     << ",\"fused\":" << (S.fused ? 1 : 0) << ",\"n_groups\":" << S.groups.size()
+    << ",\"gemm_groups\":" << n_gemm << ",\"job_flops\":" << total_flops
+    << ",\"gemm_form_flops\":" << gemm_flops << ",\"tensor_core_shape_flops\":" << tc_flops
+    << ",\"k_ge_32_flops\":" << k32_flops
     << ",\"prefix_launch_bytes\":" << S.prefix_launch_bytes
     << ",\"slice_launch_bytes\":" << S.slice_launch_bytes
     << ",\"upload_bytes\":"

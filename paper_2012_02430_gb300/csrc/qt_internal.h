@@ -103,10 +103,22 @@ struct SGroup {
   int out = -1;                  // result of the last step
   int u = 0, nsum = 1, c = 0;
   int64_t flops = 0, bytes = 0;  // flops: sum over the steps; bytes: operands once + result
+  // GEMM form (complex precisions only): with A and B the two largest operands and
+  // every other operand's indices inside A or inside B, the launch is
+  //   out[bt][m][n] = sum_k A'[bt][m][k] B'[bt][n][k]
+  // A' = A times the operands folded into it, summed over the summed indices only A
+  // has (B' likewise); k: summed indices both have; m, n: output indices of A only,
+  // B only; bt: output indices of both. Masks are over the group's U bits.
+  bool gemm = false;
+  int gA = -1, gB = -1;              // indices into ops
+  std::vector<int8_t> side;          // per operand: 0 folded into A', 1 into B'
+  uint32_t mK = 0, mSA = 0, mSB = 0, mM = 0, mN = 0, mBt = 0;
+  int64_t scratch_a = 0, scratch_b = 0;  // arena offsets of A', B' (planar re | im)
 };
 
 struct Schedule {
   bool valid = false;
+  bool force_gemm = false;       // copy of the network option at compile time
   bool fused = true;             // steps grouped into fused launches
   uint64_t generation = 0;      // changes with every compile
   int precision = QT_FP32_SIMT;
@@ -185,6 +197,7 @@ struct qt_net {
   int64_t launches = 0;          // kernel launches issued by this network
   bool graphs = true;            // replay runs as captured CUDA graphs
   bool fuse = true;              // fuse bucket steps whose summed indices die together
+  bool force_gemm = false;       // GEMM-form launches by default also in FP32 mode
   void* engine = nullptr;        // engine.cu: launch descriptors and graph cache
   ~qt_net();
 };

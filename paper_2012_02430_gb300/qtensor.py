@@ -18,8 +18,8 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libqtensor.so")
 
 QT_OK, QT_EINVAL, QT_ENOMEM, QT_ECUDA, QT_ETIMEOUT, QT_ESTATE, QT_ERANGE = range(7)
 QT_GREEDY_MINFILL, QT_GREEDY_MINDEG = 0, 1
-QT_FP32_SIMT, QT_FP64 = 0, 4
-QT_OPT_FUSION, QT_OPT_GRAPHS = 1, 2
+QT_FP32_SIMT, QT_TF32, QT_BF16, QT_3XTF32, QT_FP64 = 0, 1, 2, 3, 4
+QT_OPT_FUSION, QT_OPT_GRAPHS, QT_OPT_GEMM = 1, 2, 3
 QT_PROPOSAL_FEATURES = 16
 
 STATUS_NAMES = {0: "QT_OK", 1: "QT_EINVAL", 2: "QT_ENOMEM", 3: "QT_ECUDA",

@@ -143,7 +143,7 @@ def test_errors(qt):
             qt.qt_slice(h, 0, 1)
         assert e.value.status == qt.QT_EINVAL
         with pytest.raises(QtError) as e:
-            qt.qt_prepare(h, 3, 1)
+            qt.qt_prepare(h, 7, 1)
         assert e.value.status == qt.QT_EINVAL
         need = qt.qt_prepare(h, 0, 1)
         assert need > 0
