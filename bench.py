@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "slices/s & complex TFLOP/s vs plain FP32 greedy GPU path at rel.err<=1e-5"
 WORKLOAD = dict(n=80, p=2, seed=1002, width_limit=26, max_vars=20, r=1, algo="greedy-minfill")
 L2_FLUSH_BYTES = 512 << 20
+PRECISIONS = {"fp32": 0, "tf32": 1, "bf16": 2, "3xtf32": 3, "fp64": 4}
 
 
 def parse():
@@ -40,7 +41,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=list(PRECISIONS))
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="weak: every rank its own amplitude; strong: one amplitude's slices "
+                         "sharded over the ranks (partial sums exchanged)")
+    ap.add_argument("--no-modes", action="store_true", help="skip the precision-mode table")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-slices", type=int, default=1)
     return ap.parse_args()
@@ -203,7 +208,7 @@ def ours(args):
         if dist is not None:
             dist.barrier()
 
-    prec = Q.QT_FP64 if args.precision == "fp64" else Q.QT_FP32_SIMT
+    prec = PRECISIONS[args.precision]
     edges, gammas, betas, z = instance(rank)
     net = Q.Network(edges, WORKLOAD["n"], WORKLOAD["p"], gammas, betas, z)
     t_plan = time.perf_counter()
@@ -219,8 +224,17 @@ def ours(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step():
-        net.run(0, nslices, out)
+    from paper_2012_02430_gb300 import dist as qdist
+    if args.scaling == "strong":
+        lo, hi = qdist.slice_range(nslices, rank, world)
+        if hi <= lo:
+            raise SystemExit("strong scaling needs at least one slice per rank")
+
+        def step():
+            net.run(lo, hi - lo, out)
+    else:
+        def step():
+            net.run(0, nslices, out)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -249,11 +263,16 @@ def ours(args):
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    value = world * nslices * args.steps / (total_ms / 1e3)
-    amp = complex(out[0].item(), out[1].item())
+    units = nslices if args.scaling == "strong" else world * nslices
+    value = units * args.steps / (total_ms / 1e3)
+    if args.scaling == "strong":
+        amp = qdist.sharded_sum(qdist.gpu_partial(net, out), nslices, rank, world, device="cuda")
+    else:
+        amp = complex(out[0].item(), out[1].item())
     flops_per_step = st["prefix_flops"] + st["slice_flops"] * nslices
     bytes_per_step = (st["prefix_bytes"] + st["slice_bytes"] * nslices) * (st["elem_bytes"] // 8)
-    tflops = world * flops_per_step * args.steps / (total_ms / 1e3) / 1e12
+    tflops = (1 if args.scaling == "strong" else world) * flops_per_step * args.steps / (
+        total_ms / 1e3) / 1e12
 
     # per-launch times of the same workload (events around every launch)
     Q.qt_profile(net.handle, 1)
@@ -309,6 +328,8 @@ def ours(args):
     del plain
 
     energy_line = batched_energy(args, Q, torch, flush, stream)
+    modes_line = None if args.no_modes else precision_modes(Q, torch, edges, gammas, betas, z,
+                                                            flush, stream)
 
     # end to end: host inputs -> amplitude on the host, through qt_contract
     from paper_2012_02430_gb300.inputs import random_angles
@@ -331,8 +352,8 @@ def ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "c64" if prec == Q.QT_FP32_SIMT else "c128", "data": "synthetic",
+        "higher_is_better": True, "scaling": args.scaling, "vs_baseline": None,
+        "dtype": "c128" if prec == Q.QT_FP64 else "c64", "data": "synthetic",
         "config": {"workload": "qaoa-maxcut-amplitude N=80 p=2 3-regular seed=1002 "
                                "min-fill sliced to width<=26",
                    **WORKLOAD, "k": k, "slices": nslices, "width": width,
@@ -346,6 +367,7 @@ def ours(args):
         * (st["elem_bytes"] // 8),
         "plain_fp32_greedy_path": plain_line,
         "batched_energy": energy_line,
+        "precision_modes": modes_line,
         "amplitude": [amp.real, amp.imag],
         "gpu_launches": launches,
         "roofline": roofline, "clocks": clk, "e2e": e2e,
@@ -364,6 +386,41 @@ def ours(args):
 
 
 ENERGY_WORKLOAD = dict(n=1000, p=2, seed=1004)
+
+
+def precision_modes(Q, torch, edges, gammas, betas, z, flush, stream, reps=5):
+    """Every precision mode on the same workload (autotuned, device-resident, CUDA events,
+    L2 flushed between runs): ms per amplitude and rel.err against the FP64 path (which the
+    GPU tests hold within 1e-10 of the oracle)."""
+    res, ref = {}, None
+    for name in ("fp64", "fp32", "3xtf32", "tf32", "bf16"):
+        net = Q.Network(edges, WORKLOAD["n"], WORKLOAD["p"], gammas, betas, z)
+        net.order(Q.QT_GREEDY_MINFILL)
+        k, _ = net.slice(WORKLOAD["width_limit"], WORKLOAD["max_vars"], WORKLOAD["r"])
+        net.prepare(PRECISIONS[name], batch=1 << k)
+        net.upload()
+        net.autotune()
+        out = torch.zeros(2, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            net.run(0, 1 << k, out)
+        tot = 0.0
+        for i in range(reps):
+            flush.fill_(i & 0xFF)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            net.run(0, 1 << k, out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        amp = complex(out[0].item(), out[1].item())
+        ref = amp if ref is None else ref
+        st = net.stats()
+        res[name] = {"ms_per_amplitude": tot / reps, "slices_per_s": (1 << k) / (tot / reps / 1e3),
+                     "rel_err_vs_fp64": abs(amp - ref) / abs(ref),
+                     "tensor_core_shape_flop_fraction": st["tensor_core_shape_flops"] / st["job_flops"]}
+        del net
+    return res
 
 
 def batched_energy(args, Q, torch, flush, stream):

@@ -23,18 +23,6 @@ namespace qt {
 
 namespace {
 
-__device__ __forceinline__ unsigned int pdep32(unsigned int x, unsigned int m) {
-  unsigned int r = 0;
-  int k = 0;
-  while (m) {
-    const int b = __ffs(m) - 1;
-    r |= ((x >> k) & 1u) << b;
-    ++k;
-    m &= m - 1;
-  }
-  return r;
-}
-
 __device__ __forceinline__ unsigned long long pext64g(unsigned long long x, unsigned int m) {
   unsigned long long r = 0;
   int k = 0;
@@ -55,36 +43,111 @@ __device__ __forceinline__ int scale_exp_g(unsigned int maxabs_bits) {
 
 __device__ __forceinline__ float pow2_neg_g(int s) { return __int_as_float((127 - s) << 23); }
 
-// A' (side 0) or B' (side 1): one packed element per thread
-__global__ void k_gemm_pack(const GemmArgs a, int side, float* data, const GMeta* meta) {
-  const int kb = __popc(a.mK), xb = __popc(side ? a.mN : a.mM), bb = __popc(a.mBt);
+// Byte-sliced lookup tables in shared memory replace per-element bit loops:
+// pdep(x, mask) for a dimension's index = sum over its bytes of T[byte][value],
+// pext(U, umask) for an operand = sum over the four bytes of U of P[byte][value].
+struct PdepLut {
+  unsigned int t[3][256];
+};
+
+__device__ __forceinline__ void build_pdep(PdepLut& L, unsigned int mask) {
+  for (int e = threadIdx.x; e < 3 * 256; e += blockDim.x) {
+    const int c = e >> 8, v = e & 255;
+    // the mask's set bits number c*8 .. c*8+7 take the bits of v
+    unsigned int m = mask, r = 0;
+    int k = 0;
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1;
+      if (k >= 8 * c && k < 8 * c + 8 && ((v >> (k - 8 * c)) & 1)) r |= 1u << b;
+      ++k;
+    }
+    L.t[c][v] = r;
+  }
+}
+
+__device__ __forceinline__ unsigned int pdep_lut(const PdepLut& L, unsigned int x) {
+  return L.t[0][x & 255] | L.t[1][(x >> 8) & 255] | L.t[2][(x >> 16) & 255];
+}
+
+__device__ __forceinline__ void build_pext(unsigned int (*P)[256], unsigned int umask) {
+  for (int e = threadIdx.x; e < 4 * 256; e += blockDim.x) {
+    const int c = e >> 8, v = e & 255;
+    const unsigned int x = (unsigned int)v << (8 * c);
+    unsigned int m = umask, r = 0;
+    int k = 0;
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1;
+      r |= ((x >> b) & 1u) << k;
+      ++k;
+    }
+    P[c][v] = r;
+  }
+}
+
+__device__ __forceinline__ unsigned int pext_lut(const unsigned int (*P)[256], unsigned int U) {
+  return P[0][U & 255] + P[1][(U >> 8) & 255] + P[2][(U >> 16) & 255] + P[3][U >> 24];
+}
+
+constexpr int PACK_MAXOPS = 8;
+
+// A' (side 0) or B' (side 1): one packed element (bt, x, k) per thread; the
+// sum over the side's one-sided summed indices runs inside the thread.
+__global__ void __launch_bounds__(256) k_gemm_pack(const GemmArgs a, int side, float* data,
+                                                   const GMeta* meta) {
+  __shared__ PdepLut Lk, Lx, Lb, Ls;
+  __shared__ unsigned int P[PACK_MAXOPS][4][256];
+  __shared__ int opj[PACK_MAXOPS];
+  __shared__ int nops;
   const unsigned int mX = side ? a.mN : a.mM, mS = side ? a.mSB : a.mSA;
-  const int sb = __popc(mS);
+  build_pdep(Lk, a.mK);
+  build_pdep(Lx, mX);
+  build_pdep(Lb, a.mBt);
+  build_pdep(Ls, mS);
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int j = 0; j < a.m; ++j)
+      if (a.op[j].side == side) opj[c++] = j;
+    nops = c;
+  }
+  __syncthreads();
+  for (int q = 0; q < nops; ++q) build_pext(P[q], a.op[opj[q]].umask);
+  __syncthreads();
+  const int kb = __popc(a.mK), xb = __popc(mX), bb = __popc(a.mBt), sb = __popc(mS);
   const long long per = 1ll << (bb + xb + kb);
   const long long total = a.nslices * per;
   float* plane = data + 2 * (side ? a.scratch_b : a.scratch_a);
   const long long sstride = 2 * a.scratch_stride;
+  long long cur = -1;
+  float sc[PACK_MAXOPS];
+  long long obase[PACK_MAXOPS];
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const long long i = e / per;
     const long long loc = e - i * per;
+    if (i != cur) {  // per-slice operand bases and scales
+      cur = i;
+      const unsigned long long sid = (unsigned long long)(a.slice_first + i);
+      for (int q = 0; q < nops; ++q) {
+        const GOp& o = a.op[opj[q]];
+        long long off = o.base + i * o.slice_stride;
+        if (o.smask) off += (long long)(pext64g(sid, o.smask) << o.sshift);
+        obase[q] = off;
+        sc[q] = pow2_neg_g(scale_exp_g(meta[o.meta + (o.meta_per_slice ? i : 0)].maxabs));
+      }
+    }
     const unsigned int k = (unsigned int)(loc & ((1ll << kb) - 1));
     const unsigned int x = (unsigned int)((loc >> kb) & ((1ll << xb) - 1));
     const unsigned int bt = (unsigned int)(loc >> (kb + xb));
-    const unsigned int U0 = pdep32(k, a.mK) | pdep32(x, mX) | pdep32(bt, a.mBt);
-    const unsigned long long sid = (unsigned long long)(a.slice_first + i);
+    const unsigned int U0 = pdep_lut(Lk, k) | pdep_lut(Lx, x) | pdep_lut(Lb, bt);
     float accr = 0.f, acci = 0.f;
     for (unsigned int t = 0; t < (1u << sb); ++t) {
-      const unsigned int U = U0 | pdep32(t, mS);
+      const unsigned int U = U0 | pdep_lut(Ls, t);
       float pr = 1.f, pi = 0.f;
-      for (int j = 0; j < a.m; ++j) {
-        const GOp& o = a.op[j];
-        if (o.side != side) continue;
-        long long off = o.base + i * o.slice_stride + (long long)pext64g(U, o.umask);
-        if (o.smask) off += (long long)(pext64g(sid, o.smask) << o.sshift);
-        const float sc = pow2_neg_g(scale_exp_g(meta[o.meta + (o.meta_per_slice ? i : 0)].maxabs));
-        const float2 v = reinterpret_cast<const float2*>(data)[off];
-        const float vr = v.x * sc, vi = v.y * sc;
+      for (int q = 0; q < nops; ++q) {
+        const float2 v = reinterpret_cast<const float2*>(data)[obase[q] + pext_lut(P[q], U)];
+        const float vr = v.x * sc[q], vi = v.y * sc[q];
         const float nr = pr * vr - pi * vi, ni = pr * vi + pi * vr;
         pr = nr;
         pi = ni;
@@ -96,12 +159,6 @@ __global__ void k_gemm_pack(const GemmArgs a, int side, float* data, const GMeta
     pl[loc] = accr;
     pl[per + loc] = acci;
   }
-}
-
-__device__ __forceinline__ long long out_index(const GemmArgs& a, unsigned int bt, unsigned int m,
-                                               unsigned int n) {
-  const unsigned int U = pdep32(bt, a.mBt) | pdep32(m, a.mM) | pdep32(n, a.mN);
-  return (long long)(U >> a.nsum);
 }
 
 __device__ __forceinline__ void write_meta_e(const GemmArgs& a, GMeta* meta, long long i) {
@@ -120,8 +177,19 @@ __device__ __forceinline__ void flush_max(const GemmArgs& a, GMeta* meta, long l
     atomicMax(&meta[a.out_meta + (a.out_meta_per_slice ? i : 0)].maxabs, v);
 }
 
+__device__ __forceinline__ long long out_index_lut(const GemmArgs& a, const PdepLut& Lb,
+                                                   const PdepLut& Lm, const PdepLut& Ln,
+                                                   unsigned int bt, unsigned int m, unsigned int n) {
+  return (long long)((pdep_lut(Lb, bt) | pdep_lut(Lm, m) | pdep_lut(Ln, n)) >> a.nsum);
+}
+
 // CUDA-core GEMM: one output element per thread, k summed in order
-__global__ void k_gemm_simt(const GemmArgs a, float* data, GMeta* meta) {
+__global__ void __launch_bounds__(256) k_gemm_simt(const GemmArgs a, float* data, GMeta* meta) {
+  __shared__ PdepLut Lb, Lm, Ln;
+  build_pdep(Lb, a.mBt);
+  build_pdep(Lm, a.mM);
+  build_pdep(Ln, a.mN);
+  __syncthreads();
   const int kb = __popc(a.mK), mb = __popc(a.mM), nb = __popc(a.mN), bb = __popc(a.mBt);
   const long long per = 1ll << (bb + mb + nb);
   const long long total = a.nslices * per;
@@ -154,7 +222,7 @@ __global__ void k_gemm_simt(const GemmArgs a, float* data, GMeta* meta) {
         cr += ar * br - ai * bi;
         ci += ar * bi + ai * br;
       }
-      const long long o = a.out_base + i * a.out_slice_stride + out_index(a, bt, m, n);
+      const long long o = a.out_base + i * a.out_slice_stride + out_index_lut(a, Lb, Lm, Ln, bt, m, n);
       reinterpret_cast<float2*>(data)[o] = make_float2(cr, ci);
       mx = fmaxf(mx, fmaxf(fabsf(cr), fabsf(ci)));
       if (loc == 0) write_meta_e(a, meta, i);
@@ -197,17 +265,25 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned int (&a)[
 // Fragment layouts of mma.m16n8k8 (tf32) / m16n8k16 (bf16), with g = lane / 4,
 // t = lane % 4: A row g (+8), columns t (+4) [tf32] or 2t, 2t+1 (+8) [bf16];
 // B column g, rows t (+4) [tf32] or 2t, 2t+1 (+8) [bf16]; C rows g (+8),
-// columns 2t, 2t+1. Out-of-range rows, columns and k read as 0.
+// columns 2t, 2t+1. The launch requires M >= 16 and N >= 8 (powers of two, so
+// every tile is full); k beyond K (K < 8, or K < 16 in BF16) reads as 0.
 template <int MODE>
-__global__ void k_gemm_tc(const GemmArgs a, float* data, GMeta* meta) {
+__global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs a, float* data, GMeta* meta) {
+  __shared__ PdepLut Lb, Lm, Ln;
+  build_pdep(Lb, a.mBt);
+  build_pdep(Lm, a.mM);
+  build_pdep(Ln, a.mN);
+  __syncthreads();
   const int kb = __popc(a.mK), mb = __popc(a.mM), nb = __popc(a.mN), bb = __popc(a.mBt);
-  const int M = 1 << mb, N = 1 << nb, K = 1 << kb;
-  const int mt = (M + 15) / 16, nt = (N + 7) / 8;
+  const int K = 1 << kb;
+  const int mt = (1 << mb) / 16, nt = (1 << nb) / 8;
   const long long per = (long long)mt * nt << bb;
   const long long items = a.nslices * per;
   const long long pa = 1ll << (bb + mb + kb), pb = 1ll << (bb + nb + kb);
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const long long warps = (long long)gridDim.x * (blockDim.x / 32);
+  constexpr int KSTEP = MODE == GEMM_TC_BF16 ? 16 : 8;
+  const bool kfull = K >= KSTEP;
   long long cur = -1;
   float mx = 0.f;
   for (long long w = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; w < items;
@@ -222,35 +298,33 @@ __global__ void k_gemm_tc(const GemmArgs a, float* data, GMeta* meta) {
       cur = i;
       mx = 0.f;
     }
-    const float* Ar = data + 2 * (a.scratch_a + i * a.scratch_stride) + ((long long)bt << (mb + kb));
-    const float* Ai = Ar + pa;
-    const float* Br = data + 2 * (a.scratch_b + i * a.scratch_stride) + ((long long)bt << (nb + kb));
-    const float* Bi = Br + pb;
     const int m0 = mtile * 16, n0 = ntile * 8;
-    auto ld = [&](const float* P, int row, int rows, int k) -> float {
-      return (row < rows && k < K) ? P[((long long)row << kb) + k] : 0.f;
-    };
+    // row pointers of this lane's fragment rows
+    const float* A0 = data + 2 * (a.scratch_a + i * a.scratch_stride) +
+                      ((((long long)bt << mb) + m0 + g) << kb);
+    const float* A8 = A0 + (8ll << kb);
+    const float* Bn = data + 2 * (a.scratch_b + i * a.scratch_stride) +
+                      ((((long long)bt << nb) + n0 + g) << kb);
+    auto kv = [&](const float* P, int k) -> float { return (kfull || k < K) ? P[k] : 0.f; };
     float cr[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f};
     if constexpr (MODE == GEMM_TC_BF16) {
       for (int k0 = 0; k0 < K; k0 += 16) {
-        unsigned int ar_[4], ai_[4], nai_[4], br_[2], bi_[2];
         const int ka = k0 + 2 * t;
-        ar_[0] = pack_bf16(ld(Ar, m0 + g, M, ka), ld(Ar, m0 + g, M, ka + 1));
-        ar_[1] = pack_bf16(ld(Ar, m0 + g + 8, M, ka), ld(Ar, m0 + g + 8, M, ka + 1));
-        ar_[2] = pack_bf16(ld(Ar, m0 + g, M, ka + 8), ld(Ar, m0 + g, M, ka + 9));
-        ar_[3] = pack_bf16(ld(Ar, m0 + g + 8, M, ka + 8), ld(Ar, m0 + g + 8, M, ka + 9));
-        ai_[0] = pack_bf16(ld(Ai, m0 + g, M, ka), ld(Ai, m0 + g, M, ka + 1));
-        ai_[1] = pack_bf16(ld(Ai, m0 + g + 8, M, ka), ld(Ai, m0 + g + 8, M, ka + 1));
-        ai_[2] = pack_bf16(ld(Ai, m0 + g, M, ka + 8), ld(Ai, m0 + g, M, ka + 9));
-        ai_[3] = pack_bf16(ld(Ai, m0 + g + 8, M, ka + 8), ld(Ai, m0 + g + 8, M, ka + 9));
-        nai_[0] = ai_[0] ^ 0x80008000u;
-        nai_[1] = ai_[1] ^ 0x80008000u;
-        nai_[2] = ai_[2] ^ 0x80008000u;
-        nai_[3] = ai_[3] ^ 0x80008000u;
-        br_[0] = pack_bf16(ld(Br, n0 + g, N, ka), ld(Br, n0 + g, N, ka + 1));
-        br_[1] = pack_bf16(ld(Br, n0 + g, N, ka + 8), ld(Br, n0 + g, N, ka + 9));
-        bi_[0] = pack_bf16(ld(Bi, n0 + g, N, ka), ld(Bi, n0 + g, N, ka + 1));
-        bi_[1] = pack_bf16(ld(Bi, n0 + g, N, ka + 8), ld(Bi, n0 + g, N, ka + 9));
+        unsigned int ar_[4], ai_[4], nai_[4], br_[2], bi_[2];
+        ar_[0] = pack_bf16(kv(A0, ka), kv(A0, ka + 1));
+        ar_[1] = pack_bf16(kv(A8, ka), kv(A8, ka + 1));
+        ar_[2] = pack_bf16(kv(A0, ka + 8), kv(A0, ka + 9));
+        ar_[3] = pack_bf16(kv(A8, ka + 8), kv(A8, ka + 9));
+        ai_[0] = pack_bf16(kv(A0 + pa, ka), kv(A0 + pa, ka + 1));
+        ai_[1] = pack_bf16(kv(A8 + pa, ka), kv(A8 + pa, ka + 1));
+        ai_[2] = pack_bf16(kv(A0 + pa, ka + 8), kv(A0 + pa, ka + 9));
+        ai_[3] = pack_bf16(kv(A8 + pa, ka + 8), kv(A8 + pa, ka + 9));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) nai_[q] = ai_[q] ^ 0x80008000u;
+        br_[0] = pack_bf16(kv(Bn, ka), kv(Bn, ka + 1));
+        br_[1] = pack_bf16(kv(Bn, ka + 8), kv(Bn, ka + 9));
+        bi_[0] = pack_bf16(kv(Bn + pb, ka), kv(Bn + pb, ka + 1));
+        bi_[1] = pack_bf16(kv(Bn + pb, ka + 8), kv(Bn + pb, ka + 9));
         mma_bf16(cr, ar_, br_);
         mma_bf16(cr, nai_, bi_);
         mma_bf16(ci, ar_, bi_);
@@ -258,12 +332,11 @@ __global__ void k_gemm_tc(const GemmArgs a, float* data, GMeta* meta) {
       }
     } else {
       for (int k0 = 0; k0 < K; k0 += 8) {
-        const float far[4] = {ld(Ar, m0 + g, M, k0 + t), ld(Ar, m0 + g + 8, M, k0 + t),
-                              ld(Ar, m0 + g, M, k0 + t + 4), ld(Ar, m0 + g + 8, M, k0 + t + 4)};
-        const float fai[4] = {ld(Ai, m0 + g, M, k0 + t), ld(Ai, m0 + g + 8, M, k0 + t),
-                              ld(Ai, m0 + g, M, k0 + t + 4), ld(Ai, m0 + g + 8, M, k0 + t + 4)};
-        const float fbr[2] = {ld(Br, n0 + g, N, k0 + t), ld(Br, n0 + g, N, k0 + t + 4)};
-        const float fbi[2] = {ld(Bi, n0 + g, N, k0 + t), ld(Bi, n0 + g, N, k0 + t + 4)};
+        const float far[4] = {kv(A0, k0 + t), kv(A8, k0 + t), kv(A0, k0 + t + 4), kv(A8, k0 + t + 4)};
+        const float fai[4] = {kv(A0 + pa, k0 + t), kv(A8 + pa, k0 + t), kv(A0 + pa, k0 + t + 4),
+                              kv(A8 + pa, k0 + t + 4)};
+        const float fbr[2] = {kv(Bn, k0 + t), kv(Bn, k0 + t + 4)};
+        const float fbi[2] = {kv(Bn + pb, k0 + t), kv(Bn + pb, k0 + t + 4)};
         unsigned int arh[4], aih[4], naih[4], brh[2], bih[2];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -293,7 +366,6 @@ __global__ void k_gemm_tc(const GemmArgs a, float* data, GMeta* meta) {
             brl[q] = to_tf32(fbr[q] - __uint_as_float(brh[q]));
             bil[q] = to_tf32(fbi[q] - __uint_as_float(bih[q]));
           }
-          // hi*lo and lo*hi terms
           mma_tf32(cr, arh, brl);
           mma_tf32(cr, naih, bil);
           mma_tf32(ci, arh, bil);
@@ -305,15 +377,15 @@ __global__ void k_gemm_tc(const GemmArgs a, float* data, GMeta* meta) {
         }
       }
     }
+    const long long obase = a.out_base + i * a.out_slice_stride;
+    const unsigned int ub = pdep_lut(Lb, bt);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int m = m0 + g + (q >= 2 ? 8 : 0);
       const int n = n0 + 2 * t + (q & 1);
-      if (m < M && n < N) {
-        const long long o = a.out_base + i * a.out_slice_stride + out_index(a, bt, m, n);
-        reinterpret_cast<float2*>(data)[o] = make_float2(cr[q], ci[q]);
-        mx = fmaxf(mx, fmaxf(fabsf(cr[q]), fabsf(ci[q])));
-      }
+      const unsigned int U = ub | pdep_lut(Lm, (unsigned)m) | pdep_lut(Ln, (unsigned)n);
+      reinterpret_cast<float2*>(data)[obase + (U >> a.nsum)] = make_float2(cr[q], ci[q]);
+      mx = fmaxf(mx, fmaxf(fabsf(cr[q]), fabsf(ci[q])));
     }
     if (r == 0 && lane == 0) write_meta_e(a, meta, i);
   }
@@ -337,8 +409,7 @@ int gemm_launch(const GemmArgs& a, int mode, float* data, GMeta* meta, cudaStrea
     const long long outs = a.nslices << (bb + mb + nb);
     k_gemm_simt<<<grid_for(outs, 256), 256, 0, s>>>(a, data, meta);
   } else {
-    const long long items =
-        a.nslices * (long long)(((1 << mb) + 15) / 16) * (((1 << nb) + 7) / 8) << bb;
+    const long long items = a.nslices * (long long)((1 << mb) / 16) * ((1 << nb) / 8) << bb;
     const unsigned grid = grid_for(items * 32, 128);
     if (mode == GEMM_TC_TF32) k_gemm_tc<GEMM_TC_TF32><<<grid, 128, 0, s>>>(a, data, meta);
     else if (mode == GEMM_TC_BF16) k_gemm_tc<GEMM_TC_BF16><<<grid, 128, 0, s>>>(a, data, meta);

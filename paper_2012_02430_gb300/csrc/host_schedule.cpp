@@ -312,7 +312,13 @@ bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePla
       g.mM = O & A & ~B;
       g.mN = O & B & ~A;
       g.mBt = O & A & B;
-      if (__builtin_popcount(g.mK) > 7) continue;
+      int per_side[2] = {0, 0};
+      for (int8_t sd : side) per_side[sd]++;
+      if (__builtin_popcount(g.mK) > 7 || g.u > 32 || per_side[0] > 8 || per_side[1] > 8 ||
+          __builtin_popcount(g.mM) > 24 || __builtin_popcount(g.mN) > 24 ||
+          __builtin_popcount(g.mBt) > 24 || __builtin_popcount(g.mSA) > 8 ||
+          __builtin_popcount(g.mSB) > 8)
+        continue;
       g.gemm = true;
       g.gA = a;
       g.gB = bb;
