@@ -98,6 +98,23 @@ qt_status qt_set_angles(qt_net* net, const double* gammas, const double* betas);
 qt_status qt_set_bitstring(qt_net* net, const uint8_t* bitstring);
 
 /*
+ * A batch of 2^a amplitudes in one contraction (Sec. VII): the last mixer of
+ * each listed qubit keeps its output index open instead of being fixed to z_v.
+ * Open qubit j (qubits[j], distinct, in [0, n_vertices)) becomes variable
+ * n_vertices*p + j; the open indices form a clique of the line graph, are never
+ * eliminated nor sliced, and the result is a tensor over them: entry b
+ * (bit j of b = value of qubit qubits[j]) is the amplitude of the bitstring z
+ * with those qubits replaced. The bits of z at open qubits are ignored.
+ * a = 0 (qubits may be NULL) returns to a single amplitude. Discards the order,
+ * slicing and schedule (call qt_order again). qt_run then writes 2^a
+ * amplitudes; qt_contract_batch returns them.
+ * Errors: QT_EINVAL for a < 0, a > QT_MAX_OPEN, a null list with a > 0, a
+ * repeated or out-of-range qubit.
+ */
+enum { QT_MAX_OPEN = 16 };
+qt_status qt_set_open(qt_net* net, const int32_t* qubits, int32_t a);
+
+/*
  * Greedy elimination order of the line graph (Sec. V.A.1) and its contraction
  * width c = max over steps of the eliminated vertex's neighbour count
  * (Sec. IV.B). seed is reserved for randomised rules and ignored by the greedy
@@ -174,7 +191,8 @@ qt_status qt_upload(qt_net* net, void* workspace, size_t workspace_bytes, void* 
  * Device-resident run: contracts slices [first, first + count) of the uploaded
  * network and writes their FP64 sum (times 2^(-N/2)) as two doubles (re, im)
  * to the DEVICE pointer d_out, asynchronously on `stream`; no host copy, no
- * synchronisation. The unsliced prefix (contract_first) is recomputed by every
+ * synchronisation. With a open qubits (qt_set_open) d_out receives 2^a such
+ * pairs, amplitude b at d_out[2b], d_out[2b+1]. The unsliced prefix (contract_first) is recomputed by every
  * call. Errors: QT_ESTATE before qt_prepare; QT_EINVAL for a range outside
  * [0, 2^k) or a null d_out; QT_ENOMEM for a small workspace; QT_ECUDA.
  */
@@ -189,6 +207,15 @@ qt_status qt_run(qt_net* net, int64_t first, int64_t count, void* workspace, siz
  */
 qt_status qt_contract(qt_net* net, int32_t precision, void* workspace, size_t workspace_bytes,
                       void* stream, double* amp_re, double* amp_im);
+
+/*
+ * As qt_contract for a network with a >= 0 open qubits (Sec. VII): writes the
+ * 2^a amplitudes to the HOST array amps (2^(a+1) doubles, amplitude b at
+ * amps[2b], amps[2b+1]). qt_contract itself requires a = 0 (QT_ESTATE
+ * otherwise). Errors: as qt_contract; QT_EINVAL for a null amps.
+ */
+qt_status qt_contract_batch(qt_net* net, int32_t precision, void* workspace,
+                            size_t workspace_bytes, void* stream, double* amps);
 
 /* Plan bookkeeping: greedy ordering runs made by the last qt_order/qt_slice/
  * qt_slice_learned and the plan's cost sum over its steps of 2^width. */
@@ -271,10 +298,17 @@ void qt_mlp_free(qt_mlp* mlp);
  *                  (slice range, workspace, output) and replays the CUDA
  *                  graph; 0: direct launches.
  *   QT_OPT_GEMM    1: launches in GEMM form also use it in QT_FP32_SIMT mode
- *                  (CUDA-core GEMM); 0 (default): there only the autotuner may
+ *                  (CUDA-core GEMM: when every summed index is in both large
+ *                  tensors, a shared-memory tiled kernel over the lowest U bits
+ *                  after folding the small tensors into their side; else pack
+ *                  kernels + GEMM); 0 (default): there only the autotuner may
  *                  pick it. Discards the prepared schedule.
+ *   QT_OPT_SEGMENTS 1 (default): two or more consecutive small launches (union
+ *                  of at most 14 indices) run as one segment launch, one block
+ *                  per slice stepping through them with block barriers; 0: one
+ *                  launch each. Discards the prepared schedule.
  * Errors: QT_EINVAL for a null network or an unknown option. */
-enum { QT_OPT_FUSION = 1, QT_OPT_GRAPHS = 2, QT_OPT_GEMM = 3 };
+enum { QT_OPT_FUSION = 1, QT_OPT_GRAPHS = 2, QT_OPT_GEMM = 3, QT_OPT_SEGMENTS = 4 };
 qt_status qt_set_option(qt_net* net, int32_t option, int64_t value);
 
 /*

@@ -92,35 +92,48 @@ def fix_indices(tensors, values):
     return out
 
 
-def contract_amplitude(tensors, order, sliced=(), slice_step=0, slice_ids=None):
+def _finish(scalar, rest, open_vars):
+    """Product of the scalar and the tensors left over the open variables (outer
+    product into a tensor with axis j = open_vars[j]); a scalar when none is open."""
+    if not open_vars:
+        if rest:
+            raise ValueError("variables left uneliminated")
+        return scalar
+    for labels, _ in rest:
+        if not set(labels) <= set(open_vars):
+            raise ValueError("variables left uneliminated")
+    out = _einsum_product_sum(rest, list(open_vars)) if rest else np.ones((2,) * len(open_vars))
+    return scalar * np.asarray(out)
+
+
+def contract_amplitude(tensors, order, sliced=(), slice_step=0, slice_ids=None, open_vars=()):
     """Full contraction of the network along `order` with the given slicing.
 
     Returns (total, per_slice): total is the sum of the slice results over
     slice_ids (all 2^k ids when None) and per_slice the list of those results.
-    Without sliced variables there is one slice and slice_step is ignored.
+    Without sliced variables there is one slice and slice_step is ignored. With
+    open variables (a batch of amplitudes, Sec. VII) the results are tensors over
+    them (axis j = open_vars[j]).
     """
     sliced = list(sliced)
     k = len(sliced)
     pos = {v: i for i, v in enumerate(order)}
     if k == 0:
         s, rest = eliminate_buckets(tensors, list(order), pos)
-        if rest:
-            raise ValueError("variables left uneliminated")
-        return s, [s]
+        res = _finish(s, rest, open_vars)
+        return res, [res]
     prefix = list(order[:slice_step])
     suffix = list(order[slice_step:])
     pre_scalar, remaining = eliminate_buckets(tensors, prefix, pos)
     if slice_ids is None:
         slice_ids = range(1 << k)
     per_slice = []
-    total = complex(0.0)
+    total = 0
     for sid in slice_ids:
         values = {v: (sid >> j) & 1 for j, v in enumerate(sliced)}
         part = fix_indices(remaining, values)
         s, rest = eliminate_buckets(part, suffix, pos)
-        if rest:
-            raise ValueError("variables left uneliminated")
-        res = pre_scalar * s
+        res = pre_scalar * _finish(s, rest, open_vars)
         per_slice.append(res)
-        total += res
+        total = total + res
     return total, per_slice

@@ -46,17 +46,25 @@ def phase_matrix(gamma: float) -> np.ndarray:
     return np.array([[1.0, e], [e, 1.0]], dtype=np.complex128)
 
 
-def build_network(n, edges, p, gammas, betas, z):
+def build_network(n, edges, p, gammas, betas, z, open_qubits=()):
     """Tensors of <z| U(gamma, beta) |+>^N, unnormalised.
 
     Returns (tensors, n_vars, norm): tensors is a list of (labels, data) with
     labels a tuple of variable ids and data an ndarray of shape (2,)*len(labels)
     whose axis t is labels[t]; the amplitude is norm * (full contraction).
+
+    Several amplitudes (Sec. VII): for the j-th qubit v of open_qubits the last
+    mixer keeps its output index as the variable n*p + j instead of being folded
+    with z_v; the contraction is then a tensor over those a variables whose entry
+    b (bit j = b_j) is the amplitude of z with z_v replaced by b_j.
     """
     if p < 1:
         raise ValueError("p must be >= 1")
     if len(gammas) != p or len(betas) != p or len(z) != n:
         raise ValueError("length mismatch")
+    open_index = {v: j for j, v in enumerate(open_qubits)}
+    if len(open_index) != len(open_qubits) or any(not 0 <= v < n for v in open_qubits):
+        raise ValueError("bad open qubits")
     tensors = []
     plus = np.array([1.0, 1.0], dtype=np.complex128)
     for v in range(n):
@@ -69,9 +77,21 @@ def build_network(n, edges, p, gammas, betas, z):
         for v in range(n):
             if k < p:
                 tensors.append(((var_id(v, k - 1, n), var_id(v, k, n)), mmat.copy()))
+            elif v in open_index:
+                tensors.append(((var_id(v, p - 1, n), n * p + open_index[v]), mmat.copy()))
             else:
                 tensors.append(((var_id(v, p - 1, n),), mmat[:, z[v]].copy()))
-    return tensors, n * p, 2.0 ** (-n / 2.0)
+    return tensors, n * p + len(open_index), 2.0 ** (-n / 2.0)
+
+
+def open_clique(adj_sets, n, p, a):
+    """The clique the open variables form (Sec. VII: the result tensor over them)."""
+    opens = [n * p + j for j in range(a)]
+    for x in opens:
+        for y in opens:
+            if x != y:
+                adj_sets[x].add(y)
+    return adj_sets
 
 
 def line_graph(tensors, n_vars):

@@ -30,20 +30,22 @@ def adjacency_matrix(adj_sets, n_vars):
     return a
 
 
-def greedy_order(adj: np.ndarray, alive=None, algo: int = MIN_FILL):
+def greedy_order(adj: np.ndarray, alive=None, algo: int = MIN_FILL, keep=None):
     """Greedy order of the alive vertices of the symmetric boolean matrix adj.
 
     Returns (order, widths): widths[i] is the neighbour count of order[i] when it
-    is eliminated. adj is not modified.
+    is eliminated. adj is not modified. Vertices marked in `keep` (open indices of
+    a batch of amplitudes) stay in the graph and are never eliminated.
     """
     a = adj.copy()
     n = a.shape[0]
     alive = np.ones(n, dtype=bool) if alive is None else alive.copy()
+    keep = np.zeros(n, dtype=bool) if keep is None else np.asarray(keep, dtype=bool)
     np.fill_diagonal(a, False)
     a[~alive, :] = False
     a[:, ~alive] = False
     order, widths = [], []
-    while alive.any():
+    while (alive & ~keep).any():
         ids = np.flatnonzero(alive)
         sub = a[np.ix_(ids, ids)]
         deg = sub.sum(axis=1).astype(np.int64)
@@ -57,6 +59,7 @@ def greedy_order(adj: np.ndarray, alive=None, algo: int = MIN_FILL):
             key = np.lexsort((ids, deg))
         else:
             raise ValueError("unknown ordering algorithm")
+        key = [i for i in key if not keep[ids[i]]]
         v = int(ids[key[0]])
         nb = np.flatnonzero(a[v])
         order.append(v)

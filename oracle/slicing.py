@@ -41,19 +41,21 @@ def _plan_cost(widths):
 
 
 def step_dependent_slicing(adj: np.ndarray, algo: int = MIN_FILL, width_limit: int = 1 << 30,
-                           max_vars: int = 0, r: int = 1):
-    """Returns a dict with the schedule: order, sliced, slice_step, rounds, width, widths."""
+                           max_vars: int = 0, r: int = 1, keep=None):
+    """Returns a dict with the schedule: order, sliced, slice_step, rounds, width, widths.
+    Vertices in `keep` (open indices) are never eliminated nor sliced."""
     if width_limit < 1 or r < 1 or max_vars < 0:
         raise ValueError("bad slicing parameters")
     a = adj.copy()
     np.fill_diagonal(a, False)
     n = a.shape[0]
     alive = np.ones(n, dtype=bool)
-    order, widths = greedy_order(a, alive, algo)
+    keep = np.zeros(n, dtype=bool) if keep is None else np.asarray(keep, dtype=bool)
+    order, widths = greedy_order(a, alive, algo, keep)
     done_order, done_widths = [], []
     sliced, rounds = [], []
     width = max(widths, default=0)
-    while width > width_limit and len(sliced) < max_vars and alive.any():
+    while width > width_limit and len(sliced) < max_vars and (alive & ~keep).any():
         rr = min(r, max_vars - len(sliced))
         peak = int(np.argmax(widths))
         best = None
@@ -64,14 +66,14 @@ def step_dependent_slicing(adj: np.ndarray, algo: int = MIN_FILL, width_limit: i
                 eliminate(b, al, v)
             removed = []
             for _ in range(rr):
-                ids = np.flatnonzero(al)
+                ids = np.flatnonzero(al & ~keep)
                 if len(ids) == 0:
                     break
                 deg = b[ids].sum(axis=1)
                 v = int(ids[np.lexsort((ids, -deg))[0]])
                 remove_vertex(b, al, v)
                 removed.append(v)
-            o2, w2 = greedy_order(b, al, algo)
+            o2, w2 = greedy_order(b, al, algo, keep)
             plan_w = done_widths + widths[:s] + w2
             key = (max(plan_w, default=0), _plan_cost(plan_w), s)
             if best is None or key < best[0]:

@@ -15,7 +15,8 @@ void build_stage(qt_net* net);
 qt_status upload(qt_net* net, void* ws, size_t bytes, void* stream, std::string& err);
 qt_status run(qt_net* net, long long first, long long count, void* ws, void* stream,
               double* d_out, std::string& err);
-qt_status download_result(const double* d_out, double* host, void* stream, std::string& err);
+qt_status download_result(const double* d_out, double* host, int64_t n_doubles, void* stream,
+                          std::string& err);
 void prof_clear(qt_net* net);
 qt_status autotune(qt_net* net, void* ws, void* stream, std::string& report, std::string& err);
 qt_status prof_read(qt_net* net, std::string& out, std::string& err);
@@ -52,8 +53,15 @@ void make_tensors(qt_net* net) {
       T.push_back({{var(u, k - 1), var(w, k - 1)}, {1.0, 0.0, er, ei, er, ei, 1.0, 0.0}});
     }
     for (int v = 0; v < n; ++v) {
+      int j = -1;  // open qubit number, Sec. VII
+      if (k == p)
+        for (size_t t = 0; t < net->open.size(); ++t)
+          if (net->open[t] == v) j = (int)t;
       if (k < p) {
         T.push_back({{var(v, k - 1), var(v, k)}, {c, 0.0, 0.0, -s, 0.0, -s, c, 0.0}});
+      } else if (j >= 0) {
+        // the whole mixer, its output index left open as variable n*p + j
+        T.push_back({{var(v, p - 1), n * p + j}, {c, 0.0, 0.0, -s, 0.0, -s, c, 0.0}});
       } else {
         // row a' = z_v of M, as a function of a
         if (net->z[v] == 0) T.push_back({{var(v, p - 1)}, {c, 0.0, 0.0, -s}});
@@ -149,13 +157,35 @@ qt_status qt_set_bitstring(qt_net* net, const uint8_t* bitstring) {
   return ok();
 }
 
+qt_status qt_set_open(qt_net* net, const int32_t* qubits, int32_t a) {
+  if (!check_net(net)) return fail(QT_EINVAL, "qt_set_open: null network");
+  if (a < 0 || a > QT_MAX_OPEN || (a > 0 && !qubits))
+    return fail(QT_EINVAL, "qt_set_open: need 0 <= a <= QT_MAX_OPEN and a qubit list");
+  std::set<int32_t> seen;
+  for (int j = 0; j < a; ++j)
+    if (qubits[j] < 0 || qubits[j] >= net->n || !seen.insert(qubits[j]).second)
+      return fail(QT_EINVAL, "qt_set_open: qubit repeated or out of range");
+  try {
+    net->open.assign(qubits, qubits + a);
+    net->n_vars = net->n * net->p + a;
+    make_tensors(net);
+  } catch (const std::bad_alloc&) {
+    return fail(QT_ENOMEM, "qt_set_open: out of host memory");
+  }
+  net->plan = qt::SlicePlan();
+  net->ordered = false;
+  net->sched = qt::Schedule();
+  net->stage_dirty = true;
+  return ok();
+}
+
 qt_status qt_order(qt_net* net, int32_t algo, uint64_t seed, int32_t* width_out) {
   (void)seed;
   if (!check_net(net)) return fail(QT_EINVAL, "qt_order: null network");
   if (algo != QT_GREEDY_MINFILL && algo != QT_GREEDY_MINDEG)
     return fail(QT_EINVAL, "qt_order: unknown ordering rule");
   try {
-    qt::BitGraph g = qt::line_graph(net->tensors, net->n_vars);
+    qt::BitGraph g = qt::network_graph(net);
     qt::OrderResult r = qt::greedy_order(g, algo);
     net->plan = qt::SlicePlan();
     net->plan.order = r.order;
@@ -181,7 +211,7 @@ qt_status qt_slice(qt_net* net, int32_t width_limit, int32_t max_vars, int32_t r
   if (width_limit < 1 || r < 1 || max_vars < 0 || max_vars > 30)
     return fail(QT_EINVAL, "qt_slice: need width_limit >= 1, r >= 1, 0 <= max_vars <= 30");
   try {
-    qt::BitGraph g = qt::line_graph(net->tensors, net->n_vars);
+    qt::BitGraph g = qt::network_graph(net);
     net->plan = qt::step_dependent_slicing(g, net->algo, width_limit, max_vars, r);
     net->sched = qt::Schedule();
     net->stage_dirty = true;
@@ -250,7 +280,7 @@ qt_status qt_prepare(qt_net* net, int32_t precision, int32_t batch, size_t* work
   std::string err;
   try {
     if (!qt::compile_schedule(net->tensors, net->n_vars, net->plan, precision, batch, net->fuse,
-                              net->sched, err)) {
+                              net->sched, err, (int)net->open.size())) {
       net->sched = qt::Schedule();
       return fail(err.find("rank") != std::string::npos ? QT_ERANGE : QT_EINVAL,
                   "qt_prepare: " + err);
@@ -315,10 +345,10 @@ qt_status qt_run(qt_net* net, int64_t first, int64_t count, void* workspace, siz
   return ok();
 }
 
-qt_status qt_contract(qt_net* net, int32_t precision, void* workspace, size_t workspace_bytes,
-                      void* stream, double* amp_re, double* amp_im) {
-  if (!check_net(net) || !amp_re || !amp_im) return fail(QT_EINVAL, "qt_contract: null argument");
-  if (!net->ordered) return fail(QT_ESTATE, "qt_contract: call qt_order first");
+static qt_status contract_impl(qt_net* net, int32_t precision, void* workspace,
+                               size_t workspace_bytes, void* stream, double* host_out,
+                               const char* who) {
+  if (!net->ordered) return fail(QT_ESTATE, std::string(who) + ": call qt_order first");
   if (!net->sched.valid || net->sched.precision != precision) {
     // the largest batch whose workspace fits
     size_t need = 0;
@@ -335,20 +365,38 @@ qt_status qt_contract(qt_net* net, int32_t precision, void* workspace, size_t wo
     s = qt_prepare(net, precision, (int32_t)lo, &need);
     if (s != QT_OK) return s;
   }
-  qt_status s = check_ws(net, workspace, workspace_bytes, "qt_contract");
+  qt_status s = check_ws(net, workspace, workspace_bytes, who);
   if (s != QT_OK) return s;
   std::string err;
   s = qt::upload(net, workspace, workspace_bytes, stream, err);
-  if (s != QT_OK) return fail(s, "qt_contract: " + err);
-  double* d_out = reinterpret_cast<double*>((char*)workspace + net->sched.off_acc + 16);
+  if (s != QT_OK) return fail(s, std::string(who) + ": " + err);
+  const int64_t A = net->sched.n_amps;
+  double* d_out = reinterpret_cast<double*>((char*)workspace + net->sched.off_acc + 16 * A);
   s = qt::run(net, 0, net->sched.nslices, workspace, stream, d_out, err);
-  if (s != QT_OK) return fail(s, "qt_contract: " + err);
+  if (s != QT_OK) return fail(s, std::string(who) + ": " + err);
+  s = qt::download_result(d_out, host_out, 2 * A, stream, err);
+  if (s != QT_OK) return fail(s, std::string(who) + ": " + err);
+  return ok();
+}
+
+qt_status qt_contract(qt_net* net, int32_t precision, void* workspace, size_t workspace_bytes,
+                      void* stream, double* amp_re, double* amp_im) {
+  if (!check_net(net) || !amp_re || !amp_im) return fail(QT_EINVAL, "qt_contract: null argument");
+  if (!net->open.empty())
+    return fail(QT_ESTATE, "qt_contract: the network has open qubits; use qt_contract_batch");
   double h[2];
-  s = qt::download_result(d_out, h, stream, err);
-  if (s != QT_OK) return fail(s, "qt_contract: " + err);
+  qt_status s = contract_impl(net, precision, workspace, workspace_bytes, stream, h, "qt_contract");
+  if (s != QT_OK) return s;
   *amp_re = h[0];
   *amp_im = h[1];
   return ok();
+}
+
+qt_status qt_contract_batch(qt_net* net, int32_t precision, void* workspace,
+                            size_t workspace_bytes, void* stream, double* amps) {
+  if (!check_net(net) || !amps) return fail(QT_EINVAL, "qt_contract_batch: null argument");
+  return contract_impl(net, precision, workspace, workspace_bytes, stream, amps,
+                       "qt_contract_batch");
 }
 
 qt_status qt_profile(qt_net* net, int32_t enable) {
@@ -447,6 +495,10 @@ qt_status qt_set_option(qt_net* net, int32_t option, int64_t value) {
       break;
     case QT_OPT_GEMM:
       net->force_gemm = value != 0;
+      net->sched = qt::Schedule();  // prepare again
+      break;
+    case QT_OPT_SEGMENTS:
+      net->segments = value != 0;
       net->sched = qt::Schedule();  // prepare again
       break;
     default:

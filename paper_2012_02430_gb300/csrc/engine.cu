@@ -58,10 +58,12 @@ struct Meta {
   int E;                // exponent: true value = stored * 2^E
 };
 
+// A factor of the slice result: a tensor over open (omask, bit j = open index j)
+// and sliced (smask) indices only, stored (open bits, slice bits) from bit 0 up.
 struct ScalarTerm {
   long long base, slice_stride, meta;
-  unsigned int smask;
-  int per_slice;
+  unsigned int smask, omask;
+  int per_slice, pad;
 };
 static_assert(sizeof(ScalarTerm) == kScalarTermBytes, "scalar table record size");
 
@@ -206,6 +208,84 @@ __global__ void __launch_bounds__(256) k_bucket_flat(const KStep st, R* data, Me
     const unsigned int red = __reduce_max_sync(peers, __float_as_uint(mx));
     if (active && lane == __ffs(peers) - 1 && red != 0u)
       atomicMax(&meta[st.out_meta + (st.out_meta_per_slice ? i : 0)].maxabs, red);
+  }
+}
+
+static_assert(sizeof(KStep) <= kStepRecordBytes, "step record size");
+
+// Segment kernel: a run of consecutive small launches as one launch. Block b
+// handles slice b of the batch and runs the run's steps one after another with
+// a block barrier between them (a step's operands are earlier results of the
+// same slice, gates or prefix tensors, so no other block is waited for). Each
+// step is the flat kernel's arithmetic restricted to one slice.
+constexpr int SEG_THREADS = 512;
+constexpr int SEG_MAX_U = 14;
+
+template <typename R>
+__global__ void __launch_bounds__(SEG_THREADS) k_segment(const KStep* steps, int nsteps, R* data,
+                                                        Meta* meta, long long slice_first) {
+  __shared__ KStep st;
+  const long long i = blockIdx.x;
+  const unsigned long long sid = (unsigned long long)(slice_first + i);
+  const int lane = threadIdx.x & 31;
+  for (int q = 0; q < nsteps; ++q) {
+    const int* src = reinterpret_cast<const int*>(steps + q);
+    int* dst = reinterpret_cast<int*>(&st);
+    for (int w = threadIdx.x; w < (int)(sizeof(KStep) / 4); w += blockDim.x) dst[w] = src[w];
+    __syncthreads();
+    const long long npairs = 1ll << (st.u - 1);
+    const int grp = 1 << (st.nsum - 1);
+    int Eout = 0;
+    for (int j = 0; j < st.m; ++j) {
+      const Meta mt = meta[st.op[j].meta + (st.op[j].meta_per_slice ? i : 0)];
+      Eout += mt.E + scale_exp(mt.maxabs);
+    }
+    float mx = 0.f;
+    for (long long b0 = 0; b0 < npairs; b0 += blockDim.x) {
+      const long long g = b0 + threadIdx.x;
+      const bool active = g < npairs;
+      const unsigned long long I = (unsigned long long)(active ? g : 0) << 1;
+      R p0r = 1, p0i = 0, p1r = 1, p1i = 0;
+      if (active) {
+        for (int j = 0; j < st.m; ++j) {
+          const KOp& o = st.op[j];
+          if (o.level != 0) continue;
+          long long off = o.base + i * o.slice_stride + (long long)pext64(I, o.umask);
+          if (o.smask) off += (long long)(pext64(sid, o.smask) << o.sshift);
+          const R sc = pow2_neg<R>(scale_exp(meta[o.meta + (o.meta_per_slice ? i : 0)].maxabs));
+          R r0, i0, r1, i1;
+          load_pair<R>(data, off, o.umask & 1u, r0, i0, r1, i1);
+          cmul<R>(p0r, p0i, r0 * sc, i0 * sc);
+          cmul<R>(p1r, p1i, r1 * sc, i1 * sc);
+        }
+      }
+      R sr = active ? p0r + p1r : R(0), si = active ? p0i + p1i : R(0);
+      for (int l = 1; l < st.nsum; ++l) {
+        if (active) {
+          for (int j = 0; j < st.m; ++j) {
+            const KOp& o = st.op[j];
+            if (o.level != l) continue;
+            long long off = o.base + i * o.slice_stride + (long long)pext64(I, o.umask);
+            if (o.smask) off += (long long)(pext64(sid, o.smask) << o.sshift);
+            const R sc = pow2_neg<R>(scale_exp(meta[o.meta + (o.meta_per_slice ? i : 0)].maxabs));
+            using C2 = typename CT<R>::c2;
+            const C2 a = *reinterpret_cast<const C2*>(data + 2 * off);
+            cmul<R>(sr, si, a.x * sc, a.y * sc);
+          }
+        }
+        sr += __shfl_xor_sync(0xffffffffu, sr, 1 << (l - 1));
+        si += __shfl_xor_sync(0xffffffffu, si, 1 << (l - 1));
+      }
+      if (active && (lane & (grp - 1)) == 0) {
+        store_out<R>(data, st.out_base + i * st.out_slice_stride + (long long)(I >> st.nsum), sr, si);
+        mx = fmaxf(mx, absmax(sr, si));
+      }
+    }
+    const unsigned int red = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+    if (lane == 0 && red != 0u)
+      atomicMax(&meta[st.out_meta + (st.out_meta_per_slice ? i : 0)].maxabs, red);
+    if (threadIdx.x == 0) meta[st.out_meta + (st.out_meta_per_slice ? i : 0)].E = Eout;
+    __syncthreads();
   }
 }
 
@@ -527,19 +607,23 @@ __global__ void __launch_bounds__(TILE_THREADS, variant_minb(V))
     atomicMax(&meta[st.out_meta + (st.out_meta_per_slice ? cur_slice : 0)].maxabs, blkmax);
 }
 
-// Per slice: product of the scalar factors in FP64, exponent applied.
+// Per (slice, amplitude): product of the slice result's factors in FP64 with
+// the exponent applied; partials[i][b], b over the 2^a open-index values.
 template <typename R>
 __global__ void k_finalize(const ScalarTerm* terms, int nterms, const R* data, const Meta* meta,
-                           long long nslices, long long slice_first, double2* partials) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nslices) return;
+                           long long nslices, long long slice_first, int a, double2* partials) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (nslices << a)) return;
+  const long long i = idx >> a;
+  const unsigned int b = (unsigned int)(idx & ((1ll << a) - 1));
   const unsigned long long sid = (unsigned long long)(slice_first + i);
   double pr = 1.0, pi = 0.0;
   long long E = 0;
   for (int t = 0; t < nterms; ++t) {
     const ScalarTerm& s = terms[t];
     long long off = s.base + (s.per_slice ? i * s.slice_stride : 0);
-    if (s.smask) off += (long long)pext64(sid, s.smask);
+    if (s.omask) off += (long long)pext64(b, s.omask);
+    if (s.smask) off += (long long)pext64(sid, s.smask) << __popc(s.omask);
     const double vr = (double)data[2 * off], vi = (double)data[2 * off + 1];
     const double nr = pr * vr - pi * vi, ni = pr * vi + pi * vr;
     pr = nr;
@@ -547,18 +631,21 @@ __global__ void k_finalize(const ScalarTerm* terms, int nterms, const R* data, c
     E += meta[s.meta + (s.per_slice ? i : 0)].E;
   }
   const int e = (int)max(-100000ll, min(100000ll, E));
-  partials[i] = make_double2(ldexp(pr, e), ldexp(pi, e));
+  partials[idx] = make_double2(ldexp(pr, e), ldexp(pi, e));
 }
 
-// Fixed-order FP64 sum of a batch's slice results into the accumulator:
-// thread t adds partials t, t+1024, ... in order, then a fixed tree.
-__global__ void __launch_bounds__(1024) k_reduce(const double2* partials, long long n,
+// Fixed-order FP64 sum of a batch's slice results into the accumulators: block
+// b handles amplitude b; thread t adds slices t, t+1024, ... in order, then a
+// fixed tree.
+__global__ void __launch_bounds__(1024) k_reduce(const double2* partials, long long n, int a,
                                                  double2* acc, int first_batch) {
   __shared__ double sr[1024], si[1024];
+  const long long A = 1ll << a;
+  const long long b = blockIdx.x;
   double r = 0.0, im = 0.0;
   for (long long j = threadIdx.x; j < n; j += 1024) {
-    r += partials[j].x;
-    im += partials[j].y;
+    r += partials[j * A + b].x;
+    im += partials[j * A + b].y;
   }
   sr[threadIdx.x] = r;
   si[threadIdx.x] = im;
@@ -572,18 +659,20 @@ __global__ void __launch_bounds__(1024) k_reduce(const double2* partials, long l
   }
   if (threadIdx.x == 0) {
     if (first_batch) {
-      acc->x = sr[0];
-      acc->y = si[0];
+      acc[b].x = sr[0];
+      acc[b].y = si[0];
     } else {
-      acc->x += sr[0];
-      acc->y += si[0];
+      acc[b].x += sr[0];
+      acc[b].y += si[0];
     }
   }
 }
 
-__global__ void k_write_out(const double2* acc, double norm, double* out) {
-  out[0] = acc->x * norm;
-  out[1] = acc->y * norm;
+__global__ void k_write_out(const double2* acc, long long n_amps, double norm, double* out) {
+  const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_amps) return;
+  out[2 * b] = acc[b].x * norm;
+  out[2 * b + 1] = acc[b].y * norm;
 }
 
 // ------------------------------ host driver ---------------------------------
@@ -688,6 +777,10 @@ void build_stage(qt_net* net) {
     st.slice_stride = t.kind == TK_SLICE ? S.slice_elems : 0;
     st.per_slice = t.kind == TK_SLICE;
     st.smask = t.kind == TK_SLICE ? 0u : t.smask;
+    for (int32_t l : t.labels) {  // open indices are the pos range [n_order, n_order + n_open)
+      const int j = S.pos[l] - (int)(S.pos.size() - S.k - S.n_open);
+      if (j >= 0 && j < S.n_open) st.omask |= 1u << j;
+    }
     st.meta = t.meta;
     terms.push_back(st);
   }
@@ -724,8 +817,11 @@ static size_t n_gate_meta(const Schedule& S) {
   return n;
 }
 
+static void segtab_dirty(qt_net* net);
+
 qt_status upload(qt_net* net, void* ws, size_t bytes, void* stream, std::string& err) {
   const Schedule& S = net->sched;
+  segtab_dirty(net);
   if (net->stage_dirty) build_stage(net);
   const size_t eb = (size_t)S.elem_bytes;
   const size_t gate_bytes = (size_t)S.gate_elems * eb;
@@ -783,11 +879,14 @@ struct LaunchDesc {
   KStep k;
   GemmArgs ga;  // kind 3
   int group;    // schedule launch group
-  int kind;     // 0 flat, 1 tiled, 3 GEMM form (pack A', pack B', GEMM)
+  int kind;     // 0 flat, 1 tiled, 3 GEMM form (pack A', pack B', GEMM), 4 GEMM form
+                // (fold A', fold B', shared-memory tiled GEMM), 5 segment (a run of small
+                // flat launches, one block per slice)
   int variant;  // 0..2 tiled kernel variants, 3 GEMM form
   int gemm_mode;
   unsigned grid;
   int64_t bytes, flops;  // ledger counts per slice
+  int seg_first = 0, seg_count = 0;  // kind 5: records in the segment table
 };
 
 constexpr int VARIANT_GEMM = 3;
@@ -841,11 +940,30 @@ static void fill_gemm(const Schedule& S, const SGroup& g, long long nslices, Gem
     q.meta_per_slice = o.meta_per_slice;
     q.side = g.side[j];
   }
+  a.gA = g.gA;
+  a.gB = g.gB;
+  // GEMM_TILE: each operand's indices in its side's big operand's bit numbering
+  for (int j = 0; j < a.m; ++j) {
+    const unsigned int X = a.op[a.op[j].side ? g.gB : g.gA].umask;
+    unsigned int xm = 0;
+    int k = 0;
+    for (int b = 0; b < 32; ++b)
+      if ((X >> b) & 1u) {
+        if ((a.op[j].umask >> b) & 1u) xm |= 1u << k;
+        ++k;
+      }
+    a.op[j].xmask = xm;
+    if (j != g.gA && j != g.gB) (a.op[j].side ? a.fold_b : a.fold_a) = 1;
+  }
+  a.tb = gemm_tile_bits(a, g.u);
 }
 
 struct EngineCache {
   uint64_t generation = 0;
   std::vector<LaunchDesc> prefix, slice;
+  std::vector<KStep> segtab;       // step records of the segment launches
+  const void* seg_ws = nullptr;    // workspace the table was last copied to
+  uint64_t seg_gen = 0;
   // captured run
   cudaGraphExec_t exec = nullptr;
   cudaStream_t capture = nullptr;
@@ -857,6 +975,23 @@ struct EngineCache {
     if (capture) cudaStreamDestroy(capture);
   }
 };
+
+static void segtab_dirty(qt_net* net) {
+  if (net->engine) static_cast<EngineCache*>(net->engine)->seg_ws = nullptr;
+}
+
+// copies the segment table into the workspace when it is not there yet
+static bool ensure_segtab(qt_net* net, EngineCache& c, char* base, cudaStream_t s,
+                          std::string& err) {
+  if (c.segtab.empty() || (c.seg_ws == base && c.seg_gen == c.generation)) return true;
+  if (!cuda_ok(cudaMemcpyAsync(base + net->sched.off_segtab, c.segtab.data(),
+                               c.segtab.size() * sizeof(KStep), cudaMemcpyHostToDevice, s),
+               "upload segment table", err))
+    return false;
+  c.seg_ws = base;
+  c.seg_gen = c.generation;
+  return true;
+}
 
 template <typename R>
 using TiledFn = void (*)(const KStep, R*, Meta*);
@@ -930,6 +1065,10 @@ static bool make_desc(const Schedule& S, int gi, long long nslices, LaunchDesc& 
     d.kind = 3;
     d.gemm_mode = gemm_mode_for(S, st);
     fill_gemm(S, st, nslices, d.ga);
+    if (d.gemm_mode == GEMM_SIMT && d.ga.tb > 0) {
+      d.gemm_mode = GEMM_TILE;
+      d.kind = 4;
+    }
     d.grid = 0;
     return true;
   }
@@ -956,6 +1095,35 @@ static bool build_cache(qt_net* net, EngineCache& c, std::string& err) {
     if (!make_desc<R>(S, gi, pre ? 1 : S.batch, d, err)) return false;
     (pre ? c.prefix : c.slice).push_back(d);
   }
+  // runs of two or more consecutive small flat launches become one segment launch
+  c.segtab.clear();
+  for (std::vector<LaunchDesc>* list : {&c.prefix, &c.slice}) {
+    std::vector<LaunchDesc> merged;
+    for (size_t i = 0; i < list->size();) {
+      size_t j = i;
+      auto small = [&](const LaunchDesc& d) { return d.kind == 0 && d.k.u <= SEG_MAX_U; };
+      while (j < list->size() && small((*list)[j])) ++j;
+      if (j - i >= 2 && net->segments) {
+        LaunchDesc d = (*list)[i];
+        d.kind = 5;
+        d.seg_first = (int)c.segtab.size();
+        d.seg_count = (int)(j - i);
+        d.bytes = d.flops = 0;
+        for (size_t q = i; q < j; ++q) {
+          c.segtab.push_back((*list)[q].k);
+          d.bytes += (*list)[q].bytes;
+          d.flops += (*list)[q].flops;
+        }
+        merged.push_back(d);
+        i = j;
+      } else {
+        merged.push_back((*list)[i]);
+        ++i;
+      }
+    }
+    *list = merged;
+  }
+  c.seg_ws = nullptr;
   if (c.exec) cudaGraphExecDestroy(c.exec);
   c.exec = nullptr;
   c.first = c.count = -1;
@@ -967,6 +1135,19 @@ template <typename R>
 static void launch_desc(qt_net* net, const LaunchDesc& d0, long long nslices, long long slice_first,
                         char* base, cudaStream_t s) {
   const Schedule& S = net->sched;
+  if (d0.kind == 5) {
+    R* data = reinterpret_cast<R*>(base);
+    Meta* meta = reinterpret_cast<Meta*>(base + S.off_meta);
+    ProfRec pr{S.groups[d0.group].first, 5, nslices, d0.bytes * nslices, d0.flops * nslices,
+               nullptr, nullptr};
+    if (net->prof) prof_begin(net, s, pr);
+    net->launches++;
+    const KStep* tab = reinterpret_cast<const KStep*>(base + S.off_segtab) + d0.seg_first;
+    k_segment<R><<<(unsigned)nslices, SEG_THREADS, 0, s>>>(tab, d0.seg_count, data, meta,
+                                                          slice_first);
+    if (net->prof) prof_end(net, s, pr);
+    return;
+  }
   KStep k = d0.k;
   k.nslices = nslices;
   k.slice_first = slice_first;
@@ -982,7 +1163,7 @@ static void launch_desc(qt_net* net, const LaunchDesc& d0, long long nslices, lo
   ProfRec pr{S.groups[d0.group].first, d0.kind, nslices, d0.bytes * nslices, d0.flops * nslices,
              nullptr, nullptr};
   if (net->prof) prof_begin(net, s, pr);
-  if (d0.kind == 3) {
+  if (d0.kind >= 3) {
     GemmArgs ga = d0.ga;
     ga.nslices = nslices;
     ga.slice_first = slice_first;
@@ -1028,14 +1209,17 @@ static qt_status enqueue_run(qt_net* net, EngineCache& c, long long first, long 
     ProfRec pr{-1, 2, nb, 0, 0, nullptr, nullptr};
     if (net->prof) prof_begin(net, s, pr);
     net->launches += 2;
-    k_finalize<R><<<(unsigned)((nb + 127) / 128), 128, 0, s>>>(
-        terms, nterms, reinterpret_cast<const R*>(base), meta, nb, b0, partials);
-    k_reduce<<<1, 1024, 0, s>>>(partials, nb, acc, first_batch ? 1 : 0);
+    const long long nthreads = nb * S.n_amps;
+    k_finalize<R><<<(unsigned)((nthreads + 127) / 128), 128, 0, s>>>(
+        terms, nterms, reinterpret_cast<const R*>(base), meta, nb, b0, S.n_open, partials);
+    k_reduce<<<(unsigned)S.n_amps, 1024, 0, s>>>(partials, nb, S.n_open, acc,
+                                                 first_batch ? 1 : 0);
     if (net->prof) prof_end(net, s, pr);
     first_batch = false;
   }
   net->launches++;
-  k_write_out<<<1, 1, 0, s>>>(acc, std::pow(2.0, -0.5 * net->n), d_out);
+  k_write_out<<<(unsigned)((S.n_amps + 255) / 256), 256, 0, s>>>(acc, S.n_amps,
+                                                                std::pow(2.0, -0.5 * net->n), d_out);
   if (!cuda_ok(cudaGetLastError(), "kernel launch", err)) return QT_ECUDA;
   return QT_OK;
 }
@@ -1050,6 +1234,7 @@ static qt_status autotune_impl(qt_net* net, char* base, cudaStream_t s, std::str
   EngineCache& c = *static_cast<EngineCache*>(net->engine);
   const Schedule& S = net->sched;
   if (c.generation != S.generation && !build_cache<R>(net, c, err)) return QT_ERANGE;
+  if (!ensure_segtab(net, c, base, s, err)) return QT_ECUDA;
   const bool prof = net->prof;
   net->prof = false;
   struct Trial {
@@ -1069,7 +1254,8 @@ static qt_status autotune_impl(qt_net* net, char* base, cudaStream_t s, std::str
       LaunchDesc& d = list[i];
       const SGroup& grp = S.groups[d.group];
       const bool can_gemm = grp.gemm && !tc_precision(S.precision) && sizeof(R) == 4;
-      if (d.kind == 0 || (d.kind == 3 && (tc_precision(S.precision) || S.force_gemm))) {
+      if (d.kind == 0 || d.kind == 5 ||
+          ((d.kind == 3 || d.kind == 4) && (tc_precision(S.precision) || S.force_gemm))) {
         launch_desc<R>(net, d, nb, b0, base, s);
         continue;
       }
@@ -1162,6 +1348,7 @@ static qt_status run_impl(qt_net* net, long long first, long long count, char* b
   EngineCache& c = *static_cast<EngineCache*>(net->engine);
   const Schedule& S = net->sched;
   if (c.generation != S.generation && !build_cache<R>(net, c, err)) return QT_ERANGE;
+  if (!ensure_segtab(net, c, base, s, err)) return QT_ECUDA;
   const long long batches = (count + S.batch - 1) / S.batch;
   const long long nlaunch = (long long)c.prefix.size() + batches * ((long long)c.slice.size() + 2) + 1;
   if (!net->graphs || net->prof || nlaunch > kMaxGraphLaunches)
@@ -1212,9 +1399,11 @@ qt_status run(qt_net* net, long long first, long long count, void* ws, void* str
   return run_impl<float>(net, first, count, base, s, d_out, err);
 }
 
-qt_status download_result(const double* d_out, double* host, void* stream, std::string& err) {
+qt_status download_result(const double* d_out, double* host, int64_t n_doubles, void* stream,
+                          std::string& err) {
   cudaStream_t s = (cudaStream_t)stream;
-  if (!cuda_ok(cudaMemcpyAsync(host, d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, s),
+  if (!cuda_ok(cudaMemcpyAsync(host, d_out, (size_t)n_doubles * sizeof(double),
+                               cudaMemcpyDeviceToHost, s),
                "download result", err))
     return QT_ECUDA;
   if (!cuda_ok(cudaStreamSynchronize(s), "stream synchronize", err)) return QT_ECUDA;

@@ -261,6 +261,158 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned int (&a)[
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+__device__ __forceinline__ unsigned int pext32g(unsigned int x, unsigned int m) {
+  unsigned int r = 0;
+  int k = 0;
+  while (m) {
+    const int b = __ffs(m) - 1;
+    r |= ((x >> b) & 1u) << k;
+    ++k;
+    m &= m - 1;
+  }
+  return r;
+}
+
+__device__ __forceinline__ long long op_slice_base(const GOp& o, long long i,
+                                                   unsigned long long sid) {
+  long long off = o.base + i * o.slice_stride;
+  if (o.smask) off += (long long)(pext64g(sid, o.smask) << o.sshift);
+  return off;
+}
+
+// GEMM_TILE, fold: X' = X times the other operands of its side, all scaled by
+// their 2^-s, in X's own canonical layout (no one-sided summed index, so nothing
+// is summed here). An operand's index at X index x is pext(x, its xmask).
+__global__ void __launch_bounds__(256) k_gemm_fold(const GemmArgs a, int side, float* data,
+                                                   const GMeta* meta) {
+  const GOp& X = a.op[side ? a.gB : a.gA];
+  const int xb = __popc(X.umask);
+  const unsigned int xall = (unsigned int)((1ull << xb) - 1ull);
+  const long long total = a.nslices << xb;
+  float2* out = reinterpret_cast<float2*>(data) + (side ? a.scratch_b : a.scratch_a);
+  const float2* d2 = reinterpret_cast<const float2*>(data);
+  long long cur = -1;
+  long long base[GEMM_MAXOP];
+  float sc[GEMM_MAXOP];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e >> xb;
+    const unsigned int x = (unsigned int)(e & xall);
+    if (i != cur) {
+      cur = i;
+      const unsigned long long sid = (unsigned long long)(a.slice_first + i);
+#pragma unroll
+      for (int j = 0; j < GEMM_MAXOP; ++j)
+        if (j < a.m && a.op[j].side == side) {
+          base[j] = op_slice_base(a.op[j], i, sid);
+          sc[j] = pow2_neg_g(scale_exp_g(meta[a.op[j].meta + (a.op[j].meta_per_slice ? i : 0)].maxabs));
+        }
+    }
+    float pr = 1.f, pi = 0.f;
+#pragma unroll
+    for (int j = 0; j < GEMM_MAXOP; ++j)
+      if (j < a.m && a.op[j].side == side) {
+        const unsigned int xm = a.op[j].xmask;
+        const unsigned int idx = xm == xall ? x : pext32g(x, xm);
+        const float2 v = d2[base[j] + idx];
+        const float vr = v.x * sc[j], vi = v.y * sc[j];
+        const float nr = pr * vr - pi * vi, ni = pr * vi + pi * vr;
+        pr = nr;
+        pi = ni;
+      }
+    out[i * a.scratch_stride + x] = make_float2(pr, pi);
+  }
+}
+
+// GEMM_TILE, the product: a tile is the 2^tb lowest output indices for fixed
+// higher ones, i.e. the lowest nsum + tb bits of U. In the canonical layout those
+// bits are the lowest bits of every operand, so the tile reads one contiguous
+// block of A' (rows = A's output indices in the tile, columns = the K summed
+// indices, all of which A and B share) and one of B', stages both in shared
+// memory and writes its 2^tb outputs as one contiguous, coalesced run.
+__global__ void __launch_bounds__(256) k_gemm_tile(const GemmArgs a, int u, float* data,
+                                                   GMeta* meta) {
+  extern __shared__ float4 gsm[];
+  const int nsum = a.nsum, t = a.tb, c = u - nsum;
+  const int K = 1 << nsum, RS = K + 2;  // row stride (complex): keeps rows 16-byte aligned
+  const GOp& OA = a.op[a.gA];
+  const GOp& OB = a.op[a.gB];
+  const unsigned int L = (nsum + t >= 32) ? 0xffffffffu : ((1u << (nsum + t)) - 1u);
+  const int la = __popc(OA.umask & L), lb = __popc(OB.umask & L);
+  const int rows_a = 1 << (la - nsum), rows_b = 1 << (lb - nsum);
+  float2* sA = reinterpret_cast<float2*>(gsm);
+  float2* sB = sA + rows_a * RS;
+  unsigned int* RT = reinterpret_cast<unsigned int*>(sB + rows_b * RS);
+  const unsigned int ma = (OA.umask & L) >> nsum, mb = (OB.umask & L) >> nsum;
+  const int T = 1 << t;
+  for (int o = threadIdx.x; o < T; o += blockDim.x)
+    RT[o] = pext32g((unsigned)o, ma) | (pext32g((unsigned)o, mb) << 16);
+  const long long per = 1ll << (c - t);
+  const long long ntiles = a.nslices * per;
+  const float2* d2 = reinterpret_cast<const float2*>(data);
+  long long cur = -1, baseA = 0, baseB = 0;
+  float scA = 1.f, scB = 1.f, mx = 0.f;
+  __syncthreads();
+  for (long long w = blockIdx.x; w < ntiles; w += gridDim.x) {
+    const long long i = w / per, tau = w - i * per;
+    if (i != cur) {
+      if (cur >= 0) flush_max(a, meta, cur, mx);
+      mx = 0.f;
+      cur = i;
+      const unsigned long long sid = (unsigned long long)(a.slice_first + i);
+      if (a.fold_a) {
+        baseA = a.scratch_a + i * a.scratch_stride;
+        scA = 1.f;
+      } else {
+        baseA = op_slice_base(OA, i, sid);
+        scA = pow2_neg_g(scale_exp_g(meta[OA.meta + (OA.meta_per_slice ? i : 0)].maxabs));
+      }
+      if (a.fold_b) {
+        baseB = a.scratch_b + i * a.scratch_stride;
+        scB = 1.f;
+      } else {
+        baseB = op_slice_base(OB, i, sid);
+        scB = pow2_neg_g(scale_exp_g(meta[OB.meta + (OB.meta_per_slice ? i : 0)].maxabs));
+      }
+      if (tau == 0 && threadIdx.x == 0) write_meta_e(a, meta, i);
+    }
+    const unsigned long long Uh = (unsigned long long)tau << (nsum + t);
+    const long long ta = baseA + ((long long)pext64g(Uh, OA.umask & ~L) << la);
+    const long long tb = baseB + ((long long)pext64g(Uh, OB.umask & ~L) << lb);
+    for (int e = threadIdx.x; e < (rows_a << nsum); e += blockDim.x) {
+      const float2 v = d2[ta + e];
+      sA[(e >> nsum) * RS + (e & (K - 1))] = make_float2(v.x * scA, v.y * scA);
+    }
+    for (int e = threadIdx.x; e < (rows_b << nsum); e += blockDim.x) {
+      const float2 v = d2[tb + e];
+      sB[(e >> nsum) * RS + (e & (K - 1))] = make_float2(v.x * scB, v.y * scB);
+    }
+    __syncthreads();
+    float2* out = reinterpret_cast<float2*>(data) + a.out_base + i * a.out_slice_stride + (tau << t);
+    for (int o = threadIdx.x; o < T; o += blockDim.x) {
+      const unsigned int rt = RT[o];
+      const float4* pa = reinterpret_cast<const float4*>(sA + (rt & 0xffffu) * RS);
+      const float4* pb = reinterpret_cast<const float4*>(sB + (rt >> 16) * RS);
+      float cr = 0.f, ci = 0.f;
+      for (int k2 = 0; k2 < (K >> 1); ++k2) {
+        const float4 x = pa[k2], y = pb[k2];
+        cr = fmaf(x.x, y.x, cr);
+        cr = fmaf(-x.y, y.y, cr);
+        ci = fmaf(x.x, y.y, ci);
+        ci = fmaf(x.y, y.x, ci);
+        cr = fmaf(x.z, y.z, cr);
+        cr = fmaf(-x.w, y.w, cr);
+        ci = fmaf(x.z, y.w, ci);
+        ci = fmaf(x.w, y.z, ci);
+      }
+      out[o] = make_float2(cr, ci);
+      mx = fmaxf(mx, fmaxf(fabsf(cr), fabsf(ci)));
+    }
+    __syncthreads();
+  }
+  if (cur >= 0) flush_max(a, meta, cur, mx);
+}
+
 // Tensor-core GEMM: one warp per (slice, bt, 16-row m tile, 8-column n tile).
 // Fragment layouts of mma.m16n8k8 (tf32) / m16n8k16 (bf16), with g = lane / 4,
 // t = lane % 4: A row g (+8), columns t (+4) [tf32] or 2t, 2t+1 (+8) [bf16];
@@ -394,7 +546,40 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs a, float* data, 
 
 }  // namespace
 
+static size_t tile_smem(const GemmArgs& a, int t) {
+  const unsigned int L = (a.nsum + t >= 32) ? 0xffffffffu : ((1u << (a.nsum + t)) - 1u);
+  const long long ra = 1ll << (__builtin_popcount(a.op[a.gA].umask & L) - a.nsum);
+  const long long rb = 1ll << (__builtin_popcount(a.op[a.gB].umask & L) - a.nsum);
+  return (size_t)((ra + rb) * ((1ll << a.nsum) + 2) * 8 + (4ll << t));
+}
+
+int gemm_tile_bits(const GemmArgs& a, int u) {
+  if (a.mSA || a.mSB || a.gA < 0 || a.gB < 0) return 0;
+  if (__builtin_popcount(a.op[a.gA].umask) > 30 || __builtin_popcount(a.op[a.gB].umask) > 30)
+    return 0;
+  const int c = u - a.nsum;
+  for (int t = std::min(c, 10); t >= 5; --t)
+    if (tile_smem(a, t) <= 48 * 1024) return t;
+  return 0;
+}
+
 int gemm_launch(const GemmArgs& a, int mode, float* data, GMeta* meta, cudaStream_t s, int sms) {
+  if (mode == GEMM_TILE) {
+    int n = 0;
+    for (int side = 0; side < 2; ++side) {
+      if (!(side ? a.fold_b : a.fold_a)) continue;
+      const long long work = a.nslices << __builtin_popcount(a.op[side ? a.gB : a.gA].umask);
+      const long long g = std::min<long long>((work + 255) / 256, (long long)sms * 16);
+      k_gemm_fold<<<(unsigned)std::max<long long>(1, g), 256, 0, s>>>(a, side, data, meta);
+      ++n;
+    }
+    int u = 0;
+    for (unsigned int m = a.mK | a.mSA | a.mSB | a.mM | a.mN | a.mBt; m; m >>= 1) ++u;
+    const long long ntiles = a.nslices << (u - a.nsum - a.tb);
+    const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(ntiles, (long long)sms * 6));
+    k_gemm_tile<<<grid, 256, tile_smem(a, a.tb), s>>>(a, u, data, meta);
+    return n + 1;
+  }
   const int kb = __builtin_popcount(a.mK), bb = __builtin_popcount(a.mBt);
   const long long pa = a.nslices << (bb + __builtin_popcount(a.mM) + kb);
   const long long pb = a.nslices << (bb + __builtin_popcount(a.mN) + kb);

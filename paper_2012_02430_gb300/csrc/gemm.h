@@ -8,7 +8,7 @@
 
 namespace qt {
 
-enum { GEMM_SIMT = 0, GEMM_TC_TF32 = 1, GEMM_TC_BF16 = 2, GEMM_TC_3XTF32 = 3 };
+enum { GEMM_SIMT = 0, GEMM_TC_TF32 = 1, GEMM_TC_BF16 = 2, GEMM_TC_3XTF32 = 3, GEMM_TILE = 4 };
 
 constexpr int GEMM_MAXOP = 12;
 
@@ -20,7 +20,8 @@ struct GMeta {
 struct GOp {
   long long base, slice_stride, meta;
   unsigned int umask, smask;
-  int sshift, meta_per_slice, side, pad;
+  int sshift, meta_per_slice, side;
+  unsigned int xmask;  // GEMM_TILE: the operand's indices in the bit numbering of its side's big operand
 };
 
 struct GemmArgs {
@@ -30,10 +31,17 @@ struct GemmArgs {
   long long out_base, out_slice_stride, out_meta;
   int out_meta_per_slice, pad;
   long long scratch_a, scratch_b, scratch_stride;  // elements (complex64 units)
+  // GEMM_TILE: big operands, output indices per tile, which sides are folded
+  int gA, gB, tb, fold_a, fold_b, pad2;
   GOp op[GEMM_MAXOP];
 };
 
-// pack A', pack B', GEMM; returns the number of kernels launched
+// Output indices per tile of the GEMM_TILE kernel for a launch (0: the launch
+// does not take that form: a one-sided summed index, or too little shared memory).
+int gemm_tile_bits(const GemmArgs& a, int u);
+
+// GEMM_TILE: fold A', fold B' (when the side has small operands), tiled GEMM;
+// other modes: pack A', pack B', GEMM. Returns the number of kernels launched.
 int gemm_launch(const GemmArgs& a, int mode, float* data, GMeta* meta, cudaStream_t s, int sms);
 
 }  // namespace qt

@@ -79,6 +79,20 @@ BitGraph line_graph(const std::vector<Tensor>& tensors, int n_vars) {
   return g;
 }
 
+BitGraph network_graph(const qt_net* net) {
+  BitGraph g = line_graph(net->tensors, net->n_vars);
+  const int a = (int)net->open.size();
+  if (a > 0) {
+    const int first = net->n_vars - a;
+    g.keep.assign(g.n, 0);
+    for (int j = 0; j < a; ++j) {
+      g.keep[first + j] = 1;
+      for (int t = j + 1; t < a; ++t) g.add_edge(first + j, first + t);
+    }
+  }
+  return g;
+}
+
 // ------------------------------- greedy ------------------------------------
 // Number of missing edges among v's neighbours (the fill-in of eliminating v).
 static int64_t fill_in(const BitGraph& g, int v, int deg) {
@@ -104,7 +118,7 @@ OrderResult greedy_order(const BitGraph& g0, int algo) {
   int remaining = 0;
   for (int v = 0; v < n; ++v) {
     if (!g.alive[v]) continue;
-    ++remaining;
+    remaining += g.takeable(v);
     deg[v] = g.degree(v);
     if (algo == QT_GREEDY_MINFILL) fill[v] = fill_in(g, v, (int)deg[v]);
   }
@@ -115,7 +129,7 @@ OrderResult greedy_order(const BitGraph& g0, int algo) {
   while (remaining > 0) {
     int best = -1;
     for (int v = 0; v < n; ++v) {
-      if (!g.alive[v]) continue;
+      if (!g.takeable(v)) continue;
       if (best < 0) { best = v; continue; }
       bool better;
       if (algo == QT_GREEDY_MINFILL)
@@ -186,7 +200,7 @@ SlicePlan step_dependent_slicing(const BitGraph& g0, int algo, int width_limit, 
   };
   int32_t width = maxw(cur.widths, 0);
   int alive_count = 0;
-  for (int v = 0; v < g.n; ++v) alive_count += g.alive[v];
+  for (int v = 0; v < g.n; ++v) alive_count += g.takeable(v);
   while (width > width_limit && (int)sliced.size() < max_vars && alive_count > 0) {
     int rr = std::min<int>(r, max_vars - (int)sliced.size());
     int peak = 0;
@@ -212,7 +226,7 @@ SlicePlan step_dependent_slicing(const BitGraph& g0, int algo, int width_limit, 
       for (int t = 0; t < rr; ++t) {
         int bestv = -1, bestd = -1;
         for (int v = 0; v < b.n; ++v) {
-          if (!b.alive[v]) continue;
+          if (!b.takeable(v)) continue;
           int d = b.degree(v);
           if (d > bestd) { bestd = d; bestv = v; }
         }

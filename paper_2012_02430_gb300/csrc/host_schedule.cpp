@@ -91,7 +91,8 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 }  // namespace
 
 bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePlan& plan,
-                      int precision, int64_t batch, bool fuse, Schedule& S, std::string& err) {
+                      int precision, int64_t batch, bool fuse, Schedule& S, std::string& err,
+                      int n_open) {
   static uint64_t next_generation = 1;
   S = Schedule();
   S.fused = fuse;
@@ -102,11 +103,32 @@ bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePla
   S.k = (int)plan.sliced.size();
   S.nslices = (int64_t)1 << S.k;
   S.batch = std::max<int64_t>(1, std::min<int64_t>(batch, S.nslices));
+  if (n_open < 0 || n_open > QT_MAX_OPEN || n_open > n_vars) {
+    err = "bad number of open indices";
+    return false;
+  }
+  S.n_open = n_open;
+  S.n_amps = (int64_t)1 << n_open;
   S.pos.assign(n_vars, -1);
-  std::vector<int> slice_bit(n_vars, -1);
+  std::vector<int> slice_bit(n_vars, -1), open_bit(n_vars, -1);
   for (int i = 0; i < n_order; ++i) S.pos[plan.order[i]] = i;
+  // open indices sit above every eliminated one and below the sliced ones, so a
+  // tensor left over the open (and sliced) indices is indexed (open bits, slice bits)
+  for (int j = 0; j < n_open; ++j) {
+    const int v = n_vars - n_open + j;
+    if (S.pos[v] >= 0) {
+      err = "an open index is in the elimination order";
+      return false;
+    }
+    S.pos[v] = n_order + j;
+    open_bit[v] = j;
+  }
   for (int j = 0; j < S.k; ++j) {
-    S.pos[plan.sliced[j]] = n_order + j;
+    if (open_bit[plan.sliced[j]] >= 0) {
+      err = "an open index is sliced";
+      return false;
+    }
+    S.pos[plan.sliced[j]] = n_order + n_open + j;
     slice_bit[plan.sliced[j]] = j;
   }
   for (int v = 0; v < n_vars; ++v)
@@ -122,10 +144,11 @@ bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePla
     STensor& t = S.tensors[tid];
     int e = -1;
     for (int32_t l : t.labels)
-      if (slice_bit[l] < 0 && (e < 0 || S.pos[l] < e)) e = S.pos[l];
+      if (slice_bit[l] < 0 && open_bit[l] < 0 && (e < 0 || S.pos[l] < e)) e = S.pos[l];
     (void)region_of_creation;
     if (e < 0) {
-      S.scalars.push_back(tid);  // rank 0, or only sliced indices: a per-slice factor
+      // only sliced and open indices left: a factor of the slice's result tensor
+      S.scalars.push_back(tid);
     } else {
       buckets[e].push_back(tid);
     }
@@ -296,11 +319,13 @@ bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePla
       const uint32_t A = mask[a], B = mask[bb];
       bool ok = true;
       std::vector<int8_t> side(g.ops.size(), 0);
+      // the other operands fold into B' when they fit in B (the smaller one, so the
+      // fold touches fewer elements), else into A'
       for (size_t j = 0; j < g.ops.size(); ++j) {
         if ((int)j == a) side[j] = 0;
         else if ((int)j == bb) side[j] = 1;
-        else if ((mask[j] & ~A) == 0u) side[j] = 0;
         else if ((mask[j] & ~B) == 0u) side[j] = 1;
+        else if ((mask[j] & ~A) == 0u) side[j] = 0;
         else ok = false;
       }
       const uint32_t all = g.u >= 32 ? 0xffffffffu : ((1u << g.u) - 1u);
@@ -390,11 +415,13 @@ bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePla
   S.off_meta = off;
   off = align256(off + (size_t)(shared + per_slice * S.batch) * 16);
   S.off_partials = off;
-  off = align256(off + (size_t)S.batch * 16);
-  S.off_acc = off;
-  off = align256(off + 64);
+  off = align256(off + (size_t)S.batch * (size_t)S.n_amps * 16);
+  S.off_acc = off;  // n_amps accumulators, then the n_amps results
+  off = align256(off + std::max<size_t>(64, (size_t)S.n_amps * 32));
   S.off_terms = off;
   off = align256(off + S.scalars.size() * kScalarTermBytes);
+  S.off_segtab = off;  // step records of the segment launches (runs of small launches)
+  off = align256(off + S.groups.size() * kStepRecordBytes);
   S.total_bytes = off;
   S.valid = true;
   return true;
@@ -414,6 +441,7 @@ std::string schedule_json(const Schedule& S, const SlicePlan& plan) {
     if (__builtin_popcount(g.mK) >= 5) k32_flops += f;
   }
   o << "{\"k\":" << S.k << ",\"nslices\":" << S.nslices << ",\"batch\":" << S.batch
+    << ",\"n_open\":" << S.n_open
     << ",\"precision\":" << S.precision << ",\"elem_bytes\":" << S.elem_bytes
     << ",\"plan_width\":" << plan.width << ",\"slice_step\":" << plan.slice_step
     << ",\"prefix_flops\":" << S.prefix_flops << ",\"prefix_bytes\":" << S.prefix_bytes

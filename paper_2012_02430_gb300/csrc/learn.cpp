@@ -68,7 +68,7 @@ static std::vector<Candidate> round_candidates(const BitGraph& g, const std::vec
     int64_t deg_sum = 0;
     int alive = 0;
     for (int x = 0; x < h.n; ++x) {
-      if (!h.alive[x]) continue;
+      if (!h.takeable(x)) continue;
       const int d = h.degree(x);
       ranked.push_back({-d, x});
       deg_sum += d;
@@ -133,7 +133,7 @@ static Eval evaluate(const BitGraph& g, const std::vector<int32_t>& order,
   for (int t = 1; t < r; ++t) {
     int best = -1, bestd = -1;
     for (int x = 0; x < e.g.n; ++x) {
-      if (!e.g.alive[x]) continue;
+      if (!e.g.takeable(x)) continue;
       const int d = e.g.degree(x);
       if (d > bestd) {
         bestd = d;
@@ -190,7 +190,7 @@ void mlp_forward_host(const float* params, int nf, int hidden, const float* x, i
 
 bool slice_dataset(const qt_net* net, int topv, std::vector<float>& feats,
                    std::vector<float>& labels, std::vector<int32_t>& meta) {
-  BitGraph g = line_graph(net->tensors, net->n_vars);
+  BitGraph g = network_graph(net);
   OrderResult cur = greedy_order(g, net->algo);
   std::vector<Candidate> cands = round_candidates(g, cur.order, cur.widths, net->n_vars, topv);
   int W = 0;
@@ -211,7 +211,7 @@ bool slice_dataset(const qt_net* net, int topv, std::vector<float>& feats,
 SlicePlan learned_slicing(const qt_net* net, const float* params, int hidden, int width_limit,
                           int max_vars, int r, int topv, int topm, int spread,
                           int64_t& greedy_runs) {
-  BitGraph g = line_graph(net->tensors, net->n_vars);
+  BitGraph g = network_graph(net);
   const int algo = net->algo;
   OrderResult cur = greedy_order(g, algo);
   greedy_runs = 1;
@@ -220,7 +220,7 @@ SlicePlan learned_slicing(const qt_net* net, const float* params, int hidden, in
   int32_t width = 0;
   for (int32_t x : cur.widths) width = std::max(width, x);
   int alive = 0;
-  for (int v = 0; v < g.n; ++v) alive += g.alive[v];
+  for (int v = 0; v < g.n; ++v) alive += g.takeable(v);
   while (width > width_limit && (int)sliced.size() < max_vars && alive > 0) {
     const int rr = std::min<int>(r, max_vars - (int)sliced.size());
     std::vector<Candidate> cands = round_candidates(g, cur.order, cur.widths, net->n_vars, topv);

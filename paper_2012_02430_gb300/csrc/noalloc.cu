@@ -25,7 +25,8 @@ namespace qt {
 qt_status upload(qt_net* net, void* ws, size_t bytes, void* stream, std::string& err);
 qt_status run(qt_net* net, long long first, long long count, void* ws, void* stream,
               double* d_out, std::string& err);
-qt_status download_result(const double* d_out, double* host, void* stream, std::string& err);
+qt_status download_result(const double* d_out, double* host, int64_t n_doubles, void* stream,
+                          std::string& err);
 void set_last_error(const std::string& msg);  // api.cpp: the message qt_last_error() returns
 }  // namespace qt
 
@@ -73,6 +74,8 @@ qt_status qt_contract_static(qt_net* net, int32_t precision, void* stream, doubl
                              double* amp_im) {
   if (!net || !amp_re || !amp_im) return fail(QT_EINVAL, "qt_contract_static: null argument");
   if (!net->ordered) return fail(QT_ESTATE, "qt_contract_static: call qt_order first");
+  if (!net->open.empty())
+    return fail(QT_ESTATE, "qt_contract_static: the network has open qubits");
   void* ws = nullptr;
   qt_status s = static_workspace(&ws);
   if (s != QT_OK) return s;
@@ -125,7 +128,7 @@ qt_status qt_contract_static(qt_net* net, int32_t precision, void* stream, doubl
   double* d_out = reinterpret_cast<double*>((char*)ws + net->sched.off_acc + 16);
   if (s == QT_OK) s = qt::run(net, 0, net->sched.nslices, ws, stream, d_out, err);
   double h[2] = {0.0, 0.0};
-  if (s == QT_OK) s = qt::download_result(d_out, h, stream, err);
+  if (s == QT_OK) s = qt::download_result(d_out, h, 2, stream, err);
   net->prof = prof;
   net->graphs = graphs;
   restore();

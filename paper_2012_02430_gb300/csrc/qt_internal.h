@@ -26,6 +26,10 @@ struct BitGraph {
   int W = 0;  // 64-bit words per row
   std::vector<uint64_t> rows;
   std::vector<uint8_t> alive;
+  std::vector<uint8_t> keep;  // open indices (Sec. VII): never eliminated nor sliced; empty = none
+
+  // an alive vertex that an order or a slicing round may take
+  bool takeable(int v) const { return alive[v] && (keep.empty() || !keep[v]); }
 
   void init(int nv);
   uint64_t* row(int v) { return rows.data() + (size_t)v * W; }
@@ -124,6 +128,8 @@ struct Schedule {
   int precision = QT_FP32_SIMT;
   int elem_bytes = 8;
   int k = 0;
+  int n_open = 0;                // open indices: the result has 2^n_open amplitudes
+  int64_t n_amps = 1;
   int64_t nslices = 1;
   int64_t batch = 1;
   std::vector<int32_t> pos;     // variable -> canonical position
@@ -137,7 +143,7 @@ struct Schedule {
   int64_t n_shared_meta = 0, n_slice_meta_tensors = 0;
   // workspace layout (bytes)
   size_t off_gates = 0, off_prefix = 0, off_slices = 0, off_meta = 0, off_partials = 0,
-         off_acc = 0, off_terms = 0, total_bytes = 0;
+         off_acc = 0, off_terms = 0, off_segtab = 0, total_bytes = 0;
   // ledger
   int64_t prefix_flops = 0, prefix_bytes = 0, slice_flops = 0, slice_bytes = 0;
   int64_t prefix_launch_bytes = 0, slice_launch_bytes = 0;  // bytes of the (fused) launches
@@ -147,12 +153,16 @@ struct Schedule {
 constexpr int kMaxFusedSum = 6;   // indices summed by one launch
 constexpr int kMaxGroupOps = 12;  // operands of one launch
 
+// The last n_open variable ids are open indices (Sec. VII): never summed, they
+// index the result.
 bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePlan& plan,
-                      int precision, int64_t batch, bool fuse, Schedule& out, std::string& err);
+                      int precision, int64_t batch, bool fuse, Schedule& out, std::string& err,
+                      int n_open = 0);
 
 std::string schedule_json(const Schedule& s, const SlicePlan& plan);
 
-constexpr size_t kScalarTermBytes = 32;  // device ScalarTerm record
+constexpr size_t kScalarTermBytes = 40;  // device ScalarTerm record
+constexpr size_t kStepRecordBytes = 1024;  // upper bound of a device step record (segment table)
 
 // Canonical-layout copy of a gate tensor's data (FP64 interleaved).
 std::vector<double> canonical_data(const Tensor& t, const std::vector<int32_t>& canon_labels);
@@ -181,6 +191,7 @@ struct qt_net {
   std::vector<int32_t> edges;
   std::vector<double> gammas, betas;
   std::vector<uint8_t> z;
+  std::vector<int32_t> open;     // open qubits (Sec. VII); open j is variable n*p + j
   std::vector<qt::Tensor> tensors;
   bool ordered = false;
   int algo = QT_GREEDY_MINFILL;
@@ -198,6 +209,13 @@ struct qt_net {
   bool graphs = true;            // replay runs as captured CUDA graphs
   bool fuse = true;              // fuse bucket steps whose summed indices die together
   bool force_gemm = false;       // GEMM-form launches by default also in FP32 mode
+  bool segments = true;          // runs of small launches as one segment launch
   void* engine = nullptr;        // engine.cu: launch descriptors and graph cache
   ~qt_net();
 };
+
+namespace qt {
+// Line graph of the network plus the clique on its open indices (Sec. VII: the
+// result tensor over them), those indices marked as kept.
+BitGraph network_graph(const qt_net* net);
+}  // namespace qt

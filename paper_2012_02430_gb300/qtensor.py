@@ -19,8 +19,9 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libqtensor.so")
 QT_OK, QT_EINVAL, QT_ENOMEM, QT_ECUDA, QT_ETIMEOUT, QT_ESTATE, QT_ERANGE = range(7)
 QT_GREEDY_MINFILL, QT_GREEDY_MINDEG = 0, 1
 QT_FP32_SIMT, QT_TF32, QT_BF16, QT_3XTF32, QT_FP64 = 0, 1, 2, 3, 4
-QT_OPT_FUSION, QT_OPT_GRAPHS, QT_OPT_GEMM = 1, 2, 3
+QT_OPT_FUSION, QT_OPT_GRAPHS, QT_OPT_GEMM, QT_OPT_SEGMENTS = 1, 2, 3, 4
 QT_PROPOSAL_FEATURES = 16
+QT_MAX_OPEN = 16
 
 STATUS_NAMES = {0: "QT_OK", 1: "QT_EINVAL", 2: "QT_ENOMEM", 3: "QT_ECUDA",
                 4: "QT_ETIMEOUT", 5: "QT_ESTATE", 6: "QT_ERANGE"}
@@ -46,6 +47,8 @@ _SIGS = {
                          C.POINTER(_vp)],
     "qt_set_angles": [_vp, _f64p, _f64p],
     "qt_set_bitstring": [_vp, _u8p],
+    "qt_set_open": [_vp, _i32p, C.c_int32],
+    "qt_contract_batch": [_vp, C.c_int32, _vp, C.c_size_t, _vp, _f64p],
     "qt_order": [_vp, C.c_int32, C.c_uint64, _i32p],
     "qt_slice": [_vp, C.c_int32, C.c_int32, C.c_int32, _i32p, _i32p],
     "qt_get_order": [_vp, _i32p, C.c_int32, _i32p],
@@ -133,6 +136,11 @@ def qt_set_bitstring(net, bitstring):
     _check(lib.qt_set_bitstring(net, _arr(C.c_uint8, bitstring)))
 
 
+def qt_set_open(net, qubits):
+    qubits = [int(q) for q in qubits]
+    _check(lib.qt_set_open(net, _arr(C.c_int32, qubits) if qubits else None, len(qubits)))
+
+
 def qt_order(net, algo=QT_GREEDY_MINFILL, seed=0):
     w = C.c_int32()
     _check(lib.qt_order(net, int(algo), int(seed), C.byref(w)))
@@ -210,6 +218,14 @@ def qt_contract(net, precision, workspace_ptr, workspace_bytes, stream_ptr):
     _check(lib.qt_contract(net, int(precision), _vp(workspace_ptr), int(workspace_bytes),
                            _vp(stream_ptr), C.byref(re), C.byref(im)))
     return complex(re.value, im.value)
+
+
+def qt_contract_batch(net, precision, workspace_ptr, workspace_bytes, stream_ptr, a):
+    """The 2^a amplitudes of a network with a open qubits; entry b has bit j = open qubit j."""
+    buf = (C.c_double * (2 << a))()
+    _check(lib.qt_contract_batch(net, int(precision), _vp(workspace_ptr), int(workspace_bytes),
+                                 _vp(stream_ptr), buf))
+    return [complex(buf[2 * b], buf[2 * b + 1]) for b in range(1 << a)]
 
 
 def qt_contract_static(net, precision, stream_ptr):
@@ -369,6 +385,12 @@ class Network:
         self.handle = qt_build_network(edges, n_vertices, p, gammas, betas, bitstring)
         self.workspace = None
         self.ws_bytes = 0
+        self.open = []
+
+    def set_open(self, qubits):
+        """Leave these qubits' output indices open: contract_batch then gives 2^a amplitudes."""
+        qt_set_open(self.handle, qubits)
+        self.open = [int(q) for q in qubits]
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -405,10 +427,14 @@ class Network:
         qt_upload(self.handle, self.workspace.data_ptr(), self.workspace.numel(), self._stream())
 
     def run(self, first, count, out):
-        """Device-resident run; out is a float64 CUDA tensor with >= 2 elements."""
+        """Device-resident run; out is a float64 CUDA tensor with >= 2 * 2^a elements."""
         qt_run(self.handle, first, count, self.workspace.data_ptr(), self.workspace.numel(),
                self._stream(), out.data_ptr())
 
     def contract(self, precision=QT_FP32_SIMT):
         return qt_contract(self.handle, precision, self.workspace.data_ptr(),
                            self.workspace.numel(), self._stream())
+
+    def contract_batch(self, precision=QT_FP32_SIMT):
+        return qt_contract_batch(self.handle, precision, self.workspace.data_ptr(),
+                                 self.workspace.numel(), self._stream(), len(self.open))

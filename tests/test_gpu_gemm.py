@@ -39,8 +39,18 @@ def _amp(qt, n, p, seed, off, prec, force_gemm=False, profile=False):
 
 @pytest.mark.parametrize("case", CASES)
 def test_gemm_form_fp32_cuda_cores(qt, case):
+    """FP32 GEMM form: the shared-memory tiled kernel (kind 4) where every summed index is
+    in both big operands, the pack + CUDA-core GEMM (kind 3) elsewhere."""
     amp, ref, st, kinds = _amp(qt, *case, 0, force_gemm=True, profile=True)
-    assert st["gemm_groups"] >= 1 and 3 in kinds
+    assert st["gemm_groups"] >= 1 and kinds & {3, 4}
+    assert rel_err(amp, ref) <= TOL["fp32gemm"], (amp, ref)
+
+
+def test_gemm_tile_bench_workload(qt):
+    """N=80, p=2, seed 1002 sliced to width 26, every GEMM-form launch forced: the tiled
+    GEMM kernel runs and the amplitude meets the complex64 bar."""
+    amp, ref, st, kinds = _amp(qt, 80, 2, 1002, 26 - 35, 0, force_gemm=True, profile=True)
+    assert 4 in kinds
     assert rel_err(amp, ref) <= TOL["fp32gemm"], (amp, ref)
 
 

@@ -7,7 +7,7 @@ import os
 
 import pytest
 
-from helpers import oracle_plan, oracle_problem
+from helpers import oracle_plan, oracle_problem, oracle_problem_open
 from oracle import ledger
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -160,6 +160,81 @@ def test_errors(qt):
         with pytest.raises(QtError) as e:
             qt.qt_run(h, 0, 1, 256, need - 1, 0, 256)
         assert e.value.status == qt.QT_ENOMEM
+    finally:
+        qt.qt_free(h)
+
+
+OPEN_CASES = [(8, 1, 1, [0], 3, 4, 1), (12, 2, 3, [5, 1], 7, 4, 1), (12, 3, 3, [2, 9, 4], 8, 4, 2),
+              (24, 2, 15, [0, 23, 7, 11], 10, 6, 1), (30, 2, 11, [3, 4, 5, 6, 7, 8], 12, 6, 1)]
+
+
+@pytest.mark.parametrize("algo", [0, 1])
+@pytest.mark.parametrize("case", OPEN_CASES)
+def test_open_plan_bit_exact(qt, case, algo):
+    """Open qubits (Sec. VII): tensors, greedy order, slicing plan and launch groups of the
+    library equal the oracle's, the open variables never eliminated nor sliced."""
+    n, p, seed, opens, lim, mv, r = case
+    (edges, gammas, betas, z, tensors, nv, norm, adj, keep,
+     open_vars) = oracle_problem_open(n, p, seed, opens)
+    h = qt.qt_build_network(edges, n, p, gammas, betas, z)
+    try:
+        qt.qt_set_open(h, opens)
+        cnt, nvars = qt.qt_num_tensors(h)
+        assert cnt == len(tensors) and nvars == nv
+        for t, (labels, data) in enumerate(tensors):
+            lab, flat = qt.qt_get_tensor(h, t)
+            assert tuple(lab) == tuple(labels)
+            for e in range(1 << len(lab)):
+                want = data[tuple((e >> x) & 1 for x in range(len(lab)))]
+                assert abs(complex(flat[2 * e], flat[2 * e + 1]) - want) < 1e-15
+        from oracle import ordering
+        o, w = ordering.greedy_order(adj, None, {0: ordering.MIN_FILL, 1: ordering.MIN_DEGREE}[algo],
+                                     keep)
+        assert qt.qt_order(h, algo) == max(w)
+        assert qt.qt_get_order(h) == o and qt.qt_get_widths(h) == w
+        plan = oracle_plan(adj, algo, lim, mv, r, keep)
+        k, width = qt.qt_slice(h, lim, mv, r)
+        assert qt.qt_get_slices(h) == (plan["sliced"], plan["slice_step"])
+        assert qt.qt_get_order(h) == plan["order"] and width == plan["width"]
+        assert not set(plan["order"] + plan["sliced"]) & set(open_vars)
+        qt.qt_prepare(h, 0, 2)
+        st = qt.qt_stats(h)
+        assert st["n_open"] == len(opens)
+        tot, steps = ledger.ledger([l for l, _ in tensors], plan["order"], plan["sliced"],
+                                   plan["slice_step"])
+        for key in ("prefix_flops", "slice_flops", "slice_bytes", "n_slice_steps"):
+            assert st[key] == tot[key], key
+        groups = ledger.launch_groups([l for l, _ in tensors], plan["order"], plan["sliced"],
+                                      plan["slice_step"])
+        assert st["groups"] == groups
+        # back to one amplitude: the plain network again
+        qt.qt_set_open(h, [])
+        assert qt.qt_num_tensors(h)[1] == n * p
+        with pytest.raises(qt.QtError) as e:
+            qt.qt_prepare(h, 0, 1)
+        assert e.value.status == qt.QT_ESTATE
+    finally:
+        qt.qt_free(h)
+
+
+def test_open_errors(qt):
+    QtError = qt.QtError
+    h = qt.qt_build_network([(0, 1), (1, 2)], 3, 1, [0.1], [0.2], [0, 1, 0])
+    try:
+        for bad in ([0, 0], [3], [-1], list(range(17))):
+            with pytest.raises(QtError) as e:
+                qt.qt_set_open(h, bad)
+            assert e.value.status == qt.QT_EINVAL
+        qt.qt_set_open(h, [2, 0])
+        qt.qt_order(h, 0)
+        qt.qt_prepare(h, 0, 1)
+        # a single-amplitude call on a batched network is refused before any CUDA call
+        with pytest.raises(QtError) as e:
+            qt.qt_contract(h, 0, 256, 1 << 20, 0)
+        assert e.value.status == qt.QT_ESTATE
+        with pytest.raises(QtError) as e:
+            qt.qt_contract_static(h, 0, 0)
+        assert e.value.status == qt.QT_ESTATE
     finally:
         qt.qt_free(h)
 

@@ -160,6 +160,73 @@ def test_slicing_sum_invariant(n, p, seed, algo, drop, r):
     assert abs(tot * norm - sv) < 1e-12 * abs(sv)
 
 
+# ----------------------------- batch of amplitudes (Sec. VII) --------------
+
+def open_problem(n, p, seed, opens):
+    edges, g, b, z = qaoa_instance(n, p, seed)
+    t, nv, norm = network.build_network(n, edges, p, g, b, z, opens)
+    sets = network.open_clique(network.line_graph(t, nv), n, p, len(opens))
+    adj = ordering.adjacency_matrix(sets, nv)
+    keep = np.zeros(nv, dtype=bool)
+    keep[n * p:] = True
+    return edges, g, b, z, t, nv, norm, adj, keep
+
+
+@pytest.mark.parametrize("n,p,seed,opens,algo,drop", [
+    (8, 1, 51, [0], 0, 0), (10, 2, 52, [3, 7], 1, 0), (12, 2, 53, [11, 0, 5], 0, 2),
+    (12, 3, 54, [2, 4, 6, 8], 0, 3), (14, 2, 55, [1, 9, 13], 1, 2)])
+def test_open_batch_equals_statevector(n, p, seed, opens, algo, drop):
+    """Entry b of the open contraction is the amplitude of z with the open qubits set to
+    the bits of b (brute force over the 2^N statevector), sliced or not (Eq. 2)."""
+    edges, g, b, z, t, nv, norm, adj, keep = open_problem(n, p, seed, opens)
+    o, w = ordering.greedy_order(adj, None, algo, keep)
+    assert not set(o) & set(range(n * p, nv))
+    plan = slicing.step_dependent_slicing(adj, algo, max(w) - drop if drop else 1 << 30, 4, 1,
+                                          keep)
+    assert not set(plan["sliced"]) & set(range(n * p, nv))
+    if drop:
+        assert plan["sliced"], "the plan must slice"
+    ov = list(range(n * p, nv))
+    tot, per = contract.contract_amplitude(t, plan["order"], plan["sliced"], plan["slice_step"],
+                                           open_vars=ov)
+    psi = statevector.qaoa_state(n, edges, g, b)
+    a = len(opens)
+    for bits in range(1 << a):
+        zz = list(z)
+        for j, v in enumerate(opens):
+            zz[v] = (bits >> j) & 1
+        want = psi[sum(x << v for v, x in enumerate(zz))]
+        got = tot[tuple((bits >> j) & 1 for j in range(a))] * norm
+        assert abs(got - want) <= 1e-12 * max(abs(want), 1e-300) + 1e-15, bits
+
+
+def test_open_batch_bits_of_z_at_open_qubits_are_ignored():
+    n, p, seed, opens = 10, 2, 56, [4, 2]
+    edges, g, b, z, t, nv, norm, adj, keep = open_problem(n, p, seed, opens)
+    z2 = list(z)
+    for v in opens:
+        z2[v] ^= 1
+    t2, _, _ = network.build_network(n, edges, p, g, b, z2, opens)
+    o, _ = ordering.greedy_order(adj, None, 0, keep)
+    a1, _ = contract.contract_amplitude(t, o, open_vars=list(range(n * p, nv)))
+    a2, _ = contract.contract_amplitude(t2, o, open_vars=list(range(n * p, nv)))
+    assert np.array_equal(a1, a2)
+
+
+def test_open_greedy_hand_example():
+    """Path 0-1-2 with vertex 1 kept: min-fill takes 0 (fill 0, degree 1), then 2 (its
+    only neighbour is 1); vertex 1 is never eliminated. Without the mark: 0, 1, 2."""
+    a = adj_of(3, [(0, 1), (1, 2)])
+    keep = np.array([False, True, False])
+    assert ordering.greedy_order(a, None, 0, keep) == ([0, 2], [1, 1])
+    assert ordering.greedy_order(a, None, 0) == ([0, 1, 2], [1, 1, 0])
+    # slicing never removes a kept vertex, even the one with most neighbours
+    star = adj_of(4, [(0, 1), (0, 2), (0, 3), (1, 2)])
+    keep = np.array([True, False, False, False])
+    plan = slicing.step_dependent_slicing(star, 0, 1, 1, 1, keep)
+    assert plan["sliced"] and 0 not in plan["sliced"] and 0 not in plan["order"]
+
+
 # ----------------------------- orders and widths ----------------------------
 
 def test_greedy_hand_examples():
