@@ -124,6 +124,18 @@ qt_status qt_set_open(qt_net* net, const int32_t* qubits, int32_t a);
 qt_status qt_order(qt_net* net, int32_t algo, uint64_t seed, int32_t* width_out);
 
 /*
+ * Randomised greedy order "rgreedy" (Sec. V.A.2): each step eliminates vertex v
+ * with probability proportional to exp(-N_G(v)/tau) (N_G(v): its current
+ * neighbour count); the elimination is repeated q times from one SplitMix64
+ * stream seeded with `seed` (one uniform draw per step, vertices scanned in
+ * ascending id; weights r^(N_G(v) - min N_G) with r = exp(-1/tau)) and the
+ * order with the smallest (width, sum of 2^w, run) is kept. Open indices are
+ * never taken. A later qt_slice re-orders with QT_GREEDY_MINDEG, the rule that
+ * rgreedy randomises. Errors: QT_EINVAL for tau <= 0, a non-finite tau or q < 1.
+ */
+qt_status qt_order_rgreedy(qt_net* net, double tau, int32_t q, uint64_t seed, int32_t* width_out);
+
+/*
  * Step-dependent slicing (Sec. VI.C-D, Fig. 8, Alg. 1). Rounds repeat while the
  * plan's width exceeds width_limit and fewer than max_vars vertices are sliced.
  * A round orders the current graph greedily (rule of qt_order), and for every

@@ -204,6 +204,31 @@ qt_status qt_order(qt_net* net, int32_t algo, uint64_t seed, int32_t* width_out)
   return ok();
 }
 
+qt_status qt_order_rgreedy(qt_net* net, double tau, int32_t q, uint64_t seed, int32_t* width_out) {
+  if (!check_net(net)) return fail(QT_EINVAL, "qt_order_rgreedy: null network");
+  if (!(tau > 0.0) || !std::isfinite(tau) || q < 1)
+    return fail(QT_EINVAL, "qt_order_rgreedy: need a finite tau > 0 and q >= 1");
+  try {
+    qt::BitGraph g = qt::network_graph(net);
+    qt::OrderResult r = qt::rgreedy_order(g, tau, q, seed);
+    net->plan = qt::SlicePlan();
+    net->plan.order = r.order;
+    net->plan.widths = r.widths;
+    net->plan.greedy_runs = q;
+    int w = 0;
+    for (int x : r.widths) w = std::max(w, x);
+    net->plan.width = w;
+    net->algo = QT_GREEDY_MINDEG;  // the rule rgreedy randomises, for later slicing
+    net->ordered = true;
+    net->sched = qt::Schedule();
+    net->stage_dirty = true;
+    if (width_out) *width_out = w;
+  } catch (const std::bad_alloc&) {
+    return fail(QT_ENOMEM, "qt_order_rgreedy: out of host memory");
+  }
+  return ok();
+}
+
 qt_status qt_slice(qt_net* net, int32_t width_limit, int32_t max_vars, int32_t r, int32_t* k_out,
                    int32_t* width_out) {
   if (!check_net(net)) return fail(QT_EINVAL, "qt_slice: null network");

@@ -176,6 +176,107 @@ OrderResult greedy_order(const BitGraph& g0, int algo) {
   return res;
 }
 
+// ------------------------- randomised greedy --------------------------------
+// rgreedy (Sec. V.A.2): every step draws the next vertex with probability
+// proportional to exp(-N_G(v)/tau); best of q runs. Weights are shifted by the
+// step's smallest degree, r^(d - d_min) with r = exp(-1/tau), the power taken
+// by repeated multiplication; one uniform draw per step from a SplitMix64
+// stream (Steele, Lea, Flood, OOPSLA 2014) seeded with `seed`; the vertex taken
+// is the first, in ascending id, whose running weight sum exceeds u * total.
+namespace {
+struct SplitMix64 {
+  uint64_t s;
+  double uniform() {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  }
+};
+
+OrderResult rgreedy_run(const BitGraph& g0, const std::vector<double>& pw, SplitMix64& rng) {
+  BitGraph g = g0;
+  OrderResult res;
+  const int n = g.n;
+  std::vector<int> deg(n, 0), cand;
+  std::vector<double> w;
+  int remaining = 0;
+  for (int v = 0; v < n; ++v)
+    if (g.alive[v]) {
+      deg[v] = g.degree(v);
+      remaining += g.takeable(v);
+    }
+  std::vector<int> nb;
+  while (remaining > 0) {
+    cand.clear();
+    int dmin = 1 << 30;
+    for (int v = 0; v < n; ++v)
+      if (g.takeable(v)) {
+        cand.push_back(v);
+        dmin = std::min(dmin, deg[v]);
+      }
+    w.resize(cand.size());
+    double total = 0.0;
+    for (size_t c = 0; c < cand.size(); ++c) {
+      w[c] = pw[deg[cand[c]] - dmin];
+      total += w[c];
+    }
+    const double target = rng.uniform() * total;
+    int pick = cand.back();
+    double run = 0.0;
+    for (size_t c = 0; c < cand.size(); ++c) {
+      run += w[c];
+      if (run > target) {
+        pick = cand[c];
+        break;
+      }
+    }
+    nb.clear();
+    const uint64_t* rp = g.row(pick);
+    for (int x = 0; x < g.W; ++x) {
+      uint64_t bits = rp[x];
+      while (bits) {
+        nb.push_back(x * 64 + __builtin_ctzll(bits));
+        bits &= bits - 1;
+      }
+    }
+    res.order.push_back(pick);
+    res.widths.push_back((int32_t)nb.size());
+    g.eliminate(pick);
+    --remaining;
+    for (int a : nb) deg[a] = g.degree(a);
+  }
+  return res;
+}
+}  // namespace
+
+OrderResult rgreedy_order(const BitGraph& g, double tau, int q, uint64_t seed) {
+  SplitMix64 rng{seed};
+  const double r = std::exp(-1.0 / tau);
+  std::vector<double> pw((size_t)g.n + 1, 1.0);
+  for (size_t k = 1; k < pw.size(); ++k) pw[k] = pw[k - 1] * r;
+  OrderResult best;
+  int32_t best_w = 0;
+  double best_cost = 0.0;
+  for (int run = 0; run < q; ++run) {
+    OrderResult o = rgreedy_run(g, pw, rng);
+    int32_t w = 0;
+    double cost = 0.0;
+    for (int32_t x : o.widths) {
+      w = std::max(w, x);
+      cost += std::ldexp(1.0, x);
+    }
+    if (run == 0 || w < best_w || (w == best_w && cost < best_cost)) {
+      best = std::move(o);
+      best_w = w;
+      best_cost = cost;
+    }
+  }
+  return best;
+}
+
 // ---------------------------- slicing search --------------------------------
 static double plan_cost(const std::vector<int32_t>& a, const std::vector<int32_t>& b, int nb,
                         const std::vector<int32_t>& c) {

@@ -49,6 +49,8 @@ struct OrderResult {
 };
 
 OrderResult greedy_order(const BitGraph& g, int algo);
+// randomised greedy (Sec. V.A.2): best of q Boltzmann-weighted eliminations
+OrderResult rgreedy_order(const BitGraph& g, double tau, int q, uint64_t seed);
 
 struct SlicePlan {
   std::vector<int32_t> order;   // every non-sliced vertex, elimination order

@@ -50,6 +50,7 @@ _SIGS = {
     "qt_set_open": [_vp, _i32p, C.c_int32],
     "qt_contract_batch": [_vp, C.c_int32, _vp, C.c_size_t, _vp, _f64p],
     "qt_order": [_vp, C.c_int32, C.c_uint64, _i32p],
+    "qt_order_rgreedy": [_vp, C.c_double, C.c_int32, C.c_uint64, _i32p],
     "qt_slice": [_vp, C.c_int32, C.c_int32, C.c_int32, _i32p, _i32p],
     "qt_get_order": [_vp, _i32p, C.c_int32, _i32p],
     "qt_get_widths": [_vp, _i32p, C.c_int32, _i32p],
@@ -144,6 +145,12 @@ def qt_set_open(net, qubits):
 def qt_order(net, algo=QT_GREEDY_MINFILL, seed=0):
     w = C.c_int32()
     _check(lib.qt_order(net, int(algo), int(seed), C.byref(w)))
+    return w.value
+
+
+def qt_order_rgreedy(net, tau, q, seed):
+    w = C.c_int32()
+    _check(lib.qt_order_rgreedy(net, float(tau), int(q), int(seed), C.byref(w)))
     return w.value
 
 

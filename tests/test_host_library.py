@@ -217,6 +217,26 @@ def test_open_plan_bit_exact(qt, case, algo):
         qt.qt_free(h)
 
 
+@pytest.mark.parametrize("n,p,seed,tau,q,rs", [(10, 2, 3, 1.0, 4, 11), (24, 2, 15, 0.5, 3, 12),
+                                                 (30, 3, 11, 2.0, 2, 13), (44, 2, 14, 0.25, 5, 14),
+                                                 (12, 1, 5, 1e-3, 3, 15), (12, 1, 5, 1e9, 3, 16)])
+def test_rgreedy_bit_exact(qt, n, p, seed, tau, q, rs):
+    """rgreedy (Sec. V.A.2): the library's order and widths equal the oracle's for the same
+    seed of the draw stream."""
+    from oracle import rgreedy
+    edges, gammas, betas, z, tensors, nv, norm, adj = oracle_problem(n, p, seed)
+    o, w, _ = rgreedy.rgreedy_order(adj, tau, q, rs)
+    h = qt.qt_build_network(edges, n, p, gammas, betas, z)
+    try:
+        assert qt.qt_order_rgreedy(h, tau, q, rs) == max(w)
+        assert qt.qt_get_order(h) == o and qt.qt_get_widths(h) == w
+        with pytest.raises(qt.QtError) as e:
+            qt.qt_order_rgreedy(h, 0.0, 1, 0)
+        assert e.value.status == qt.QT_EINVAL
+    finally:
+        qt.qt_free(h)
+
+
 def test_open_errors(qt):
     QtError = qt.QtError
     h = qt.qt_build_network([(0, 1), (1, 2)], 3, 1, [0.1], [0.2], [0, 1, 0])

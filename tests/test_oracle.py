@@ -15,7 +15,7 @@ import os
 import numpy as np
 import pytest
 
-from oracle import contract, energy, ledger, network, ordering, slicing, statevector
+from oracle import contract, energy, ledger, network, ordering, rgreedy, slicing, statevector
 from paper_2012_02430_gb300.inputs import qaoa_instance, random_regular_graph
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -158,6 +158,61 @@ def test_slicing_sum_invariant(n, p, seed, algo, drop, r):
     assert abs(tot - full) < 1e-12 * abs(full)
     sv = statevector.amplitude(n, edges, g, b, z)
     assert abs(tot * norm - sv) < 1e-12 * abs(sv)
+
+
+# ----------------------------- randomised greedy (Sec. V.A.2) ---------------
+
+def test_rgreedy_boltzmann_first_pick_frequencies():
+    """Star K_{1,3}: leaves have degree 1, the centre 3. With tau = 1 the first vertex is
+    the centre with probability e^-3 / (3 e^-1 + e^-3); over 20000 seeds the observed
+    frequency is within 4 standard deviations (a sign or tau mistake fails this)."""
+    star = adj_of(4, [(0, 1), (0, 2), (0, 3)])
+    n = 20000
+    hits = 0
+    for seed in range(n):
+        o, _, _ = rgreedy.rgreedy_order(star, 1.0, 1, seed)
+        hits += o[0] == 0
+    pc = math.exp(-3) / (3 * math.exp(-1) + math.exp(-3))
+    sd = math.sqrt(pc * (1 - pc) / n)
+    assert abs(hits / n - pc) < 4 * sd, (hits / n, pc)
+
+
+def test_rgreedy_small_tau_is_min_degree():
+    """tau -> 0 puts all the weight on the smallest degrees: every step takes a vertex of
+    minimum current degree (the paper's greedy), ties broken at random."""
+    edges, g, b, z, t, nv, norm, adj = problem(14, 2, 61)
+    for seed in range(5):
+        o, w, _ = rgreedy.rgreedy_order(adj, 1e-3, 1, seed)
+        a = adj.copy()
+        alive = np.ones(nv, dtype=bool)
+        np.fill_diagonal(a, False)
+        for v in o:
+            degs = a[alive].sum(axis=1)
+            assert a[v].sum() == degs.min()
+            ordering.eliminate(a, alive, v)
+        assert sorted(o) == list(range(nv))
+
+
+def test_rgreedy_large_tau_is_uniform():
+    """tau -> infinity: the first vertex is uniform over the vertices (chi-square)."""
+    edges, g, b, z, t, nv, norm, adj = problem(8, 1, 62)
+    counts = np.zeros(nv)
+    n = 8000
+    for seed in range(n):
+        o, _, _ = rgreedy.rgreedy_order(adj, 1e12, 1, seed)
+        counts[o[0]] += 1
+    chi2 = ((counts - n / nv) ** 2 / (n / nv)).sum()
+    assert chi2 < 30.0, chi2  # 7 degrees of freedom: p < 1e-4 above 30
+
+
+def test_rgreedy_keeps_best_of_q_and_is_a_valid_order():
+    edges, g, b, z, t, nv, norm, adj = problem(16, 2, 63)
+    o, w, runs = rgreedy.rgreedy_order(adj, 0.5, 6, 7)
+    assert sorted(o) == list(range(nv)) and max(w) == min(runs)
+    assert ordering.replay_widths(adj, o) == w
+    a, _ = contract.contract_amplitude(t, o)
+    sv = statevector.amplitude(16, edges, g, b, z)
+    assert abs(a * norm - sv) <= 1e-12 * abs(sv)
 
 
 # ----------------------------- batch of amplitudes (Sec. VII) --------------
