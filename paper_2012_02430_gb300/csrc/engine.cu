@@ -217,29 +217,73 @@ static_assert(sizeof(KStep) <= kStepRecordBytes, "step record size");
 // handles slice b of the batch and runs the run's steps one after another with
 // a block barrier between them (a step's operands are earlier results of the
 // same slice, gates or prefix tensors, so no other block is waited for). Each
-// step is the flat kernel's arithmetic restricted to one slice.
+// step is the flat kernel's arithmetic restricted to one slice. The run's step
+// records are staged in shared memory once. Tensors written earlier in the same
+// launch (and their metadata, updated by L2 atomics) are read through L2 only
+// (ld.global.cg): neither the read-only path nor L1 may hold a stale copy of an
+// arena slot that an earlier step of the launch rewrote.
 constexpr int SEG_THREADS = 512;
 constexpr int SEG_MAX_U = 14;
+constexpr int SEG_MAX_STEPS = 128;  // step records per segment launch (shared memory)
+
+template <typename R>
+__device__ __forceinline__ void load_pair_cg(const R* data, long long off, bool has_bit0, R& r0,
+                                             R& i0, R& r1, R& i1) {
+  using C2 = typename CT<R>::c2;
+  if (has_bit0) {
+    if constexpr (sizeof(R) == 4) {
+      const float4 v = __ldcg(reinterpret_cast<const float4*>(data + 2 * off));
+      r0 = v.x; i0 = v.y; r1 = v.z; i1 = v.w;
+    } else {
+      const C2 a = __ldcg(reinterpret_cast<const C2*>(data + 2 * off));
+      const C2 b = __ldcg(reinterpret_cast<const C2*>(data + 2 * off + 2));
+      r0 = a.x; i0 = a.y; r1 = b.x; i1 = b.y;
+    }
+  } else {
+    const C2 a = __ldcg(reinterpret_cast<const C2*>(data + 2 * off));
+    r0 = r1 = a.x;
+    i0 = i1 = a.y;
+  }
+}
+
+__device__ __forceinline__ Meta ld_meta_cg(const Meta* m) {
+  const uint2 v = __ldcg(reinterpret_cast<const uint2*>(m));
+  return Meta{v.x, (int)v.y};
+}
 
 template <typename R>
 __global__ void __launch_bounds__(SEG_THREADS) k_segment(const KStep* steps, int nsteps, R* data,
                                                         Meta* meta, long long slice_first) {
-  __shared__ KStep st;
+  extern __shared__ KStep seg_steps[];
+  __shared__ R s_sc[MAXOP];
+  __shared__ int s_E;
   const long long i = blockIdx.x;
   const unsigned long long sid = (unsigned long long)(slice_first + i);
   const int lane = threadIdx.x & 31;
+  {
+    const int* src = reinterpret_cast<const int*>(steps);
+    int* dst = reinterpret_cast<int*>(seg_steps);
+    const int words = nsteps * (int)(sizeof(KStep) / 4);
+    for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = __ldcg(src + w);
+  }
+  __syncthreads();
   for (int q = 0; q < nsteps; ++q) {
-    const int* src = reinterpret_cast<const int*>(steps + q);
-    int* dst = reinterpret_cast<int*>(&st);
-    for (int w = threadIdx.x; w < (int)(sizeof(KStep) / 4); w += blockDim.x) dst[w] = src[w];
+    const KStep& st = seg_steps[q];
+    // operand scales and the result exponent, once per step
+    if (threadIdx.x < 32) {
+      int e = 0;
+      if (lane < st.m) {
+        const Meta mt = ld_meta_cg(meta + st.op[lane].meta + (st.op[lane].meta_per_slice ? i : 0));
+        const int sj = scale_exp(mt.maxabs);
+        s_sc[lane] = pow2_neg<R>(sj);
+        e = mt.E + sj;
+      }
+      for (int d = 16; d > 0; d >>= 1) e += __shfl_xor_sync(0xffffffffu, e, d);
+      if (lane == 0) s_E = e;
+    }
     __syncthreads();
     const long long npairs = 1ll << (st.u - 1);
     const int grp = 1 << (st.nsum - 1);
-    int Eout = 0;
-    for (int j = 0; j < st.m; ++j) {
-      const Meta mt = meta[st.op[j].meta + (st.op[j].meta_per_slice ? i : 0)];
-      Eout += mt.E + scale_exp(mt.maxabs);
-    }
     float mx = 0.f;
     for (long long b0 = 0; b0 < npairs; b0 += blockDim.x) {
       const long long g = b0 + threadIdx.x;
@@ -252,9 +296,9 @@ __global__ void __launch_bounds__(SEG_THREADS) k_segment(const KStep* steps, int
           if (o.level != 0) continue;
           long long off = o.base + i * o.slice_stride + (long long)pext64(I, o.umask);
           if (o.smask) off += (long long)(pext64(sid, o.smask) << o.sshift);
-          const R sc = pow2_neg<R>(scale_exp(meta[o.meta + (o.meta_per_slice ? i : 0)].maxabs));
+          const R sc = s_sc[j];
           R r0, i0, r1, i1;
-          load_pair<R>(data, off, o.umask & 1u, r0, i0, r1, i1);
+          load_pair_cg<R>(data, off, o.umask & 1u, r0, i0, r1, i1);
           cmul<R>(p0r, p0i, r0 * sc, i0 * sc);
           cmul<R>(p1r, p1i, r1 * sc, i1 * sc);
         }
@@ -267,9 +311,9 @@ __global__ void __launch_bounds__(SEG_THREADS) k_segment(const KStep* steps, int
             if (o.level != l) continue;
             long long off = o.base + i * o.slice_stride + (long long)pext64(I, o.umask);
             if (o.smask) off += (long long)(pext64(sid, o.smask) << o.sshift);
-            const R sc = pow2_neg<R>(scale_exp(meta[o.meta + (o.meta_per_slice ? i : 0)].maxabs));
+            const R sc = s_sc[j];
             using C2 = typename CT<R>::c2;
-            const C2 a = *reinterpret_cast<const C2*>(data + 2 * off);
+            const C2 a = __ldcg(reinterpret_cast<const C2*>(data + 2 * off));
             cmul<R>(sr, si, a.x * sc, a.y * sc);
           }
         }
@@ -284,7 +328,7 @@ __global__ void __launch_bounds__(SEG_THREADS) k_segment(const KStep* steps, int
     const unsigned int red = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
     if (lane == 0 && red != 0u)
       atomicMax(&meta[st.out_meta + (st.out_meta_per_slice ? i : 0)].maxabs, red);
-    if (threadIdx.x == 0) meta[st.out_meta + (st.out_meta_per_slice ? i : 0)].E = Eout;
+    if (threadIdx.x == 0) meta[st.out_meta + (st.out_meta_per_slice ? i : 0)].E = s_E;
     __syncthreads();
   }
 }
@@ -956,6 +1000,8 @@ static void fill_gemm(const Schedule& S, const SGroup& g, long long nslices, Gem
     if (j != g.gA && j != g.gB) (a.op[j].side ? a.fold_b : a.fold_a) = 1;
   }
   a.tb = gemm_tile_bits(a, g.u);
+  a.tile_inner = gemm_tile_inner(a, g.u);
+  gemm_tile_regs(a, a.reg_a, a.reg_b);
 }
 
 struct EngineCache {
@@ -1102,7 +1148,7 @@ static bool build_cache(qt_net* net, EngineCache& c, std::string& err) {
     for (size_t i = 0; i < list->size();) {
       size_t j = i;
       auto small = [&](const LaunchDesc& d) { return d.kind == 0 && d.k.u <= SEG_MAX_U; };
-      while (j < list->size() && small((*list)[j])) ++j;
+      while (j < list->size() && small((*list)[j]) && j - i < (size_t)SEG_MAX_STEPS) ++j;
       if (j - i >= 2 && net->segments) {
         LaunchDesc d = (*list)[i];
         d.kind = 5;
@@ -1143,8 +1189,14 @@ static void launch_desc(qt_net* net, const LaunchDesc& d0, long long nslices, lo
     if (net->prof) prof_begin(net, s, pr);
     net->launches++;
     const KStep* tab = reinterpret_cast<const KStep*>(base + S.off_segtab) + d0.seg_first;
-    k_segment<R><<<(unsigned)nslices, SEG_THREADS, 0, s>>>(tab, d0.seg_count, data, meta,
-                                                          slice_first);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_segment<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(SEG_MAX_STEPS * sizeof(KStep)));
+      attr = true;
+    }
+    k_segment<R><<<(unsigned)nslices, SEG_THREADS, d0.seg_count * sizeof(KStep), s>>>(
+        tab, d0.seg_count, data, meta, slice_first);
     if (net->prof) prof_end(net, s, pr);
     return;
   }

@@ -43,6 +43,8 @@ __device__ __forceinline__ int scale_exp_g(unsigned int maxabs_bits) {
 
 __device__ __forceinline__ float pow2_neg_g(int s) { return __int_as_float((127 - s) << 23); }
 
+__device__ __forceinline__ float absmax_g(float re, float im) { return fmaxf(fabsf(re), fabsf(im)); }
+
 // Byte-sliced lookup tables in shared memory replace per-element bit loops:
 // pdep(x, mask) for a dimension's index = sum over its bytes of T[byte][value],
 // pext(U, umask) for an operand = sum over the four bytes of U of P[byte][value].
@@ -324,89 +326,190 @@ __global__ void __launch_bounds__(256) k_gemm_fold(const GemmArgs a, int side, f
   }
 }
 
+__device__ __forceinline__ unsigned int pdep32g(unsigned int x, unsigned int m) {
+  unsigned int r = 0;
+  int k = 0;
+  while (m) {
+    const int b = __ffs(m) - 1;
+    r |= ((x >> k) & 1u) << b;
+    ++k;
+    m &= m - 1;
+  }
+  return r;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // GEMM_TILE, the product: a tile is the 2^tb lowest output indices for fixed
 // higher ones, i.e. the lowest nsum + tb bits of U. In the canonical layout those
 // bits are the lowest bits of every operand, so the tile reads one contiguous
 // block of A' (rows = A's output indices in the tile, columns = the K summed
-// indices, all of which A and B share) and one of B', stages both in shared
-// memory and writes its 2^tb outputs as one contiguous, coalesced run.
+// indices, all of which A and B share) and one of B', copies both into shared
+// memory with asynchronous 16-byte copies (the next tile's copies overlap this
+// tile's products: two buffers) and writes its 2^tb outputs as one contiguous
+// run. The operands' power-of-two scales multiply the finished sums. Tiles are
+// visited with the high output indices of one side innermost (tile_inner), so
+// consecutive tiles reuse the other side's block from L2; thread 0 locates the
+// tile after next while the block works on the current one.
+//
+// Register blocking: with an A-only output bit rA and a B-only bit rB inside the
+// tile, a thread computes the four outputs that differ in those two bits. They
+// share two A rows and two B rows, so one k step is 4 shared-memory loads for
+// 8 complex multiply-adds.
 __global__ void __launch_bounds__(256) k_gemm_tile(const GemmArgs a, int u, float* data,
                                                    GMeta* meta) {
   extern __shared__ float4 gsm[];
-  const int nsum = a.nsum, t = a.tb, c = u - nsum;
-  const int K = 1 << nsum, RS = K + 2;  // row stride (complex): keeps rows 16-byte aligned
+  __shared__ long long s_loc[3][4];  // tile slots: slice, tau, A block, B block
+  const int nsum = a.nsum, t = a.tb, c = u - nsum, h = c - t;
+  const int K = 1 << nsum, RS = K + 2;  // row stride (complex): rows stay 16-byte aligned
+  const int KC = K >> 1, lkc = nsum - 1;  // 16-byte chunks per row
   const GOp& OA = a.op[a.gA];
   const GOp& OB = a.op[a.gB];
   const unsigned int L = (nsum + t >= 32) ? 0xffffffffu : ((1u << (nsum + t)) - 1u);
   const int la = __popc(OA.umask & L), lb = __popc(OB.umask & L);
   const int rows_a = 1 << (la - nsum), rows_b = 1 << (lb - nsum);
-  float2* sA = reinterpret_cast<float2*>(gsm);
-  float2* sB = sA + rows_a * RS;
-  unsigned int* RT = reinterpret_cast<unsigned int*>(sB + rows_b * RS);
+  const int buf = (rows_a + rows_b) * RS;  // complex per buffer
+  float2* sbase = reinterpret_cast<float2*>(gsm);
+  unsigned int* RT = reinterpret_cast<unsigned int*>(sbase + 2 * buf);
+  unsigned int* RT2 = RT + (1 << t);
   const unsigned int ma = (OA.umask & L) >> nsum, mb = (OB.umask & L) >> nsum;
   const int T = 1 << t;
-  for (int o = threadIdx.x; o < T; o += blockDim.x)
+  const bool blocked = a.reg_a >= 0;
+  const unsigned int rmask = blocked ? ((1u << a.reg_a) | (1u << a.reg_b)) : 0u;
+  for (int o = threadIdx.x; o < T; o += blockDim.x) {
     RT[o] = pext32g((unsigned)o, ma) | (pext32g((unsigned)o, mb) << 16);
-  const long long per = 1ll << (c - t);
+    if (blocked && o < (T >> 2)) RT2[o] = pdep32g((unsigned)o, (unsigned)(T - 1) & ~rmask);
+  }
+  const long long per = 1ll << h;
   const long long ntiles = a.nslices * per;
+  const unsigned int inner = a.tile_inner, hmask = h >= 32 ? 0xffffffffu : ((1u << h) - 1u);
+  const int pin = __popc(inner);
   const float2* d2 = reinterpret_cast<const float2*>(data);
-  long long cur = -1, baseA = 0, baseB = 0;
-  float scA = 1.f, scB = 1.f, mx = 0.f;
+  auto locate = [&](long long w, int slot) {
+    const long long i = w / per;
+    const unsigned int tp = (unsigned int)(w - i * per);
+    const long long tau = inner ? (long long)(pdep32g(tp & ((1u << pin) - 1u), inner) |
+                                              pdep32g(tp >> pin, ~inner & hmask))
+                                : (long long)tp;
+    const unsigned long long sid = (unsigned long long)(a.slice_first + i);
+    const long long ba = a.fold_a ? a.scratch_a + i * a.scratch_stride : op_slice_base(OA, i, sid);
+    const long long bb = a.fold_b ? a.scratch_b + i * a.scratch_stride : op_slice_base(OB, i, sid);
+    const unsigned long long Uh = (unsigned long long)tau << (nsum + t);
+    s_loc[slot][0] = i;
+    s_loc[slot][1] = tau;
+    s_loc[slot][2] = ba + ((long long)pext64g(Uh, OA.umask & ~L) << la);
+    s_loc[slot][3] = bb + ((long long)pext64g(Uh, OB.umask & ~L) << lb);
+  };
+  auto issue = [&](int slot, float2* dst) {
+    const long long ta = s_loc[slot][2], tb = s_loc[slot][3];
+    float2* sA = dst;
+    float2* sB = dst + rows_a * RS;
+    for (int e = threadIdx.x; e < rows_a * KC; e += blockDim.x)
+      cp_async16(sA + (e >> lkc) * RS + 2 * (e & (KC - 1)), d2 + ta + 2 * e);
+    for (int e = threadIdx.x; e < rows_b * KC; e += blockDim.x)
+      cp_async16(sB + (e >> lkc) * RS + 2 * (e & (KC - 1)), d2 + tb + 2 * e);
+    cp_async_commit();
+  };
+  const long long G = gridDim.x;
+  long long w = blockIdx.x;
+  if (threadIdx.x == 0) {
+    if (w < ntiles) locate(w, 0);
+    if (w + G < ntiles) locate(w + G, 1);
+  }
   __syncthreads();
-  for (long long w = blockIdx.x; w < ntiles; w += gridDim.x) {
-    const long long i = w / per, tau = w - i * per;
-    if (i != cur) {
+  if (w < ntiles) issue(0, sbase);
+  long long cur = -1;
+  float sc = 1.f, mx = 0.f;
+  for (int j = 0; w < ntiles; ++j, w += G) {
+    const int slot = j % 3;
+    if (w + G < ntiles) {
+      issue((j + 1) % 3, sbase + ((j + 1) & 1) * buf);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    if (threadIdx.x == 0 && w + 2 * G < ntiles) locate(w + 2 * G, (j + 2) % 3);
+    __syncthreads();
+    const long long i_c = s_loc[slot][0], tau_c = s_loc[slot][1];
+    if (i_c != cur) {
       if (cur >= 0) flush_max(a, meta, cur, mx);
       mx = 0.f;
-      cur = i;
-      const unsigned long long sid = (unsigned long long)(a.slice_first + i);
-      if (a.fold_a) {
-        baseA = a.scratch_a + i * a.scratch_stride;
-        scA = 1.f;
-      } else {
-        baseA = op_slice_base(OA, i, sid);
-        scA = pow2_neg_g(scale_exp_g(meta[OA.meta + (OA.meta_per_slice ? i : 0)].maxabs));
-      }
-      if (a.fold_b) {
-        baseB = a.scratch_b + i * a.scratch_stride;
-        scB = 1.f;
-      } else {
-        baseB = op_slice_base(OB, i, sid);
-        scB = pow2_neg_g(scale_exp_g(meta[OB.meta + (OB.meta_per_slice ? i : 0)].maxabs));
-      }
-      if (tau == 0 && threadIdx.x == 0) write_meta_e(a, meta, i);
+      cur = i_c;
+      const float sa = a.fold_a ? 1.f
+          : pow2_neg_g(scale_exp_g(meta[OA.meta + (OA.meta_per_slice ? i_c : 0)].maxabs));
+      const float sb = a.fold_b ? 1.f
+          : pow2_neg_g(scale_exp_g(meta[OB.meta + (OB.meta_per_slice ? i_c : 0)].maxabs));
+      sc = sa * sb;
+      if (tau_c == 0 && threadIdx.x == 0) write_meta_e(a, meta, i_c);
     }
-    const unsigned long long Uh = (unsigned long long)tau << (nsum + t);
-    const long long ta = baseA + ((long long)pext64g(Uh, OA.umask & ~L) << la);
-    const long long tb = baseB + ((long long)pext64g(Uh, OB.umask & ~L) << lb);
-    for (int e = threadIdx.x; e < (rows_a << nsum); e += blockDim.x) {
-      const float2 v = d2[ta + e];
-      sA[(e >> nsum) * RS + (e & (K - 1))] = make_float2(v.x * scA, v.y * scA);
-    }
-    for (int e = threadIdx.x; e < (rows_b << nsum); e += blockDim.x) {
-      const float2 v = d2[tb + e];
-      sB[(e >> nsum) * RS + (e & (K - 1))] = make_float2(v.x * scB, v.y * scB);
-    }
-    __syncthreads();
-    float2* out = reinterpret_cast<float2*>(data) + a.out_base + i * a.out_slice_stride + (tau << t);
-    for (int o = threadIdx.x; o < T; o += blockDim.x) {
-      const unsigned int rt = RT[o];
-      const float4* pa = reinterpret_cast<const float4*>(sA + (rt & 0xffffu) * RS);
-      const float4* pb = reinterpret_cast<const float4*>(sB + (rt >> 16) * RS);
-      float cr = 0.f, ci = 0.f;
-      for (int k2 = 0; k2 < (K >> 1); ++k2) {
-        const float4 x = pa[k2], y = pb[k2];
-        cr = fmaf(x.x, y.x, cr);
-        cr = fmaf(-x.y, y.y, cr);
-        ci = fmaf(x.x, y.y, ci);
-        ci = fmaf(x.y, y.x, ci);
-        cr = fmaf(x.z, y.z, cr);
-        cr = fmaf(-x.w, y.w, cr);
-        ci = fmaf(x.z, y.w, ci);
-        ci = fmaf(x.w, y.z, ci);
+    const float2* sA = sbase + (j & 1) * buf;
+    const float2* sB = sA + rows_a * RS;
+    float2* out = reinterpret_cast<float2*>(data) + a.out_base + i_c * a.out_slice_stride +
+                  (tau_c << t);
+    if (blocked) {
+      for (int q = threadIdx.x; q < (T >> 2); q += blockDim.x) {
+        const unsigned int o00 = RT2[q];
+        const unsigned int o10 = o00 | (1u << a.reg_a), o01 = o00 | (1u << a.reg_b);
+        const unsigned int o11 = o10 | (1u << a.reg_b);
+        const float4* pa0 = reinterpret_cast<const float4*>(sA + (RT[o00] & 0xffffu) * RS);
+        const float4* pa1 = reinterpret_cast<const float4*>(sA + (RT[o10] & 0xffffu) * RS);
+        const float4* pb0 = reinterpret_cast<const float4*>(sB + (RT[o00] >> 16) * RS);
+        const float4* pb1 = reinterpret_cast<const float4*>(sB + (RT[o01] >> 16) * RS);
+        float c00r = 0.f, c00i = 0.f, c01r = 0.f, c01i = 0.f, c10r = 0.f, c10i = 0.f,
+              c11r = 0.f, c11i = 0.f;
+#pragma unroll 2
+        for (int k2 = 0; k2 < KC; ++k2) {
+          const float4 x0 = pa0[k2], x1 = pa1[k2], y0 = pb0[k2], y1 = pb1[k2];
+#define QT_CMAC2(CR, CI, P, Q)                                                          \
+  CR = fmaf(P.x, Q.x, CR); CR = fmaf(-P.y, Q.y, CR); CI = fmaf(P.x, Q.y, CI);          \
+  CI = fmaf(P.y, Q.x, CI); CR = fmaf(P.z, Q.z, CR); CR = fmaf(-P.w, Q.w, CR);          \
+  CI = fmaf(P.z, Q.w, CI); CI = fmaf(P.w, Q.z, CI);
+          QT_CMAC2(c00r, c00i, x0, y0)
+          QT_CMAC2(c01r, c01i, x0, y1)
+          QT_CMAC2(c10r, c10i, x1, y0)
+          QT_CMAC2(c11r, c11i, x1, y1)
+#undef QT_CMAC2
+        }
+        out[o00] = make_float2(c00r * sc, c00i * sc);
+        out[o01] = make_float2(c01r * sc, c01i * sc);
+        out[o10] = make_float2(c10r * sc, c10i * sc);
+        out[o11] = make_float2(c11r * sc, c11i * sc);
+        mx = fmaxf(mx, fmaxf(fmaxf(absmax_g(c00r, c00i), absmax_g(c01r, c01i)),
+                             fmaxf(absmax_g(c10r, c10i), absmax_g(c11r, c11i))) * sc);
       }
-      out[o] = make_float2(cr, ci);
-      mx = fmaxf(mx, fmaxf(fabsf(cr), fabsf(ci)));
+    } else {
+      for (int o = threadIdx.x; o < T; o += blockDim.x) {
+        const unsigned int rt = RT[o];
+        const float4* pa = reinterpret_cast<const float4*>(sA + (rt & 0xffffu) * RS);
+        const float4* pb = reinterpret_cast<const float4*>(sB + (rt >> 16) * RS);
+        float cr = 0.f, ci = 0.f;
+#pragma unroll 4
+        for (int k2 = 0; k2 < KC; ++k2) {
+          const float4 x = pa[k2], y = pb[k2];
+          cr = fmaf(x.x, y.x, cr);
+          cr = fmaf(-x.y, y.y, cr);
+          ci = fmaf(x.x, y.y, ci);
+          ci = fmaf(x.y, y.x, ci);
+          cr = fmaf(x.z, y.z, cr);
+          cr = fmaf(-x.w, y.w, cr);
+          ci = fmaf(x.z, y.w, ci);
+          ci = fmaf(x.w, y.z, ci);
+        }
+        cr *= sc;
+        ci *= sc;
+        out[o] = make_float2(cr, ci);
+        mx = fmaxf(mx, absmax_g(cr, ci));
+      }
     }
     __syncthreads();
   }
@@ -546,11 +649,13 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs a, float* data, 
 
 }  // namespace
 
+constexpr size_t kTileSmemMax = 100 * 1024;
+
 static size_t tile_smem(const GemmArgs& a, int t) {
   const unsigned int L = (a.nsum + t >= 32) ? 0xffffffffu : ((1u << (a.nsum + t)) - 1u);
   const long long ra = 1ll << (__builtin_popcount(a.op[a.gA].umask & L) - a.nsum);
   const long long rb = 1ll << (__builtin_popcount(a.op[a.gB].umask & L) - a.nsum);
-  return (size_t)((ra + rb) * ((1ll << a.nsum) + 2) * 8 + (4ll << t));
+  return (size_t)(2 * (ra + rb) * ((1ll << a.nsum) + 2) * 8 + (4ll << t) + (1ll << t));
 }
 
 int gemm_tile_bits(const GemmArgs& a, int u) {
@@ -559,8 +664,31 @@ int gemm_tile_bits(const GemmArgs& a, int u) {
     return 0;
   const int c = u - a.nsum;
   for (int t = std::min(c, 10); t >= 5; --t)
-    if (tile_smem(a, t) <= 48 * 1024) return t;
+    if (tile_smem(a, t) <= kTileSmemMax) return t;
   return 0;
+}
+
+void gemm_tile_regs(const GemmArgs& a, int& reg_a, int& reg_b) {
+  // the highest A-only and B-only output bits inside the tile (-1: none)
+  reg_a = reg_b = -1;
+  for (int b = 0; b < a.tb; ++b) {
+    if ((a.mM >> (a.nsum + b)) & 1u) reg_a = b;
+    if ((a.mN >> (a.nsum + b)) & 1u) reg_b = b;
+  }
+  if (reg_a < 0 || reg_b < 0 || a.tb < 3) reg_a = reg_b = -1;
+}
+
+unsigned int gemm_tile_inner(const GemmArgs& a, int u) {
+  // the high output bits of the side whose block is smaller go innermost, so
+  // consecutive tiles share the larger side's block
+  const int t = a.tb, hb = u - a.nsum - t;
+  if (t <= 0 || hb <= 0) return 0u;
+  const bool a_larger = __builtin_popcount(a.op[a.gA].umask) >= __builtin_popcount(a.op[a.gB].umask);
+  const unsigned int only = a_larger ? a.mN : a.mM;  // indices of the smaller side only
+  unsigned int inner = 0;
+  for (int b = 0; b < hb; ++b)
+    if ((only >> (a.nsum + t + b)) & 1u) inner |= 1u << b;
+  return inner;
 }
 
 int gemm_launch(const GemmArgs& a, int mode, float* data, GMeta* meta, cudaStream_t s, int sms) {
@@ -575,9 +703,18 @@ int gemm_launch(const GemmArgs& a, int mode, float* data, GMeta* meta, cudaStrea
     }
     int u = 0;
     for (unsigned int m = a.mK | a.mSA | a.mSB | a.mM | a.mN | a.mBt; m; m >>= 1) ++u;
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_gemm_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kTileSmemMax);
+      attr = true;
+    }
+    const size_t smem = tile_smem(a, a.tb);
     const long long ntiles = a.nslices << (u - a.nsum - a.tb);
-    const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(ntiles, (long long)sms * 6));
-    k_gemm_tile<<<grid, 256, tile_smem(a, a.tb), s>>>(a, u, data, meta);
+    const int per_sm = std::max<int>(1, std::min<int>(8, (int)((220 * 1024) / (smem + 1024))));
+    const unsigned grid =
+        (unsigned)std::max<long long>(1, std::min<long long>(ntiles, (long long)sms * per_sm));
+    k_gemm_tile<<<grid, 256, smem, s>>>(a, u, data, meta);
     return n + 1;
   }
   const int kb = __builtin_popcount(a.mK), bb = __builtin_popcount(a.mBt);

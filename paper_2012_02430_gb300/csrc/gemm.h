@@ -32,13 +32,20 @@ struct GemmArgs {
   int out_meta_per_slice, pad;
   long long scratch_a, scratch_b, scratch_stride;  // elements (complex64 units)
   // GEMM_TILE: big operands, output indices per tile, which sides are folded
-  int gA, gB, tb, fold_a, fold_b, pad2;
+  int gA, gB, tb, fold_a, fold_b;
+  unsigned int tile_inner;  // high output indices (above tb) visited innermost
+  int reg_a, reg_b;         // register-blocking bits of the tile (-1: none)
   GOp op[GEMM_MAXOP];
 };
 
 // Output indices per tile of the GEMM_TILE kernel for a launch (0: the launch
 // does not take that form: a one-sided summed index, or too little shared memory).
 int gemm_tile_bits(const GemmArgs& a, int u);
+// Tile visiting order of the GEMM_TILE kernel for a launch with tile bits a.tb.
+unsigned int gemm_tile_inner(const GemmArgs& a, int u);
+// Register-blocking bits of the GEMM_TILE kernel: an A-only and a B-only output
+// bit inside the tile, or -1, -1.
+void gemm_tile_regs(const GemmArgs& a, int& reg_a, int& reg_b);
 
 // GEMM_TILE: fold A', fold B' (when the side has small operands), tiled GEMM;
 // other modes: pack A', pack B', GEMM. Returns the number of kernels launched.
