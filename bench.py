@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-modes", action="store_true", help="skip the precision-mode table")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-slices", type=int, default=1)
+    ap.add_argument("--profile-pass", action="store_true",
+                    help="for ncu: plan, autotune and warm the amplitude path, then run one pass "
+                         "inside the NVTX range 'qt_pass' (direct launches) and print its launch list")
     return ap.parse_args()
 
 
@@ -291,7 +294,8 @@ def ours(args):
         d["n"] += 1
     kind_names = {0: "k_bucket_flat", 1: "k_bucket_tiled", 2: "k_finalize+k_reduce",
                   3: "gemm_form (k_gemm_pack x2 + k_gemm_tc/simt)",
-                  4: "gemm_tile (k_gemm_fold + k_gemm_tile)"}
+                  4: "gemm_tile (k_gemm_fold + k_gemm_tile)", 5: "k_segment",
+                  6: "k_tri_tile"}
     tot_ms = sum(d["ms"] for d in by_kind.values()) or 1.0
     dom = max(by_kind, key=lambda kk: by_kind[kk]["ms"])
     d = by_kind[dom]
@@ -345,6 +349,9 @@ def ours(args):
     del plain
 
     energy_line = batched_energy(args, Q, torch, flush, stream)
+    batch_line = batched_amplitudes(args, Q, torch, edges, gammas, betas, z, prec, flush, stream,
+                                    total_ms / args.steps)
+    order_line = orderings(Q, edges, gammas, betas, z)
     modes_line = None if args.no_modes else precision_modes(Q, torch, edges, gammas, betas, z,
                                                             flush, stream)
 
@@ -384,6 +391,8 @@ def ours(args):
         * (st["elem_bytes"] // 8),
         "plain_fp32_greedy_path": plain_line,
         "batched_energy": energy_line,
+        "batched_amplitudes": batch_line,
+        "orderings": order_line,
         "precision_modes": modes_line,
         "amplitude": [amp.real, amp.imag],
         "gpu_launches": launches,
@@ -479,13 +488,100 @@ def batched_energy(args, Q, torch, flush, stream):
             "upload_bytes": st["upload_bytes"]}
 
 
+BATCH_OPEN = 8  # open qubits of the batched-amplitude measurement: 2^8 amplitudes
+
+
+def batched_amplitudes(args, Q, torch, edges, gammas, betas, z, prec, flush, stream, ms_single):
+    """Sec. VII: the same circuit with BATCH_OPEN output indices left open (the lowest-id
+    qubits), planned with the same rule and width limit; 2^a amplitudes per contraction.
+    Device-resident, autotuned, CUDA events, L2 flushed between runs."""
+    n, p = WORKLOAD["n"], WORKLOAD["p"]
+    net = Q.Network(edges, n, p, gammas, betas, z)
+    net.set_open(list(range(BATCH_OPEN)))
+    w = net.order(Q.QT_GREEDY_MINFILL)
+    k, sw = net.slice(WORKLOAD["width_limit"], WORKLOAD["max_vars"], WORKLOAD["r"])
+    net.prepare(prec, batch=1 << k)
+    net.upload()
+    net.autotune()
+    out = torch.zeros(2 << BATCH_OPEN, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        net.run(0, 1 << k, out)
+    reps = max(3, min(args.steps, 10))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    for i in range(reps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        net.run(0, 1 << k, out)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b2) for a, b2 in ev) / reps
+    return {"open_qubits": BATCH_OPEN, "amplitudes": 1 << BATCH_OPEN, "width": w, "k": k,
+            "sliced_width": sw, "ms_per_batch": ms, "amplitudes_per_s": (1 << BATCH_OPEN) / (ms / 1e3),
+            "ms_single_amplitude": ms_single,
+            "cost_ratio_vs_single": ms / ms_single}
+
+
+def orderings(Q, edges, gammas, betas, z, taus=(0.1, 0.3, 1.0), q=128, seed=1):
+    """Sec. V.A: contraction width of the bench circuit under the greedy rules and rgreedy
+    (best of q Boltzmann-weighted runs), with the host planner's wall time."""
+    n, p = WORKLOAD["n"], WORKLOAD["p"]
+    h = Q.qt_build_network(edges, n, p, gammas, betas, z)
+    res = {}
+    try:
+        for name, algo in (("greedy_minfill", Q.QT_GREEDY_MINFILL), ("greedy_mindeg", Q.QT_GREEDY_MINDEG)):
+            t0 = time.perf_counter()
+            res[name] = {"width": Q.qt_order(h, algo), "seconds": time.perf_counter() - t0}
+        for tau in taus:
+            t0 = time.perf_counter()
+            w = Q.qt_order_rgreedy(h, tau, q, seed)
+            res[f"rgreedy_tau{tau}_q{q}"] = {"width": w, "seconds": time.perf_counter() - t0}
+    finally:
+        Q.qt_free(h)
+    return res
+
+
 def gate_upload_bytes(st):
     """Bytes of the host-to-device copies of one qt_contract (gates, gate meta, scalar table)."""
     return int(st.get("upload_bytes", 0))
 
 
+def profile_pass(args):
+    """One amplitude pass of the bench workload for ncu (--nvtx --nvtx-include qt_pass/):
+    same plan, precision, batch and autotuned variants as the timed steps; no L2 flush."""
+    import torch
+
+    from paper_2012_02430_gb300 import qtensor as Q
+    prec = PRECISIONS[args.precision]
+    edges, gammas, betas, z = instance(0)
+    net = Q.Network(edges, WORKLOAD["n"], WORKLOAD["p"], gammas, betas, z)
+    net.order(Q.QT_GREEDY_MINFILL)
+    k, _ = net.slice(WORKLOAD["width_limit"], WORKLOAD["max_vars"], WORKLOAD["r"])
+    Q.qt_set_option(net.handle, Q.QT_OPT_GRAPHS, 0)
+    net.prepare(prec, batch=1 << k)
+    net.upload()
+    net.autotune()
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        net.run(0, 1 << k, out)
+    Q.qt_profile(net.handle, 1)
+    net.run(0, 1 << k, out)
+    torch.cuda.synchronize()
+    recs = Q.qt_profile_read(net.handle)
+    Q.qt_profile(net.handle, 0)
+    torch.cuda.nvtx.range_push("qt_pass")
+    net.run(0, 1 << k, out)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_pass": [[r["step"], r["kernel"], round(r["ms"], 4)] for r in recs],
+                      "amplitude": [out[0].item(), out[1].item()]}))
+
+
 def main():
     args = parse()
+    if args.profile_pass:
+        profile_pass(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:

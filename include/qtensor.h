@@ -319,8 +319,16 @@ void qt_mlp_free(qt_mlp* mlp);
  *                  of at most 14 indices) run as one segment launch, one block
  *                  per slice stepping through them with block barriers; 0: one
  *                  launch each. Discards the prepared schedule.
+ *   QT_OPT_TRIANGLE 1: launches in triangle form run it by default (complex64
+ *                  precisions): three large tensors A, B, C with every summed
+ *                  index in exactly two of them (K: A and B, X: A and C, Y: B
+ *                  and C), the others inside C or summed-only inside K; then
+ *                  out = sum_k w(k) sum_x A[k,x] sum_y B[k,y] C'[x,y], tiled over
+ *                  the lowest U bits in shared memory. 0 (default): only the
+ *                  autotuner may pick it. Discards the prepared schedule.
  * Errors: QT_EINVAL for a null network or an unknown option. */
-enum { QT_OPT_FUSION = 1, QT_OPT_GRAPHS = 2, QT_OPT_GEMM = 3, QT_OPT_SEGMENTS = 4 };
+enum { QT_OPT_FUSION = 1, QT_OPT_GRAPHS = 2, QT_OPT_GEMM = 3, QT_OPT_SEGMENTS = 4,
+       QT_OPT_TRIANGLE = 5 };
 qt_status qt_set_option(qt_net* net, int32_t option, int64_t value);
 
 /*

@@ -311,6 +311,7 @@ qt_status qt_prepare(qt_net* net, int32_t precision, int32_t batch, size_t* work
                   "qt_prepare: " + err);
     }
     net->sched.force_gemm = net->force_gemm;
+    net->sched.force_tri = net->force_tri;
   } catch (const std::bad_alloc&) {
     net->sched = qt::Schedule();
     return fail(QT_ENOMEM, "qt_prepare: out of host memory");
@@ -524,6 +525,10 @@ qt_status qt_set_option(qt_net* net, int32_t option, int64_t value) {
       break;
     case QT_OPT_SEGMENTS:
       net->segments = value != 0;
+      net->sched = qt::Schedule();  // prepare again
+      break;
+    case QT_OPT_TRIANGLE:
+      net->force_tri = value != 0;
       net->sched = qt::Schedule();  // prepare again
       break;
     default:

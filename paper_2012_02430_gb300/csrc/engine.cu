@@ -925,7 +925,7 @@ struct LaunchDesc {
   int group;    // schedule launch group
   int kind;     // 0 flat, 1 tiled, 3 GEMM form (pack A', pack B', GEMM), 4 GEMM form
                 // (fold A', fold B', shared-memory tiled GEMM), 5 segment (a run of small
-                // flat launches, one block per slice)
+                // flat launches, one block per slice), 6 triangle form
   int variant;  // 0..2 tiled kernel variants, 3 GEMM form
   int gemm_mode;
   unsigned grid;
@@ -934,6 +934,8 @@ struct LaunchDesc {
 };
 
 constexpr int VARIANT_GEMM = 3;
+constexpr int VARIANT_TRI = 4;
+constexpr int N_ALL_VARIANTS = 5;
 
 // GEMM flavour of a GEMM-form launch in a precision mode
 static int gemm_mode_for(const Schedule& S, const SGroup& g) {
@@ -1004,6 +1006,50 @@ static void fill_gemm(const Schedule& S, const SGroup& g, long long nslices, Gem
   gemm_tile_regs(a, a.reg_a, a.reg_b);
 }
 
+// Triangle form of a launch (three large operands; see gemm.cu k_tri_tile).
+static void fill_tri(const Schedule& S, const SGroup& g, long long nslices, GemmArgs& a) {
+  a = GemmArgs{};
+  a.m = (int)g.ops.size();
+  a.nsum = g.nsum;
+  a.nslices = nslices;
+  const STensor& out = S.tensors[g.out];
+  const long long eb = S.elem_bytes;
+  const bool per_slice = out.kind == TK_SLICE;
+  const long long region = (long long)(per_slice ? S.off_slices : S.off_prefix) / eb;
+  a.out_base = region + out.offset;
+  a.out_slice_stride = per_slice ? S.slice_elems : 0;
+  a.out_meta_per_slice = per_slice ? 1 : 0;
+  a.out_meta = out.meta;
+  a.gA = a.gB = -1;
+  a.reg_a = a.reg_b = -1;
+  for (int j = 0; j < a.m; ++j) {
+    KOp o;
+    fill_op(S, g, j, o);
+    GOp& q = a.op[j];
+    q.base = o.base;
+    q.slice_stride = o.slice_stride;
+    q.meta = o.meta;
+    q.umask = o.umask;
+    q.smask = o.smask;
+    q.sshift = o.sshift;
+    q.meta_per_slice = o.meta_per_slice;
+    q.tfold = g.tfold[j];
+  }
+  a.tA = g.tA;
+  a.tB = g.tB;
+  a.tC = g.tC;
+  a.tK = g.tK;
+  a.tX = g.tX;
+  a.tY = g.tY;
+  a.tb = tri_tile_bits(a, g.u);
+  // consecutive tiles share A's or B's block: high output bits missing from A or B innermost
+  const int hb = g.u - g.nsum - a.tb;
+  const unsigned int AB = a.op[g.tA].umask & a.op[g.tB].umask;
+  a.tile_inner = 0;
+  for (int b = 0; b < hb && a.tb > 0; ++b)
+    if (!((AB >> (g.nsum + a.tb + b)) & 1u)) a.tile_inner |= 1u << b;
+}
+
 struct EngineCache {
   uint64_t generation = 0;
   std::vector<LaunchDesc> prefix, slice;
@@ -1072,7 +1118,9 @@ static bool make_desc(const Schedule& S, int gi, long long nslices, LaunchDesc& 
                       std::string& err, int variant = -1) {
   const SGroup& st = S.groups[gi];
   if (variant < 0)
-    variant = st.gemm && (tc_precision(S.precision) || S.force_gemm) ? VARIANT_GEMM : 1;
+    variant = st.gemm && (tc_precision(S.precision) || S.force_gemm)
+                  ? VARIANT_GEMM
+                  : (st.tri && S.force_tri ? VARIANT_TRI : 1);
   KStep& k = d.k;
   k = KStep{};
   k.m = (int)st.ops.size();
@@ -1118,7 +1166,15 @@ static bool make_desc(const Schedule& S, int gi, long long nslices, LaunchDesc& 
     d.grid = 0;
     return true;
   }
-  if (variant == VARIANT_GEMM) d.variant = variant = 1;
+  if (variant == VARIANT_TRI && st.tri && sizeof(R) == 4) {
+    fill_tri(S, st, nslices, d.ga);
+    if (d.ga.tb > 0) {
+      d.kind = 6;
+      d.grid = 0;
+      return true;
+    }
+  }
+  if (variant >= VARIANT_GEMM) d.variant = variant = 1;
   if (tiled) {
     const long long ntiles = nslices << (st.u - TILE_UBITS);
     d.grid = (unsigned)std::min<long long>(ntiles, tiled_grid_cap<R>(variant, k.ms));
@@ -1215,6 +1271,15 @@ static void launch_desc(qt_net* net, const LaunchDesc& d0, long long nslices, lo
   ProfRec pr{S.groups[d0.group].first, d0.kind, nslices, d0.bytes * nslices, d0.flops * nslices,
              nullptr, nullptr};
   if (net->prof) prof_begin(net, s, pr);
+  if (d0.kind == 6) {
+    GemmArgs ga = d0.ga;
+    ga.nslices = nslices;
+    ga.slice_first = slice_first;
+    net->launches += tri_launch(ga, reinterpret_cast<float*>(base), reinterpret_cast<GMeta*>(meta),
+                                s, num_sms());
+    if (net->prof) prof_end(net, s, pr);
+    return;
+  }
   if (d0.kind >= 3) {
     GemmArgs ga = d0.ga;
     ga.nslices = nslices;
@@ -1306,15 +1371,21 @@ static qt_status autotune_impl(qt_net* net, char* base, cudaStream_t s, std::str
       LaunchDesc& d = list[i];
       const SGroup& grp = S.groups[d.group];
       const bool can_gemm = grp.gemm && !tc_precision(S.precision) && sizeof(R) == 4;
+      const bool can_tri = grp.tri && !tc_precision(S.precision) && sizeof(R) == 4;
       if (d.kind == 0 || d.kind == 5 ||
-          ((d.kind == 3 || d.kind == 4) && (tc_precision(S.precision) || S.force_gemm))) {
+          ((d.kind == 3 || d.kind == 4) && (tc_precision(S.precision) || S.force_gemm)) ||
+          (d.kind == 6 && S.force_tri)) {
         launch_desc<R>(net, d, nb, b0, base, s);
         continue;
       }
-      const int nv = N_VARIANTS + (can_gemm ? 1 : 0);
+      std::vector<int> cands;
+      for (int v = 0; v < N_VARIANTS; ++v) cands.push_back(v);
+      if (can_gemm) cands.push_back(VARIANT_GEMM);
+      if (can_tri) cands.push_back(VARIANT_TRI);
+      const int nv = (int)cands.size();
       for (int pass = 0; pass < 2; ++pass)
         for (int t = 0; t < nv; ++t) {
-          const int v = pass == 0 ? t : nv - 1 - t;
+          const int v = cands[pass == 0 ? t : nv - 1 - t];
           LaunchDesc dv = d;
           std::string e2;
           make_desc<R>(S, d.group, d.k.nslices, dv, e2, v);
@@ -1348,7 +1419,7 @@ static qt_status autotune_impl(qt_net* net, char* base, cudaStream_t s, std::str
       float ms = 0.f;
       cudaEventElapsedTime(&ms, tr.a, tr.b);
       if (acc.empty() || acc.back().first.list != tr.list || acc.back().first.idx != tr.idx)
-        acc.push_back({Key{tr.list, tr.idx}, std::vector<float>(N_VARIANTS + 1, 1e30f)});
+        acc.push_back({Key{tr.list, tr.idx}, std::vector<float>(N_ALL_VARIANTS, 1e30f)});
       float& slot = acc.back().second[tr.variant];
       slot = slot >= 1e29f ? ms : slot + ms;
     }
@@ -1356,16 +1427,17 @@ static qt_status autotune_impl(qt_net* net, char* base, cudaStream_t s, std::str
     for (auto& kv : acc) {
       LaunchDesc& d = (*kv.first.list)[kv.first.idx];
       int bv = 0;
-      for (int v = 1; v <= N_VARIANTS; ++v)
+      for (int v = 1; v < N_ALL_VARIANTS; ++v)
         if (kv.second[v] < kv.second[bv]) bv = v;
       std::string e2;
       make_desc<R>(S, d.group, d.k.nslices, d, e2, bv);
       char buf[200];
       auto half = [](float x) { return x >= 1e29f ? -1.0 : x / 2.0; };
       std::snprintf(buf, sizeof buf,
-                    "%s{\"step\":%d,\"variant\":%d,\"ms\":[%.4f,%.4f,%.4f,%.4f]}",
+                    "%s{\"step\":%d,\"variant\":%d,\"ms\":[%.4f,%.4f,%.4f,%.4f,%.4f]}",
                     first ? "" : ",", S.groups[d.group].first, bv, half(kv.second[0]),
-                    half(kv.second[1]), half(kv.second[2]), half(kv.second[3]));
+                    half(kv.second[1]), half(kv.second[2]), half(kv.second[3]),
+                    half(kv.second[4]));
       report += buf;
       first = false;
     }

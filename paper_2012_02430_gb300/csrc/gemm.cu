@@ -647,6 +647,315 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs a, float* data, 
   if (cur >= 0) flush_max(a, meta, cur, mx);
 }
 
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// Triangle form of a fused launch: three large operands A, B, C, every summed
+// index in exactly two of them (K: A and B, X: A and C, Y: B and C), so
+//   out[o] = sum_k w(k) sum_x A[o; k, x] sum_y B[o; k, y] C'[o; x, y],
+// C' = C times the operands inside C, w = the product of the summed-only
+// operands inside K. Against the elementwise nested sum (3 loads per U element)
+// this reads |X||Y| + |K|(|X| + |Y|) values per output instead of 3|K||X||Y|.
+// A tile is the 2^tb lowest output indices for fixed higher ones (the lowest
+// nsum + tb bits of U), so each operand's block is contiguous; the blocks are
+// copied into shared memory transposed ([summed column][row], 8-byte async
+// copies, two buffers), making the lanes' rows (consecutive outputs) consecutive
+// words. Thread 0 locates the tile after next while the block works.
+struct TriLayout {
+  int laA, laB, laC, sA, sB, sC, rA, rB, rC, nA, nB, nC, nK, nX, nY, buf;
+  size_t off_cf, off_rt, off_col, off_w, bytes;
+};
+
+__host__ __device__ inline int popc_h(unsigned int x) {
+#ifdef __CUDA_ARCH__
+  return __popc(x);
+#else
+  return __builtin_popcount(x);
+#endif
+}
+
+__host__ __device__ inline TriLayout tri_layout(const GemmArgs& a, int t) {
+  TriLayout l{};
+  const unsigned int L = (a.nsum + t >= 32) ? 0xffffffffu : ((1u << (a.nsum + t)) - 1u);
+  const unsigned int Sm = (1u << a.nsum) - 1u;
+  const unsigned int mA = a.op[a.tA].umask, mB = a.op[a.tB].umask, mC = a.op[a.tC].umask;
+  l.laA = popc_h(mA & L); l.laB = popc_h(mB & L); l.laC = popc_h(mC & L);
+  l.sA = popc_h(mA & Sm); l.sB = popc_h(mB & Sm); l.sC = popc_h(mC & Sm);
+  l.rA = 1 << (l.laA - l.sA); l.rB = 1 << (l.laB - l.sB); l.rC = 1 << (l.laC - l.sC);
+  l.nA = 1 << l.laA; l.nB = 1 << l.laB; l.nC = 1 << l.laC;
+  l.nK = 1 << popc_h(a.tK); l.nX = 1 << popc_h(a.tX); l.nY = 1 << popc_h(a.tY);
+  l.buf = l.nA + l.nB + l.nC;
+  size_t off = (size_t)2 * l.buf * 8;            // two buffers of complex64
+  l.off_cf = off;  off += (size_t)l.nC * 8;       // C'
+  l.off_rt = off;  off += (size_t)3 * 2 * (1u << t);  // row tables (uint16)
+  off = (off + 15) / 16 * 16;
+  l.off_col = off; off += (size_t)4 * (l.nK * l.nX + l.nK * l.nY + l.nX * l.nY);
+  off = (off + 15) / 16 * 16;
+  l.off_w = off;   off += (size_t)8 * l.nK;
+  l.bytes = off;
+  return l;
+}
+
+template <int NX, int NY>
+__global__ void __launch_bounds__(256) k_tri_tile(const GemmArgs a, int u, float* data,
+                                                  GMeta* meta) {
+  extern __shared__ float4 trsm[];
+  __shared__ long long s_loc[3][5];   // tile slots: slice, tau, A, B, C block starts
+  __shared__ long long s_fb[GEMM_MAXOP];  // tile bases of the operands folded into C
+  __shared__ unsigned int s_fx[GEMM_MAXOP];  // their indices in C's local bit numbering
+  __shared__ float s_fs[GEMM_MAXOP];  // their scales
+  __shared__ float s_sc;
+  const int nsum = a.nsum, t = a.tb, c = u - nsum, h = c - t;
+  const TriLayout ly = tri_layout(a, t);
+  const unsigned int L = (nsum + t >= 32) ? 0xffffffffu : ((1u << (nsum + t)) - 1u);
+  const unsigned int Sm = (1u << nsum) - 1u;
+  const GOp& OA = a.op[a.tA];
+  const GOp& OB = a.op[a.tB];
+  const GOp& OC = a.op[a.tC];
+  char* sm = reinterpret_cast<char*>(trsm);
+  float2* bufs = reinterpret_cast<float2*>(sm);
+  float2* sCf = reinterpret_cast<float2*>(sm + ly.off_cf);
+  unsigned short* RA = reinterpret_cast<unsigned short*>(sm + ly.off_rt);
+  const int T = 1 << t;
+  unsigned short* RB = RA + T;
+  unsigned short* RC = RB + T;
+  int* colA = reinterpret_cast<int*>(sm + ly.off_col);
+  int* colB = colA + ly.nK * NX;
+  int* colC = colB + ly.nK * NY;
+  float2* W = reinterpret_cast<float2*>(sm + ly.off_w);
+  const int nK = ly.nK;
+  // per-launch tables
+  {
+    const unsigned int ma = (OA.umask & L) >> nsum, mb = (OB.umask & L) >> nsum,
+                       mc = (OC.umask & L) >> nsum;
+    for (int o = threadIdx.x; o < T; o += blockDim.x) {
+      RA[o] = (unsigned short)pext32g((unsigned)o, ma);
+      RB[o] = (unsigned short)pext32g((unsigned)o, mb);
+      RC[o] = (unsigned short)pext32g((unsigned)o, mc);
+    }
+    for (int e = threadIdx.x; e < nK * NX; e += blockDim.x) {
+      const unsigned int U = pdep32g((unsigned)(e / NX), a.tK) | pdep32g((unsigned)(e % NX), a.tX);
+      colA[e] = (int)pext32g(U, OA.umask & Sm) * ly.rA;
+    }
+    for (int e = threadIdx.x; e < nK * NY; e += blockDim.x) {
+      const unsigned int U = pdep32g((unsigned)(e / NY), a.tK) | pdep32g((unsigned)(e % NY), a.tY);
+      colB[e] = (int)pext32g(U, OB.umask & Sm) * ly.rB;
+    }
+    for (int e = threadIdx.x; e < NX * NY; e += blockDim.x) {
+      const unsigned int U = pdep32g((unsigned)(e / NY), a.tX) | pdep32g((unsigned)(e % NY), a.tY);
+      colC[e] = (int)pext32g(U, OC.umask & Sm) * ly.rC;
+    }
+    for (int j = threadIdx.x; j < a.m; j += blockDim.x)
+      s_fx[j] = pext32g(a.op[j].umask & L, OC.umask & L);
+  }
+  const long long per = 1ll << h;
+  const long long ntiles = a.nslices * per;
+  const unsigned int inner = a.tile_inner, hmask = h >= 32 ? 0xffffffffu : ((1u << h) - 1u);
+  const int pin = __popc(inner);
+  const float2* d2 = reinterpret_cast<const float2*>(data);
+  auto tile_base = [&](const GOp& o, long long i, unsigned long long sid,
+                       unsigned long long Uh) -> long long {
+    return op_slice_base(o, i, sid) + ((long long)pext64g(Uh, o.umask & ~L) << __popc(o.umask & L));
+  };
+  auto locate = [&](long long w, int slot) {
+    const long long i = w / per;
+    const unsigned int tp = (unsigned int)(w - i * per);
+    const long long tau = inner ? (long long)(pdep32g(tp & ((1u << pin) - 1u), inner) |
+                                              pdep32g(tp >> pin, ~inner & hmask))
+                                : (long long)tp;
+    const unsigned long long sid = (unsigned long long)(a.slice_first + i);
+    const unsigned long long Uh = (unsigned long long)tau << (nsum + t);
+    s_loc[slot][0] = i;
+    s_loc[slot][1] = tau;
+    s_loc[slot][2] = tile_base(OA, i, sid, Uh);
+    s_loc[slot][3] = tile_base(OB, i, sid, Uh);
+    s_loc[slot][4] = tile_base(OC, i, sid, Uh);
+  };
+  auto issue = [&](int slot, float2* dst) {
+    const float2* srcA = d2 + s_loc[slot][2];
+    const float2* srcB = d2 + s_loc[slot][3];
+    const float2* srcC = d2 + s_loc[slot][4];
+    float2* dA = dst;
+    float2* dB = dA + ly.nA;
+    float2* dC = dB + ly.nB;
+    for (int e = threadIdx.x; e < ly.nA; e += blockDim.x)
+      cp_async8(dA + (e & ((1 << ly.sA) - 1)) * ly.rA + (e >> ly.sA), srcA + e);
+    for (int e = threadIdx.x; e < ly.nB; e += blockDim.x)
+      cp_async8(dB + (e & ((1 << ly.sB) - 1)) * ly.rB + (e >> ly.sB), srcB + e);
+    for (int e = threadIdx.x; e < ly.nC; e += blockDim.x)
+      cp_async8(dC + (e & ((1 << ly.sC) - 1)) * ly.rC + (e >> ly.sC), srcC + e);
+    cp_async_commit();
+  };
+  const long long G = gridDim.x;
+  long long w = blockIdx.x;
+  if (threadIdx.x == 0) {
+    if (w < ntiles) locate(w, 0);
+    if (w + G < ntiles) locate(w + G, 1);
+  }
+  __syncthreads();
+  if (w < ntiles) issue(0, bufs);
+  long long cur = -1;
+  float mx = 0.f;
+  bool has_fold = false, has_w = false;
+  for (int j = 0; j < a.m; ++j) {
+    has_fold |= a.op[j].tfold == 1;
+    has_w |= a.op[j].tfold == 2;
+  }
+  for (int jt = 0; w < ntiles; ++jt, w += G) {
+    const int slot = jt % 3;
+    if (w + G < ntiles) {
+      issue((jt + 1) % 3, bufs + ((jt + 1) & 1) * ly.buf);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    if (threadIdx.x == 0 && w + 2 * G < ntiles) locate(w + 2 * G, (jt + 2) % 3);
+    const long long i_c = s_loc[slot][0], tau_c = s_loc[slot][1];
+    const unsigned long long sid = (unsigned long long)(a.slice_first + i_c);
+    const unsigned long long Uh = (unsigned long long)tau_c << (nsum + t);
+    if (i_c != cur) {
+      // per slice: the weight over K and the large operands' scales
+      if (has_w)
+        for (int k = threadIdx.x; k < nK; k += blockDim.x) {
+          float wr = 1.f, wi = 0.f;
+          const unsigned int U = pdep32g((unsigned)k, a.tK);
+          for (int q = 0; q < a.m; ++q) {
+            const GOp& o = a.op[q];
+            if (o.tfold != 2) continue;
+            const float sc = pow2_neg_g(scale_exp_g(meta[o.meta + (o.meta_per_slice ? i_c : 0)].maxabs));
+            const float2 v = d2[op_slice_base(o, i_c, sid) + pext32g(U, o.umask)];
+            const float vr = v.x * sc, vi = v.y * sc;
+            const float nr = wr * vr - wi * vi, ni = wr * vi + wi * vr;
+            wr = nr;
+            wi = ni;
+          }
+          W[k] = make_float2(wr, wi);
+        }
+      if (threadIdx.x == 0) {
+        s_sc = pow2_neg_g(scale_exp_g(meta[OA.meta + (OA.meta_per_slice ? i_c : 0)].maxabs)) *
+               pow2_neg_g(scale_exp_g(meta[OB.meta + (OB.meta_per_slice ? i_c : 0)].maxabs));
+        for (int q = 0; q < a.m; ++q)
+          if (q == a.tC || a.op[q].tfold == 1)
+            s_fs[q] = pow2_neg_g(scale_exp_g(meta[a.op[q].meta + (a.op[q].meta_per_slice ? i_c : 0)].maxabs));
+      }
+    }
+    if (threadIdx.x < a.m && a.op[threadIdx.x].tfold == 1)
+      s_fb[threadIdx.x] = tile_base(a.op[threadIdx.x], i_c, sid, Uh);
+    __syncthreads();
+    if (i_c != cur) {
+      if (cur >= 0) flush_max(a, meta, cur, mx);
+      mx = 0.f;
+      cur = i_c;
+      if (tau_c == 0 && threadIdx.x == 0) write_meta_e(a, meta, i_c);
+    }
+    const float2* sA = bufs + (jt & 1) * ly.buf;
+    const float2* sB = sA + ly.nA;
+    const float2* sC = sB + ly.nB;
+    // C' = C times the operands folded into it (same transposed layout)
+    {
+      const float scC = s_fs[a.tC];
+      for (int e = threadIdx.x; e < ly.nC; e += blockDim.x) {
+        const int pos = (e & ((1 << ly.sC) - 1)) * ly.rC + (e >> ly.sC);
+        float2 v = sC[pos];
+        float pr = v.x * scC, pi = v.y * scC;
+        if (has_fold)
+          for (int q = 0; q < a.m; ++q) {
+            if (a.op[q].tfold != 1) continue;
+            const float2 f = d2[s_fb[q] + pext32g((unsigned)e, s_fx[q])];
+            const float fr = f.x * s_fs[q], fi = f.y * s_fs[q];
+            const float nr = pr * fr - pi * fi, ni = pr * fi + pi * fr;
+            pr = nr;
+            pi = ni;
+          }
+        sCf[pos] = make_float2(pr, pi);
+      }
+    }
+    __syncthreads();
+    float2* out = reinterpret_cast<float2*>(data) + a.out_base + i_c * a.out_slice_stride +
+                  (tau_c << t);
+    const float sc = s_sc;
+    for (int o = threadIdx.x; o < T; o += blockDim.x) {
+      const int ra = RA[o], rb = RB[o], rc = RC[o];
+      float cvr[NX * NY], cvi[NX * NY];
+#pragma unroll
+      for (int xy = 0; xy < NX * NY; ++xy) {
+        const float2 v = sCf[colC[xy] + rc];
+        cvr[xy] = v.x;
+        cvi[xy] = v.y;
+      }
+      float accr = 0.f, acci = 0.f;
+      for (int k = 0; k < nK; ++k) {
+        float bvr[NY], bvi[NY];
+#pragma unroll
+        for (int y = 0; y < NY; ++y) {
+          const float2 v = sB[colB[k * NY + y] + rb];
+          bvr[y] = v.x;
+          bvi[y] = v.y;
+        }
+        float sr = 0.f, si = 0.f;
+#pragma unroll
+        for (int x = 0; x < NX; ++x) {
+          float yr = 0.f, yi = 0.f;
+#pragma unroll
+          for (int y = 0; y < NY; ++y) {
+            yr = fmaf(bvr[y], cvr[x * NY + y], yr);
+            yr = fmaf(-bvi[y], cvi[x * NY + y], yr);
+            yi = fmaf(bvr[y], cvi[x * NY + y], yi);
+            yi = fmaf(bvi[y], cvr[x * NY + y], yi);
+          }
+          const float2 av = sA[colA[k * NX + x] + ra];
+          sr = fmaf(av.x, yr, sr);
+          sr = fmaf(-av.y, yi, sr);
+          si = fmaf(av.x, yi, si);
+          si = fmaf(av.y, yr, si);
+        }
+        if (has_w) {
+          const float2 wk = W[k];
+          accr = fmaf(wk.x, sr, accr);
+          accr = fmaf(-wk.y, si, accr);
+          acci = fmaf(wk.x, si, acci);
+          acci = fmaf(wk.y, sr, acci);
+        } else {
+          accr += sr;
+          acci += si;
+        }
+      }
+      accr *= sc;
+      acci *= sc;
+      out[o] = make_float2(accr, acci);
+      mx = fmaxf(mx, absmax_g(accr, acci));
+    }
+    __syncthreads();
+  }
+  if (cur >= 0) flush_max(a, meta, cur, mx);
+}
+
+using TriFn = void (*)(const GemmArgs, int, float*, GMeta*);
+
+template <int NX, int NY>
+TriFn tri_fn_xy() {
+  return k_tri_tile<NX, NY>;
+}
+
+TriFn tri_fn(int nx, int ny) {
+  switch (nx * 8 + ny) {
+    case 1 * 8 + 1: return tri_fn_xy<1, 1>();
+    case 2 * 8 + 1: return tri_fn_xy<2, 1>();
+    case 4 * 8 + 1: return tri_fn_xy<4, 1>();
+    case 8 * 8 + 1: return tri_fn_xy<8, 1>();
+    case 16 * 8 + 1: return tri_fn_xy<16, 1>();
+    case 2 * 8 + 2: return tri_fn_xy<2, 2>();
+    case 4 * 8 + 2: return tri_fn_xy<4, 2>();
+    case 8 * 8 + 2: return tri_fn_xy<8, 2>();
+    case 4 * 8 + 4: return tri_fn_xy<4, 4>();
+    default: return nullptr;
+  }
+}
+
+constexpr size_t kTriSmemMax = 100 * 1024;
+
 }  // namespace
 
 constexpr size_t kTileSmemMax = 100 * 1024;
@@ -689,6 +998,39 @@ unsigned int gemm_tile_inner(const GemmArgs& a, int u) {
   for (int b = 0; b < hb; ++b)
     if ((only >> (a.nsum + t + b)) & 1u) inner |= 1u << b;
   return inner;
+}
+
+int tri_tile_bits(const GemmArgs& a, int u) {
+  if (a.tA < 0) return 0;
+  const int nx = 1 << __builtin_popcount(a.tX), ny = 1 << __builtin_popcount(a.tY);
+  if (!tri_fn(nx, ny)) return 0;
+  const int c = u - a.nsum;
+  for (int t = std::min(c, 10); t >= 7; --t) {
+    const TriLayout l = tri_layout(a, t);
+    if (l.bytes <= kTriSmemMax && l.rA <= 65535 && l.rB <= 65535 && l.rC <= 65535) return t;
+  }
+  return 0;
+}
+
+int tri_launch(const GemmArgs& a, float* data, GMeta* meta, cudaStream_t s, int sms) {
+  int u = 0;
+  for (unsigned int m = a.op[a.tA].umask | a.op[a.tB].umask | a.op[a.tC].umask; m; m >>= 1) ++u;
+  const int nx = 1 << __builtin_popcount(a.tX), ny = 1 << __builtin_popcount(a.tY);
+  TriFn fn = tri_fn(nx, ny);
+  static bool attr[5][5] = {};
+  const int ix = __builtin_ctz(nx), iy = __builtin_ctz(ny);
+  if (!attr[ix][iy]) {
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriSmemMax);
+    attr[ix][iy] = true;
+  }
+  const TriLayout l = tri_layout(a, a.tb);
+  const long long ntiles = a.nslices << (u - a.nsum - a.tb);
+  const int threads = std::min(256, 1 << a.tb);
+  const int per_sm = std::max<int>(1, std::min<int>(8, (int)((220 * 1024) / (l.bytes + 2048))));
+  const unsigned grid =
+      (unsigned)std::max<long long>(1, std::min<long long>(ntiles, (long long)sms * per_sm));
+  fn<<<grid, threads, l.bytes, s>>>(a, u, data, meta);
+  return 1;
 }
 
 int gemm_launch(const GemmArgs& a, int mode, float* data, GMeta* meta, cudaStream_t s, int sms) {

@@ -22,6 +22,7 @@ struct GOp {
   unsigned int umask, smask;
   int sshift, meta_per_slice, side;
   unsigned int xmask;  // GEMM_TILE: the operand's indices in the bit numbering of its side's big operand
+  int tfold, pad;      // triangle form: 0 large, 1 folded into C, 2 weight over K
 };
 
 struct GemmArgs {
@@ -35,6 +36,8 @@ struct GemmArgs {
   int gA, gB, tb, fold_a, fold_b;
   unsigned int tile_inner;  // high output indices (above tb) visited innermost
   int reg_a, reg_b;         // register-blocking bits of the tile (-1: none)
+  int tA, tB, tC;           // triangle form: the large operands
+  unsigned int tK, tX, tY;  // triangle form: summed bits of each class
   GOp op[GEMM_MAXOP];
 };
 
@@ -46,6 +49,11 @@ unsigned int gemm_tile_inner(const GemmArgs& a, int u);
 // Register-blocking bits of the GEMM_TILE kernel: an A-only and a B-only output
 // bit inside the tile, or -1, -1.
 void gemm_tile_regs(const GemmArgs& a, int& reg_a, int& reg_b);
+
+// Triangle form (three large operands): output indices per tile (0: not taken)
+// and the launch (one kernel).
+int tri_tile_bits(const GemmArgs& a, int u);
+int tri_launch(const GemmArgs& a, float* data, GMeta* meta, cudaStream_t s, int sms);
 
 // GEMM_TILE: fold A', fold B' (when the side has small operands), tiled GEMM;
 // other modes: pack A', pack B', GEMM. Returns the number of kernels launched.

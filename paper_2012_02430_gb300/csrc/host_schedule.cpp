@@ -350,6 +350,56 @@ bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePla
       g.side = side;
     }
   }
+  // triangle form of large groups with three large operands (complex64 precisions)
+  if (precision != QT_FP64) {
+    for (SGroup& g : S.groups) {
+      if (g.u < 16 || g.ops.size() < 3 || g.nsum > 6) continue;
+      std::vector<uint32_t> mask(g.ops.size(), 0u);
+      for (size_t j = 0; j < g.ops.size(); ++j)
+        for (int32_t l : seen_labels(g.ops[j], g.region))
+          for (int b = 0; b < g.u; ++b)
+            if (g.ulabels[b] == l) mask[j] |= 1u << b;
+      // the three largest operands (ties: earlier operand)
+      std::vector<int> idx(g.ops.size());
+      for (size_t j = 0; j < idx.size(); ++j) idx[j] = (int)j;
+      std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+        return __builtin_popcount(mask[x]) > __builtin_popcount(mask[y]);
+      });
+      int a = idx[0], b = idx[1], c = idx[2];
+      const uint32_t Sm = (1u << g.nsum) - 1u;
+      uint32_t K = 0, X = 0, Y = 0;
+      bool ok = __builtin_popcount(mask[c]) >= 4;
+      for (int bit = 0; bit < g.nsum && ok; ++bit) {
+        const bool ia = (mask[a] >> bit) & 1u, ib = (mask[b] >> bit) & 1u, ic = (mask[c] >> bit) & 1u;
+        if (ia && ib && !ic) K |= 1u << bit;
+        else if (ia && ic && !ib) X |= 1u << bit;
+        else if (ib && ic && !ia) Y |= 1u << bit;
+        else ok = false;  // in all three, or in one only
+      }
+      if (!ok) continue;
+      if (__builtin_popcount(Y) > __builtin_popcount(X)) {  // Y the smaller class
+        std::swap(a, b);
+        std::swap(X, Y);
+      }
+      std::vector<int8_t> fold(g.ops.size(), 0);
+      for (size_t j = 0; j < g.ops.size() && ok; ++j) {
+        if ((int)j == a || (int)j == b || (int)j == c) continue;
+        if ((mask[j] & ~mask[c]) == 0u) fold[j] = 1;
+        else if ((mask[j] & ~K) == 0u) fold[j] = 2;
+        else ok = false;
+      }
+      const int nx = 1 << __builtin_popcount(X), ny = 1 << __builtin_popcount(Y);
+      if (!ok || ny > 4 || nx * ny > 16) continue;
+      g.tri = true;
+      g.tA = a;
+      g.tB = b;
+      g.tC = c;
+      g.tK = K;
+      g.tX = X;
+      g.tY = Y;
+      g.tfold = fold;
+    }
+  }
   // liveness by group: a stored tensor lives from its group to the last group reading it
   const int end_group = (int)S.groups.size();
   for (STensor& t : S.tensors) t.last_use = -1;
@@ -430,7 +480,8 @@ bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePla
 std::string schedule_json(const Schedule& S, const SlicePlan& plan) {
   std::ostringstream o;
   int64_t gemm_flops = 0, tc_flops = 0, k32_flops = 0, total_flops = 0;
-  int n_gemm = 0;
+  int n_gemm = 0, n_tri = 0;
+  for (const SGroup& g : S.groups) n_tri += g.tri;
   for (const SGroup& g : S.groups) {
     const int64_t f = g.flops * (g.region == 1 ? S.nslices : 1);
     total_flops += f;
@@ -453,7 +504,8 @@ std::string schedule_json(const Schedule& S, const SlicePlan& plan) {
     << ",\"prefix_arena_bytes\":" << S.prefix_elems * S.elem_bytes
     << ",\"slice_arena_bytes\":" << S.slice_elems * S.elem_bytes
     << ",\"fused\":" << (S.fused ? 1 : 0) << ",\"n_groups\":" << S.groups.size()
-    << ",\"gemm_groups\":" << n_gemm << ",\"job_flops\":" << total_flops
+    << ",\"gemm_groups\":" << n_gemm << ",\"tri_groups\":" << n_tri
+    << ",\"job_flops\":" << total_flops
     << ",\"gemm_form_flops\":" << gemm_flops << ",\"tensor_core_shape_flops\":" << tc_flops
     << ",\"k_ge_32_flops\":" << k32_flops
     << ",\"prefix_launch_bytes\":" << S.prefix_launch_bytes

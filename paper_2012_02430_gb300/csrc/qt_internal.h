@@ -120,11 +120,20 @@ struct SGroup {
   std::vector<int8_t> side;          // per operand: 0 folded into A', 1 into B'
   uint32_t mK = 0, mSA = 0, mSB = 0, mM = 0, mN = 0, mBt = 0;
   int64_t scratch_a = 0, scratch_b = 0;  // arena offsets of A', B' (planar re | im)
+  // Triangle form (complex precisions): three large operands A, B, C and every
+  // summed index in exactly two of them -- class K (A and B), X (A and C), Y (B and
+  // C); the other operands lie inside C (folded into C) or are summed-only inside
+  // K (a weight over K). Then out = sum_k w(k) sum_x A[k,x] sum_y B[k,y] C[x,y].
+  bool tri = false;
+  int tA = -1, tB = -1, tC = -1;     // indices into ops
+  uint32_t tK = 0, tX = 0, tY = 0;   // summed U bits of each class
+  std::vector<int8_t> tfold;         // per operand: 0 large, 1 folded into C, 2 weight over K
 };
 
 struct Schedule {
   bool valid = false;
   bool force_gemm = false;       // copy of the network option at compile time
+  bool force_tri = false;        // copy of the network option at compile time
   bool fused = true;             // steps grouped into fused launches
   uint64_t generation = 0;      // changes with every compile
   int precision = QT_FP32_SIMT;
@@ -212,6 +221,7 @@ struct qt_net {
   bool fuse = true;              // fuse bucket steps whose summed indices die together
   bool force_gemm = false;       // GEMM-form launches by default also in FP32 mode
   bool segments = true;          // runs of small launches as one segment launch
+  bool force_tri = false;        // triangle-form launches by default where they apply
   void* engine = nullptr;        // engine.cu: launch descriptors and graph cache
   ~qt_net();
 };
