@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -42,15 +43,39 @@ struct KOp {
   int sshift;              // position of the slice block (unsliced rank)
   int meta_per_slice;
   int level;               // nested-sum level at which the operand is multiplied in
-  int pad;
+  int soff;                // segment launch: element offset in the block's shared arena (-1: global)
+  int tid;                 // schedule tensor id
+  int mslot;               // segment launch: slot of its metadata in the block's cache
 };
 
 struct KStep {
   int m, u, nsum, ms;  // ms: streaming operands (tiled kernel), placed first
   long long nslices, slice_first;
   long long out_base, out_slice_stride, out_meta;
-  int out_meta_per_slice, pad1;
+  int out_meta_per_slice;
+  int out_soff;        // segment launch: shared-arena offset of the result (-1: none)
+  int out_global;      // segment launch: the result is also stored to global memory
+  int out_mslot;       // segment launch: slot of the result's metadata in the block's cache
   KOp op[MAXOP];
+};
+
+// A tensor a segment launch reads but does not produce, staged into the block's
+// shared arena at the start of the launch (its block for the block's slice).
+struct SegStage {
+  long long base, slice_stride;
+  unsigned int smask;
+  int sshift;
+  int n;     // elements
+  int soff;  // arena offset
+  int cum;   // elements staged by the records before this one
+  int pad;
+};
+
+// One dependency level of a segment launch: its steps read only results of
+// earlier levels. Steps [first, first + nwarp) are small (at most 32 value
+// pairs) and run one per warp, concurrently; the next nblock steps use the block.
+struct SegLevel {
+  int first, nwarp, nblock, pad;
 };
 
 struct Meta {
@@ -222,9 +247,10 @@ static_assert(sizeof(KStep) <= kStepRecordBytes, "step record size");
 // launch (and their metadata, updated by L2 atomics) are read through L2 only
 // (ld.global.cg): neither the read-only path nor L1 may hold a stale copy of an
 // arena slot that an earlier step of the launch rewrote.
-constexpr int SEG_THREADS = 512;
-constexpr int SEG_MAX_U = 14;
-constexpr int SEG_MAX_STEPS = 128;  // step records per segment launch (shared memory)
+template <typename R>
+constexpr int seg_threads() { return sizeof(R) == 4 ? 384 : 256; }
+constexpr int SEG_MAX_U = 13;
+constexpr int SEG_MAX_STEPS = 64;  // step records per segment launch (shared memory)
 
 template <typename R>
 __device__ __forceinline__ void load_pair_cg(const R* data, long long off, bool has_bit0, R& r0,
@@ -251,84 +277,215 @@ __device__ __forceinline__ Meta ld_meta_cg(const Meta* m) {
   return Meta{v.x, (int)v.y};
 }
 
+// The block's metadata (every shared slot and this slice's per-slice slots) is
+// cached in shared memory for the whole launch: operand scales are read there,
+// and each step's result metadata is reduced in the block and written to both
+// the cache and global memory (no global atomics, no metadata round trip
+// through L2 between steps). Per-slice slot t of slice i is global slot
+// n_shared + t * batch + i and cache slot n_shared + t.
+constexpr int SEG_META_MAX = 6144;  // cached metadata slots (48 KB)
+constexpr size_t SEG_ARENA_BYTES = 96 * 1024;  // shared arena for results that stay in the launch
+
+// Results read only by later steps of the same launch live in a per-block shared
+// arena (offsets planned on the host by dependency level); inputs produced before
+// the launch are staged into the arena once; results read after the launch are
+// also stored to global memory. The steps run level by level (a level's steps
+// read only earlier levels): small steps one per warp, concurrently, larger ones
+// with the whole block; one block barrier per level.
+
+// the pair index I of one value pair of a step: loads every operand, multiplies
+// level by level (levels >= 1 summed across lanes by shuffles over the lanes that
+// share the pair's higher bits), returns the lane's partial result
 template <typename R>
-__global__ void __launch_bounds__(SEG_THREADS) k_segment(const KStep* steps, int nsteps, R* data,
-                                                        Meta* meta, long long slice_first) {
+__device__ __forceinline__ void seg_pair(const KStep& st, const R* sc, bool active,
+                                         unsigned long long I, long long i,
+                                         unsigned long long sid, const R* data, const R* arena,
+                                         R& sr, R& si) {
+  using C2 = typename CT<R>::c2;
+  const int m = st.m;
+  R vr0[MAXOP], vi0[MAXOP], vr1[MAXOP], vi1[MAXOP];
+#pragma unroll
+  for (int j = 0; j < MAXOP; ++j) {
+    if (j >= m) break;
+    vr0[j] = vi0[j] = vr1[j] = vi1[j] = R(0);
+    if (active) {
+      const KOp& o = st.op[j];
+      const long long loc = (long long)pext64(I, o.umask);
+      if (o.soff >= 0) {
+        const R* p = arena + 2 * (o.soff + loc);
+        vr0[j] = p[0];
+        vi0[j] = p[1];
+        if (o.level == 0) {
+          const int d = (o.umask & 1u) ? 2 : 0;
+          vr1[j] = p[d];
+          vi1[j] = p[d + 1];
+        }
+      } else {
+        long long off = o.base + i * o.slice_stride + loc;
+        if (o.smask) off += (long long)(pext64(sid, o.smask) << o.sshift);
+        if (o.level == 0) {
+          load_pair_cg<R>(data, off, o.umask & 1u, vr0[j], vi0[j], vr1[j], vi1[j]);
+        } else {
+          const C2 a = __ldcg(reinterpret_cast<const C2*>(data + 2 * off));
+          vr0[j] = a.x;
+          vi0[j] = a.y;
+        }
+      }
+    }
+  }
+  R p0r = 1, p0i = 0, p1r = 1, p1i = 0;
+#pragma unroll
+  for (int j = 0; j < MAXOP; ++j) {
+    if (j >= m) break;
+    if (st.op[j].level == 0) {
+      cmul<R>(p0r, p0i, vr0[j] * sc[j], vi0[j] * sc[j]);
+      cmul<R>(p1r, p1i, vr1[j] * sc[j], vi1[j] * sc[j]);
+    }
+  }
+  sr = active ? p0r + p1r : R(0);
+  si = active ? p0i + p1i : R(0);
+  for (int l = 1; l < st.nsum; ++l) {
+#pragma unroll
+    for (int j = 0; j < MAXOP; ++j) {
+      if (j >= m) break;
+      if (st.op[j].level == l) cmul<R>(sr, si, vr0[j] * sc[j], vi0[j] * sc[j]);
+    }
+    sr += __shfl_xor_sync(0xffffffffu, sr, 1 << (l - 1));
+    si += __shfl_xor_sync(0xffffffffu, si, 1 << (l - 1));
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void seg_store(const KStep& st, long long i, unsigned long long I,
+                                          R sr, R si, R* data, R* arena) {
+  const long long oi = (long long)(I >> st.nsum);
+  if (st.out_soff >= 0) {
+    arena[2 * (st.out_soff + oi)] = sr;
+    arena[2 * (st.out_soff + oi) + 1] = si;
+  }
+  if (st.out_global) store_out<R>(data, st.out_base + i * st.out_slice_stride + oi, sr, si);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(seg_threads<R>()) k_segment(const KStep* steps, int nsteps,
+                                                        const SegStage* stages, int nstages,
+                                                        const SegLevel* levels, int nlevels,
+                                                        R* data, Meta* meta, long long slice_first,
+                                                        int n_shared, int n_slice_t, long long batch) {
   extern __shared__ KStep seg_steps[];
-  __shared__ R s_sc[MAXOP];
-  __shared__ int s_E;
+  __shared__ unsigned int s_max;
   const long long i = blockIdx.x;
   const unsigned long long sid = (unsigned long long)(slice_first + i);
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  SegStage* sst = reinterpret_cast<SegStage*>(seg_steps + nsteps);
+  SegLevel* slv = reinterpret_cast<SegLevel*>(sst + nstages);
+  Meta* mc = reinterpret_cast<Meta*>(slv + nlevels);
+  R* arena = reinterpret_cast<R*>(mc + ((n_shared + n_slice_t + 1) & ~1));
+  using C2 = typename CT<R>::c2;
   {
     const int* src = reinterpret_cast<const int*>(steps);
     int* dst = reinterpret_cast<int*>(seg_steps);
-    const int words = nsteps * (int)(sizeof(KStep) / 4);
+    const int words = (nsteps * (int)sizeof(KStep) + nstages * (int)sizeof(SegStage) +
+                       nlevels * (int)sizeof(SegLevel)) / 4;
     for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = __ldcg(src + w);
+    for (int q = threadIdx.x; q < n_shared + n_slice_t; q += blockDim.x) {
+      const long long g = q < n_shared ? q : n_shared + (long long)(q - n_shared) * batch + i;
+      mc[q] = ld_meta_cg(meta + g);
+    }
+    if (threadIdx.x == 0) s_max = 0u;
   }
   __syncthreads();
-  for (int q = 0; q < nsteps; ++q) {
-    const KStep& st = seg_steps[q];
-    // operand scales and the result exponent, once per step
-    if (threadIdx.x < 32) {
+  // inputs from outside the run: one parallel copy into the arena
+  if (nstages > 0) {
+    const int total = sst[nstages - 1].cum + sst[nstages - 1].n;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+      int lo = 0, hi = nstages - 1;  // last record with cum <= e
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sst[mid].cum <= e) lo = mid;
+        else hi = mid - 1;
+      }
+      const SegStage& sg = sst[lo];
+      long long src = sg.base + i * sg.slice_stride + (e - sg.cum);
+      if (sg.smask) src += (long long)(pext64(sid, sg.smask) << sg.sshift);
+      const C2 v = __ldcg(reinterpret_cast<const C2*>(data + 2 * src));
+      arena[2 * (sg.soff + e - sg.cum)] = v.x;
+      arena[2 * (sg.soff + e - sg.cum) + 1] = v.y;
+    }
+  }
+  __syncthreads();
+  for (int L = 0; L < nlevels; ++L) {
+    const SegLevel lv = slv[L];
+    // small steps: one warp each
+    for (int ws = warp; ws < lv.nwarp; ws += nwarps) {
+      const KStep& st = seg_steps[lv.first + ws];
+      R scj = R(1);
       int e = 0;
       if (lane < st.m) {
-        const Meta mt = ld_meta_cg(meta + st.op[lane].meta + (st.op[lane].meta_per_slice ? i : 0));
+        const Meta mt = mc[st.op[lane].mslot];
         const int sj = scale_exp(mt.maxabs);
-        s_sc[lane] = pow2_neg<R>(sj);
+        scj = pow2_neg<R>(sj);
         e = mt.E + sj;
       }
       for (int d = 16; d > 0; d >>= 1) e += __shfl_xor_sync(0xffffffffu, e, d);
-      if (lane == 0) s_E = e;
-    }
-    __syncthreads();
-    const long long npairs = 1ll << (st.u - 1);
-    const int grp = 1 << (st.nsum - 1);
-    float mx = 0.f;
-    for (long long b0 = 0; b0 < npairs; b0 += blockDim.x) {
-      const long long g = b0 + threadIdx.x;
-      const bool active = g < npairs;
-      const unsigned long long I = (unsigned long long)(active ? g : 0) << 1;
-      R p0r = 1, p0i = 0, p1r = 1, p1i = 0;
-      if (active) {
-        for (int j = 0; j < st.m; ++j) {
-          const KOp& o = st.op[j];
-          if (o.level != 0) continue;
-          long long off = o.base + i * o.slice_stride + (long long)pext64(I, o.umask);
-          if (o.smask) off += (long long)(pext64(sid, o.smask) << o.sshift);
-          const R sc = s_sc[j];
-          R r0, i0, r1, i1;
-          load_pair_cg<R>(data, off, o.umask & 1u, r0, i0, r1, i1);
-          cmul<R>(p0r, p0i, r0 * sc, i0 * sc);
-          cmul<R>(p1r, p1i, r1 * sc, i1 * sc);
-        }
+      R sc[MAXOP];
+#pragma unroll
+      for (int j = 0; j < MAXOP; ++j) sc[j] = __shfl_sync(0xffffffffu, scj, j);
+      const long long npairs = 1ll << (st.u - 1);
+      const bool active = lane < npairs;
+      const unsigned long long I = (unsigned long long)(active ? lane : 0) << 1;
+      R sr, si;
+      seg_pair<R>(st, sc, active, I, i, sid, data, arena, sr, si);
+      float mx = 0.f;
+      if (active && (lane & ((1 << (st.nsum - 1)) - 1)) == 0) {
+        seg_store<R>(st, i, I, sr, si, data, arena);
+        mx = absmax(sr, si);
       }
-      R sr = active ? p0r + p1r : R(0), si = active ? p0i + p1i : R(0);
-      for (int l = 1; l < st.nsum; ++l) {
-        if (active) {
-          for (int j = 0; j < st.m; ++j) {
-            const KOp& o = st.op[j];
-            if (o.level != l) continue;
-            long long off = o.base + i * o.slice_stride + (long long)pext64(I, o.umask);
-            if (o.smask) off += (long long)(pext64(sid, o.smask) << o.sshift);
-            const R sc = s_sc[j];
-            using C2 = typename CT<R>::c2;
-            const C2 a = __ldcg(reinterpret_cast<const C2*>(data + 2 * off));
-            cmul<R>(sr, si, a.x * sc, a.y * sc);
-          }
-        }
-        sr += __shfl_xor_sync(0xffffffffu, sr, 1 << (l - 1));
-        si += __shfl_xor_sync(0xffffffffu, si, 1 << (l - 1));
-      }
-      if (active && (lane & (grp - 1)) == 0) {
-        store_out<R>(data, st.out_base + i * st.out_slice_stride + (long long)(I >> st.nsum), sr, si);
-        mx = fmaxf(mx, absmax(sr, si));
+      const unsigned int red = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+      if (lane == 0) {
+        const Meta mo{red, e};
+        mc[st.out_mslot] = mo;
+        meta[st.out_meta + (st.out_meta_per_slice ? i : 0)] = mo;
       }
     }
-    const unsigned int red = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
-    if (lane == 0 && red != 0u)
-      atomicMax(&meta[st.out_meta + (st.out_meta_per_slice ? i : 0)].maxabs, red);
-    if (threadIdx.x == 0) meta[st.out_meta + (st.out_meta_per_slice ? i : 0)].E = s_E;
+    // larger steps: the whole block
+    for (int bs = 0; bs < lv.nblock; ++bs) {
+      const KStep& st = seg_steps[lv.first + lv.nwarp + bs];
+      R sc[MAXOP];
+      int e = 0;
+#pragma unroll
+      for (int j = 0; j < MAXOP; ++j) {
+        if (j >= st.m) break;
+        const Meta mt = mc[st.op[j].mslot];
+        const int sj = scale_exp(mt.maxabs);
+        sc[j] = pow2_neg<R>(sj);
+        e += mt.E + sj;
+      }
+      const long long npairs = 1ll << (st.u - 1);
+      float mx = 0.f;
+      for (long long b0 = 0; b0 < npairs; b0 += blockDim.x) {
+        if (b0 + (threadIdx.x & ~31) >= npairs) break;
+        const long long g = b0 + threadIdx.x;
+        const bool active = g < npairs;
+        const unsigned long long I = (unsigned long long)(active ? g : 0) << 1;
+        R sr, si;
+        seg_pair<R>(st, sc, active, I, i, sid, data, arena, sr, si);
+        if (active && (lane & ((1 << (st.nsum - 1)) - 1)) == 0) {
+          seg_store<R>(st, i, I, sr, si, data, arena);
+          mx = fmaxf(mx, absmax(sr, si));
+        }
+      }
+      const unsigned int red = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+      if (lane == 0 && red != 0u) atomicMax(&s_max, red);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const Meta mo{s_max, e};
+        mc[st.out_mslot] = mo;
+        meta[st.out_meta + (st.out_meta_per_slice ? i : 0)] = mo;
+        s_max = 0u;
+      }
+      __syncthreads();
+    }
     __syncthreads();
   }
 }
@@ -930,7 +1087,9 @@ struct LaunchDesc {
   int gemm_mode;
   unsigned grid;
   int64_t bytes, flops;  // ledger counts per slice
-  int seg_first = 0, seg_count = 0;  // kind 5: records in the segment table
+  long long seg_off = 0;             // kind 5: byte offset of its records in the segment table
+  int seg_count = 0, stage_count = 0, level_count = 0;
+  long long seg_arena = 0;           // kind 5: shared-arena elements per block
 };
 
 constexpr int VARIANT_GEMM = 3;
@@ -1035,6 +1194,23 @@ static void fill_tri(const Schedule& S, const SGroup& g, long long nslices, Gemm
     q.meta_per_slice = o.meta_per_slice;
     q.tfold = g.tfold[j];
   }
+  // operands inside C: folded into C' once per slice (scratch in C's own layout)
+  const unsigned int C = a.op[g.tC].umask;
+  for (int j = 0; j < a.m; ++j) {
+    if (a.op[j].tfold != 1) continue;
+    a.fold_a = 1;
+    unsigned int xm = 0;
+    int k = 0;
+    for (int b = 0; b < 32; ++b)
+      if ((C >> b) & 1u) {
+        if ((a.op[j].umask >> b) & 1u) xm |= 1u << k;
+        ++k;
+      }
+    a.op[j].xmask = xm;
+  }
+  const bool per_slice_out = S.tensors[g.out].kind == TK_SLICE;
+  a.scratch_a = (long long)(per_slice_out ? S.off_slices : S.off_prefix) / S.elem_bytes + g.scratch_t;
+  a.scratch_stride = per_slice_out ? S.slice_elems : 0;
   a.tA = g.tA;
   a.tB = g.tB;
   a.tC = g.tC;
@@ -1053,7 +1229,7 @@ static void fill_tri(const Schedule& S, const SGroup& g, long long nslices, Gemm
 struct EngineCache {
   uint64_t generation = 0;
   std::vector<LaunchDesc> prefix, slice;
-  std::vector<KStep> segtab;       // step records of the segment launches
+  std::vector<unsigned char> segtab;  // per segment launch: step records, stage records, levels
   const void* seg_ws = nullptr;    // workspace the table was last copied to
   uint64_t seg_gen = 0;
   // captured run
@@ -1076,8 +1252,8 @@ static void segtab_dirty(qt_net* net) {
 static bool ensure_segtab(qt_net* net, EngineCache& c, char* base, cudaStream_t s,
                           std::string& err) {
   if (c.segtab.empty() || (c.seg_ws == base && c.seg_gen == c.generation)) return true;
-  if (!cuda_ok(cudaMemcpyAsync(base + net->sched.off_segtab, c.segtab.data(),
-                               c.segtab.size() * sizeof(KStep), cudaMemcpyHostToDevice, s),
+  if (!cuda_ok(cudaMemcpyAsync(base + net->sched.off_segtab, c.segtab.data(), c.segtab.size(),
+                               cudaMemcpyHostToDevice, s),
                "upload segment table", err))
     return false;
   c.seg_ws = base;
@@ -1143,7 +1319,13 @@ static bool make_desc(const Schedule& S, int gi, long long nslices, LaunchDesc& 
     err = "bucket with more operands than the kernels take";
     return false;
   }
-  for (int j = 0; j < k.m; ++j) fill_op(S, st, j, k.op[j]);
+  for (int j = 0; j < k.m; ++j) {
+    fill_op(S, st, j, k.op[j]);
+    k.op[j].tid = st.ops[j];
+    k.op[j].soff = -1;
+  }
+  k.out_soff = -1;
+  k.out_global = 1;
   // streaming operands (indices among the tiled kernel's loop or tile bits) first
   std::stable_partition(k.op, k.op + k.m, [](const KOp& o) { return (o.umask >> TILE_LOCAL_BITS) != 0u; });
   k.ms = 0;
@@ -1199,31 +1381,180 @@ static bool build_cache(qt_net* net, EngineCache& c, std::string& err) {
   }
   // runs of two or more consecutive small flat launches become one segment launch
   c.segtab.clear();
+  const int nsh = (int)S.n_shared_meta;
+  auto mslot_of = [&](long long g, bool per_slice) -> int {
+    return per_slice ? nsh + (int)((g - nsh) / S.batch) : (int)g;
+  };
   for (std::vector<LaunchDesc>* list : {&c.prefix, &c.slice}) {
     std::vector<LaunchDesc> merged;
+    // Plans the run [i, j): its steps are ordered by dependency level, so every value a
+    // step reads inside the run must come from the shared arena (a reordered step may
+    // already have reused the global slot of a tensor that dies in the run); returns
+    // false when some input or internal result does not fit.
+    auto plan = [&](size_t i, size_t j, LaunchDesc& d, std::vector<KStep>& recs,
+                    std::vector<SegStage>& stages, std::vector<SegLevel>& levels) -> bool {
+      const int n = (int)(j - i);
+      const int gi_last = (*list)[j - 1].group;
+      std::map<int, int> producer;  // tid -> step index in the run
+      std::vector<int> lev(n, 0);
+      for (int q = 0; q < n; ++q) {
+        const KStep& k = (*list)[i + q].k;
+        for (int o = 0; o < k.m; ++o) {
+          auto it = producer.find(k.op[o].tid);
+          if (it != producer.end()) lev[q] = std::max(lev[q], lev[it->second] + 1);
+        }
+        producer[S.groups[(*list)[i + q].group].out] = q;
+      }
+      const int nlev = *std::max_element(lev.begin(), lev.end()) + 1;
+      std::map<int, int> last_lev;  // last level reading each tensor inside the run
+      for (int q = 0; q < n; ++q) {
+        const KStep& k = (*list)[i + q].k;
+        for (int o = 0; o < k.m; ++o) {
+          auto it = last_lev.find(k.op[o].tid);
+          if (it == last_lev.end() || it->second < lev[q]) last_lev[k.op[o].tid] = lev[q];
+        }
+      }
+      const long long cap = (long long)(SEG_ARENA_BYTES / (2 * sizeof(R)));
+      std::map<long long, long long> free_blocks{{0, cap}};
+      long long peak = 0;
+      auto take = [&](long long cnt) -> long long {
+        cnt = (cnt + 1) & ~1ll;
+        for (auto it = free_blocks.begin(); it != free_blocks.end(); ++it)
+          if (it->second >= cnt) {
+            const long long off = it->first, rest = it->second - cnt;
+            free_blocks.erase(it);
+            if (rest > 0) free_blocks[off + cnt] = rest;
+            peak = std::max(peak, off + cnt);
+            return off;
+          }
+        return -1;
+      };
+      auto give = [&](long long off, long long cnt) {
+        cnt = (cnt + 1) & ~1ll;
+        auto it = free_blocks.emplace(off, cnt).first;
+        auto nx = std::next(it);
+        if (nx != free_blocks.end() && it->first + it->second == nx->first) {
+          it->second += nx->second;
+          free_blocks.erase(nx);
+        }
+        if (it != free_blocks.begin()) {
+          auto pv = std::prev(it);
+          if (pv->first + pv->second == it->first) {
+            pv->second += it->second;
+            free_blocks.erase(it);
+          }
+        }
+      };
+      std::map<int, std::pair<long long, long long>> slot;  // tid -> (offset, elements)
+      recs.clear();
+      stages.clear();
+      levels.clear();
+      // inputs produced before the run: staged at the start, kept for the whole run
+      int cum = 0;
+      for (int q = 0; q < n; ++q) {
+        const KStep& k = (*list)[i + q].k;
+        const bool region1 = S.groups[(*list)[i + q].group].region == 1;
+        for (int o = 0; o < k.m; ++o) {
+          const int tid = k.op[o].tid;
+          if (producer.count(tid) || slot.count(tid)) continue;
+          const STensor& tt = S.tensors[tid];
+          const long long cnt = 1ll << (tt.rank - (region1 ? tt.nsliced : 0));
+          const long long off = take(cnt);
+          if (off < 0) return false;
+          slot[tid] = {off, cnt};
+          stages.push_back(SegStage{k.op[o].base, k.op[o].slice_stride, k.op[o].smask,
+                                    k.op[o].sshift, (int)cnt, (int)off, cum, 0});
+          cum += (int)cnt;
+        }
+      }
+      d = (*list)[i];
+      d.kind = 5;
+      d.bytes = d.flops = 0;
+      for (int L = 0; L < nlev; ++L) {
+        // results no longer read at this level or later give their slot back
+        for (auto it = slot.begin(); it != slot.end();) {
+          auto ll = last_lev.find(it->first);
+          if (producer.count(it->first) && (ll == last_lev.end() || ll->second < L)) {
+            give(it->second.first, it->second.second);
+            it = slot.erase(it);
+          } else {
+            ++it;
+          }
+        }
+        SegLevel sl{(int)recs.size(), 0, 0, 0};
+        for (int pass = 0; pass < 2; ++pass)  // warp steps, then block steps
+          for (int q = 0; q < n; ++q) {
+            if (lev[q] != L) continue;
+            KStep k = (*list)[i + q].k;
+            const bool warp_step = k.u <= 6;
+            if (warp_step != (pass == 0)) continue;
+            for (int o = 0; o < k.m; ++o) {
+              auto it = slot.find(k.op[o].tid);
+              if (it == slot.end()) return false;
+              k.op[o].soff = (int)it->second.first;
+              k.op[o].mslot = mslot_of(k.op[o].meta, k.op[o].meta_per_slice != 0);
+            }
+            const int out = S.groups[(*list)[i + q].group].out;
+            const STensor& ot = S.tensors[out];
+            k.out_soff = -1;
+            k.out_mslot = mslot_of(k.out_meta, k.out_meta_per_slice != 0);
+            if (last_lev.count(out)) {
+              const long long cnt = 1ll << (ot.rank - (ot.kind == TK_SLICE ? ot.nsliced : 0));
+              const long long off = take(cnt);
+              if (off < 0) return false;
+              k.out_soff = (int)off;
+              slot[out] = {off, cnt};
+            }
+            k.out_global = (ot.last_use > gi_last || k.out_soff < 0) ? 1 : 0;
+            recs.push_back(k);
+            (pass == 0 ? sl.nwarp : sl.nblock)++;
+            d.bytes += (*list)[i + q].bytes;
+            d.flops += (*list)[i + q].flops;
+          }
+        levels.push_back(sl);
+      }
+      d.seg_count = n;
+      d.stage_count = (int)stages.size();
+      d.level_count = nlev;
+      d.seg_arena = peak;
+      return true;
+    };
     for (size_t i = 0; i < list->size();) {
       size_t j = i;
       auto small = [&](const LaunchDesc& d) { return d.kind == 0 && d.k.u <= SEG_MAX_U; };
       while (j < list->size() && small((*list)[j]) && j - i < (size_t)SEG_MAX_STEPS) ++j;
-      if (j - i >= 2 && net->segments) {
-        LaunchDesc d = (*list)[i];
-        d.kind = 5;
-        d.seg_first = (int)c.segtab.size();
-        d.seg_count = (int)(j - i);
-        d.bytes = d.flops = 0;
-        for (size_t q = i; q < j; ++q) {
-          c.segtab.push_back((*list)[q].k);
-          d.bytes += (*list)[q].bytes;
-          d.flops += (*list)[q].flops;
-        }
-        merged.push_back(d);
-        i = j;
-      } else {
+      LaunchDesc d;
+      std::vector<KStep> recs;
+      std::vector<SegStage> stages;
+      std::vector<SegLevel> levels;
+      bool ok = false;
+      if (net->segments && S.n_shared_meta + S.n_slice_meta_tensors <= SEG_META_MAX)
+        for (; j - i >= 2; --j)
+          if (plan(i, j, d, recs, stages, levels)) {
+            ok = true;
+            break;
+          }
+      if (!ok) {
         merged.push_back((*list)[i]);
         ++i;
+        continue;
       }
+      d.seg_off = (long long)c.segtab.size();
+      auto append = [&](const void* p, size_t bytes) {
+        const unsigned char* b = static_cast<const unsigned char*>(p);
+        c.segtab.insert(c.segtab.end(), b, b + bytes);
+      };
+      append(recs.data(), recs.size() * sizeof(KStep));
+      append(stages.data(), stages.size() * sizeof(SegStage));
+      append(levels.data(), levels.size() * sizeof(SegLevel));
+      merged.push_back(d);
+      i = j;
     }
     *list = merged;
+  }
+  if (c.segtab.size() > S.groups.size() * kStepRecordBytes) {
+    err = "segment tables exceed their workspace region";
+    return false;
   }
   c.seg_ws = nullptr;
   if (c.exec) cudaGraphExecDestroy(c.exec);
@@ -1244,15 +1575,23 @@ static void launch_desc(qt_net* net, const LaunchDesc& d0, long long nslices, lo
                nullptr, nullptr};
     if (net->prof) prof_begin(net, s, pr);
     net->launches++;
-    const KStep* tab = reinterpret_cast<const KStep*>(base + S.off_segtab) + d0.seg_first;
+    const KStep* tab = reinterpret_cast<const KStep*>(base + S.off_segtab + d0.seg_off);
+    const SegStage* stab = reinterpret_cast<const SegStage*>(tab + d0.seg_count);
+    const SegLevel* ltab = reinterpret_cast<const SegLevel*>(stab + d0.stage_count);
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(k_segment<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(SEG_MAX_STEPS * sizeof(KStep)));
+                           (int)(220 * 1024));
       attr = true;
     }
-    k_segment<R><<<(unsigned)nslices, SEG_THREADS, d0.seg_count * sizeof(KStep), s>>>(
-        tab, d0.seg_count, data, meta, slice_first);
+    const int nsh = (int)S.n_shared_meta, nst = (int)S.n_slice_meta_tensors;
+    const size_t smem = d0.seg_count * sizeof(KStep) + d0.stage_count * sizeof(SegStage) +
+                        d0.level_count * sizeof(SegLevel) +
+                        (size_t)((nsh + nst + 1) & ~1) * sizeof(Meta) +
+                        (size_t)d0.seg_arena * 2 * sizeof(R);
+    k_segment<R><<<(unsigned)nslices, seg_threads<R>(), smem, s>>>(
+        tab, d0.seg_count, stab, d0.stage_count, ltab, d0.level_count, data, meta, slice_first,
+        nsh, nst, (long long)S.batch);
     if (net->prof) prof_end(net, s, pr);
     return;
   }

@@ -338,6 +338,21 @@ __device__ __forceinline__ unsigned int pdep32g(unsigned int x, unsigned int m) 
   return r;
 }
 
+// Bit extract / deposit over a 32-bit mask computed by a whole warp, one lane per
+// mask bit (every lane must call; all lanes get the result).
+__device__ __forceinline__ unsigned int warp_pext(unsigned long long x, unsigned int m) {
+  const int lane = threadIdx.x & 31;
+  const unsigned int below = m & ((1u << lane) - 1u);
+  const unsigned int bit = ((m >> lane) & 1u) ? (unsigned int)((x >> lane) & 1ull) : 0u;
+  return __reduce_or_sync(0xffffffffu, bit << __popc(below));
+}
+__device__ __forceinline__ unsigned int warp_pdep(unsigned int x, unsigned int m) {
+  const int lane = threadIdx.x & 31;
+  const unsigned int below = m & ((1u << lane) - 1u);
+  const unsigned int bit = ((m >> lane) & 1u) ? ((x >> __popc(below)) & 1u) : 0u;
+  return __reduce_or_sync(0xffffffffu, bit << lane);
+}
+
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
@@ -395,20 +410,24 @@ __global__ void __launch_bounds__(256) k_gemm_tile(const GemmArgs a, int u, floa
   const unsigned int inner = a.tile_inner, hmask = h >= 32 ? 0xffffffffu : ((1u << h) - 1u);
   const int pin = __popc(inner);
   const float2* d2 = reinterpret_cast<const float2*>(data);
+  // tile w -> slot; called by all lanes of warp 0 (lane-parallel bit extracts)
   auto locate = [&](long long w, int slot) {
     const long long i = w / per;
     const unsigned int tp = (unsigned int)(w - i * per);
-    const long long tau = inner ? (long long)(pdep32g(tp & ((1u << pin) - 1u), inner) |
-                                              pdep32g(tp >> pin, ~inner & hmask))
-                                : (long long)tp;
+    const unsigned int tau = inner ? (warp_pdep(tp & ((1u << pin) - 1u), inner) |
+                                      warp_pdep(tp >> pin, ~inner & hmask))
+                                   : tp;
     const unsigned long long sid = (unsigned long long)(a.slice_first + i);
-    const long long ba = a.fold_a ? a.scratch_a + i * a.scratch_stride : op_slice_base(OA, i, sid);
-    const long long bb = a.fold_b ? a.scratch_b + i * a.scratch_stride : op_slice_base(OB, i, sid);
-    const unsigned long long Uh = (unsigned long long)tau << (nsum + t);
-    s_loc[slot][0] = i;
-    s_loc[slot][1] = tau;
-    s_loc[slot][2] = ba + ((long long)pext64g(Uh, OA.umask & ~L) << la);
-    s_loc[slot][3] = bb + ((long long)pext64g(Uh, OB.umask & ~L) << lb);
+    const unsigned int hiA = (OA.umask & ~L) >> (nsum + t), hiB = (OB.umask & ~L) >> (nsum + t);
+    const long long pa = (long long)warp_pext(tau, hiA), pb = (long long)warp_pext(tau, hiB);
+    if ((threadIdx.x & 31) == 0) {
+      const long long ba = a.fold_a ? a.scratch_a + i * a.scratch_stride : op_slice_base(OA, i, sid);
+      const long long bb = a.fold_b ? a.scratch_b + i * a.scratch_stride : op_slice_base(OB, i, sid);
+      s_loc[slot][0] = i;
+      s_loc[slot][1] = tau;
+      s_loc[slot][2] = ba + (pa << la);
+      s_loc[slot][3] = bb + (pb << lb);
+    }
   };
   auto issue = [&](int slot, float2* dst) {
     const long long ta = s_loc[slot][2], tb = s_loc[slot][3];
@@ -422,7 +441,7 @@ __global__ void __launch_bounds__(256) k_gemm_tile(const GemmArgs a, int u, floa
   };
   const long long G = gridDim.x;
   long long w = blockIdx.x;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
     if (w < ntiles) locate(w, 0);
     if (w + G < ntiles) locate(w + G, 1);
   }
@@ -438,7 +457,7 @@ __global__ void __launch_bounds__(256) k_gemm_tile(const GemmArgs a, int u, floa
     } else {
       cp_async_wait<0>();
     }
-    if (threadIdx.x == 0 && w + 2 * G < ntiles) locate(w + 2 * G, (j + 2) % 3);
+    if (threadIdx.x < 32 && w + 2 * G < ntiles) locate(w + 2 * G, (j + 2) % 3);
     __syncthreads();
     const long long i_c = s_loc[slot][0], tau_c = s_loc[slot][1];
     if (i_c != cur) {
@@ -664,7 +683,9 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 // copies, two buffers), making the lanes' rows (consecutive outputs) consecutive
 // words. Thread 0 locates the tile after next while the block works.
 struct TriLayout {
-  int laA, laB, laC, sA, sB, sC, rA, rB, rC, nA, nB, nC, nK, nX, nY, buf;
+  // per operand: la local bits, s summed bits, r rows, n elements, p column stride
+  // (rows + 1, odd: consecutive columns of one row fall in different banks)
+  int laA, laB, laC, sA, sB, sC, rA, rB, rC, nA, nB, nC, pA, pB, pC, zA, zB, zC, nK, nX, nY, buf;
   size_t off_cf, off_rt, off_col, off_w, bytes;
 };
 
@@ -685,17 +706,49 @@ __host__ __device__ inline TriLayout tri_layout(const GemmArgs& a, int t) {
   l.sA = popc_h(mA & Sm); l.sB = popc_h(mB & Sm); l.sC = popc_h(mC & Sm);
   l.rA = 1 << (l.laA - l.sA); l.rB = 1 << (l.laB - l.sB); l.rC = 1 << (l.laC - l.sC);
   l.nA = 1 << l.laA; l.nB = 1 << l.laB; l.nC = 1 << l.laC;
+  l.pA = l.rA + 1; l.pB = l.rB + 1; l.pC = l.rC + 1;
+  l.zA = l.pA << l.sA; l.zB = l.pB << l.sB; l.zC = l.pC << l.sC;  // padded sizes
   l.nK = 1 << popc_h(a.tK); l.nX = 1 << popc_h(a.tX); l.nY = 1 << popc_h(a.tY);
-  l.buf = l.nA + l.nB + l.nC;
+  l.buf = l.zA + l.zB + l.zC;
   size_t off = (size_t)2 * l.buf * 8;            // two buffers of complex64
-  l.off_cf = off;  off += (size_t)l.nC * 8;       // C'
+  l.off_cf = 0;
   l.off_rt = off;  off += (size_t)3 * 2 * (1u << t);  // row tables (uint16)
   off = (off + 15) / 16 * 16;
-  l.off_col = off; off += (size_t)4 * (l.nK * l.nX + l.nK * l.nY + l.nX * l.nY);
+  l.off_col = off; off += (size_t)4 * (2 * l.nK + l.nX + l.nY + l.nX * l.nY);
   off = (off + 15) / 16 * 16;
   l.off_w = off;   off += (size_t)8 * l.nK;
   l.bytes = off;
   return l;
+}
+
+// C' = C times the operands inside C, once per slice, in C's own layout (the
+// triangle form's fold; an operand's index at C index x is pext(x, its xmask)).
+__global__ void __launch_bounds__(256) k_tri_fold(const GemmArgs a, float* data, const GMeta* meta) {
+  const GOp& X = a.op[a.tC];
+  const int xb = __popc(X.umask);
+  const unsigned int xall = (unsigned int)((1ull << xb) - 1ull);
+  const long long total = a.nslices << xb;
+  float2* out = reinterpret_cast<float2*>(data) + a.scratch_a;
+  const float2* d2 = reinterpret_cast<const float2*>(data);
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e >> xb;
+    const unsigned int x = (unsigned int)(e & xall);
+    const unsigned long long sid = (unsigned long long)(a.slice_first + i);
+    float pr = 1.f, pi = 0.f;
+    for (int j = 0; j < a.m; ++j) {
+      const GOp& o = a.op[j];
+      if (j != a.tC && o.tfold != 1) continue;
+      const float sc = pow2_neg_g(scale_exp_g(meta[o.meta + (o.meta_per_slice ? i : 0)].maxabs));
+      const unsigned int idx = j == a.tC ? x : pext32g(x, o.xmask);
+      const float2 v = d2[op_slice_base(o, i, sid) + idx];
+      const float vr = v.x * sc, vi = v.y * sc;
+      const float nr = pr * vr - pi * vi, ni = pr * vi + pi * vr;
+      pr = nr;
+      pi = ni;
+    }
+    out[i * a.scratch_stride + x] = make_float2(pr, pi);
+  }
 }
 
 template <int NX, int NY>
@@ -703,9 +756,6 @@ __global__ void __launch_bounds__(256) k_tri_tile(const GemmArgs a, int u, float
                                                   GMeta* meta) {
   extern __shared__ float4 trsm[];
   __shared__ long long s_loc[3][5];   // tile slots: slice, tau, A, B, C block starts
-  __shared__ long long s_fb[GEMM_MAXOP];  // tile bases of the operands folded into C
-  __shared__ unsigned int s_fx[GEMM_MAXOP];  // their indices in C's local bit numbering
-  __shared__ float s_fs[GEMM_MAXOP];  // their scales
   __shared__ float s_sc;
   const int nsum = a.nsum, t = a.tb, c = u - nsum, h = c - t;
   const TriLayout ly = tri_layout(a, t);
@@ -716,17 +766,19 @@ __global__ void __launch_bounds__(256) k_tri_tile(const GemmArgs a, int u, float
   const GOp& OC = a.op[a.tC];
   char* sm = reinterpret_cast<char*>(trsm);
   float2* bufs = reinterpret_cast<float2*>(sm);
-  float2* sCf = reinterpret_cast<float2*>(sm + ly.off_cf);
   unsigned short* RA = reinterpret_cast<unsigned short*>(sm + ly.off_rt);
   const int T = 1 << t;
   unsigned short* RB = RA + T;
   unsigned short* RC = RB + T;
-  int* colA = reinterpret_cast<int*>(sm + ly.off_col);
-  int* colB = colA + ly.nK * NX;
-  int* colC = colB + ly.nK * NY;
+  // column offsets: pext over disjoint bit sets adds, so A's column of (k, x) is
+  // ka[k] + xa[x] and B's of (k, y) is kb[k] + yb[y] (times the column stride)
+  int* ka = reinterpret_cast<int*>(sm + ly.off_col);
+  int* kb = ka + ly.nK;
+  int* xa = kb + ly.nK;
+  int* yb = xa + NX;
+  int* colC = yb + NY;
   float2* W = reinterpret_cast<float2*>(sm + ly.off_w);
   const int nK = ly.nK;
-  // per-launch tables
   {
     const unsigned int ma = (OA.umask & L) >> nsum, mb = (OB.umask & L) >> nsum,
                        mc = (OC.umask & L) >> nsum;
@@ -735,62 +787,64 @@ __global__ void __launch_bounds__(256) k_tri_tile(const GemmArgs a, int u, float
       RB[o] = (unsigned short)pext32g((unsigned)o, mb);
       RC[o] = (unsigned short)pext32g((unsigned)o, mc);
     }
-    for (int e = threadIdx.x; e < nK * NX; e += blockDim.x) {
-      const unsigned int U = pdep32g((unsigned)(e / NX), a.tK) | pdep32g((unsigned)(e % NX), a.tX);
-      colA[e] = (int)pext32g(U, OA.umask & Sm) * ly.rA;
+    for (int k = threadIdx.x; k < nK; k += blockDim.x) {
+      const unsigned int U = pdep32g((unsigned)k, a.tK);
+      ka[k] = (int)pext32g(U, OA.umask & Sm) * ly.pA;
+      kb[k] = (int)pext32g(U, OB.umask & Sm) * ly.pB;
     }
-    for (int e = threadIdx.x; e < nK * NY; e += blockDim.x) {
-      const unsigned int U = pdep32g((unsigned)(e / NY), a.tK) | pdep32g((unsigned)(e % NY), a.tY);
-      colB[e] = (int)pext32g(U, OB.umask & Sm) * ly.rB;
-    }
+    for (int x = threadIdx.x; x < NX; x += blockDim.x)
+      xa[x] = (int)pext32g(pdep32g((unsigned)x, a.tX), OA.umask & Sm) * ly.pA;
+    for (int y = threadIdx.x; y < NY; y += blockDim.x)
+      yb[y] = (int)pext32g(pdep32g((unsigned)y, a.tY), OB.umask & Sm) * ly.pB;
     for (int e = threadIdx.x; e < NX * NY; e += blockDim.x) {
       const unsigned int U = pdep32g((unsigned)(e / NY), a.tX) | pdep32g((unsigned)(e % NY), a.tY);
-      colC[e] = (int)pext32g(U, OC.umask & Sm) * ly.rC;
+      colC[e] = (int)pext32g(U, OC.umask & Sm) * ly.pC;
     }
-    for (int j = threadIdx.x; j < a.m; j += blockDim.x)
-      s_fx[j] = pext32g(a.op[j].umask & L, OC.umask & L);
   }
   const long long per = 1ll << h;
   const long long ntiles = a.nslices * per;
   const unsigned int inner = a.tile_inner, hmask = h >= 32 ? 0xffffffffu : ((1u << h) - 1u);
   const int pin = __popc(inner);
   const float2* d2 = reinterpret_cast<const float2*>(data);
-  auto tile_base = [&](const GOp& o, long long i, unsigned long long sid,
-                       unsigned long long Uh) -> long long {
-    return op_slice_base(o, i, sid) + ((long long)pext64g(Uh, o.umask & ~L) << __popc(o.umask & L));
-  };
+  // tile w -> slot; called by all lanes of warp 0 (lane-parallel bit extracts)
   auto locate = [&](long long w, int slot) {
     const long long i = w / per;
     const unsigned int tp = (unsigned int)(w - i * per);
-    const long long tau = inner ? (long long)(pdep32g(tp & ((1u << pin) - 1u), inner) |
-                                              pdep32g(tp >> pin, ~inner & hmask))
-                                : (long long)tp;
+    const unsigned int tau = inner ? (warp_pdep(tp & ((1u << pin) - 1u), inner) |
+                                      warp_pdep(tp >> pin, ~inner & hmask))
+                                   : tp;
     const unsigned long long sid = (unsigned long long)(a.slice_first + i);
-    const unsigned long long Uh = (unsigned long long)tau << (nsum + t);
-    s_loc[slot][0] = i;
-    s_loc[slot][1] = tau;
-    s_loc[slot][2] = tile_base(OA, i, sid, Uh);
-    s_loc[slot][3] = tile_base(OB, i, sid, Uh);
-    s_loc[slot][4] = tile_base(OC, i, sid, Uh);
+    const int sh = nsum + t;
+    const long long pa = (long long)warp_pext(tau, (OA.umask & ~L) >> sh);
+    const long long pb = (long long)warp_pext(tau, (OB.umask & ~L) >> sh);
+    const long long pc = (long long)warp_pext(tau, (OC.umask & ~L) >> sh);
+    if ((threadIdx.x & 31) == 0) {
+      s_loc[slot][0] = i;
+      s_loc[slot][1] = tau;
+      s_loc[slot][2] = op_slice_base(OA, i, sid) + (pa << ly.laA);
+      s_loc[slot][3] = op_slice_base(OB, i, sid) + (pb << ly.laB);
+      const long long cb = a.fold_a ? a.scratch_a + i * a.scratch_stride : op_slice_base(OC, i, sid);
+      s_loc[slot][4] = cb + (pc << ly.laC);
+    }
   };
   auto issue = [&](int slot, float2* dst) {
     const float2* srcA = d2 + s_loc[slot][2];
     const float2* srcB = d2 + s_loc[slot][3];
     const float2* srcC = d2 + s_loc[slot][4];
     float2* dA = dst;
-    float2* dB = dA + ly.nA;
-    float2* dC = dB + ly.nB;
+    float2* dB = dA + ly.zA;
+    float2* dC = dB + ly.zB;
     for (int e = threadIdx.x; e < ly.nA; e += blockDim.x)
-      cp_async8(dA + (e & ((1 << ly.sA) - 1)) * ly.rA + (e >> ly.sA), srcA + e);
+      cp_async8(dA + (e & ((1 << ly.sA) - 1)) * ly.pA + (e >> ly.sA), srcA + e);
     for (int e = threadIdx.x; e < ly.nB; e += blockDim.x)
-      cp_async8(dB + (e & ((1 << ly.sB) - 1)) * ly.rB + (e >> ly.sB), srcB + e);
+      cp_async8(dB + (e & ((1 << ly.sB) - 1)) * ly.pB + (e >> ly.sB), srcB + e);
     for (int e = threadIdx.x; e < ly.nC; e += blockDim.x)
-      cp_async8(dC + (e & ((1 << ly.sC) - 1)) * ly.rC + (e >> ly.sC), srcC + e);
+      cp_async8(dC + (e & ((1 << ly.sC) - 1)) * ly.pC + (e >> ly.sC), srcC + e);
     cp_async_commit();
   };
   const long long G = gridDim.x;
   long long w = blockIdx.x;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
     if (w < ntiles) locate(w, 0);
     if (w + G < ntiles) locate(w + G, 1);
   }
@@ -798,11 +852,8 @@ __global__ void __launch_bounds__(256) k_tri_tile(const GemmArgs a, int u, float
   if (w < ntiles) issue(0, bufs);
   long long cur = -1;
   float mx = 0.f;
-  bool has_fold = false, has_w = false;
-  for (int j = 0; j < a.m; ++j) {
-    has_fold |= a.op[j].tfold == 1;
-    has_w |= a.op[j].tfold == 2;
-  }
+  bool has_w = false;
+  for (int j = 0; j < a.m; ++j) has_w |= a.op[j].tfold == 2;
   for (int jt = 0; w < ntiles; ++jt, w += G) {
     const int slot = jt % 3;
     if (w + G < ntiles) {
@@ -811,13 +862,12 @@ __global__ void __launch_bounds__(256) k_tri_tile(const GemmArgs a, int u, float
     } else {
       cp_async_wait<0>();
     }
-    if (threadIdx.x == 0 && w + 2 * G < ntiles) locate(w + 2 * G, (jt + 2) % 3);
+    if (threadIdx.x < 32 && w + 2 * G < ntiles) locate(w + 2 * G, (jt + 2) % 3);
     const long long i_c = s_loc[slot][0], tau_c = s_loc[slot][1];
-    const unsigned long long sid = (unsigned long long)(a.slice_first + i_c);
-    const unsigned long long Uh = (unsigned long long)tau_c << (nsum + t);
     if (i_c != cur) {
-      // per slice: the weight over K and the large operands' scales
-      if (has_w)
+      // per slice: the weight over K and the scales of A, B (and C unless folded)
+      if (has_w) {
+        const unsigned long long sid = (unsigned long long)(a.slice_first + i_c);
         for (int k = threadIdx.x; k < nK; k += blockDim.x) {
           float wr = 1.f, wi = 0.f;
           const unsigned int U = pdep32g((unsigned)k, a.tK);
@@ -833,16 +883,15 @@ __global__ void __launch_bounds__(256) k_tri_tile(const GemmArgs a, int u, float
           }
           W[k] = make_float2(wr, wi);
         }
+      }
       if (threadIdx.x == 0) {
-        s_sc = pow2_neg_g(scale_exp_g(meta[OA.meta + (OA.meta_per_slice ? i_c : 0)].maxabs)) *
-               pow2_neg_g(scale_exp_g(meta[OB.meta + (OB.meta_per_slice ? i_c : 0)].maxabs));
-        for (int q = 0; q < a.m; ++q)
-          if (q == a.tC || a.op[q].tfold == 1)
-            s_fs[q] = pow2_neg_g(scale_exp_g(meta[a.op[q].meta + (a.op[q].meta_per_slice ? i_c : 0)].maxabs));
+        float sc = pow2_neg_g(scale_exp_g(meta[OA.meta + (OA.meta_per_slice ? i_c : 0)].maxabs)) *
+                   pow2_neg_g(scale_exp_g(meta[OB.meta + (OB.meta_per_slice ? i_c : 0)].maxabs));
+        if (!a.fold_a)
+          sc *= pow2_neg_g(scale_exp_g(meta[OC.meta + (OC.meta_per_slice ? i_c : 0)].maxabs));
+        s_sc = sc;
       }
     }
-    if (threadIdx.x < a.m && a.op[threadIdx.x].tfold == 1)
-      s_fb[threadIdx.x] = tile_base(a.op[threadIdx.x], i_c, sid, Uh);
     __syncthreads();
     if (i_c != cur) {
       if (cur >= 0) flush_max(a, meta, cur, mx);
@@ -851,46 +900,35 @@ __global__ void __launch_bounds__(256) k_tri_tile(const GemmArgs a, int u, float
       if (tau_c == 0 && threadIdx.x == 0) write_meta_e(a, meta, i_c);
     }
     const float2* sA = bufs + (jt & 1) * ly.buf;
-    const float2* sB = sA + ly.nA;
-    const float2* sC = sB + ly.nB;
-    // C' = C times the operands folded into it (same transposed layout)
-    {
-      const float scC = s_fs[a.tC];
-      for (int e = threadIdx.x; e < ly.nC; e += blockDim.x) {
-        const int pos = (e & ((1 << ly.sC) - 1)) * ly.rC + (e >> ly.sC);
-        float2 v = sC[pos];
-        float pr = v.x * scC, pi = v.y * scC;
-        if (has_fold)
-          for (int q = 0; q < a.m; ++q) {
-            if (a.op[q].tfold != 1) continue;
-            const float2 f = d2[s_fb[q] + pext32g((unsigned)e, s_fx[q])];
-            const float fr = f.x * s_fs[q], fi = f.y * s_fs[q];
-            const float nr = pr * fr - pi * fi, ni = pr * fi + pi * fr;
-            pr = nr;
-            pi = ni;
-          }
-        sCf[pos] = make_float2(pr, pi);
-      }
-    }
-    __syncthreads();
+    const float2* sB = sA + ly.zA;
+    const float2* sC = sB + ly.zB;
     float2* out = reinterpret_cast<float2*>(data) + a.out_base + i_c * a.out_slice_stride +
                   (tau_c << t);
     const float sc = s_sc;
+    int xo[NX], yo[NY];
+#pragma unroll
+    for (int x = 0; x < NX; ++x) xo[x] = xa[x];
+#pragma unroll
+    for (int y = 0; y < NY; ++y) yo[y] = yb[y];
     for (int o = threadIdx.x; o < T; o += blockDim.x) {
-      const int ra = RA[o], rb = RB[o], rc = RC[o];
+      const float2* pa = sA + RA[o];
+      const float2* pb = sB + RB[o];
+      const int rc = RC[o];
       float cvr[NX * NY], cvi[NX * NY];
 #pragma unroll
       for (int xy = 0; xy < NX * NY; ++xy) {
-        const float2 v = sCf[colC[xy] + rc];
+        const float2 v = sC[colC[xy] + rc];
         cvr[xy] = v.x;
         cvi[xy] = v.y;
       }
       float accr = 0.f, acci = 0.f;
       for (int k = 0; k < nK; ++k) {
+        const float2* pak = pa + ka[k];
+        const float2* pbk = pb + kb[k];
         float bvr[NY], bvi[NY];
 #pragma unroll
         for (int y = 0; y < NY; ++y) {
-          const float2 v = sB[colB[k * NY + y] + rb];
+          const float2 v = pbk[yo[y]];
           bvr[y] = v.x;
           bvi[y] = v.y;
         }
@@ -905,7 +943,7 @@ __global__ void __launch_bounds__(256) k_tri_tile(const GemmArgs a, int u, float
             yi = fmaf(bvr[y], cvi[x * NY + y], yi);
             yi = fmaf(bvi[y], cvr[x * NY + y], yi);
           }
-          const float2 av = sA[colA[k * NX + x] + ra];
+          const float2 av = pak[xo[x]];
           sr = fmaf(av.x, yr, sr);
           sr = fmaf(-av.y, yi, sr);
           si = fmaf(av.x, yi, si);
@@ -1007,7 +1045,9 @@ int tri_tile_bits(const GemmArgs& a, int u) {
   const int c = u - a.nsum;
   for (int t = std::min(c, 10); t >= 7; --t) {
     const TriLayout l = tri_layout(a, t);
-    if (l.bytes <= kTriSmemMax && l.rA <= 65535 && l.rB <= 65535 && l.rC <= 65535) return t;
+    if (l.bytes <= kTriSmemMax && l.zA < (1 << 30) && l.rA <= 65535 && l.rB <= 65535 &&
+        l.rC <= 65535)
+      return t;
   }
   return 0;
 }
@@ -1023,6 +1063,13 @@ int tri_launch(const GemmArgs& a, float* data, GMeta* meta, cudaStream_t s, int 
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriSmemMax);
     attr[ix][iy] = true;
   }
+  int n = 0;
+  if (a.fold_a) {
+    const long long work = a.nslices << __builtin_popcount(a.op[a.tC].umask);
+    const long long g = std::min<long long>((work + 255) / 256, (long long)sms * 16);
+    k_tri_fold<<<(unsigned)std::max<long long>(1, g), 256, 0, s>>>(a, data, meta);
+    ++n;
+  }
   const TriLayout l = tri_layout(a, a.tb);
   const long long ntiles = a.nslices << (u - a.nsum - a.tb);
   const int threads = std::min(256, 1 << a.tb);
@@ -1030,7 +1077,7 @@ int tri_launch(const GemmArgs& a, float* data, GMeta* meta, cudaStream_t s, int 
   const unsigned grid =
       (unsigned)std::max<long long>(1, std::min<long long>(ntiles, (long long)sms * per_sm));
   fn<<<grid, threads, l.bytes, s>>>(a, u, data, meta);
-  return 1;
+  return n + 1;
 }
 
 int gemm_launch(const GemmArgs& a, int mode, float* data, GMeta* meta, cudaStream_t s, int sms) {

@@ -398,6 +398,7 @@ bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePla
       g.tX = X;
       g.tY = Y;
       g.tfold = fold;
+      g.tCbits = __builtin_popcount(mask[c]);
     }
   }
   // liveness by group: a stored tensor lives from its group to the last group reading it
@@ -426,6 +427,11 @@ bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePla
     Arena& ar = o.kind == TK_PREFIX ? pre : sl;
     o.offset = ar.alloc((int64_t)1 << o.rank, kArenaAlign);
     if (o.last_use < 0) o.last_use = gi;
+    if (g.tri) {  // C' lives only during the group
+      const int64_t nc = (int64_t)1 << g.tCbits;
+      g.scratch_t = ar.alloc(nc, kArenaAlign);
+      ar.release(g.scratch_t, nc, kArenaAlign);
+    }
     if (g.gemm) {  // A', B' live only during the group
       const int kb = __builtin_popcount(g.mK), bt = __builtin_popcount(g.mBt);
       const int64_t na = (int64_t)1 << (bt + __builtin_popcount(g.mM) + kb);

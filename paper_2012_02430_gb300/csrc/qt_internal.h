@@ -128,6 +128,8 @@ struct SGroup {
   int tA = -1, tB = -1, tC = -1;     // indices into ops
   uint32_t tK = 0, tX = 0, tY = 0;   // summed U bits of each class
   std::vector<int8_t> tfold;         // per operand: 0 large, 1 folded into C, 2 weight over K
+  int tCbits = 0;                    // indices of C (its folded copy C' has 2^tCbits elements)
+  int64_t scratch_t = 0;             // arena offset of C'
 };
 
 struct Schedule {
@@ -173,7 +175,7 @@ bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePla
 std::string schedule_json(const Schedule& s, const SlicePlan& plan);
 
 constexpr size_t kScalarTermBytes = 40;  // device ScalarTerm record
-constexpr size_t kStepRecordBytes = 1024;  // upper bound of a device step record (segment table)
+constexpr size_t kStepRecordBytes = 2048;  // segment-table bytes reserved per launch group
 
 // Canonical-layout copy of a gate tensor's data (FP64 interleaved).
 std::vector<double> canonical_data(const Tensor& t, const std::vector<int32_t>& canon_labels);
