@@ -349,6 +349,7 @@ def ours(args):
     del plain
 
     energy_line = batched_energy(args, Q, torch, flush, stream)
+    sweep_line = angle_sweep(args, Q, torch, flush, stream)
     batch_line = batched_amplitudes(args, Q, torch, edges, gammas, betas, z, prec, flush, stream,
                                     total_ms / args.steps)
     order_line = orderings(Q, edges, gammas, betas, z)
@@ -392,6 +393,7 @@ def ours(args):
         "plain_fp32_greedy_path": plain_line,
         "batched_energy": energy_line,
         "batched_amplitudes": batch_line,
+        "angle_sweep": sweep_line,
         "orderings": order_line,
         "precision_modes": modes_line,
         "amplitude": [amp.real, amp.imag],
@@ -486,6 +488,52 @@ def batched_energy(args, Q, torch, flush, stream):
             "block_threads": threads, "blocks": st["blocks"], "lightcone_width_hist": st["width_hist"],
             "ledger_flops": st["flops"], "launch_bytes": st["bytes"],
             "upload_bytes": st["upload_bytes"]}
+
+
+SWEEP_SETS = 64  # angle sets of the sweep measurement
+
+
+def angle_sweep(args, Q, torch, flush, stream):
+    """Energies of SWEEP_SETS angle sets of the batched-energy graph in one persistent
+    launch over (set, edge) work items (orders and schedules reused): device time of the
+    launch (gate images already resident), and end to end with the host gate images,
+    the copies and the D2H of the energies."""
+    from paper_2012_02430_gb300.inputs import qaoa_instance, random_angles
+    n, p, seed = ENERGY_WORKLOAD["n"], ENERGY_WORKLOAD["p"], ENERGY_WORKLOAD["seed"]
+    edges, g, b, _ = qaoa_instance(n, p, seed)
+    en = Q.Energy(edges, n, p, g, b)
+    en.prepare(Q.QT_FP32_SIMT)
+    en.upload()
+    en.autotune()
+    sets = [random_angles(p, 7000 + q) for q in range(SWEEP_SETS)]
+    gs, bs = [x[0] for x in sets], [x[1] for x in sets]
+    en.sweep_prepare(SWEEP_SETS)
+    energies = torch.zeros(SWEEP_SETS, dtype=torch.float64, device="cuda")
+    en.sweep_upload(gs, bs)
+    for _ in range(3):
+        en.sweep_run(SWEEP_SETS, energies)
+    reps = max(3, min(args.steps, 10))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    for i in range(reps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        en.sweep_run(SWEEP_SETS, energies)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b2) for a, b2 in ev) / reps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        en.sweep(gs, bs, energies)
+        host = energies.cpu()
+    e2e_ms = 1e3 * (time.perf_counter() - t0) / 3
+    return {"workload": f"{SWEEP_SETS} angle sets of the p={p} N={n} energy, one launch",
+            "ms_per_sweep": ms, "energies_per_s": SWEEP_SETS / (ms / 1e3),
+            "lightcones_per_s": SWEEP_SETS * len(edges) / (ms / 1e3),
+            "e2e_ms_per_sweep": e2e_ms,
+            "e2e_includes": "host gate images for every set, H2D, launch, D2H of the energies",
+            "energy_first_set": float(host[0].item())}
 
 
 BATCH_OPEN = 8  # open qubits of the batched-amplitude measurement: 2^8 amplitudes

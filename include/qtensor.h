@@ -429,6 +429,33 @@ qt_status qt_energy_get_order(const qt_energy* e, int32_t edge, int32_t* order, 
                               int32_t* len, int32_t* n_vars, int32_t* width);
 /* JSON: edges, steps, widths histogram, ledger flops/bytes, launch shape. */
 qt_status qt_energy_stats(const qt_energy* e, char* buf, size_t cap, size_t* needed);
+/*
+ * Angle sweep (toward parameter optimisation; the order and schedule depend only
+ * on the structure, Sec. VIII): the energy for n_sets angle sets in one persistent
+ * launch over (set, edge) work items, every lightcone network's order and schedule
+ * reused. qt_energy_sweep_prepare (after qt_energy_prepare) lays out a workspace
+ * for up to n_sets sets and returns its size. qt_energy_sweep takes gammas, betas
+ * as HOST arrays [n_sets][p] (layer 1 first), builds each set's gate data on the
+ * host (a staging buffer the handle owns: do not call again before the stream has
+ * passed the copy), copies it with the network tables into the workspace and
+ * launches; it writes the energies to the DEVICE array d_energy (n_sets doubles)
+ * and, if d_zz is not NULL, <Z_u Z_v> to the DEVICE array d_zz [n_sets][n_edges].
+ * Asynchronous on `stream`. Errors: QT_ESTATE before qt_energy_prepare;
+ * QT_EINVAL for n_sets outside [1, the prepared size], a non-finite angle, a
+ * null or unaligned pointer; QT_ENOMEM for a small workspace; QT_ECUDA.
+ * qt_energy_sweep is qt_energy_sweep_upload (gate data and tables) followed by
+ * qt_energy_sweep_run (the launch alone, repeatable on the uploaded sets).
+ */
+qt_status qt_energy_sweep_prepare(qt_energy* e, int32_t n_sets, size_t* workspace_bytes);
+qt_status qt_energy_sweep_upload(qt_energy* e, int32_t n_sets, const double* gammas,
+                                 const double* betas, void* workspace, size_t workspace_bytes,
+                                 void* stream);
+qt_status qt_energy_sweep_run(qt_energy* e, int32_t n_sets, void* workspace, size_t workspace_bytes,
+                              void* stream, double* d_energy, double* d_zz);
+qt_status qt_energy_sweep(qt_energy* e, int32_t n_sets, const double* gammas, const double* betas,
+                          void* workspace, size_t workspace_bytes, void* stream, double* d_energy,
+                          double* d_zz);
+
 void qt_energy_free(qt_energy* e);
 
 /* Frees a network (NULL is a no-op). */

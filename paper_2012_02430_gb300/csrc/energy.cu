@@ -110,23 +110,30 @@ __device__ void block_step(const EStep& st, const EOp* ops, const R* gates, R* a
 
 // Persistent kernel: each block repeatedly takes the next network index from
 // the counter (no waiting: an atomic add) until none is left.
+// With an angle sweep, work item w is network w % nnets of angle set w / nnets: the
+// set's gate image starts gate_stride elements after the previous one, and its
+// <Z_u Z_v> go to zz[set * nnets + edge].
 template <typename R>
-__global__ void k_energy(const ENet* nets, int nnets, const EStep* steps, const EOp* ops,
-                         const uint32_t* scalars, const R* gates, R* arenas, long long arena_elems,
-                         int* counter, double* zz) {
+__global__ void k_energy(const ENet* nets, int nnets, int nsets, long long gate_stride,
+                         const EStep* steps, const EOp* ops, const uint32_t* scalars,
+                         const R* gates, R* arenas, long long arena_elems, int* counter,
+                         double* zz) {
   using C2 = typename C2T<R>::t;
   R* arena = arenas + 2 * arena_elems * (long long)blockIdx.x;
   __shared__ int cur;
+  const int nwork = nnets * nsets;
   for (;;) {
     if (threadIdx.x == 0) cur = atomicAdd(counter, 1);
     __syncthreads();
-    const int ni = cur;
+    const int w = cur;
     __syncthreads();
-    if (ni >= nnets) break;
+    if (w >= nwork) break;
+    const int set = w / nnets, ni = w - set * nnets;
     const ENet nd = nets[ni];
+    const R* g = gates + 2 * gate_stride * (long long)set;
     for (uint32_t s = 0; s < nd.nsteps; ++s) {
       const EStep st = steps[nd.first_step + s];
-      block_step<R>(st, ops + st.first_op, gates, arena);
+      block_step<R>(st, ops + st.first_op, g, arena);
       __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -138,15 +145,17 @@ __global__ void k_energy(const ENet* nets, int nnets, const EStep* steps, const 
         pr = nr;
         pi = nim;
       }
-      zz[nd.edge] = pr * nd.norm;
+      zz[(long long)set * nnets + nd.edge] = pr * nd.norm;
     }
     __syncthreads();
   }
 }
 
-// energy = sum over edges of (1 - zz_e) / 2, fixed order
+// energy = sum over edges of (1 - zz_e) / 2, fixed order; block b: angle set b
 __global__ void __launch_bounds__(1024) k_energy_sum(const double* zz, int n, double* out) {
   __shared__ double sh[1024];
+  zz += (long long)blockIdx.x * n;
+  out += blockIdx.x;
   double acc = 0.0;
   for (int e = threadIdx.x; e < n; e += 1024) acc += 0.5 * (1.0 - zz[e]);
   sh[threadIdx.x] = acc;
@@ -225,13 +234,56 @@ void layout(qt_energy* E) {
   E->total_bytes_ws = off;
 }
 
+void layout_sweep(qt_energy* E, int nsets) {
+  const size_t eb = (size_t)E->elem_bytes;
+  size_t off = 0;
+  E->sw_off_gates = off;
+  off = a256(off + (size_t)nsets * (size_t)E->gate_elems * eb);
+  E->sw_off_ops = off;
+  off = a256(off + E->h_ops.size() * sizeof(EOp));
+  E->sw_off_steps = off;
+  off = a256(off + E->h_steps.size() * sizeof(EStep));
+  E->sw_off_nets = off;
+  off = a256(off + E->h_nets.size() * sizeof(ENet));
+  E->sw_off_scalars = off;
+  off = a256(off + E->h_scalars.size() * sizeof(uint32_t) + 4);
+  E->sw_off_zz = off;
+  off = a256(off + (size_t)nsets * E->h_nets.size() * sizeof(double));
+  E->sw_off_energy = off;
+  off = a256(off + (size_t)nsets * sizeof(double));
+  E->sw_off_counter = off;
+  off = a256(off + 64);
+  E->sw_off_arenas = off;
+  off = a256(off + (size_t)E->blocks * (size_t)E->arena_elems * eb);
+  E->sw_total = off;
+  E->sweep_sets = nsets;
+}
+
+template <typename R>
+qt_status enqueue_sweep(qt_energy* E, int nsets, char* base, cudaStream_t s, double* zz,
+                        double* energy, std::string& err) {
+  if (!cuda_ok(cudaMemsetAsync(base + E->sw_off_counter, 0, sizeof(int), s), "reset counter", err))
+    return QT_ECUDA;
+  k_energy<R><<<E->blocks, E->block_threads, 0, s>>>(
+      reinterpret_cast<const ENet*>(base + E->sw_off_nets), (int)E->h_nets.size(), nsets,
+      (long long)E->gate_elems, reinterpret_cast<const EStep*>(base + E->sw_off_steps),
+      reinterpret_cast<const EOp*>(base + E->sw_off_ops),
+      reinterpret_cast<const uint32_t*>(base + E->sw_off_scalars),
+      reinterpret_cast<const R*>(base + E->sw_off_gates),
+      reinterpret_cast<R*>(base + E->sw_off_arenas), (long long)E->arena_elems,
+      reinterpret_cast<int*>(base + E->sw_off_counter), zz);
+  k_energy_sum<<<nsets, 1024, 0, s>>>(zz, (int)E->h_nets.size(), energy);
+  if (!cuda_ok(cudaGetLastError(), "energy sweep launch", err)) return QT_ECUDA;
+  return QT_OK;
+}
+
 template <typename R>
 qt_status enqueue(qt_energy* E, char* base, cudaStream_t s, double* zz, double* energy,
                   std::string& err) {
   if (!cuda_ok(cudaMemsetAsync(base + E->off_counter, 0, sizeof(int), s), "reset counter", err))
     return QT_ECUDA;
   k_energy<R><<<E->blocks, E->block_threads, 0, s>>>(
-      reinterpret_cast<const ENet*>(base + E->off_nets), (int)E->h_nets.size(),
+      reinterpret_cast<const ENet*>(base + E->off_nets), (int)E->h_nets.size(), 1, 0ll,
       reinterpret_cast<const EStep*>(base + E->off_steps),
       reinterpret_cast<const EOp*>(base + E->off_ops),
       reinterpret_cast<const uint32_t*>(base + E->off_scalars),
@@ -552,6 +604,82 @@ qt_status qt_energy_stats(const qt_energy* E, char* buf, size_t cap, size_t* nee
   }
   qt::set_last_error("");
   return QT_OK;
+}
+
+qt_status qt_energy_sweep_prepare(qt_energy* E, int32_t n_sets, size_t* workspace_bytes) {
+  if (!E) return fail(QT_EINVAL, "qt_energy_sweep_prepare: null handle");
+  if (!E->compiled) return fail(QT_ESTATE, "qt_energy_sweep_prepare: call qt_energy_prepare first");
+  if (n_sets < 1 || (int64_t)n_sets * (int64_t)E->h_nets.size() >= (int64_t(1) << 31))
+    return fail(QT_EINVAL, "qt_energy_sweep_prepare: n_sets out of range");
+  layout_sweep(E, n_sets);
+  if (workspace_bytes) *workspace_bytes = E->sw_total;
+  qt::set_last_error("");
+  return QT_OK;
+}
+
+qt_status qt_energy_sweep_upload(qt_energy* E, int32_t n_sets, const double* gammas,
+                                 const double* betas, void* ws, size_t bytes, void* stream) {
+  if (!E || !gammas || !betas) return fail(QT_EINVAL, "qt_energy_sweep_upload: null argument");
+  if (!E->compiled) return fail(QT_ESTATE, "qt_energy_sweep_upload: call qt_energy_prepare first");
+  if (n_sets < 1 || n_sets > E->sweep_sets)
+    return fail(QT_EINVAL, "qt_energy_sweep_upload: n_sets outside [1, the prepared sweep size]");
+  if (!ws || (uintptr_t)ws % 256) return fail(QT_EINVAL, "qt_energy_sweep_upload: bad workspace");
+  if (bytes < E->sw_total) return fail(QT_ENOMEM, "qt_energy_sweep_upload: workspace too small");
+  for (int64_t q = 0; q < (int64_t)n_sets * E->p; ++q)
+    if (!std::isfinite(gammas[q]) || !std::isfinite(betas[q]))
+      return fail(QT_EINVAL, "qt_energy_sweep_upload: angle not finite");
+  const size_t img = (size_t)E->gate_elems * (size_t)E->elem_bytes;
+  try {
+    E->sweep_stage.assign((size_t)n_sets * img, 0);
+  } catch (const std::bad_alloc&) {
+    return fail(QT_ENOMEM, "qt_energy_sweep_upload: out of host memory");
+  }
+  for (int q = 0; q < n_sets; ++q)
+    qt::energy_gate_image(E, gammas + (size_t)q * E->p, betas + (size_t)q * E->p,
+                          E->sweep_stage.data() + (size_t)q * img);
+  std::string err;
+  char* base = (char*)ws;
+  cudaStream_t st = (cudaStream_t)stream;
+  struct Part { size_t off; const void* src; size_t n; };
+  const Part parts[] = {
+      {E->sw_off_gates, E->sweep_stage.data(), E->sweep_stage.size()},
+      {E->sw_off_ops, E->h_ops.data(), E->h_ops.size() * sizeof(qt::EOp)},
+      {E->sw_off_steps, E->h_steps.data(), E->h_steps.size() * sizeof(qt::EStep)},
+      {E->sw_off_nets, E->h_nets.data(), E->h_nets.size() * sizeof(qt::ENet)},
+      {E->sw_off_scalars, E->h_scalars.data(), E->h_scalars.size() * sizeof(uint32_t)}};
+  for (const Part& p : parts)
+    if (p.n && !cuda_ok(cudaMemcpyAsync(base + p.off, p.src, p.n, cudaMemcpyHostToDevice, st),
+                        "sweep upload", err))
+      return fail(QT_ECUDA, "qt_energy_sweep_upload: " + err);
+  qt::set_last_error("");
+  return QT_OK;
+}
+
+qt_status qt_energy_sweep_run(qt_energy* E, int32_t n_sets, void* ws, size_t bytes, void* stream,
+                              double* d_energy, double* d_zz) {
+  if (!E || !d_energy) return fail(QT_EINVAL, "qt_energy_sweep_run: null argument");
+  if (!E->compiled) return fail(QT_ESTATE, "qt_energy_sweep_run: call qt_energy_prepare first");
+  if (n_sets < 1 || n_sets > E->sweep_sets)
+    return fail(QT_EINVAL, "qt_energy_sweep_run: n_sets outside [1, the prepared sweep size]");
+  if (!ws || (uintptr_t)ws % 256) return fail(QT_EINVAL, "qt_energy_sweep_run: bad workspace");
+  if (bytes < E->sw_total) return fail(QT_ENOMEM, "qt_energy_sweep_run: workspace too small");
+  std::string err;
+  char* base = (char*)ws;
+  double* zz = d_zz ? d_zz : reinterpret_cast<double*>(base + E->sw_off_zz);
+  qt_status s = E->precision == QT_FP64
+                    ? enqueue_sweep<double>(E, n_sets, base, (cudaStream_t)stream, zz, d_energy, err)
+                    : enqueue_sweep<float>(E, n_sets, base, (cudaStream_t)stream, zz, d_energy, err);
+  if (s != QT_OK) return fail(s, "qt_energy_sweep_run: " + err);
+  qt::set_last_error("");
+  return QT_OK;
+}
+
+qt_status qt_energy_sweep(qt_energy* E, int32_t n_sets, const double* gammas, const double* betas,
+                          void* ws, size_t bytes, void* stream, double* d_energy, double* d_zz) {
+  if (!d_energy) return fail(QT_EINVAL, "qt_energy_sweep: null output");
+  qt_status s = qt_energy_sweep_upload(E, n_sets, gammas, betas, ws, bytes, stream);
+  if (s != QT_OK) return s;
+  return qt_energy_sweep_run(E, n_sets, ws, bytes, stream, d_energy, d_zz);
 }
 
 void qt_energy_free(qt_energy* E) { delete E; }

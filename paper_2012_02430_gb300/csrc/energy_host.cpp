@@ -23,7 +23,8 @@
 
 namespace qt {
 
-static void lightcone(const qt_energy* E, int u, int v, std::vector<Tensor>& T, int& n_vars,
+static void lightcone(const qt_energy* E, const double* gammas, const double* betas, int u,
+                      int v, std::vector<Tensor>& T, std::vector<int32_t>& tags, int& n_vars,
                       double& norm) {
   const int n = E->n, p = E->p;
   // distances to {u, v}
@@ -60,26 +61,36 @@ static void lightcone(const qt_energy* E, int u, int v, std::vector<Tensor>& T, 
     return t >= nmix[w] ? var(0, w, 0) : var(side, w, t);
   };
   T.clear();
+  tags.clear();
   for (int side = 1; side <= 2; ++side) {
     const double sgn = side == 1 ? 1.0 : -1.0;  // bra: complex conjugate
-    for (int w : qubits) T.push_back({{idx(side, w, 0)}, {1.0, 0.0, 1.0, 0.0}});
+    for (int w : qubits) {
+      T.push_back({{idx(side, w, 0)}, {1.0, 0.0, 1.0, 0.0}});
+      tags.push_back(0);
+    }
     for (int k = 1; k <= p; ++k) {
-      const double g = E->gammas[k - 1], b = E->betas[k - 1];
+      const double g = gammas[k - 1], b = betas[k - 1];
       const double er = std::cos(g), ei = -std::sin(g) * sgn;
       const double c = std::cos(b), s = std::sin(b) * sgn;
       for (size_t e = 0; e < E->edges.size() / 2; ++e) {
         const int a = E->edges[2 * e], bb = E->edges[2 * e + 1];
-        if (d[a] >= 0 && d[bb] >= 0 && std::min(d[a], d[bb]) <= p - k)
+        if (d[a] >= 0 && d[bb] >= 0 && std::min(d[a], d[bb]) <= p - k) {
           T.push_back({{idx(side, a, k - 1), idx(side, bb, k - 1)},
                        {1.0, 0.0, er, ei, er, ei, 1.0, 0.0}});
+          tags.push_back(1 | (k << 4) | (side << 12));
+        }
       }
       for (int w : qubits)
-        if (d[w] <= p - k)
+        if (d[w] <= p - k) {
           T.push_back({{idx(side, w, k - 1), idx(side, w, k)}, {c, 0.0, 0.0, -s, 0.0, -s, c, 0.0}});
+          tags.push_back(2 | (k << 4) | (side << 12));
+        }
     }
   }
   T.push_back({{var(0, u, 0)}, {1.0, 0.0, -1.0, 0.0}});
   T.push_back({{var(0, v, 0)}, {1.0, 0.0, -1.0, 0.0}});
+  tags.push_back(0);
+  tags.push_back(0);
   n_vars = (int)ids.size();
   norm = std::ldexp(1.0, -(int)qubits.size());
 }
@@ -89,7 +100,8 @@ bool energy_build_networks(qt_energy* E, std::string& err) {
   E->nets.assign(ne, EnergyNet{});
   for (int e = 0; e < ne; ++e) {
     EnergyNet& N = E->nets[e];
-    lightcone(E, E->edges[2 * e], E->edges[2 * e + 1], N.tensors, N.n_vars, N.norm);
+    lightcone(E, E->gammas.data(), E->betas.data(), E->edges[2 * e], E->edges[2 * e + 1],
+              N.tensors, N.tags, N.n_vars, N.norm);
     BitGraph g = line_graph(N.tensors, N.n_vars);
     OrderResult o = greedy_order(g, E->algo);
     N.plan = SlicePlan();
@@ -203,6 +215,44 @@ bool energy_compile(qt_energy* E, int precision, std::string& err) {
   }
   E->compiled = true;
   return true;
+}
+
+void energy_gate_image(const qt_energy* E, const double* gammas, const double* betas,
+                       unsigned char* dst) {
+  const size_t eb = (size_t)E->elem_bytes;
+  int64_t base = 0;
+  for (const EnergyNet& N : E->nets) {
+    const Schedule& S = N.sched;
+    for (const STensor& t : S.tensors) {
+      if (t.kind != TK_GATE) continue;
+      Tensor g = N.tensors[t.gate];
+      const int tag = N.tags[t.gate];
+      const int kind = tag & 15, k = (tag >> 4) & 255, side = tag >> 12;
+      if (kind != 0) {
+        const double sgn = side == 1 ? 1.0 : -1.0;
+        if (kind == 1) {
+          const double er = std::cos(gammas[k - 1]), ei = -std::sin(gammas[k - 1]) * sgn;
+          g.data = {1.0, 0.0, er, ei, er, ei, 1.0, 0.0};
+        } else {
+          const double c = std::cos(betas[k - 1]), s = std::sin(betas[k - 1]) * sgn;
+          g.data = {c, 0.0, 0.0, -s, 0.0, -s, c, 0.0};
+        }
+      }
+      const std::vector<double> dd = canonical_data(g, t.labels);
+      for (size_t q = 0; q < dd.size(); ++q) {
+        const size_t at = (size_t)(base + t.offset) * 2 + q;
+        if (E->precision == QT_FP64) {
+          const double x = dd[q];
+          std::memcpy(dst + at * sizeof(double), &x, sizeof(double));
+        } else {
+          const float x = (float)dd[q];
+          std::memcpy(dst + at * sizeof(float), &x, sizeof(float));
+        }
+      }
+    }
+    base += S.gate_elems;
+  }
+  (void)eb;
 }
 
 }  // namespace qt

@@ -12,6 +12,10 @@ namespace qt {
 // one edge's lightcone network, its order and its compiled schedule
 struct EnergyNet {
   std::vector<Tensor> tensors;
+  // per tensor: how its data follows from the angles (angle sweeps rebuild the gate
+  // data without re-planning): kind (0 constant, 1 phase of layer k, 2 mixer of
+  // layer k) | layer k << 4 | side << 12 (1 ket, 2 bra)
+  std::vector<int32_t> tags;
   int n_vars = 0;
   double norm = 1.0;  // 2^(-|S|)
   SlicePlan plan;
@@ -63,10 +67,18 @@ struct qt_energy {
   size_t off_gates = 0, off_ops = 0, off_steps = 0, off_nets = 0, off_scalars = 0,
          off_arenas = 0, off_zz = 0, off_counter = 0, total_bytes_ws = 0;
   void* engine = nullptr;  // graph cache
+  // angle sweep: workspace layout for sweep_sets angle sets, staged gate images
+  int sweep_sets = 0;
+  size_t sw_off_gates = 0, sw_off_ops = 0, sw_off_steps = 0, sw_off_nets = 0, sw_off_scalars = 0,
+         sw_off_zz = 0, sw_off_energy = 0, sw_off_counter = 0, sw_off_arenas = 0, sw_total = 0;
+  std::vector<unsigned char> sweep_stage;
   ~qt_energy();
 };
 
 namespace qt {
 bool energy_build_networks(qt_energy* E, std::string& err);
 bool energy_compile(qt_energy* E, int precision, std::string& err);
+// gate data of every network for one angle set, in the compiled precision and layout
+void energy_gate_image(const qt_energy* E, const double* gammas, const double* betas,
+                       unsigned char* dst);
 }  // namespace qt

@@ -89,6 +89,10 @@ _SIGS = {
     "qt_energy_compute": [_vp, C.c_int32, _vp, C.c_size_t, _vp, _f64p, _f64p],
     "qt_energy_get_order": [_vp, C.c_int32, _i32p, C.c_int32, _i32p, _i32p, _i32p],
     "qt_energy_stats": [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)],
+    "qt_energy_sweep_prepare": [_vp, C.c_int32, C.POINTER(C.c_size_t)],
+    "qt_energy_sweep": [_vp, C.c_int32, _f64p, _f64p, _vp, C.c_size_t, _vp, _vp, _vp],
+    "qt_energy_sweep_upload": [_vp, C.c_int32, _f64p, _f64p, _vp, C.c_size_t, _vp],
+    "qt_energy_sweep_run": [_vp, C.c_int32, _vp, C.c_size_t, _vp, _vp, _vp],
     "qt_autotune": [_vp, _vp, C.c_size_t, _vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)],
     "qt_profile_read": [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)],
 }
@@ -380,6 +384,38 @@ class Energy:
 
     def stats(self):
         return qt_energy_stats(self.handle)
+
+    def sweep_prepare(self, n_sets, device="cuda"):
+        """Workspace for angle sweeps of up to n_sets sets (after prepare)."""
+        import torch
+        need = C.c_size_t()
+        _check(lib.qt_energy_sweep_prepare(self.handle, int(n_sets), C.byref(need)))
+        self.sweep_ws = torch.empty(need.value, dtype=torch.uint8, device=device)
+        return need.value
+
+    def sweep_upload(self, gammas, betas):
+        flat_g = [float(x) for row in gammas for x in row]
+        flat_b = [float(x) for row in betas for x in row]
+        _check(lib.qt_energy_sweep_upload(self.handle, len(gammas), _arr(C.c_double, flat_g),
+                                          _arr(C.c_double, flat_b), _vp(self.sweep_ws.data_ptr()),
+                                          int(self.sweep_ws.numel()), _vp(self._stream())))
+
+    def sweep_run(self, n_sets, energies, zz=None):
+        _check(lib.qt_energy_sweep_run(self.handle, int(n_sets), _vp(self.sweep_ws.data_ptr()),
+                                       int(self.sweep_ws.numel()), _vp(self._stream()),
+                                       _vp(energies.data_ptr()),
+                                       _vp(zz.data_ptr()) if zz is not None else None))
+
+    def sweep(self, gammas, betas, energies, zz=None):
+        """Energies of len(gammas) angle sets (each a list of p angles) into the float64
+        CUDA tensor `energies`; per-edge <Z_u Z_v> into `zz` [n_sets][n_edges] if given."""
+        flat_g = [float(x) for row in gammas for x in row]
+        flat_b = [float(x) for row in betas for x in row]
+        _check(lib.qt_energy_sweep(self.handle, len(gammas), _arr(C.c_double, flat_g),
+                                   _arr(C.c_double, flat_b), _vp(self.sweep_ws.data_ptr()),
+                                   int(self.sweep_ws.numel()), _vp(self._stream()),
+                                   _vp(energies.data_ptr()),
+                                   _vp(zz.data_ptr()) if zz is not None else None))
 
 
 # ------------------------ convenience wrapper (torch) ------------------------

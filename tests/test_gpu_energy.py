@@ -98,3 +98,47 @@ def test_energy_device_run(qt):
     E_ref, zz_ref = energy.energy_lightcone(n, edges, p, g, b)
     assert abs(E.item() - E_ref) <= 1e-5 * abs(E_ref)
     assert max(abs(x - y) for x, y in zip(zz.tolist(), zz_ref)) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", [0, 4])
+def test_energy_angle_sweep_vs_statevector(qt, prec):
+    """Angle sweep: 6 angle sets of one N=14, p=2 graph in one persistent launch; each
+    set's energy and <Z_u Z_v> equal the 2^14 statevector's."""
+    from paper_2012_02430_gb300.inputs import random_angles
+    n, p, seed = 14, 2, 6
+    edges, g, b, z = qaoa_instance(n, p, seed)
+    en = qt.Energy(edges, n, p, g, b)
+    en.prepare(prec)
+    sets = [random_angles(p, 300 + s) for s in range(6)]
+    en.sweep_prepare(len(sets))
+    E = torch.zeros(len(sets), dtype=torch.float64, device="cuda")
+    zz = torch.zeros(len(sets), len(edges), dtype=torch.float64, device="cuda")
+    en.sweep([s[0] for s in sets], [s[1] for s in sets], E, zz)
+    torch.cuda.synchronize()
+    for q, (gs, bs) in enumerate(sets):
+        e_sv = statevector.maxcut_energy(n, edges, gs, bs)
+        zz_sv = statevector.zz_expectations(n, edges, gs, bs)
+        assert abs(E[q].item() - e_sv) <= TOL[prec] * abs(e_sv)
+        assert max(abs(zz[q, i].item() - zz_sv[i]) for i in range(len(edges))) <= TOL[prec]
+
+
+def test_energy_angle_sweep_matches_single_runs(qt):
+    """N=200, p=2: a sweep of 4 angle sets gives each set's single-run energy and the
+    oracle's lightcone energy."""
+    from paper_2012_02430_gb300.inputs import random_angles
+    n, p, seed = 200, 2, 1004
+    edges, g, b, z = qaoa_instance(n, p, seed)
+    en = qt.Energy(edges, n, p, g, b)
+    en.prepare(0)
+    sets = [random_angles(p, 400 + s) for s in range(4)]
+    en.sweep_prepare(len(sets))
+    E = torch.zeros(len(sets), dtype=torch.float64, device="cuda")
+    en.sweep([s[0] for s in sets], [s[1] for s in sets], E)
+    torch.cuda.synchronize()
+    for q, (gs, bs) in enumerate(sets):
+        E_ref, _ = energy.energy_lightcone(n, edges, p, gs, bs)
+        assert abs(E[q].item() - E_ref) <= TOL[0] * abs(E_ref)
+        single = qt.Energy(edges, n, p, gs, bs)
+        single.prepare(0)
+        e1, _ = single.compute(0)
+        assert abs(E[q].item() - e1) <= 1e-9 * abs(e1)

@@ -324,6 +324,19 @@ def test_energy_lightcone_orders_bit_exact(qt, n, p, seed, algo):
         qt.qt_energy_free(h)
 
 
+def test_energy_sweep_errors(qt):
+    """Angle sweeps refuse to run before qt_energy_prepare (no CUDA call is made)."""
+    import ctypes as C
+    h = qt.qt_energy_build([(0, 1), (1, 2), (2, 0)], 3, 1, [0.1], [0.2])
+    try:
+        need = C.c_size_t()
+        assert qt.lib.qt_energy_sweep_prepare(h, 2, C.byref(need)) == qt.QT_ESTATE
+        g = (C.c_double * 2)(0.1, 0.2)
+        assert qt.lib.qt_energy_sweep(h, 2, g, g, None, 0, None, None, None) == qt.QT_EINVAL
+    finally:
+        qt.qt_energy_free(h)
+
+
 def test_energy_errors(qt):
     with pytest.raises(qt.QtError) as e:
         qt.qt_energy_build([(0, 1), (1, 1)], 3, 1, [0.1], [0.2])
