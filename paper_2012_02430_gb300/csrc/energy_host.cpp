@@ -219,40 +219,49 @@ bool energy_compile(qt_energy* E, int precision, std::string& err) {
 
 void energy_gate_image(const qt_energy* E, const double* gammas, const double* betas,
                        unsigned char* dst) {
-  const size_t eb = (size_t)E->elem_bytes;
+  // the phase and mixer matrices are symmetric, so their canonical layout is their
+  // own element order whatever the label order; constant tensors are copied
+  const int p = E->p;
+  std::vector<double> ph(4 * (size_t)p), mx(4 * (size_t)p);  // [k][side]: (re, im) pairs
+  for (int k = 0; k < p; ++k)
+    for (int side = 1; side <= 2; ++side) {
+      const double sgn = side == 1 ? 1.0 : -1.0;
+      ph[4 * k + 2 * (side - 1)] = std::cos(gammas[k]);
+      ph[4 * k + 2 * (side - 1) + 1] = -std::sin(gammas[k]) * sgn;
+      mx[4 * k + 2 * (side - 1)] = std::cos(betas[k]);
+      mx[4 * k + 2 * (side - 1) + 1] = std::sin(betas[k]) * sgn;
+    }
+  const bool f64 = E->precision == QT_FP64;
+  auto put = [&](size_t at, double v) {
+    if (f64) std::memcpy(dst + at * sizeof(double), &v, sizeof(double));
+    else {
+      const float x = (float)v;
+      std::memcpy(dst + at * sizeof(float), &x, sizeof(float));
+    }
+  };
   int64_t base = 0;
   for (const EnergyNet& N : E->nets) {
     const Schedule& S = N.sched;
     for (const STensor& t : S.tensors) {
       if (t.kind != TK_GATE) continue;
-      Tensor g = N.tensors[t.gate];
       const int tag = N.tags[t.gate];
       const int kind = tag & 15, k = (tag >> 4) & 255, side = tag >> 12;
-      if (kind != 0) {
-        const double sgn = side == 1 ? 1.0 : -1.0;
-        if (kind == 1) {
-          const double er = std::cos(gammas[k - 1]), ei = -std::sin(gammas[k - 1]) * sgn;
-          g.data = {1.0, 0.0, er, ei, er, ei, 1.0, 0.0};
-        } else {
-          const double c = std::cos(betas[k - 1]), s = std::sin(betas[k - 1]) * sgn;
-          g.data = {c, 0.0, 0.0, -s, 0.0, -s, c, 0.0};
-        }
-      }
-      const std::vector<double> dd = canonical_data(g, t.labels);
-      for (size_t q = 0; q < dd.size(); ++q) {
-        const size_t at = (size_t)(base + t.offset) * 2 + q;
-        if (E->precision == QT_FP64) {
-          const double x = dd[q];
-          std::memcpy(dst + at * sizeof(double), &x, sizeof(double));
-        } else {
-          const float x = (float)dd[q];
-          std::memcpy(dst + at * sizeof(float), &x, sizeof(float));
-        }
+      const size_t at = (size_t)(base + t.offset) * 2;
+      if (kind == 0) {
+        const std::vector<double> dd = canonical_data(N.tensors[t.gate], t.labels);
+        for (size_t q = 0; q < dd.size(); ++q) put(at + q, dd[q]);
+      } else if (kind == 1) {
+        const double er = ph[4 * (k - 1) + 2 * (side - 1)], ei = ph[4 * (k - 1) + 2 * (side - 1) + 1];
+        const double v[8] = {1.0, 0.0, er, ei, er, ei, 1.0, 0.0};
+        for (int q = 0; q < 8; ++q) put(at + q, v[q]);
+      } else {
+        const double c = mx[4 * (k - 1) + 2 * (side - 1)], sn = mx[4 * (k - 1) + 2 * (side - 1) + 1];
+        const double v[8] = {c, 0.0, 0.0, -sn, 0.0, -sn, c, 0.0};
+        for (int q = 0; q < 8; ++q) put(at + q, v[q]);
       }
     }
     base += S.gate_elems;
   }
-  (void)eb;
 }
 
 }  // namespace qt

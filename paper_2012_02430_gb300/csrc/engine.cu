@@ -1094,7 +1094,8 @@ struct LaunchDesc {
 
 constexpr int VARIANT_GEMM = 3;
 constexpr int VARIANT_TRI = 4;
-constexpr int N_ALL_VARIANTS = 5;
+constexpr int VARIANT_FLAT = 5;  // the flat kernel for a launch the tiled kernel takes
+constexpr int N_ALL_VARIANTS = 6;
 
 // GEMM flavour of a GEMM-form launch in a precision mode
 static int gemm_mode_for(const Schedule& S, const SGroup& g) {
@@ -1356,8 +1357,14 @@ static bool make_desc(const Schedule& S, int gi, long long nslices, LaunchDesc& 
       return true;
     }
   }
-  if (variant >= VARIANT_GEMM) d.variant = variant = 1;
-  if (tiled) {
+  bool use_tiled = tiled;
+  if (variant == VARIANT_FLAT) {
+    use_tiled = false;
+    d.kind = 0;
+  } else if (variant >= VARIANT_GEMM) {
+    d.variant = variant = 1;
+  }
+  if (use_tiled) {
     const long long ntiles = nslices << (st.u - TILE_UBITS);
     d.grid = (unsigned)std::min<long long>(ntiles, tiled_grid_cap<R>(variant, k.ms));
   } else {
@@ -1721,6 +1728,7 @@ static qt_status autotune_impl(qt_net* net, char* base, cudaStream_t s, std::str
       for (int v = 0; v < N_VARIANTS; ++v) cands.push_back(v);
       if (can_gemm) cands.push_back(VARIANT_GEMM);
       if (can_tri) cands.push_back(VARIANT_TRI);
+      if (grp.u <= 20) cands.push_back(VARIANT_FLAT);  // small launches: one pair per thread
       const int nv = (int)cands.size();
       for (int pass = 0; pass < 2; ++pass)
         for (int t = 0; t < nv; ++t) {
@@ -1773,10 +1781,10 @@ static qt_status autotune_impl(qt_net* net, char* base, cudaStream_t s, std::str
       char buf[200];
       auto half = [](float x) { return x >= 1e29f ? -1.0 : x / 2.0; };
       std::snprintf(buf, sizeof buf,
-                    "%s{\"step\":%d,\"variant\":%d,\"ms\":[%.4f,%.4f,%.4f,%.4f,%.4f]}",
+                    "%s{\"step\":%d,\"variant\":%d,\"ms\":[%.4f,%.4f,%.4f,%.4f,%.4f,%.4f]}",
                     first ? "" : ",", S.groups[d.group].first, bv, half(kv.second[0]),
                     half(kv.second[1]), half(kv.second[2]), half(kv.second[3]),
-                    half(kv.second[4]));
+                    half(kv.second[4]), half(kv.second[5]));
       report += buf;
       first = false;
     }
