@@ -17,6 +17,8 @@ qt_status run(qt_net* net, long long first, long long count, void* ws, void* str
               double* d_out, std::string& err);
 qt_status download_result(const double* d_out, double* host, int64_t n_doubles, void* stream,
                           std::string& err);
+qt_status read_status(const qt_net* net, const void* ws, void* stream, int* status,
+                      std::string& err);
 void prof_clear(qt_net* net);
 qt_status autotune(qt_net* net, void* ws, void* stream, std::string& report, std::string& err);
 qt_status prof_read(qt_net* net, std::string& out, std::string& err);
@@ -402,6 +404,10 @@ static qt_status contract_impl(qt_net* net, int32_t precision, void* workspace,
   if (s != QT_OK) return fail(s, std::string(who) + ": " + err);
   s = qt::download_result(d_out, host_out, 2 * A, stream, err);
   if (s != QT_OK) return fail(s, std::string(who) + ": " + err);
+  int status = 0;
+  s = qt::read_status(net, workspace, stream, &status, err);
+  if (s != QT_OK) return fail(s, std::string(who) + ": " + err);
+  if (status) return fail(QT_ETIMEOUT, std::string(who) + ": a bounded device wait gave up");
   return ok();
 }
 
@@ -529,6 +535,10 @@ qt_status qt_set_option(qt_net* net, int32_t option, int64_t value) {
       break;
     case QT_OPT_TRIANGLE:
       net->force_tri = value != 0;
+      net->sched = qt::Schedule();  // prepare again
+      break;
+    case QT_OPT_TMA:
+      net->tma = value != 0;
       net->sched = qt::Schedule();  // prepare again
       break;
     default:

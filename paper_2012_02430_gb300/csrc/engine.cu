@@ -1630,6 +1630,8 @@ static void launch_desc(qt_net* net, const LaunchDesc& d0, long long nslices, lo
     GemmArgs ga = d0.ga;
     ga.nslices = nslices;
     ga.slice_first = slice_first;
+    ga.err = reinterpret_cast<int*>(base + S.off_err);
+    ga.use_tma = net->tma ? 1 : 0;
     net->launches += gemm_launch(ga, d0.gemm_mode, reinterpret_cast<float*>(base),
                                  reinterpret_cast<GMeta*>(meta), s, num_sms());
     if (net->prof) prof_end(net, s, pr);
@@ -1650,6 +1652,8 @@ static qt_status enqueue_run(qt_net* net, EngineCache& c, long long first, long 
   const Schedule& S = net->sched;
   const size_t ngm = n_gate_meta(S);
   Meta* meta = reinterpret_cast<Meta*>(base + S.off_meta);
+  if (!cuda_ok(cudaMemsetAsync(base + S.off_err, 0, sizeof(int), s), "reset status", err))
+    return QT_ECUDA;
   // prefix (contract_first): once, unsliced
   if (S.n_shared_meta > (int64_t)ngm &&
       !cuda_ok(cudaMemsetAsync(meta + ngm, 0, (S.n_shared_meta - ngm) * sizeof(Meta), s),
@@ -1868,6 +1872,18 @@ qt_status run(qt_net* net, long long first, long long count, void* ws, void* str
   cudaStream_t s = (cudaStream_t)stream;
   if (net->sched.precision == QT_FP64) return run_impl<double>(net, first, count, base, s, d_out, err);
   return run_impl<float>(net, first, count, base, s, d_out, err);
+}
+
+// the device status word of a run: nonzero when a bounded wait gave up
+qt_status read_status(const qt_net* net, const void* ws, void* stream, int* status,
+                      std::string& err) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!cuda_ok(cudaMemcpyAsync(status, (const char*)ws + net->sched.off_err, sizeof(int),
+                               cudaMemcpyDeviceToHost, s),
+               "read status", err) ||
+      !cuda_ok(cudaStreamSynchronize(s), "stream synchronize", err))
+    return QT_ECUDA;
+  return QT_OK;
 }
 
 qt_status download_result(const double* d_out, double* host, int64_t n_doubles, void* stream,

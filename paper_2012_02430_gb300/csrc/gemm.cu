@@ -353,6 +353,53 @@ __device__ __forceinline__ unsigned int warp_pdep(unsigned int x, unsigned int m
   return __reduce_or_sync(0xffffffffu, bit << lane);
 }
 
+// Bulk asynchronous copies (TMA, cp.async.bulk) completing on a shared-memory
+// mbarrier, and a bounded wait on the barrier's phase: after kMbarSpins failed
+// tries the wait gives up, raises *err and returns false (the caller's results are
+// then invalid and the host reports a timeout) instead of spinning forever.
+constexpr unsigned int kMbarSpins = 1u << 24;
+
+__device__ __forceinline__ unsigned int smem_u32(const void* p) {
+  return (unsigned int)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned int bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy(void* smem, const void* gmem, unsigned int bytes,
+                                          unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_u32(smem)),
+      "l"(gmem), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned int parity, int* err) {
+  for (unsigned int it = 0; it < kMbarSpins; ++it) {
+    unsigned int done = 0;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  if (err) atomicExch(err, 1);
+  return false;
+}
+
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
@@ -381,10 +428,13 @@ __device__ __forceinline__ void cp_async_wait() {
 // tile, a thread computes the four outputs that differ in those two bits. They
 // share two A rows and two B rows, so one k step is 4 shared-memory loads for
 // 8 complex multiply-adds.
+template <bool TMA>
 __global__ void __launch_bounds__(256) k_gemm_tile(const GemmArgs a, int u, float* data,
                                                    GMeta* meta) {
   extern __shared__ float4 gsm[];
   __shared__ long long s_loc[3][4];  // tile slots: slice, tau, A block, B block
+  __shared__ alignas(8) unsigned long long s_bar[2];  // TMA: one barrier per buffer
+  __shared__ int s_fail;
   const int nsum = a.nsum, t = a.tb, c = u - nsum, h = c - t;
   const int K = 1 << nsum, RS = K + 2;  // row stride (complex): rows stay 16-byte aligned
   const int KC = K >> 1, lkc = nsum - 1;  // 16-byte chunks per row
@@ -429,36 +479,74 @@ __global__ void __launch_bounds__(256) k_gemm_tile(const GemmArgs a, int u, floa
       s_loc[slot][3] = bb + (pb << lb);
     }
   };
-  auto issue = [&](int slot, float2* dst) {
+  // the copies of one tile into buffer b: cp.async by every thread, or (TMA) one bulk
+  // copy per row issued by warp 0, completing on buffer b's barrier
+  auto issue = [&](int slot, int b) {
+    float2* sA = sbase + b * buf;
+    float2* sB = sA + rows_a * RS;
     const long long ta = s_loc[slot][2], tb = s_loc[slot][3];
-    float2* sA = dst;
-    float2* sB = dst + rows_a * RS;
-    for (int e = threadIdx.x; e < rows_a * KC; e += blockDim.x)
-      cp_async16(sA + (e >> lkc) * RS + 2 * (e & (KC - 1)), d2 + ta + 2 * e);
-    for (int e = threadIdx.x; e < rows_b * KC; e += blockDim.x)
-      cp_async16(sB + (e >> lkc) * RS + 2 * (e & (KC - 1)), d2 + tb + 2 * e);
-    cp_async_commit();
+    if constexpr (TMA) {
+      if (threadIdx.x < 32) {
+        fence_proxy_async();  // the buffer's last generic reads precede the bulk writes
+        if (threadIdx.x == 0) mbar_expect_tx(&s_bar[b], (unsigned)((rows_a + rows_b) * K * 8));
+        __syncwarp();
+        const unsigned int rb = (unsigned)(K * 8);
+        for (int r = threadIdx.x; r < rows_a + rows_b; r += 32) {
+          if (r < rows_a) bulk_copy(sA + r * RS, d2 + ta + (long long)r * K, rb, &s_bar[b]);
+          else bulk_copy(sB + (r - rows_a) * RS, d2 + tb + (long long)(r - rows_a) * K, rb, &s_bar[b]);
+        }
+      }
+    } else {
+      for (int e = threadIdx.x; e < rows_a * KC; e += blockDim.x)
+        cp_async16(sA + (e >> lkc) * RS + 2 * (e & (KC - 1)), d2 + ta + 2 * e);
+      for (int e = threadIdx.x; e < rows_b * KC; e += blockDim.x)
+        cp_async16(sB + (e >> lkc) * RS + 2 * (e & (KC - 1)), d2 + tb + 2 * e);
+      cp_async_commit();
+    }
   };
   const long long G = gridDim.x;
   long long w = blockIdx.x;
+  if (TMA && threadIdx.x == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    mbar_fence_init();
+    s_fail = 0;
+  }
   if (threadIdx.x < 32) {
     if (w < ntiles) locate(w, 0);
     if (w + G < ntiles) locate(w + G, 1);
   }
   __syncthreads();
-  if (w < ntiles) issue(0, sbase);
+  if (w < ntiles) issue(0, 0);
   long long cur = -1;
   float sc = 1.f, mx = 0.f;
+  int pending = -1;  // TMA: the tile whose copies were issued and not yet waited for
   for (int j = 0; w < ntiles; ++j, w += G) {
     const int slot = j % 3;
-    if (w + G < ntiles) {
-      issue((j + 1) % 3, sbase + ((j + 1) & 1) * buf);
-      cp_async_wait<1>();
+    if constexpr (TMA) {
+      if (w + G < ntiles) {
+        issue((j + 1) % 3, (j + 1) & 1);
+        pending = j + 1;
+      } else {
+        pending = -1;
+      }
+      if (!mbar_wait(&s_bar[j & 1], (unsigned)((j >> 1) & 1), a.err)) s_fail = 1;
     } else {
-      cp_async_wait<0>();
+      if (w + G < ntiles) {
+        issue((j + 1) % 3, (j + 1) & 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
     }
     if (threadIdx.x < 32 && w + 2 * G < ntiles) locate(w + 2 * G, (j + 2) % 3);
     __syncthreads();
+    if (TMA && s_fail) {
+      // a copy never arrived: stop (the host reports the timeout), after a bounded wait
+      // for the next tile's copies still in flight into this block's shared memory
+      if (pending >= 0) mbar_wait(&s_bar[pending & 1], (unsigned)((pending >> 1) & 1), nullptr);
+      break;
+    }
     const long long i_c = s_loc[slot][0], tau_c = s_loc[slot][1];
     if (i_c != cur) {
       if (cur >= 0) flush_max(a, meta, cur, mx);
@@ -1094,7 +1182,9 @@ int gemm_launch(const GemmArgs& a, int mode, float* data, GMeta* meta, cudaStrea
     for (unsigned int m = a.mK | a.mSA | a.mSB | a.mM | a.mN | a.mBt; m; m >>= 1) ++u;
     static bool attr = false;
     if (!attr) {
-      cudaFuncSetAttribute(k_gemm_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(k_gemm_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kTileSmemMax);
+      cudaFuncSetAttribute(k_gemm_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kTileSmemMax);
       attr = true;
     }
@@ -1103,7 +1193,8 @@ int gemm_launch(const GemmArgs& a, int mode, float* data, GMeta* meta, cudaStrea
     const int per_sm = std::max<int>(1, std::min<int>(8, (int)((220 * 1024) / (smem + 1024))));
     const unsigned grid =
         (unsigned)std::max<long long>(1, std::min<long long>(ntiles, (long long)sms * per_sm));
-    k_gemm_tile<<<grid, 256, smem, s>>>(a, u, data, meta);
+    if (a.use_tma && a.err) k_gemm_tile<true><<<grid, 256, smem, s>>>(a, u, data, meta);
+    else k_gemm_tile<false><<<grid, 256, smem, s>>>(a, u, data, meta);
     return n + 1;
   }
   const int kb = __builtin_popcount(a.mK), bb = __builtin_popcount(a.mBt);

@@ -38,6 +38,8 @@ struct GemmArgs {
   int reg_a, reg_b;         // register-blocking bits of the tile (-1: none)
   int tA, tB, tC;           // triangle form: the large operands
   unsigned int tK, tX, tY;  // triangle form: summed bits of each class
+  int use_tma;              // GEMM_TILE: stage operand rows with bulk copies (TMA)
+  int* err;                 // device status word: set to 1 when a bounded wait gives up
   GOp op[GEMM_MAXOP];
 };
 

@@ -478,6 +478,8 @@ bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePla
   off = align256(off + S.scalars.size() * kScalarTermBytes);
   S.off_segtab = off;  // step records of the segment launches (runs of small launches)
   off = align256(off + S.groups.size() * kStepRecordBytes);
+  S.off_err = off;  // device status word: set when a bounded wait in a kernel gives up
+  off = align256(off + 16);
   S.total_bytes = off;
   S.valid = true;
   return true;

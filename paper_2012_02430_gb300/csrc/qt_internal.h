@@ -156,7 +156,7 @@ struct Schedule {
   int64_t n_shared_meta = 0, n_slice_meta_tensors = 0;
   // workspace layout (bytes)
   size_t off_gates = 0, off_prefix = 0, off_slices = 0, off_meta = 0, off_partials = 0,
-         off_acc = 0, off_terms = 0, off_segtab = 0, total_bytes = 0;
+         off_acc = 0, off_terms = 0, off_segtab = 0, off_err = 0, total_bytes = 0;
   // ledger
   int64_t prefix_flops = 0, prefix_bytes = 0, slice_flops = 0, slice_bytes = 0;
   int64_t prefix_launch_bytes = 0, slice_launch_bytes = 0;  // bytes of the (fused) launches
@@ -224,6 +224,7 @@ struct qt_net {
   bool force_gemm = false;       // GEMM-form launches by default also in FP32 mode
   bool segments = true;          // runs of small launches as one segment launch
   bool force_tri = false;        // triangle-form launches by default where they apply
+  bool tma = false;              // tiled GEMM stages operand rows with bulk copies (TMA)
   void* engine = nullptr;        // engine.cu: launch descriptors and graph cache
   ~qt_net();
 };
