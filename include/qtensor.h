@@ -327,11 +327,12 @@ void qt_mlp_free(qt_mlp* mlp);
  *                  out = sum_k w(k) sum_x A[k,x] sum_y B[k,y] C'[x,y], tiled over
  *                  the lowest U bits in shared memory. 0 (default): only the
  *                  autotuner may pick it. Discards the prepared schedule.
- *   QT_OPT_TMA     1: the FP32 tiled GEMM stages its operand rows with bulk
- *                  asynchronous copies (cp.async.bulk, one per row, completing
- *                  on a shared-memory mbarrier; bounded waits raise QT_ETIMEOUT
- *                  in qt_contract); 0 (default): 16-byte cp.async copies by
- *                  every thread, measured faster for these short rows.
+ *   QT_OPT_TMA     1 (default): the FP32 tiled GEMM stages its operand blocks
+ *                  with tensor copies (cp.async.bulk.tensor over 2-D tensor maps
+ *                  of the workspace, completing on shared-memory mbarriers;
+ *                  bounded waits raise QT_ETIMEOUT in qt_contract), when every
+ *                  block starts on a whole row; 0: 16-byte cp.async copies by
+ *                  every thread. Both give the same results, bit for bit.
  * Errors: QT_EINVAL for a null network or an unknown option. */
 enum { QT_OPT_FUSION = 1, QT_OPT_GRAPHS = 2, QT_OPT_GEMM = 3, QT_OPT_SEGMENTS = 4,
        QT_OPT_TRIANGLE = 5, QT_OPT_TMA = 6 };

@@ -328,7 +328,8 @@ qt_status qt_stats(const qt_net* net, char* buf, size_t cap, size_t* needed) {
   if (!net->sched.valid) return fail(QT_ESTATE, "qt_stats: call qt_prepare first");
   std::string s = qt::schedule_json(net->sched, net->plan);
   s.pop_back();
-  s += ",\"launches\":" + std::to_string(net->launches) + "}";
+  s += ",\"launches\":" + std::to_string(net->launches) +
+       ",\"tma_gemm_launches\":" + std::to_string(net->tma_launches) + "}";
   if (needed) *needed = s.size() + 1;
   if (buf && cap > 0) {
     size_t n = std::min(cap - 1, s.size());

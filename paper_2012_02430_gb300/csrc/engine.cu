@@ -1163,6 +1163,8 @@ static void fill_gemm(const Schedule& S, const SGroup& g, long long nslices, Gem
   }
   a.tb = gemm_tile_bits(a, g.u);
   a.tile_inner = gemm_tile_inner(a, g.u);
+  a.stay = gemm_tile_stay(a);
+  a.ws_elems = (long long)(S.total_bytes / 8);
   gemm_tile_regs(a, a.reg_a, a.reg_b);
 }
 
@@ -1632,8 +1634,10 @@ static void launch_desc(qt_net* net, const LaunchDesc& d0, long long nslices, lo
     ga.slice_first = slice_first;
     ga.err = reinterpret_cast<int*>(base + S.off_err);
     ga.use_tma = net->tma ? 1 : 0;
+    bool tma = false;
     net->launches += gemm_launch(ga, d0.gemm_mode, reinterpret_cast<float*>(base),
-                                 reinterpret_cast<GMeta*>(meta), s, num_sms());
+                                 reinterpret_cast<GMeta*>(meta), s, num_sms(), &tma);
+    if (tma) net->tma_launches++;
     if (net->prof) prof_end(net, s, pr);
     return;
   }

@@ -13,6 +13,7 @@
 // a = a_hi + a_lo with a_hi = tf32(a), products a_hi b_hi + a_hi b_lo + a_lo b_hi),
 // and the epilogue scatters each result to its place in the canonical layout
 // of the output (index = the output's U bits, shifted down by the summed ones).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -353,8 +354,8 @@ __device__ __forceinline__ unsigned int warp_pdep(unsigned int x, unsigned int m
   return __reduce_or_sync(0xffffffffu, bit << lane);
 }
 
-// Bulk asynchronous copies (TMA, cp.async.bulk) completing on a shared-memory
-// mbarrier, and a bounded wait on the barrier's phase: after kMbarSpins failed
+// Shared-memory mbarriers for asynchronous (TMA) copies, and a bounded wait on a
+// barrier's phase: after kMbarSpins failed
 // tries the wait gives up, raises *err and returns false (the caller's results are
 // then invalid and the host reports a timeout) instead of spinning forever.
 constexpr unsigned int kMbarSpins = 1u << 24;
@@ -374,13 +375,8 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned
                "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ void bulk_copy(void* smem, const void* gmem, unsigned int bytes,
-                                          unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-          smem_u32(smem)),
-      "l"(gmem), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -416,25 +412,29 @@ __device__ __forceinline__ void cp_async_wait() {
 // higher ones, i.e. the lowest nsum + tb bits of U. In the canonical layout those
 // bits are the lowest bits of every operand, so the tile reads one contiguous
 // block of A' (rows = A's output indices in the tile, columns = the K summed
-// indices, all of which A and B share) and one of B', copies both into shared
-// memory with asynchronous 16-byte copies (the next tile's copies overlap this
-// tile's products: two buffers) and writes its 2^tb outputs as one contiguous
-// run. The operands' power-of-two scales multiply the finished sums. Tiles are
-// visited with the high output indices of one side innermost (tile_inner), so
-// consecutive tiles reuse the other side's block from L2; thread 0 locates the
-// tile after next while the block works on the current one.
+// indices, all of which A and B share) and one of B', and writes its 2^tb outputs
+// as one contiguous run. The operands' power-of-two scales multiply the finished
+// sums.
+//
+// Tiles are numbered with the high output indices of one side (tile_inner, the
+// indices only the smaller operand has) varying fastest, and each block takes one
+// contiguous range of tile numbers. Consecutive tiles of a block then share the
+// other side's block, which stays in shared memory: a side's block is copied
+// only when its place changes. Each side has two buffers; the copies of the next
+// tile (16-byte cp.async) overlap the products of this one, and one barrier per
+// tile separates them. Warp 0 locates the tile after next meanwhile.
 //
 // Register blocking: with an A-only output bit rA and a B-only bit rB inside the
 // tile, a thread computes the four outputs that differ in those two bits. They
 // share two A rows and two B rows, so one k step is 4 shared-memory loads for
-// 8 complex multiply-adds.
-template <bool TMA>
-__global__ void __launch_bounds__(256) k_gemm_tile(const GemmArgs a, int u, float* data,
+// 8 complex multiply-adds. The tile is the same for every tile number, so each
+// thread's rows and outputs are computed once, before the loop.
+constexpr int kTileQuads = 2;  // quads per thread: tiles of up to 2^11 outputs
+
+__global__ void __launch_bounds__(256, 4) k_gemm_tile(const GemmArgs a, int u, float* data,
                                                    GMeta* meta) {
   extern __shared__ float4 gsm[];
   __shared__ long long s_loc[3][4];  // tile slots: slice, tau, A block, B block
-  __shared__ alignas(8) unsigned long long s_bar[2];  // TMA: one barrier per buffer
-  __shared__ int s_fail;
   const int nsum = a.nsum, t = a.tb, c = u - nsum, h = c - t;
   const int K = 1 << nsum, RS = K + 2;  // row stride (complex): rows stay 16-byte aligned
   const int KC = K >> 1, lkc = nsum - 1;  // 16-byte chunks per row
@@ -443,27 +443,21 @@ __global__ void __launch_bounds__(256) k_gemm_tile(const GemmArgs a, int u, floa
   const unsigned int L = (nsum + t >= 32) ? 0xffffffffu : ((1u << (nsum + t)) - 1u);
   const int la = __popc(OA.umask & L), lb = __popc(OB.umask & L);
   const int rows_a = 1 << (la - nsum), rows_b = 1 << (lb - nsum);
-  const int buf = (rows_a + rows_b) * RS;  // complex per buffer
-  float2* sbase = reinterpret_cast<float2*>(gsm);
-  unsigned int* RT = reinterpret_cast<unsigned int*>(sbase + 2 * buf);
-  unsigned int* RT2 = RT + (1 << t);
+  float2* sbase = reinterpret_cast<float2*>(gsm);  // A buffers 0, 1, then B buffers 0, 1
   const unsigned int ma = (OA.umask & L) >> nsum, mb = (OB.umask & L) >> nsum;
   const int T = 1 << t;
-  const bool blocked = a.reg_a >= 0;
-  const unsigned int rmask = blocked ? ((1u << a.reg_a) | (1u << a.reg_b)) : 0u;
-  for (int o = threadIdx.x; o < T; o += blockDim.x) {
-    RT[o] = pext32g((unsigned)o, ma) | (pext32g((unsigned)o, mb) << 16);
-    if (blocked && o < (T >> 2)) RT2[o] = pdep32g((unsigned)o, (unsigned)(T - 1) & ~rmask);
-  }
   const long long per = 1ll << h;
   const long long ntiles = a.nslices * per;
+  const long long chunk = (ntiles + gridDim.x - 1) / gridDim.x;
+  const long long w0 = (long long)blockIdx.x * chunk;
+  const long long w1 = min(ntiles, w0 + chunk);
   const unsigned int inner = a.tile_inner, hmask = h >= 32 ? 0xffffffffu : ((1u << h) - 1u);
   const int pin = __popc(inner);
   const float2* d2 = reinterpret_cast<const float2*>(data);
   // tile w -> slot; called by all lanes of warp 0 (lane-parallel bit extracts)
   auto locate = [&](long long w, int slot) {
-    const long long i = w / per;
-    const unsigned int tp = (unsigned int)(w - i * per);
+    const long long i = w >> h;
+    const unsigned int tp = (unsigned int)(w & (per - 1));
     const unsigned int tau = inner ? (warp_pdep(tp & ((1u << pin) - 1u), inner) |
                                       warp_pdep(tp >> pin, ~inner & hmask))
                                    : tp;
@@ -479,73 +473,65 @@ __global__ void __launch_bounds__(256) k_gemm_tile(const GemmArgs a, int u, floa
       s_loc[slot][3] = bb + (pb << lb);
     }
   };
-  // the copies of one tile into buffer b: cp.async by every thread, or (TMA) one bulk
-  // copy per row issued by warp 0, completing on buffer b's barrier
-  auto issue = [&](int slot, int b) {
-    float2* sA = sbase + b * buf;
-    float2* sB = sA + rows_a * RS;
-    const long long ta = s_loc[slot][2], tb = s_loc[slot][3];
-    if constexpr (TMA) {
-      if (threadIdx.x < 32) {
-        fence_proxy_async();  // the buffer's last generic reads precede the bulk writes
-        if (threadIdx.x == 0) mbar_expect_tx(&s_bar[b], (unsigned)((rows_a + rows_b) * K * 8));
-        __syncwarp();
-        const unsigned int rb = (unsigned)(K * 8);
-        for (int r = threadIdx.x; r < rows_a + rows_b; r += 32) {
-          if (r < rows_a) bulk_copy(sA + r * RS, d2 + ta + (long long)r * K, rb, &s_bar[b]);
-          else bulk_copy(sB + (r - rows_a) * RS, d2 + tb + (long long)(r - rows_a) * K, rb, &s_bar[b]);
-        }
-      }
-    } else {
-      for (int e = threadIdx.x; e < rows_a * KC; e += blockDim.x)
-        cp_async16(sA + (e >> lkc) * RS + 2 * (e & (KC - 1)), d2 + ta + 2 * e);
-      for (int e = threadIdx.x; e < rows_b * KC; e += blockDim.x)
-        cp_async16(sB + (e >> lkc) * RS + 2 * (e & (KC - 1)), d2 + tb + 2 * e);
-      cp_async_commit();
-    }
+  // one side's block (rows x K complex, contiguous) into buffer b of that side
+  auto copy_rows = [&](long long src, float2* dst, int rows) {
+    for (int e = threadIdx.x; e < rows * KC; e += blockDim.x)
+      cp_async16(dst + (e >> lkc) * RS + 2 * (e & (KC - 1)), d2 + src + 2 * e);
   };
-  const long long G = gridDim.x;
-  long long w = blockIdx.x;
-  if (TMA && threadIdx.x == 0) {
-    mbar_init(&s_bar[0], 1);
-    mbar_init(&s_bar[1], 1);
-    mbar_fence_init();
-    s_fail = 0;
+  float2* const bufA = sbase;
+  float2* const bufB = sbase + 2 * rows_a * RS;
+  // this thread's work in every tile: quads (blocked) or single outputs
+  const bool blocked = a.reg_a >= 0;
+  const unsigned int rmask = blocked ? ((1u << a.reg_a) | (1u << a.reg_b)) : 0u;
+  const int items = blocked ? (T >> 2) : T;
+  int nmine = 0;
+  unsigned int o_of[kTileQuads];
+  int ra0[kTileQuads], ra1[kTileQuads], rb0[kTileQuads], rb1[kTileQuads];
+#pragma unroll
+  for (int r = 0; r < kTileQuads; ++r) {
+    const int q = threadIdx.x + r * blockDim.x;
+    o_of[r] = 0u;
+    ra0[r] = ra1[r] = rb0[r] = rb1[r] = 0;
+    if (blocked && q < items) {
+      const unsigned int o00 = pdep32g((unsigned)q, (unsigned)(T - 1) & ~rmask);
+      o_of[r] = o00;
+      ra0[r] = (int)pext32g(o00, ma) * RS;
+      ra1[r] = (int)pext32g(o00 | (1u << a.reg_a), ma) * RS;
+      rb0[r] = (int)pext32g(o00, mb) * RS;
+      rb1[r] = (int)pext32g(o00 | (1u << a.reg_b), mb) * RS;
+      nmine = r + 1;
+    }
   }
   if (threadIdx.x < 32) {
-    if (w < ntiles) locate(w, 0);
-    if (w + G < ntiles) locate(w + G, 1);
+    if (w0 < w1) locate(w0, 0);
+    if (w0 + 1 < w1) locate(w0 + 1, 1);
   }
   __syncthreads();
-  if (w < ntiles) issue(0, 0);
+  int ba = 0, bb = 0;  // buffers holding this tile's A and B blocks
+  if (w0 < w1) {
+    copy_rows(s_loc[0][2], bufA, rows_a);
+    copy_rows(s_loc[0][3], bufB, rows_b);
+    cp_async_commit();
+  }
   long long cur = -1;
   float sc = 1.f, mx = 0.f;
-  int pending = -1;  // TMA: the tile whose copies were issued and not yet waited for
-  for (int j = 0; w < ntiles; ++j, w += G) {
-    const int slot = j % 3;
-    if constexpr (TMA) {
-      if (w + G < ntiles) {
-        issue((j + 1) % 3, (j + 1) & 1);
-        pending = j + 1;
-      } else {
-        pending = -1;
+  for (int j = 0, slot = 0; w0 + j < w1; ++j, slot = slot == 2 ? 0 : slot + 1) {
+    const long long w = w0 + j;
+    cp_async_wait<0>();
+    __syncthreads();  // this tile's blocks are in; every thread is done with the last tile
+    const int ns = slot == 2 ? 0 : slot + 1;  // the slots of tiles j + 1 and j + 2
+    if (threadIdx.x < 32 && w + 2 < w1) locate(w + 2, ns == 2 ? 0 : ns + 1);
+    int nba = ba, nbb = bb;
+    if (w + 1 < w1) {
+      if (s_loc[ns][2] != s_loc[slot][2]) {
+        nba = ba ^ 1;
+        copy_rows(s_loc[ns][2], bufA + nba * rows_a * RS, rows_a);
       }
-      if (!mbar_wait(&s_bar[j & 1], (unsigned)((j >> 1) & 1), a.err)) s_fail = 1;
-    } else {
-      if (w + G < ntiles) {
-        issue((j + 1) % 3, (j + 1) & 1);
-        cp_async_wait<1>();
-      } else {
-        cp_async_wait<0>();
+      if (s_loc[ns][3] != s_loc[slot][3]) {
+        nbb = bb ^ 1;
+        copy_rows(s_loc[ns][3], bufB + nbb * rows_b * RS, rows_b);
       }
-    }
-    if (threadIdx.x < 32 && w + 2 * G < ntiles) locate(w + 2 * G, (j + 2) % 3);
-    __syncthreads();
-    if (TMA && s_fail) {
-      // a copy never arrived: stop (the host reports the timeout), after a bounded wait
-      // for the next tile's copies still in flight into this block's shared memory
-      if (pending >= 0) mbar_wait(&s_bar[pending & 1], (unsigned)((pending >> 1) & 1), nullptr);
-      break;
+      cp_async_commit();
     }
     const long long i_c = s_loc[slot][0], tau_c = s_loc[slot][1];
     if (i_c != cur) {
@@ -559,19 +545,18 @@ __global__ void __launch_bounds__(256) k_gemm_tile(const GemmArgs a, int u, floa
       sc = sa * sb;
       if (tau_c == 0 && threadIdx.x == 0) write_meta_e(a, meta, i_c);
     }
-    const float2* sA = sbase + (j & 1) * buf;
-    const float2* sB = sA + rows_a * RS;
+    const float2* sA = bufA + ba * rows_a * RS;
+    const float2* sB = bufB + bb * rows_b * RS;
     float2* out = reinterpret_cast<float2*>(data) + a.out_base + i_c * a.out_slice_stride +
                   (tau_c << t);
     if (blocked) {
-      for (int q = threadIdx.x; q < (T >> 2); q += blockDim.x) {
-        const unsigned int o00 = RT2[q];
-        const unsigned int o10 = o00 | (1u << a.reg_a), o01 = o00 | (1u << a.reg_b);
-        const unsigned int o11 = o10 | (1u << a.reg_b);
-        const float4* pa0 = reinterpret_cast<const float4*>(sA + (RT[o00] & 0xffffu) * RS);
-        const float4* pa1 = reinterpret_cast<const float4*>(sA + (RT[o10] & 0xffffu) * RS);
-        const float4* pb0 = reinterpret_cast<const float4*>(sB + (RT[o00] >> 16) * RS);
-        const float4* pb1 = reinterpret_cast<const float4*>(sB + (RT[o01] >> 16) * RS);
+#pragma unroll
+      for (int r = 0; r < kTileQuads; ++r) {
+        if (r >= nmine) break;
+        const float4* pa0 = reinterpret_cast<const float4*>(sA + ra0[r]);
+        const float4* pa1 = reinterpret_cast<const float4*>(sA + ra1[r]);
+        const float4* pb0 = reinterpret_cast<const float4*>(sB + rb0[r]);
+        const float4* pb1 = reinterpret_cast<const float4*>(sB + rb1[r]);
         float c00r = 0.f, c00i = 0.f, c01r = 0.f, c01i = 0.f, c10r = 0.f, c10i = 0.f,
               c11r = 0.f, c11i = 0.f;
 #pragma unroll 2
@@ -587,18 +572,18 @@ __global__ void __launch_bounds__(256) k_gemm_tile(const GemmArgs a, int u, floa
           QT_CMAC2(c11r, c11i, x1, y1)
 #undef QT_CMAC2
         }
+        const unsigned int o00 = o_of[r];
         out[o00] = make_float2(c00r * sc, c00i * sc);
-        out[o01] = make_float2(c01r * sc, c01i * sc);
-        out[o10] = make_float2(c10r * sc, c10i * sc);
-        out[o11] = make_float2(c11r * sc, c11i * sc);
+        out[o00 | (1u << a.reg_b)] = make_float2(c01r * sc, c01i * sc);
+        out[o00 | (1u << a.reg_a)] = make_float2(c10r * sc, c10i * sc);
+        out[o00 | rmask] = make_float2(c11r * sc, c11i * sc);
         mx = fmaxf(mx, fmaxf(fmaxf(absmax_g(c00r, c00i), absmax_g(c01r, c01i)),
                              fmaxf(absmax_g(c10r, c10i), absmax_g(c11r, c11i))) * sc);
       }
     } else {
       for (int o = threadIdx.x; o < T; o += blockDim.x) {
-        const unsigned int rt = RT[o];
-        const float4* pa = reinterpret_cast<const float4*>(sA + (rt & 0xffffu) * RS);
-        const float4* pb = reinterpret_cast<const float4*>(sB + (rt >> 16) * RS);
+        const float4* pa = reinterpret_cast<const float4*>(sA + pext32g((unsigned)o, ma) * RS);
+        const float4* pb = reinterpret_cast<const float4*>(sB + pext32g((unsigned)o, mb) * RS);
         float cr = 0.f, ci = 0.f;
 #pragma unroll 4
         for (int k2 = 0; k2 < KC; ++k2) {
@@ -618,9 +603,277 @@ __global__ void __launch_bounds__(256) k_gemm_tile(const GemmArgs a, int u, floa
         mx = fmaxf(mx, absmax_g(cr, ci));
       }
     }
-    __syncthreads();
+    ba = nba;
+    bb = nbb;
   }
   if (cur >= 0) flush_max(a, meta, cur, mx);
+}
+
+// GEMM_TILE with tensor-copy (TMA) staging and a producer warp: the same tiles,
+// tile numbering, block ranges, register blocking and arithmetic (so the same
+// results, bit for bit) as k_gemm_tile, with the summed-index count a
+// compile-time constant. The workspace is seen by two 2-D tensor maps, rows of K
+// complex (2K floats); a block of R rows is one or more box copies
+// (cp.async.bulk.tensor.2d) completing on the buffer's "full" mbarrier. Each
+// map's box is 2K + 4 floats wide: the 4 floats past the row lie outside the
+// tensor and arrive as zeros, which pads every row in shared memory to K + 2
+// complex (no bank conflicts) without any thread touching the data.
+//
+// Warp specialisation: warp 8 locates tiles and issues the copies, running ahead
+// of the 8 consumer warps, which wait on a buffer's "full" barrier, compute, and
+// arrive on its "empty" barrier; nothing else synchronises the block. The side
+// whose block is shared by a group of tiles (the tiles differing only in the
+// tile_inner indices) has two buffers and its next group's block is requested at
+// the first tile of this group; the other side has a ring of nmove buffers, one
+// per tile. Every wait is bounded: on a timeout the block raises the status word
+// and stops, waiting (bounded) for its copies still in flight; the host reports
+// QT_ETIMEOUT.
+__device__ __forceinline__ void tma_load_2d(void* smem, const CUtensorMap* map, int x, int y,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(smem_u32(smem)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+constexpr int kTmaBoxRows = 256;  // rows per box copy (the hardware's limit)
+constexpr int kTmaConsumers = 256;
+constexpr int kTmaThreads = kTmaConsumers + 32;
+constexpr int kMoveStagesMax = 4;
+
+template <int NSUM>
+__global__ void __launch_bounds__(kTmaThreads, 3) k_gemm_tma(
+    const GemmArgs a, const __grid_constant__ CUtensorMap mapA,
+    const __grid_constant__ CUtensorMap mapB, int u, int nmove, float* data, GMeta* meta) {
+  constexpr int K = 1 << NSUM, RS = K + 2, KC = K / 2;
+  extern __shared__ float4 gsm[];
+  __shared__ long long s_loc[kMoveStagesMax][2];  // per ring buffer: slice, tau of its tile
+  // barriers: 0, 1 the shared side's buffers, 2 + s the ring's
+  __shared__ alignas(8) unsigned long long s_full[2 + kMoveStagesMax];
+  __shared__ alignas(8) unsigned long long s_empty[2 + kMoveStagesMax];
+  __shared__ volatile int s_fail;
+  const int t = a.tb, c = u - NSUM, h = c - t;
+  const GOp& OA = a.op[a.gA];
+  const GOp& OB = a.op[a.gB];
+  const unsigned int L = (NSUM + t >= 32) ? 0xffffffffu : ((1u << (NSUM + t)) - 1u);
+  const int la = __popc(OA.umask & L), lb = __popc(OB.umask & L);
+  const int rows_a = 1 << (la - NSUM), rows_b = 1 << (lb - NSUM);
+  const int stay = a.stay, move = stay ^ 1;  // stay: 0 the groups share A's block, 1 B's
+  const int rows_s = stay ? rows_b : rows_a, rows_m = stay ? rows_a : rows_b;
+  // buffers of 1024-byte multiples from a 1024-byte aligned base
+  const int szS = (rows_s * RS + 127) & ~127, szM = (rows_m * RS + 127) & ~127;  // float2
+  // (offset from gsm itself, so the compiler keeps these shared-memory pointers)
+  float2* const bufS = reinterpret_cast<float2*>(reinterpret_cast<char*>(gsm) +
+                                                 ((1024u - (smem_u32(gsm) & 1023u)) & 1023u));
+  float2* const bufM = bufS + 2 * szS;
+  const long long ntiles = a.nslices << h;
+  const long long chunk = (ntiles + gridDim.x - 1) / gridDim.x;
+  const long long w0 = (long long)blockIdx.x * chunk;
+  const long long w1 = min(ntiles, w0 + chunk);
+  const int pin = __popc(a.tile_inner);
+  const long long gmask = ((long long)1 << pin) - 1;
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2 + nmove; ++b) {
+      mbar_init(&s_full[b], 1);
+      mbar_init(&s_empty[b], kTmaConsumers / 32);
+    }
+    mbar_fence_init();
+    s_fail = 0;
+  }
+  __syncthreads();
+  unsigned int issued = 0u;  // producer lane 0, barrier b: bit b some fill, bit 8 + b parity
+  if (threadIdx.x >= kTmaConsumers) {
+    // ---- producer warp ----
+    const int lane = threadIdx.x & 31;
+    const unsigned int inner = a.tile_inner, hmask = h >= 32 ? 0xffffffffu : ((1u << h) - 1u);
+    const unsigned int hiA = (OA.umask & ~L) >> (NSUM + t), hiB = (OB.umask & ~L) >> (NSUM + t);
+    const CUtensorMap* mapS = stay ? &mapB : &mapA;
+    const CUtensorMap* mapM = stay ? &mapA : &mapB;
+    // tile w: slice, tau and the block offsets (complex) of its sides, to lane 0
+    auto locate = [&](long long w, long long& i, long long& tau, long long& offS, long long& offM) {
+      i = w >> h;
+      const unsigned int tp = (unsigned int)(w & (((long long)1 << h) - 1));
+      const unsigned int tu = inner ? (warp_pdep(tp & ((1u << pin) - 1u), inner) |
+                                       warp_pdep(tp >> pin, ~inner & hmask))
+                                    : tp;
+      tau = tu;
+      const long long pa = (long long)warp_pext(tu, hiA), pb = (long long)warp_pext(tu, hiB);
+      if (lane == 0) {
+        const unsigned long long sid = (unsigned long long)(a.slice_first + i);
+        const long long oA =
+            (a.fold_a ? a.scratch_a + i * a.scratch_stride : op_slice_base(OA, i, sid)) + (pa << la);
+        const long long oB =
+            (a.fold_b ? a.scratch_b + i * a.scratch_stride : op_slice_base(OB, i, sid)) + (pb << lb);
+        offS = stay ? oB : oA;
+        offM = stay ? oA : oB;
+      }
+    };
+    auto load = [&](const CUtensorMap* map, long long off, float2* dst, int rows, int b) {
+      unsigned long long* bar = &s_full[b];
+      const int box = min(rows, kTmaBoxRows);
+      const int row0 = (int)(off >> NSUM);
+      mbar_expect_tx(bar, (unsigned)(rows * RS * 8));
+      for (int r = 0; r < rows; r += box) tma_load_2d(dst + r * RS, map, 0, row0 + r, bar);
+      issued = (issued | (1u << b)) ^ (256u << b);
+    };
+    for (long long w = w0; w < w1; ++w) {
+      if (__shfl_sync(0xffffffffu, s_fail, 0)) break;  // one decision for the whole warp
+      const int jj = (int)(w - w0);
+      const int sgi = (int)((w >> pin) - (w0 >> pin));
+      long long i = 0, tau = 0, offS = 0, offM = 0;
+      locate(w, i, tau, offS, offM);
+      bool ok = true;
+      if (lane == 0) {
+        const int ms = jj % nmove, f = jj / nmove;
+        // the ring buffer is free once the tile nmove earlier is done
+        if (f > 0) ok = mbar_wait(&s_empty[2 + ms], (unsigned)((f - 1) & 1), a.err);
+        if (ok) {
+          s_loc[ms][0] = i;
+          s_loc[ms][1] = tau;
+          fence_proxy_async();  // the buffer's last generic reads precede the tensor copies
+          load(mapM, offM, bufM + ms * szM, rows_m, 2 + ms);
+          if (w == w0) load(mapS, offS, bufS, rows_s, 0);
+        }
+      }
+      // the next group's shared block, as soon as its buffer is free
+      const long long g1 = ((w >> pin) + 1) << pin;
+      if (__shfl_sync(0xffffffffu, ok ? 1 : 0, 0) && (w == w0 || (w & gmask) == 0) && g1 < w1) {
+        locate(g1, i, tau, offS, offM);
+        if (lane == 0) {
+          const int nb = (sgi + 1) & 1, f = (sgi + 1) >> 1;
+          if (f > 0) ok = mbar_wait(&s_empty[nb], (unsigned)((f - 1) & 1), a.err);
+          if (ok) {
+            fence_proxy_async();
+            load(mapS, offS, bufS + nb * szS, rows_s, nb);
+          }
+        }
+      }
+      if (lane == 0 && !ok) s_fail = 1;
+      __syncwarp();
+    }
+  } else {
+    // ---- consumer warps ----
+    const unsigned int ma = (OA.umask & L) >> NSUM, mb = (OB.umask & L) >> NSUM;
+    const int T = 1 << t;
+    const bool blocked = a.reg_a >= 0;
+    const unsigned int rmask = blocked ? ((1u << a.reg_a) | (1u << a.reg_b)) : 0u;
+    const int items = blocked ? (T >> 2) : T;
+    int nmine = 0;
+    unsigned int o_of[kTileQuads];
+    int ra0[kTileQuads], ra1[kTileQuads], rb0[kTileQuads], rb1[kTileQuads];
+#pragma unroll
+    for (int r = 0; r < kTileQuads; ++r) {
+      const int q = threadIdx.x + r * kTmaConsumers;
+      o_of[r] = 0u;
+      ra0[r] = ra1[r] = rb0[r] = rb1[r] = 0;
+      if (blocked && q < items) {
+        const unsigned int o00 = pdep32g((unsigned)q, (unsigned)(T - 1) & ~rmask);
+        o_of[r] = o00;
+        ra0[r] = (int)pext32g(o00, ma) * RS;
+        ra1[r] = (int)pext32g(o00 | (1u << a.reg_a), ma) * RS;
+        rb0[r] = (int)pext32g(o00, mb) * RS;
+        rb1[r] = (int)pext32g(o00 | (1u << a.reg_b), mb) * RS;
+        nmine = r + 1;
+      }
+    }
+    long long cur = -1;
+    float sc = 1.f, mx = 0.f;
+    for (long long w = w0; w < w1; ++w) {
+      const int jj = (int)(w - w0);
+      const int sgi = (int)((w >> pin) - (w0 >> pin));
+      const int ms = jj % nmove, sb = sgi & 1;
+      const bool ok = mbar_wait(&s_full[2 + ms], (unsigned)((jj / nmove) & 1), a.err) &&
+                      mbar_wait(&s_full[sb], (unsigned)((sgi >> 1) & 1), a.err);
+      if (!__all_sync(0xffffffffu, ok)) {  // the warp leaves together
+        s_fail = 1;
+        break;
+      }
+      const long long i_c = s_loc[ms][0], tau_c = s_loc[ms][1];
+      if (i_c != cur) {
+        if (cur >= 0) flush_max(a, meta, cur, mx);
+        mx = 0.f;
+        cur = i_c;
+        const float sa = a.fold_a ? 1.f
+            : pow2_neg_g(scale_exp_g(meta[OA.meta + (OA.meta_per_slice ? i_c : 0)].maxabs));
+        const float sbs = a.fold_b ? 1.f
+            : pow2_neg_g(scale_exp_g(meta[OB.meta + (OB.meta_per_slice ? i_c : 0)].maxabs));
+        sc = sa * sbs;
+        if (tau_c == 0 && threadIdx.x == 0) write_meta_e(a, meta, i_c);
+      }
+      const float2* sA = stay ? bufM + ms * szM : bufS + sb * szS;
+      const float2* sB = stay ? bufS + sb * szS : bufM + ms * szM;
+      float2* out = reinterpret_cast<float2*>(data) + a.out_base + i_c * a.out_slice_stride +
+                    (tau_c << t);
+      if (blocked) {
+#pragma unroll
+        for (int r = 0; r < kTileQuads; ++r) {
+          if (r >= nmine) break;
+          const float4* pa0 = reinterpret_cast<const float4*>(sA + ra0[r]);
+          const float4* pa1 = reinterpret_cast<const float4*>(sA + ra1[r]);
+          const float4* pb0 = reinterpret_cast<const float4*>(sB + rb0[r]);
+          const float4* pb1 = reinterpret_cast<const float4*>(sB + rb1[r]);
+          float c00r = 0.f, c00i = 0.f, c01r = 0.f, c01i = 0.f, c10r = 0.f, c10i = 0.f,
+                c11r = 0.f, c11i = 0.f;
+#pragma unroll
+          for (int k2 = 0; k2 < KC; ++k2) {
+            const float4 x0 = pa0[k2], x1 = pa1[k2], y0 = pb0[k2], y1 = pb1[k2];
+#define QT_CMAC2(CR, CI, P, Q)                                                          \
+  CR = fmaf(P.x, Q.x, CR); CR = fmaf(-P.y, Q.y, CR); CI = fmaf(P.x, Q.y, CI);          \
+  CI = fmaf(P.y, Q.x, CI); CR = fmaf(P.z, Q.z, CR); CR = fmaf(-P.w, Q.w, CR);          \
+  CI = fmaf(P.z, Q.w, CI); CI = fmaf(P.w, Q.z, CI);
+            QT_CMAC2(c00r, c00i, x0, y0)
+            QT_CMAC2(c01r, c01i, x0, y1)
+            QT_CMAC2(c10r, c10i, x1, y0)
+            QT_CMAC2(c11r, c11i, x1, y1)
+#undef QT_CMAC2
+          }
+          const unsigned int o00 = o_of[r];
+          out[o00] = make_float2(c00r * sc, c00i * sc);
+          out[o00 | (1u << a.reg_b)] = make_float2(c01r * sc, c01i * sc);
+          out[o00 | (1u << a.reg_a)] = make_float2(c10r * sc, c10i * sc);
+          out[o00 | rmask] = make_float2(c11r * sc, c11i * sc);
+          mx = fmaxf(mx, fmaxf(fmaxf(absmax_g(c00r, c00i), absmax_g(c01r, c01i)),
+                               fmaxf(absmax_g(c10r, c10i), absmax_g(c11r, c11i))) * sc);
+        }
+      } else {
+        for (int o = threadIdx.x; o < T; o += kTmaConsumers) {
+          const float4* pa = reinterpret_cast<const float4*>(sA + pext32g((unsigned)o, ma) * RS);
+          const float4* pb = reinterpret_cast<const float4*>(sB + pext32g((unsigned)o, mb) * RS);
+          float cr = 0.f, ci = 0.f;
+#pragma unroll
+          for (int k2 = 0; k2 < KC; ++k2) {
+            const float4 x = pa[k2], y = pb[k2];
+            cr = fmaf(x.x, y.x, cr);
+            cr = fmaf(-x.y, y.y, cr);
+            ci = fmaf(x.x, y.y, ci);
+            ci = fmaf(x.y, y.x, ci);
+            cr = fmaf(x.z, y.z, cr);
+            cr = fmaf(-x.w, y.w, cr);
+            ci = fmaf(x.z, y.w, ci);
+            ci = fmaf(x.w, y.z, ci);
+          }
+          cr *= sc;
+          ci *= sc;
+          out[o] = make_float2(cr, ci);
+          mx = fmaxf(mx, absmax_g(cr, ci));
+        }
+      }
+      // release the tile's buffers: one arrival per warp once all its lanes are done
+      __syncwarp();
+      if ((threadIdx.x & 31) == 0) {
+        mbar_arrive(&s_empty[2 + ms]);
+        if (w + 1 == w1 || ((w + 1) & gmask) == 0) mbar_arrive(&s_empty[sb]);
+      }
+    }
+    if (cur >= 0) flush_max(a, meta, cur, mx);
+  }
+  __syncthreads();
+  if (s_fail && threadIdx.x == kTmaConsumers) {
+    // bounded waits for the copies still in flight into this block's shared memory
+    for (int b = 0; b < 2 + nmove; ++b)
+      if ((issued >> b) & 1u) mbar_wait(&s_full[b], ((issued >> (8 + b)) & 1u) ^ 1u, nullptr);
+  }
 }
 
 // Tensor-core GEMM: one warp per (slice, bt, 16-row m tile, 8-column n tile).
@@ -1085,12 +1338,15 @@ constexpr size_t kTriSmemMax = 100 * 1024;
 }  // namespace
 
 constexpr size_t kTileSmemMax = 100 * 1024;
+// Largest tile: 2^11 outputs, i.e. at most kTileQuads quads per thread of 256.
+constexpr int kTileMaxBits = 11;
 
 static size_t tile_smem(const GemmArgs& a, int t) {
+  // two buffers of each side's block, rows padded to K + 2 complex
   const unsigned int L = (a.nsum + t >= 32) ? 0xffffffffu : ((1u << (a.nsum + t)) - 1u);
   const long long ra = 1ll << (__builtin_popcount(a.op[a.gA].umask & L) - a.nsum);
   const long long rb = 1ll << (__builtin_popcount(a.op[a.gB].umask & L) - a.nsum);
-  return (size_t)(2 * (ra + rb) * ((1ll << a.nsum) + 2) * 8 + (4ll << t) + (1ll << t));
+  return (size_t)(2 * (ra + rb) * ((1ll << a.nsum) + 2) * 8);
 }
 
 int gemm_tile_bits(const GemmArgs& a, int u) {
@@ -1098,8 +1354,8 @@ int gemm_tile_bits(const GemmArgs& a, int u) {
   if (__builtin_popcount(a.op[a.gA].umask) > 30 || __builtin_popcount(a.op[a.gB].umask) > 30)
     return 0;
   const int c = u - a.nsum;
-  for (int t = std::min(c, 10); t >= 5; --t)
-    if (tile_smem(a, t) <= kTileSmemMax) return t;
+  for (int t = std::min(c, kTileMaxBits); t >= 5; --t)
+    if (tile_smem(a, t) + 3072 <= kTileSmemMax) return t;
   return 0;
 }
 
@@ -1118,12 +1374,16 @@ unsigned int gemm_tile_inner(const GemmArgs& a, int u) {
   // consecutive tiles share the larger side's block
   const int t = a.tb, hb = u - a.nsum - t;
   if (t <= 0 || hb <= 0) return 0u;
-  const bool a_larger = __builtin_popcount(a.op[a.gA].umask) >= __builtin_popcount(a.op[a.gB].umask);
+  const bool a_larger = gemm_tile_stay(a) == 0;
   const unsigned int only = a_larger ? a.mN : a.mM;  // indices of the smaller side only
   unsigned int inner = 0;
   for (int b = 0; b < hb; ++b)
     if ((only >> (a.nsum + t + b)) & 1u) inner |= 1u << b;
   return inner;
+}
+
+int gemm_tile_stay(const GemmArgs& a) {
+  return __builtin_popcount(a.op[a.gA].umask) >= __builtin_popcount(a.op[a.gB].umask) ? 0 : 1;
 }
 
 int tri_tile_bits(const GemmArgs& a, int u) {
@@ -1168,7 +1428,87 @@ int tri_launch(const GemmArgs& a, float* data, GMeta* meta, cudaStream_t s, int 
   return n + 1;
 }
 
-int gemm_launch(const GemmArgs& a, int mode, float* data, GMeta* meta, cudaStream_t s, int sms) {
+// cuTensorMapEncodeTiled, from the driver through the runtime (no link-time libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// The workspace as rows of K complex (2K floats); boxes of box_rows rows, 2K + 4
+// floats wide (the last 4 lie outside every row and arrive as zeros: padding).
+static bool row_map(CUtensorMap& m, float* data, long long ws_elems, int nsum, int box_rows) {
+  EncodeTiledFn fn = encode_tiled();
+  const long long K = 1ll << nsum;
+  const long long rows = ws_elems / K;
+  if (!fn || rows < 1 || rows > 0x7fffffffll || 2 * K + 4 > 256) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)(2 * K), (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(K * 8)};
+  const cuuint32_t box[2] = {(cuuint32_t)(2 * K + 4), (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, data, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Every block a tile can read starts on a whole row of K complex.
+static bool rows_aligned(const GemmArgs& a) {
+  const long long K = 1ll << a.nsum;
+  for (int side = 0; side < 2; ++side) {
+    const GOp& o = a.op[side ? a.gB : a.gA];
+    if (side ? a.fold_b : a.fold_a) {
+      if ((side ? a.scratch_b : a.scratch_a) % K || a.scratch_stride % K) return false;
+    } else {
+      if (o.base % K || o.slice_stride % K) return false;
+      if (o.smask && o.sshift < a.nsum) return false;
+    }
+  }
+  return true;
+}
+
+// shared side: two buffers; the other side: a ring of nmove buffers
+static size_t tma_smem(const GemmArgs& a, int nmove) {
+  const unsigned int L = (a.nsum + a.tb >= 32) ? 0xffffffffu : ((1u << (a.nsum + a.tb)) - 1u);
+  const long long RS = (1ll << a.nsum) + 2;
+  const long long ra = 1ll << (__builtin_popcount(a.op[a.gA].umask & L) - a.nsum);
+  const long long rb = 1ll << (__builtin_popcount(a.op[a.gB].umask & L) - a.nsum);
+  const long long szA = (ra * RS + 127) & ~127ll, szB = (rb * RS + 127) & ~127ll;
+  const long long szS = a.stay ? szB : szA, szM = a.stay ? szA : szB;
+  return (size_t)((2 * szS + nmove * szM) * 8 + 1024);
+}
+
+typedef void (*TmaFn)(const GemmArgs, const CUtensorMap, const CUtensorMap, int, int, float*,
+                      GMeta*);
+
+static TmaFn tma_fn(int nsum) {
+  switch (nsum) {
+    case 1: return k_gemm_tma<1>;
+    case 2: return k_gemm_tma<2>;
+    case 3: return k_gemm_tma<3>;
+    case 4: return k_gemm_tma<4>;
+    case 5: return k_gemm_tma<5>;
+    case 6: return k_gemm_tma<6>;
+    default: return nullptr;
+  }
+}
+
+int gemm_launch(const GemmArgs& a, int mode, float* data, GMeta* meta, cudaStream_t s, int sms,
+                bool* used_tma) {
+  if (used_tma) *used_tma = false;
   if (mode == GEMM_TILE) {
     int n = 0;
     for (int side = 0; side < 2; ++side) {
@@ -1180,21 +1520,49 @@ int gemm_launch(const GemmArgs& a, int mode, float* data, GMeta* meta, cudaStrea
     }
     int u = 0;
     for (unsigned int m = a.mK | a.mSA | a.mSB | a.mM | a.mN | a.mBt; m; m >>= 1) ++u;
+    const long long ntiles = a.nslices << (u - a.nsum - a.tb);
+    // one block per resident slot (each block takes one range of tiles)
+    // one block per resident slot (each block takes one range of tiles)
+    auto grid_for = [&](const void* f, int threads, size_t smem) {
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, smem) != cudaSuccess)
+        per_sm = 1;
+      per_sm = std::max(1, per_sm);
+      return (unsigned)std::max<long long>(1, std::min<long long>(ntiles, (long long)sms * per_sm));
+    };
+    // tensor-copy staging when the rows line up and the maps encode; the ring as
+    // deep as it can be without fewer resident blocks than a ring of 2
+    TmaFn fn = tma_fn(a.nsum);
+    if (a.use_tma && a.err && fn && tma_smem(a, 2) <= kTileSmemMax && rows_aligned(a)) {
+      const unsigned int L = (a.nsum + a.tb >= 32) ? 0xffffffffu : ((1u << (a.nsum + a.tb)) - 1u);
+      const int ra = 1 << (__builtin_popcount(a.op[a.gA].umask & L) - a.nsum);
+      const int rb = 1 << (__builtin_popcount(a.op[a.gB].umask & L) - a.nsum);
+      CUtensorMap mA, mB;
+      if (row_map(mA, data, a.ws_elems, a.nsum, std::min(ra, 256)) &&
+          row_map(mB, data, a.ws_elems, a.nsum, std::min(rb, 256))) {
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmemMax);
+        const size_t per2 = (220 * 1024) / (tma_smem(a, 2) + 1024);
+        int nmove = 2;
+        for (int m = kMoveStagesMax; m > 2; --m)
+          if (tma_smem(a, m) <= kTileSmemMax && (220 * 1024) / (tma_smem(a, m) + 1024) >= per2) {
+            nmove = m;
+            break;
+          }
+        const size_t tsm = tma_smem(a, nmove);
+        fn<<<grid_for((const void*)fn, kTmaThreads, tsm), kTmaThreads, tsm, s>>>(a, mA, mB, u, nmove,
+                                                                                  data, meta);
+        if (used_tma) *used_tma = true;
+        return n + 1;
+      }
+    }
     static bool attr = false;
     if (!attr) {
-      cudaFuncSetAttribute(k_gemm_tile<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kTileSmemMax);
-      cudaFuncSetAttribute(k_gemm_tile<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(k_gemm_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kTileSmemMax);
       attr = true;
     }
     const size_t smem = tile_smem(a, a.tb);
-    const long long ntiles = a.nslices << (u - a.nsum - a.tb);
-    const int per_sm = std::max<int>(1, std::min<int>(8, (int)((220 * 1024) / (smem + 1024))));
-    const unsigned grid =
-        (unsigned)std::max<long long>(1, std::min<long long>(ntiles, (long long)sms * per_sm));
-    if (a.use_tma && a.err) k_gemm_tile<true><<<grid, 256, smem, s>>>(a, u, data, meta);
-    else k_gemm_tile<false><<<grid, 256, smem, s>>>(a, u, data, meta);
+    k_gemm_tile<<<grid_for((const void*)k_gemm_tile, 256, smem), 256, smem, s>>>(a, u, data, meta);
     return n + 1;
   }
   const int kb = __builtin_popcount(a.mK), bb = __builtin_popcount(a.mBt);

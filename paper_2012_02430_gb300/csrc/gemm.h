@@ -38,7 +38,9 @@ struct GemmArgs {
   int reg_a, reg_b;         // register-blocking bits of the tile (-1: none)
   int tA, tB, tC;           // triangle form: the large operands
   unsigned int tK, tX, tY;  // triangle form: summed bits of each class
-  int use_tma;              // GEMM_TILE: stage operand rows with bulk copies (TMA)
+  int use_tma;              // GEMM_TILE: stage the blocks with tensor copies (TMA)
+  int stay;                 // GEMM_TILE: 0 the tiles of a group share A's block, 1 B's
+  long long ws_elems;       // workspace size (complex): the extent of the tensor maps
   int* err;                 // device status word: set to 1 when a bounded wait gives up
   GOp op[GEMM_MAXOP];
 };
@@ -46,8 +48,11 @@ struct GemmArgs {
 // Output indices per tile of the GEMM_TILE kernel for a launch (0: the launch
 // does not take that form: a one-sided summed index, or too little shared memory).
 int gemm_tile_bits(const GemmArgs& a, int u);
-// Tile visiting order of the GEMM_TILE kernel for a launch with tile bits a.tb.
+// Tile visiting order of the GEMM_TILE kernel for a launch with tile bits a.tb:
+// the high output indices visited innermost (those only the smaller operand has),
+// and the side whose block the tiles differing only in them share (0 A, 1 B).
 unsigned int gemm_tile_inner(const GemmArgs& a, int u);
+int gemm_tile_stay(const GemmArgs& a);
 // Register-blocking bits of the GEMM_TILE kernel: an A-only and a B-only output
 // bit inside the tile, or -1, -1.
 void gemm_tile_regs(const GemmArgs& a, int& reg_a, int& reg_b);
@@ -57,8 +62,10 @@ void gemm_tile_regs(const GemmArgs& a, int& reg_a, int& reg_b);
 int tri_tile_bits(const GemmArgs& a, int u);
 int tri_launch(const GemmArgs& a, float* data, GMeta* meta, cudaStream_t s, int sms);
 
-// GEMM_TILE: fold A', fold B' (when the side has small operands), tiled GEMM;
+// GEMM_TILE: fold A', fold B' (when the side has small operands), tiled GEMM
+// (tensor-copy staging when a.use_tma and the blocks allow it: *used_tma);
 // other modes: pack A', pack B', GEMM. Returns the number of kernels launched.
-int gemm_launch(const GemmArgs& a, int mode, float* data, GMeta* meta, cudaStream_t s, int sms);
+int gemm_launch(const GemmArgs& a, int mode, float* data, GMeta* meta, cudaStream_t s, int sms,
+                bool* used_tma = nullptr);
 
 }  // namespace qt

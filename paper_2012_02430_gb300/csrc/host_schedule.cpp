@@ -535,6 +535,43 @@ std::string schedule_json(const Schedule& S, const SlicePlan& plan) {
     o << "[" << g.region << "," << g.first << "," << g.nsteps << "," << g.ops.size() << ","
       << g.u << "," << g.nsum << "," << g.flops << "," << g.bytes << "]";
   }
+  // GEMM-form launches: first step, then the masks over the group's U bits (summed
+  // in both, summed in A only, in B only, output in A only, in B only, in both) and
+  // the index masks of the two large operands A and B
+  o << "],\"gemm_masks\":[";
+  bool first = true;
+  for (const SGroup& g : S.groups) {
+    if (!g.gemm) continue;
+    uint32_t um[2] = {0, 0};
+    for (int s = 0; s < 2; ++s) {
+      const STensor& t = S.tensors[g.ops[s ? g.gB : g.gA]];
+      for (int b = 0; b < g.u; ++b)
+        if (std::find(t.labels.begin(), t.labels.end(), g.ulabels[b]) != t.labels.end())
+          um[s] |= 1u << b;
+    }
+    o << (first ? "" : ",") << "[" << g.first << "," << g.u << "," << g.mK << "," << g.mSA << ","
+      << g.mSB << "," << g.mM << "," << g.mN << "," << g.mBt << "," << um[0] << "," << um[1]
+      << "]";
+    first = false;
+  }
+  // triangle-form launches: first step, U, the summed bits of each class (K, X, Y)
+  // and the index masks of the three large operands A, B, C
+  o << "],\"tri_masks\":[";
+  first = true;
+  for (const SGroup& g : S.groups) {
+    if (!g.tri) continue;
+    uint32_t um[3] = {0, 0, 0};
+    const int which[3] = {g.tA, g.tB, g.tC};
+    for (int s = 0; s < 3; ++s) {
+      const STensor& t = S.tensors[g.ops[which[s]]];
+      for (int b = 0; b < g.u; ++b)
+        if (std::find(t.labels.begin(), t.labels.end(), g.ulabels[b]) != t.labels.end())
+          um[s] |= 1u << b;
+    }
+    o << (first ? "" : ",") << "[" << g.first << "," << g.u << "," << g.tK << "," << g.tX << ","
+      << g.tY << "," << um[0] << "," << um[1] << "," << um[2] << "]";
+    first = false;
+  }
   o << "]}";
   return o.str();
 }

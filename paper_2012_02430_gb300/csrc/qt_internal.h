@@ -224,7 +224,8 @@ struct qt_net {
   bool force_gemm = false;       // GEMM-form launches by default also in FP32 mode
   bool segments = true;          // runs of small launches as one segment launch
   bool force_tri = false;        // triangle-form launches by default where they apply
-  bool tma = false;              // tiled GEMM stages operand rows with bulk copies (TMA)
+  bool tma = true;               // tiled GEMM stages its blocks with tensor copies (TMA)
+  int64_t tma_launches = 0;      // tiled GEMM launches that took the tensor-copy staging
   void* engine = nullptr;        // engine.cu: launch descriptors and graph cache
   ~qt_net();
 };

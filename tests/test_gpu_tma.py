@@ -1,5 +1,6 @@
-"""The tiled GEMM's bulk-copy (TMA) staging against the FP64 oracle: the same
-amplitudes as the default cp.async staging, no bounded wait giving up."""
+"""The tiled GEMM's tensor-copy (TMA) staging against the FP64 oracle: the same
+amplitudes, bit for bit, as the cp.async staging, no bounded wait giving up, and
+the tensor-copy kernel really launched."""
 
 import pytest
 
@@ -22,6 +23,9 @@ def test_tma_staging_matches_oracle(qt, case):
         net.slice(w + off, 6, 1)
         net.prepare(0, batch=4)
         amps[tma] = net.contract(0)  # raises QT_ETIMEOUT if a bounded wait gave up
+        st = net.stats()
+        assert st["gemm_groups"] > 0
+        assert (st["tma_gemm_launches"] > 0) == bool(tma), st["tma_gemm_launches"]
     plan = oracle_plan(adj, 0, w + off, 6, 1)
     ref, _ = oracle_amplitude(tensors, norm, plan)
     for tma in (0, 1):
