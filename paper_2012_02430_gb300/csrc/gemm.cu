@@ -375,6 +375,16 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned
                "r"(bytes)
                : "memory");
 }
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned int parity) {
+  unsigned int done = 0;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
 __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -619,12 +629,12 @@ __global__ void __launch_bounds__(256, 4) k_gemm_tile(const GemmArgs a, int u, f
 // tensor and arrive as zeros, which pads every row in shared memory to K + 2
 // complex (no bank conflicts) without any thread touching the data.
 //
-// Warp specialisation: warp 8 locates tiles and issues the copies, running ahead
-// of the 8 consumer warps, which wait on a buffer's "full" barrier, compute, and
+// Warp specialisation: warp 8 locates tiles (32 at a time, one per lane) and issues
+// the copies, running ahead of the 8 consumer warps, which wait on a buffer's "full" barrier, compute, and
 // arrive on its "empty" barrier; nothing else synchronises the block. The side
 // whose block is shared by a group of tiles (the tiles differing only in the
 // tile_inner indices) has two buffers and its next group's block is requested at
-// the first tile of this group; the other side has a ring of nmove buffers, one
+// the first tile of this group and issued as soon as its buffer is free; the other side has a ring of nmove buffers, one
 // per tile. Every wait is bounded: on a timeout the block raises the status word
 // and stops, waiting (bounded) for its copies still in flight; the host reports
 // QT_ETIMEOUT.
@@ -642,13 +652,19 @@ constexpr int kTmaConsumers = 256;
 constexpr int kTmaThreads = kTmaConsumers + 32;
 constexpr int kMoveStagesMax = 4;
 
+struct TmaSlot {
+  long long i, out;  // slice, output offset (complex) of the tile
+  float sc;          // the product of the operands' scales in that slice
+  int first;         // the slice's first tile (tau = 0)
+};
+
 template <int NSUM>
 __global__ void __launch_bounds__(kTmaThreads, 3) k_gemm_tma(
     const GemmArgs a, const __grid_constant__ CUtensorMap mapA,
     const __grid_constant__ CUtensorMap mapB, int u, int nmove, float* data, GMeta* meta) {
   constexpr int K = 1 << NSUM, RS = K + 2, KC = K / 2;
   extern __shared__ float4 gsm[];
-  __shared__ long long s_loc[kMoveStagesMax][2];  // per ring buffer: slice, tau of its tile
+  __shared__ TmaSlot s_slot[kMoveStagesMax];  // per ring buffer: its tile's slice, output, scale
   // barriers: 0, 1 the shared side's buffers, 2 + s the ring's
   __shared__ alignas(8) unsigned long long s_full[2 + kMoveStagesMax];
   __shared__ alignas(8) unsigned long long s_empty[2 + kMoveStagesMax];
@@ -685,29 +701,27 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gemm_tma(
   unsigned int issued = 0u;  // producer lane 0, barrier b: bit b some fill, bit 8 + b parity
   if (threadIdx.x >= kTmaConsumers) {
     // ---- producer warp ----
+    // Windows of 32 tiles: lane l locates tile wb + l (scalar bit extracts, all lanes at
+    // once), then lane 0 walks the window, reading each tile's numbers from its lane,
+    // waiting for the buffers and issuing the copies.
     const int lane = threadIdx.x & 31;
     const unsigned int inner = a.tile_inner, hmask = h >= 32 ? 0xffffffffu : ((1u << h) - 1u);
+    const unsigned int outer = ~inner & hmask, pmask = (1u << pin) - 1u;
     const unsigned int hiA = (OA.umask & ~L) >> (NSUM + t), hiB = (OB.umask & ~L) >> (NSUM + t);
     const CUtensorMap* mapS = stay ? &mapB : &mapA;
     const CUtensorMap* mapM = stay ? &mapA : &mapB;
-    // tile w: slice, tau and the block offsets (complex) of its sides, to lane 0
-    auto locate = [&](long long w, long long& i, long long& tau, long long& offS, long long& offM) {
+    // tile w: slice, tau and the block offsets (complex) of the shared and other sides
+    auto where = [&](long long w, long long& i, unsigned int& tau, long long& offS, long long& offM) {
       i = w >> h;
       const unsigned int tp = (unsigned int)(w & (((long long)1 << h) - 1));
-      const unsigned int tu = inner ? (warp_pdep(tp & ((1u << pin) - 1u), inner) |
-                                       warp_pdep(tp >> pin, ~inner & hmask))
-                                    : tp;
-      tau = tu;
-      const long long pa = (long long)warp_pext(tu, hiA), pb = (long long)warp_pext(tu, hiB);
-      if (lane == 0) {
-        const unsigned long long sid = (unsigned long long)(a.slice_first + i);
-        const long long oA =
-            (a.fold_a ? a.scratch_a + i * a.scratch_stride : op_slice_base(OA, i, sid)) + (pa << la);
-        const long long oB =
-            (a.fold_b ? a.scratch_b + i * a.scratch_stride : op_slice_base(OB, i, sid)) + (pb << lb);
-        offS = stay ? oB : oA;
-        offM = stay ? oA : oB;
-      }
+      tau = inner ? (pdep32g(tp & pmask, inner) | pdep32g(tp >> pin, outer)) : tp;
+      const unsigned long long sid = (unsigned long long)(a.slice_first + i);
+      const long long oA = (a.fold_a ? a.scratch_a + i * a.scratch_stride : op_slice_base(OA, i, sid)) +
+                           ((long long)pext32g(tau, hiA) << la);
+      const long long oB = (a.fold_b ? a.scratch_b + i * a.scratch_stride : op_slice_base(OB, i, sid)) +
+                           ((long long)pext32g(tau, hiB) << lb);
+      offS = stay ? oB : oA;
+      offM = stay ? oA : oB;
     };
     auto load = [&](const CUtensorMap* map, long long off, float2* dst, int rows, int b) {
       unsigned long long* bar = &s_full[b];
@@ -717,40 +731,89 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gemm_tma(
       for (int r = 0; r < rows; r += box) tma_load_2d(dst + r * RS, map, 0, row0 + r, bar);
       issued = (issued | (1u << b)) ^ (256u << b);
     };
-    for (long long w = w0; w < w1; ++w) {
-      if (__shfl_sync(0xffffffffu, s_fail, 0)) break;  // one decision for the whole warp
-      const int jj = (int)(w - w0);
-      const int sgi = (int)((w >> pin) - (w0 >> pin));
-      long long i = 0, tau = 0, offS = 0, offM = 0;
-      locate(w, i, tau, offS, offM);
-      bool ok = true;
-      if (lane == 0) {
-        const int ms = jj % nmove, f = jj / nmove;
-        // the ring buffer is free once the tile nmove earlier is done
-        if (f > 0) ok = mbar_wait(&s_empty[2 + ms], (unsigned)((f - 1) & 1), a.err);
-        if (ok) {
-          s_loc[ms][0] = i;
-          s_loc[ms][1] = tau;
-          fence_proxy_async();  // the buffer's last generic reads precede the tensor copies
-          load(mapM, offM, bufM + ms * szM, rows_m, 2 + ms);
-          if (w == w0) load(mapS, offS, bufS, rows_s, 0);
+    int ms = 0, f = 0;  // ring buffer of the tile and the fill count it reaches
+    int pend_b = -1;    // lane 0: a shared-side buffer whose block waits for it to be free
+    unsigned int pend_par = 0u;
+    long long pend_off = 0;
+    long long pi = -1;  // lane 0: the slice whose scale is in sc
+    float sc = 1.f;
+    bool ok = true;
+    for (long long wb = w0; wb < w1 && ok; wb += 32) {
+      const long long wl = wb + lane;
+      long long li = 0, loffS = 0, loffM = 0, lnext = 0;
+      unsigned int ltau = 0;
+      if (wl < w1) {
+        where(wl, li, ltau, loffS, loffM);
+        // the next group's shared block, requested when tile wl starts a group
+        const long long g1 = ((wl >> pin) + 1) << pin;
+        if (g1 < w1 && (wl == w0 || (wl & gmask) == 0)) {
+          long long i1, m1;
+          unsigned int t1;
+          where(g1, i1, t1, lnext, m1);
         }
       }
-      // the next group's shared block, as soon as its buffer is free
-      const long long g1 = ((w >> pin) + 1) << pin;
-      if (__shfl_sync(0xffffffffu, ok ? 1 : 0, 0) && (w == w0 || (w & gmask) == 0) && g1 < w1) {
-        locate(g1, i, tau, offS, offM);
+      const int nwin = (int)min(32ll, w1 - wb);
+      for (int j = 0; j < nwin; ++j) {
+        const long long w = wb + j;
+        const long long i = __shfl_sync(0xffffffffu, li, j);
+        const unsigned int tau = __shfl_sync(0xffffffffu, ltau, j);
+        const long long offS = __shfl_sync(0xffffffffu, loffS, j);
+        const long long offM = __shfl_sync(0xffffffffu, loffM, j);
+        const long long onext = __shfl_sync(0xffffffffu, lnext, j);
         if (lane == 0) {
-          const int nb = (sgi + 1) & 1, f = (sgi + 1) >> 1;
-          if (f > 0) ok = mbar_wait(&s_empty[nb], (unsigned)((f - 1) & 1), a.err);
-          if (ok) {
-            fence_proxy_async();
-            load(mapS, offS, bufS + nb * szS, rows_s, nb);
+          if (s_fail) ok = false;
+          if (ok && i != pi) {
+            pi = i;
+            sc = (a.fold_a ? 1.f
+                           : pow2_neg_g(scale_exp_g(meta[OA.meta + (OA.meta_per_slice ? i : 0)].maxabs))) *
+                 (a.fold_b ? 1.f
+                           : pow2_neg_g(scale_exp_g(meta[OB.meta + (OB.meta_per_slice ? i : 0)].maxabs)));
           }
+          // the ring buffer is free once the tile nmove earlier is done
+          if (ok && f > 0) ok = mbar_wait(&s_empty[2 + ms], (unsigned)((f - 1) & 1), a.err);
+          if (ok) {
+            s_slot[ms].i = i;
+            s_slot[ms].out = a.out_base + i * a.out_slice_stride + ((long long)tau << t);
+            s_slot[ms].sc = sc;
+            s_slot[ms].first = tau == 0u;
+            load(mapM, offM, bufM + ms * szM, rows_m, 2 + ms);
+            if (w == w0) load(mapS, offS, bufS, rows_s, 0);
+          }
+          // the next group's shared block: requested at this group's first tile, issued
+          // as soon as its buffer is free (polled between ring tiles), at the latest
+          // at the next group's first tile
+          if (ok && (w == w0 || (w & gmask) == 0)) {
+            if (pend_b >= 0) {
+              ok = mbar_wait(&s_empty[pend_b], pend_par, a.err);
+              if (ok) load(mapS, pend_off, bufS + pend_b * szS, rows_s, pend_b);
+              pend_b = -1;
+            }
+            const long long g1 = ((w >> pin) + 1) << pin;
+            if (ok && g1 < w1) {
+              const int sgi = (int)((w >> pin) - (w0 >> pin));
+              const int nb = (sgi + 1) & 1, fs = (sgi + 1) >> 1;
+              if (fs == 0) {
+                load(mapS, onext, bufS + nb * szS, rows_s, nb);
+              } else {
+                pend_b = nb;
+                pend_par = (unsigned)((fs - 1) & 1);
+                pend_off = onext;
+              }
+            }
+          }
+          if (ok && pend_b >= 0 && mbar_test(&s_empty[pend_b], pend_par)) {
+            load(mapS, pend_off, bufS + pend_b * szS, rows_s, pend_b);
+            pend_b = -1;
+          }
+          if (!ok) s_fail = 1;
         }
+        if (++ms == nmove) {
+          ms = 0;
+          ++f;
+        }
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        if (!ok) break;
       }
-      if (lane == 0 && !ok) s_fail = 1;
-      __syncwarp();
     }
   } else {
     // ---- consumer warps ----
@@ -778,33 +841,32 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gemm_tma(
       }
     }
     long long cur = -1;
-    float sc = 1.f, mx = 0.f;
+    float mx = 0.f;
+    int ms = 0, sb = 0;            // ring buffer of the tile, shared-side buffer of its group
+    unsigned int ph = 0u, phs = 0u;  // the fill parities they wait for
+    long long gnext = ((w0 >> pin) + 1) << pin;  // first tile of the next group
     for (long long w = w0; w < w1; ++w) {
-      const int jj = (int)(w - w0);
-      const int sgi = (int)((w >> pin) - (w0 >> pin));
-      const int ms = jj % nmove, sb = sgi & 1;
-      const bool ok = mbar_wait(&s_full[2 + ms], (unsigned)((jj / nmove) & 1), a.err) &&
-                      mbar_wait(&s_full[sb], (unsigned)((sgi >> 1) & 1), a.err);
+      if (w == gnext) {
+        gnext += 1ll << pin;
+        sb ^= 1;
+        phs ^= (unsigned)(sb == 0);
+      }
+      const bool ok = mbar_wait(&s_full[2 + ms], ph, a.err) && mbar_wait(&s_full[sb], phs, a.err);
       if (!__all_sync(0xffffffffu, ok)) {  // the warp leaves together
         s_fail = 1;
         break;
       }
-      const long long i_c = s_loc[ms][0], tau_c = s_loc[ms][1];
+      const long long i_c = s_slot[ms].i;
+      const float sc = s_slot[ms].sc;
       if (i_c != cur) {
         if (cur >= 0) flush_max(a, meta, cur, mx);
         mx = 0.f;
         cur = i_c;
-        const float sa = a.fold_a ? 1.f
-            : pow2_neg_g(scale_exp_g(meta[OA.meta + (OA.meta_per_slice ? i_c : 0)].maxabs));
-        const float sbs = a.fold_b ? 1.f
-            : pow2_neg_g(scale_exp_g(meta[OB.meta + (OB.meta_per_slice ? i_c : 0)].maxabs));
-        sc = sa * sbs;
-        if (tau_c == 0 && threadIdx.x == 0) write_meta_e(a, meta, i_c);
+        if (s_slot[ms].first && threadIdx.x == 0) write_meta_e(a, meta, i_c);
       }
       const float2* sA = stay ? bufM + ms * szM : bufS + sb * szS;
       const float2* sB = stay ? bufS + sb * szS : bufM + ms * szM;
-      float2* out = reinterpret_cast<float2*>(data) + a.out_base + i_c * a.out_slice_stride +
-                    (tau_c << t);
+      float2* out = reinterpret_cast<float2*>(data) + s_slot[ms].out;
       if (blocked) {
 #pragma unroll
         for (int r = 0; r < kTileQuads; ++r) {
@@ -863,7 +925,11 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gemm_tma(
       __syncwarp();
       if ((threadIdx.x & 31) == 0) {
         mbar_arrive(&s_empty[2 + ms]);
-        if (w + 1 == w1 || ((w + 1) & gmask) == 0) mbar_arrive(&s_empty[sb]);
+        if (w + 1 == w1 || w + 1 == gnext) mbar_arrive(&s_empty[sb]);
+      }
+      if (++ms == nmove) {
+        ms = 0;
+        ph ^= 1u;
       }
     }
     if (cur >= 0) flush_max(a, meta, cur, mx);
