@@ -1221,6 +1221,7 @@ static void fill_tri(const Schedule& S, const SGroup& g, long long nslices, Gemm
   a.tX = g.tX;
   a.tY = g.tY;
   a.tb = tri_tile_bits(a, g.u);
+  a.ws_elems = (long long)(S.total_bytes / 8);
   // consecutive tiles share A's or B's block: high output bits missing from A or B innermost
   const int hb = g.u - g.nsum - a.tb;
   const unsigned int AB = a.op[g.tA].umask & a.op[g.tB].umask;
@@ -1623,8 +1624,12 @@ static void launch_desc(qt_net* net, const LaunchDesc& d0, long long nslices, lo
     GemmArgs ga = d0.ga;
     ga.nslices = nslices;
     ga.slice_first = slice_first;
+    ga.err = reinterpret_cast<int*>(base + S.off_err);
+    ga.use_tma = net->tma ? 1 : 0;
+    bool tma = false;
     net->launches += tri_launch(ga, reinterpret_cast<float*>(base), reinterpret_cast<GMeta*>(meta),
-                                s, num_sms());
+                                s, num_sms(), &tma);
+    if (tma) net->tma_launches++;
     if (net->prof) prof_end(net, s, pr);
     return;
   }

@@ -1399,6 +1399,394 @@ TriFn tri_fn(int nx, int ny) {
   }
 }
 
+// Triangle form with tensor-copy (TMA) staging and a producer warp: the same tiles
+// and the same sum as k_tri_tile, with the operand blocks in their natural layout
+// (row = the operand's output indices in the tile, column = its summed indices),
+// each row padded by 2 complex (box copies 4 floats wider than the row, the excess
+// lying outside the tensor and arriving as zeros). A row stride of 4 words modulo
+// 32 makes 16-byte loads by lanes on consecutive rows conflict-free, so the
+// consumers read the summed values in pairs: the two values of the operand's
+// lowest summed index (a K index, or for A an X index, for B a Y index). Per k the
+// x sum is taken first: u_y = sum_x A[k,x] C'[x,y], then sum_y u_y B[k,y]
+// (NX NY + NY complex multiply-adds per k).
+//
+// Warp 8 locates 32 tiles at a time (one per lane), waits for a ring stage to be
+// free, writes the tile's slice, output offset, scale and K weights into the
+// stage's slot and issues the copies of A's, B's and C's blocks, completing on
+// the stage's "full" barrier; the 8 consumer warps compute one output per thread
+// and arrive on the stage's "empty" barrier. Waits are bounded as in k_gemm_tma.
+constexpr int kTriStages = 2;
+constexpr int kTriMaxK = 64;
+
+struct TriSlot {
+  long long i, out;
+  float sc;
+  int first;
+  float2 w[kTriMaxK];  // the weights over K of the tile's slice
+};
+
+// One output of the triangle form from its A, B and C' rows in shared memory
+// (natural layout): A's and B's summed values are read two at a time, over k when
+// PAIRA_K (PAIRB_K), else over x (y).
+template <int NX, int NY, bool PAIRA_K, bool PAIRB_K>
+__device__ __forceinline__ float2 tri_one(const float2* pa, const float2* pb, const float2* pc,
+                                          const int* ka, const int* kb, const int (&xa)[NX],
+                                          const int (&yb)[NY], const int (&cc)[NX * NY], int nK,
+                                          bool has_w, const float2* wk) {
+  float cvr[NX * NY], cvi[NX * NY];
+#pragma unroll
+  for (int xy = 0; xy < NX * NY; ++xy) {
+    const float2 v = pc[cc[xy]];
+    cvr[xy] = v.x;
+    cvi[xy] = v.y;
+  }
+  float accr = 0.f, acci = 0.f;
+#pragma unroll 2
+  for (int k0 = 0; k0 < nK; k0 += 2) {
+    float ar[2][NX], ai[2][NX], br[2][NY], bi[2][NY];
+    if (PAIRA_K) {
+      const float2* q = pa + ka[k0];
+#pragma unroll
+      for (int x = 0; x < NX; ++x) {
+        const float4 v = *reinterpret_cast<const float4*>(q + xa[x]);
+        ar[0][x] = v.x; ai[0][x] = v.y; ar[1][x] = v.z; ai[1][x] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) {
+        const float2* q = pa + ka[k0 + kk];
+#pragma unroll
+        for (int x = 0; x < NX; x += 2) {
+          const float4 v = *reinterpret_cast<const float4*>(q + xa[x]);
+          ar[kk][x] = v.x; ai[kk][x] = v.y; ar[kk][x + 1] = v.z; ai[kk][x + 1] = v.w;
+        }
+      }
+    }
+    if (PAIRB_K) {
+      const float2* q = pb + kb[k0];
+#pragma unroll
+      for (int y = 0; y < NY; ++y) {
+        const float4 v = *reinterpret_cast<const float4*>(q + yb[y]);
+        br[0][y] = v.x; bi[0][y] = v.y; br[1][y] = v.z; bi[1][y] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) {
+        const float2* q = pb + kb[k0 + kk];
+#pragma unroll
+        for (int y = 0; y < NY; y += 2) {
+          const float4 v = *reinterpret_cast<const float4*>(q + yb[y]);
+          br[kk][y] = v.x; bi[kk][y] = v.y; br[kk][y + 1] = v.z; bi[kk][y + 1] = v.w;
+        }
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      float sr = 0.f, si = 0.f;
+#pragma unroll
+      for (int y = 0; y < NY; ++y) {
+        float ur = 0.f, ui = 0.f;
+#pragma unroll
+        for (int x = 0; x < NX; ++x) {
+          ur = fmaf(ar[kk][x], cvr[x * NY + y], ur);
+          ur = fmaf(-ai[kk][x], cvi[x * NY + y], ur);
+          ui = fmaf(ar[kk][x], cvi[x * NY + y], ui);
+          ui = fmaf(ai[kk][x], cvr[x * NY + y], ui);
+        }
+        sr = fmaf(ur, br[kk][y], sr);
+        sr = fmaf(-ui, bi[kk][y], sr);
+        si = fmaf(ur, bi[kk][y], si);
+        si = fmaf(ui, br[kk][y], si);
+      }
+      if (has_w) {
+        const float2 w = wk[k0 + kk];
+        accr = fmaf(w.x, sr, accr);
+        accr = fmaf(-w.y, si, accr);
+        acci = fmaf(w.x, si, acci);
+        acci = fmaf(w.y, sr, acci);
+      } else {
+        accr += sr;
+        acci += si;
+      }
+    }
+  }
+  return make_float2(accr, acci);
+}
+
+constexpr int kTriOutsPerThread = 2;  // tiles of up to 512 outputs
+
+template <int NX, int NY>
+__global__ void __launch_bounds__(kTmaThreads, 2) k_tri_tma(
+    const GemmArgs a, const __grid_constant__ CUtensorMap mapA,
+    const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapC, int u,
+    float* data, GMeta* meta) {
+  extern __shared__ float4 trsm[];
+  __shared__ TriSlot s_slot[kTriStages];
+  __shared__ alignas(8) unsigned long long s_full[kTriStages];
+  __shared__ alignas(8) unsigned long long s_empty[kTriStages];
+  __shared__ int s_col[2 * kTriMaxK + NX + NY + NX * NY];  // ka, kb, xa, yb, colC
+  __shared__ volatile int s_fail;
+  const int nsum = a.nsum, t = a.tb, h = u - nsum - t;
+  const unsigned int L = (nsum + t >= 32) ? 0xffffffffu : ((1u << (nsum + t)) - 1u);
+  const unsigned int Sm = (1u << nsum) - 1u;
+  const GOp& OA = a.op[a.tA];
+  const GOp& OB = a.op[a.tB];
+  const GOp& OC = a.op[a.tC];
+  const int sA = __popc(OA.umask & Sm), sB = __popc(OB.umask & Sm), sC = __popc(OC.umask & Sm);
+  const int laA = __popc(OA.umask & L), laB = __popc(OB.umask & L), laC = __popc(OC.umask & L);
+  const int rA = 1 << (laA - sA), rB = 1 << (laB - sB), rC = 1 << (laC - sC);
+  const int PA = (1 << sA) + 2, PB = (1 << sB) + 2, PC = (1 << sC) + 2;  // row strides (complex)
+  const int zA = (rA * PA + 127) & ~127, zB = (rB * PB + 127) & ~127, zC = (rC * PC + 127) & ~127;
+  const int zS = zA + zB + zC;  // one stage (float2)
+  float2* const stage0 = reinterpret_cast<float2*>(reinterpret_cast<char*>(trsm) +
+                                                   ((1024u - (smem_u32(trsm) & 1023u)) & 1023u));
+  const int nK = 1 << __popc(a.tK);
+  bool has_w = false;
+  for (int j = 0; j < a.m; ++j) has_w |= a.op[j].tfold == 2;
+  const long long ntiles = a.nslices << h;
+  const long long chunk = (ntiles + gridDim.x - 1) / gridDim.x;
+  const long long w0 = (long long)blockIdx.x * chunk;
+  const long long w1 = min(ntiles, w0 + chunk);
+  int* ka = s_col;
+  int* kb = ka + nK;
+  int* xa = kb + nK;
+  int* yb = xa + NX;
+  int* colC = yb + NY;
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < kTriStages; ++b) {
+      mbar_init(&s_full[b], 1);
+      mbar_init(&s_empty[b], kTmaConsumers / 32);
+    }
+    mbar_fence_init();
+    s_fail = 0;
+  }
+  // column of (k, x) in A's row = ka[k] + xa[x] (pext over disjoint bit sets adds)
+  for (int k = threadIdx.x; k < nK; k += blockDim.x) {
+    const unsigned int U = pdep32g((unsigned)k, a.tK);
+    ka[k] = (int)pext32g(U, OA.umask & Sm);
+    kb[k] = (int)pext32g(U, OB.umask & Sm);
+  }
+  for (int x = threadIdx.x; x < NX; x += blockDim.x)
+    xa[x] = (int)pext32g(pdep32g((unsigned)x, a.tX), OA.umask & Sm);
+  for (int y = threadIdx.x; y < NY; y += blockDim.x)
+    yb[y] = (int)pext32g(pdep32g((unsigned)y, a.tY), OB.umask & Sm);
+  for (int e = threadIdx.x; e < NX * NY; e += blockDim.x) {
+    const unsigned int U = pdep32g((unsigned)(e / NY), a.tX) | pdep32g((unsigned)(e % NY), a.tY);
+    colC[e] = (int)pext32g(U, OC.umask & Sm);
+  }
+  __syncthreads();
+  unsigned int issued = 0u;  // producer lane 0, barrier b: bit b some fill, bit 8 + b parity
+  if (threadIdx.x >= kTmaConsumers) {
+    // ---- producer warp ----
+    const int lane = threadIdx.x & 31;
+    const unsigned int inner = a.tile_inner, hmask = h >= 32 ? 0xffffffffu : ((1u << h) - 1u);
+    const int pin = __popc(inner);
+    const unsigned int outer = ~inner & hmask, pmask = (1u << pin) - 1u;
+    const int sh = nsum + t;
+    const unsigned int hiA = (OA.umask & ~L) >> sh, hiB = (OB.umask & ~L) >> sh,
+                       hiC = (OC.umask & ~L) >> sh;
+    const unsigned int bytes = (unsigned)((rA * PA + rB * PB + rC * PC) * 8);
+    auto load = [&](const CUtensorMap* map, long long off, float2* dst, int rows, int P, int s, int b) {
+      const int box = min(rows, kTmaBoxRows);
+      const int row0 = (int)(off >> s);
+      for (int r = 0; r < rows; r += box) tma_load_2d(dst + r * P, map, 0, row0 + r, &s_full[b]);
+    };
+    int ms = 0, f = 0;
+    long long pi = -1;
+    float sc = 1.f;
+    float2 wl0 = make_float2(1.f, 0.f), wl1 = make_float2(1.f, 0.f);  // W[lane], W[lane + 32]
+    bool ok = true;
+    for (long long wb = w0; wb < w1 && ok; wb += 32) {
+      const long long wl = wb + lane;
+      long long li = 0, oa = 0, ob = 0, oc = 0;
+      unsigned int ltau = 0;
+      if (wl < w1) {
+        li = wl >> h;
+        const unsigned int tp = (unsigned int)(wl & (((long long)1 << h) - 1));
+        ltau = inner ? (pdep32g(tp & pmask, inner) | pdep32g(tp >> pin, outer)) : tp;
+        const unsigned long long sid = (unsigned long long)(a.slice_first + li);
+        oa = op_slice_base(OA, li, sid) + ((long long)pext32g(ltau, hiA) << laA);
+        ob = op_slice_base(OB, li, sid) + ((long long)pext32g(ltau, hiB) << laB);
+        const long long cb = a.fold_a ? a.scratch_a + li * a.scratch_stride : op_slice_base(OC, li, sid);
+        oc = cb + ((long long)pext32g(ltau, hiC) << laC);
+      }
+      const int nwin = (int)min(32ll, w1 - wb);
+      for (int j = 0; j < nwin; ++j) {
+        const long long i = __shfl_sync(0xffffffffu, li, j);
+        const unsigned int tau = __shfl_sync(0xffffffffu, ltau, j);
+        const long long offA = __shfl_sync(0xffffffffu, oa, j);
+        const long long offB = __shfl_sync(0xffffffffu, ob, j);
+        const long long offC = __shfl_sync(0xffffffffu, oc, j);
+        if (i != pi) {  // a new slice: its scale (lane 0) and weights over K (all lanes)
+          pi = i;
+          if (lane == 0) {
+            sc = pow2_neg_g(scale_exp_g(meta[OA.meta + (OA.meta_per_slice ? i : 0)].maxabs)) *
+                 pow2_neg_g(scale_exp_g(meta[OB.meta + (OB.meta_per_slice ? i : 0)].maxabs));
+            if (!a.fold_a)
+              sc *= pow2_neg_g(scale_exp_g(meta[OC.meta + (OC.meta_per_slice ? i : 0)].maxabs));
+          }
+          if (has_w) {
+            const unsigned long long sid = (unsigned long long)(a.slice_first + i);
+            for (int half = 0; half < 2; ++half) {
+              const int k = lane + 32 * half;
+              float wr = 1.f, wi = 0.f;
+              if (k < nK) {
+                const unsigned int U = pdep32g((unsigned)k, a.tK);
+                for (int q = 0; q < a.m; ++q) {
+                  const GOp& o = a.op[q];
+                  if (o.tfold != 2) continue;
+                  const float s = pow2_neg_g(scale_exp_g(meta[o.meta + (o.meta_per_slice ? i : 0)].maxabs));
+                  const float2 v = reinterpret_cast<const float2*>(data)[op_slice_base(o, i, sid) +
+                                                                        pext32g(U, o.umask)];
+                  const float vr = v.x * s, vi = v.y * s;
+                  const float nr = wr * vr - wi * vi, ni = wr * vi + wi * vr;
+                  wr = nr;
+                  wi = ni;
+                }
+              }
+              if (half) wl1 = make_float2(wr, wi);
+              else wl0 = make_float2(wr, wi);
+            }
+          }
+        }
+        // the stage is free once the tile kTriStages earlier is done
+        if (lane == 0) {
+          if (s_fail) ok = false;
+          if (ok && f > 0) ok = mbar_wait(&s_empty[ms], (unsigned)((f - 1) & 1), a.err);
+        }
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        if (!ok) {
+          if (lane == 0) s_fail = 1;
+          break;
+        }
+        if (has_w) {
+          if (lane < nK) s_slot[ms].w[lane] = wl0;
+          if (lane + 32 < nK) s_slot[ms].w[lane + 32] = wl1;
+        }
+        if (lane == 0) {
+          s_slot[ms].i = i;
+          s_slot[ms].out = a.out_base + i * a.out_slice_stride + ((long long)tau << t);
+          s_slot[ms].sc = sc;
+          s_slot[ms].first = tau == 0u;
+        }
+        __threadfence_block();
+        __syncwarp();
+        if (lane == 0) {
+          float2* st = stage0 + ms * zS;
+          mbar_expect_tx(&s_full[ms], bytes);
+          load(&mapA, offA, st, rA, PA, sA, ms);
+          load(&mapB, offB, st + zA, rB, PB, sB, ms);
+          load(&mapC, offC, st + zA + zB, rC, PC, sC, ms);
+          issued = (issued | (1u << ms)) ^ (256u << ms);
+        }
+        if (++ms == kTriStages) {
+          ms = 0;
+          ++f;
+        }
+      }
+    }
+  } else {
+    // ---- consumer warps ----
+    const int T = 1 << t;
+    const unsigned int ma = (OA.umask & L) >> nsum, mb = (OB.umask & L) >> nsum,
+                       mc = (OC.umask & L) >> nsum;
+    // pairs: A's lowest summed index is K's lowest (pairs over k) or X's (pairs over x)
+    const bool pairA_k = ((OA.umask & Sm) & (0u - (OA.umask & Sm))) & a.tK;
+    const bool pairB_k = ((OB.umask & Sm) & (0u - (OB.umask & Sm))) & a.tK;
+    // this thread's outputs (the same in every tile) and their rows, once
+    int nmine = 0, ro[kTriOutsPerThread], rA_[kTriOutsPerThread], rB_[kTriOutsPerThread],
+        rC_[kTriOutsPerThread];
+#pragma unroll
+    for (int r = 0; r < kTriOutsPerThread; ++r) {
+      const int o = threadIdx.x + r * kTmaConsumers;
+      ro[r] = o;
+      rA_[r] = (int)pext32g((unsigned)o, ma) * PA;
+      rB_[r] = (int)pext32g((unsigned)o, mb) * PB;
+      rC_[r] = (int)pext32g((unsigned)o, mc) * PC;
+      if (o < T) nmine = r + 1;
+    }
+    int xr[NX], yr[NY], cr[NX * NY];
+#pragma unroll
+    for (int x = 0; x < NX; ++x) xr[x] = xa[x];
+#pragma unroll
+    for (int y = 0; y < NY; ++y) yr[y] = yb[y];
+#pragma unroll
+    for (int e = 0; e < NX * NY; ++e) cr[e] = colC[e];
+    long long cur = -1;
+    float mx = 0.f;
+    int ms = 0;
+    unsigned int ph = 0u;
+    for (long long w = w0; w < w1; ++w) {
+      const bool ok = mbar_wait(&s_full[ms], ph, a.err);
+      if (!__all_sync(0xffffffffu, ok)) {
+        s_fail = 1;
+        break;
+      }
+      const TriSlot& sl = s_slot[ms];
+      const long long i_c = sl.i;
+      const float sc = sl.sc;
+      if (i_c != cur) {
+        if (cur >= 0) flush_max(a, meta, cur, mx);
+        mx = 0.f;
+        cur = i_c;
+        if (sl.first && threadIdx.x == 0) write_meta_e(a, meta, i_c);
+      }
+      const float2* stA = stage0 + ms * zS;
+      const float2* stB = stA + zA;
+      const float2* stC = stB + zB;
+      float2* out = reinterpret_cast<float2*>(data) + sl.out;
+#pragma unroll
+      for (int r = 0; r < kTriOutsPerThread; ++r) {
+        if (r >= nmine) break;
+        float2 v;
+        if (pairA_k && pairB_k)
+          v = tri_one<NX, NY, true, true>(stA + rA_[r], stB + rB_[r], stC + rC_[r], ka, kb, xr, yr,
+                                          cr, nK, has_w, sl.w);
+        else if (pairA_k)
+          v = tri_one<NX, NY, true, false>(stA + rA_[r], stB + rB_[r], stC + rC_[r], ka, kb, xr,
+                                           yr, cr, nK, has_w, sl.w);
+        else if (pairB_k)
+          v = tri_one<NX, NY, false, true>(stA + rA_[r], stB + rB_[r], stC + rC_[r], ka, kb, xr,
+                                           yr, cr, nK, has_w, sl.w);
+        else
+          v = tri_one<NX, NY, false, false>(stA + rA_[r], stB + rB_[r], stC + rC_[r], ka, kb, xr,
+                                            yr, cr, nK, has_w, sl.w);
+        v.x *= sc;
+        v.y *= sc;
+        out[ro[r]] = v;
+        mx = fmaxf(mx, absmax_g(v.x, v.y));
+      }
+      __syncwarp();
+      if ((threadIdx.x & 31) == 0) mbar_arrive(&s_empty[ms]);
+      if (++ms == kTriStages) {
+        ms = 0;
+        ph ^= 1u;
+      }
+    }
+    if (cur >= 0) flush_max(a, meta, cur, mx);
+  }
+  __syncthreads();
+  if (s_fail && threadIdx.x == kTmaConsumers) {
+    for (int b = 0; b < kTriStages; ++b)
+      if ((issued >> b) & 1u) mbar_wait(&s_full[b], ((issued >> (8 + b)) & 1u) ^ 1u, nullptr);
+  }
+}
+
+
+using TriTmaFn = void (*)(const GemmArgs, const CUtensorMap, const CUtensorMap, const CUtensorMap,
+                          int, float*, GMeta*);
+
+TriTmaFn tri_tma_fn(int nx, int ny) {
+  switch (nx * 8 + ny) {
+    case 2 * 8 + 1: return k_tri_tma<2, 1>;
+    case 4 * 8 + 1: return k_tri_tma<4, 1>;
+    case 8 * 8 + 1: return k_tri_tma<8, 1>;
+    case 2 * 8 + 2: return k_tri_tma<2, 2>;
+    case 4 * 8 + 2: return k_tri_tma<4, 2>;
+    default: return nullptr;
+  }
+}
+
 constexpr size_t kTriSmemMax = 100 * 1024;
 
 }  // namespace
@@ -1466,7 +1854,51 @@ int tri_tile_bits(const GemmArgs& a, int u) {
   return 0;
 }
 
-int tri_launch(const GemmArgs& a, float* data, GMeta* meta, cudaStream_t s, int sms) {
+static bool row_map(CUtensorMap& m, float* data, long long ws_elems, int nsum, int box_rows);
+
+// The workspace as rows of 2^s complex, boxes 2^(s+1) + 4 floats wide (padding as above).
+static bool cols_map(CUtensorMap& m, float* data, long long ws_elems, int s, int box_rows) {
+  return row_map(m, data, ws_elems, s, box_rows);
+}
+
+constexpr size_t kTriTmaSmemMax = 110 * 1024;  // two blocks per SM
+
+// The tensor-copy triangle kernel's shared memory (0: not applicable).
+static size_t tri_tma_smem(const GemmArgs& a) {
+  const unsigned int L = (a.nsum + a.tb >= 32) ? 0xffffffffu : ((1u << (a.nsum + a.tb)) - 1u);
+  const unsigned int Sm = (1u << a.nsum) - 1u;
+  size_t z = 0;
+  const int ops[3] = {a.tA, a.tB, a.tC};
+  for (int q = 0; q < 3; ++q) {
+    const unsigned int m = a.op[ops[q]].umask;
+    const int s = __builtin_popcount(m & Sm), la = __builtin_popcount(m & L);
+    if (s < 1 || s > 6) return 0;
+    const long long rows = 1ll << (la - s), P = (1ll << s) + 2;
+    z += (size_t)((rows * P + 127) & ~127ll);
+  }
+  return 2 * z * 8 + 1024;
+}
+
+// Every block a triangle tile reads starts on a whole row of its operand.
+static bool tri_rows_aligned(const GemmArgs& a) {
+  const unsigned int Sm = (1u << a.nsum) - 1u;
+  const int ops[3] = {a.tA, a.tB, a.tC};
+  for (int q = 0; q < 3; ++q) {
+    const GOp& o = a.op[ops[q]];
+    const long long C = 1ll << __builtin_popcount(o.umask & Sm);
+    if (q == 2 && a.fold_a) {
+      if (a.scratch_a % C || a.scratch_stride % C) return false;
+    } else {
+      if (o.base % C || o.slice_stride % C) return false;
+      if (o.smask && (1ll << o.sshift) % C) return false;
+    }
+  }
+  return true;
+}
+
+int tri_launch(const GemmArgs& a, float* data, GMeta* meta, cudaStream_t s, int sms,
+               bool* used_tma) {
+  if (used_tma) *used_tma = false;
   int u = 0;
   for (unsigned int m = a.op[a.tA].umask | a.op[a.tB].umask | a.op[a.tC].umask; m; m >>= 1) ++u;
   const int nx = 1 << __builtin_popcount(a.tX), ny = 1 << __builtin_popcount(a.tY);
@@ -1484,8 +1916,35 @@ int tri_launch(const GemmArgs& a, float* data, GMeta* meta, cudaStream_t s, int 
     k_tri_fold<<<(unsigned)std::max<long long>(1, g), 256, 0, s>>>(a, data, meta);
     ++n;
   }
-  const TriLayout l = tri_layout(a, a.tb);
   const long long ntiles = a.nslices << (u - a.nsum - a.tb);
+  // tensor-copy staging when the kernel exists for the shape and the rows line up
+  TriTmaFn tfn = tri_tma_fn(nx, ny);
+  const size_t tsm = tfn ? tri_tma_smem(a) : 0;
+  if (a.use_tma && a.err && tfn && tsm && tsm <= kTriTmaSmemMax && a.tK &&
+      (1 << a.tb) <= kTriOutsPerThread * kTmaConsumers && tri_rows_aligned(a)) {
+    const unsigned int L = (a.nsum + a.tb >= 32) ? 0xffffffffu : ((1u << (a.nsum + a.tb)) - 1u);
+    const unsigned int Sm = (1u << a.nsum) - 1u;
+    CUtensorMap mp[3];
+    const int ops[3] = {a.tA, a.tB, a.tC};
+    bool ok = true;
+    for (int q = 0; q < 3 && ok; ++q) {
+      const unsigned int m = a.op[ops[q]].umask;
+      const int sq = __builtin_popcount(m & Sm), la = __builtin_popcount(m & L);
+      ok = cols_map(mp[q], data, a.ws_elems, sq, std::min(1 << (la - sq), 256));
+    }
+    if (ok) {
+      cudaFuncSetAttribute(tfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriTmaSmemMax);
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tfn, kTmaThreads, tsm) != cudaSuccess)
+        per_sm = 1;
+      const unsigned grid = (unsigned)std::max<long long>(
+          1, std::min<long long>(ntiles, (long long)sms * std::max(1, per_sm)));
+      tfn<<<grid, kTmaThreads, tsm, s>>>(a, mp[0], mp[1], mp[2], u, data, meta);
+      if (used_tma) *used_tma = true;
+      return n + 1;
+    }
+  }
+  const TriLayout l = tri_layout(a, a.tb);
   const int threads = std::min(256, 1 << a.tb);
   const int per_sm = std::max<int>(1, std::min<int>(8, (int)((220 * 1024) / (l.bytes + 2048))));
   const unsigned grid =

@@ -60,7 +60,8 @@ void gemm_tile_regs(const GemmArgs& a, int& reg_a, int& reg_b);
 // Triangle form (three large operands): output indices per tile (0: not taken)
 // and the launch (one kernel).
 int tri_tile_bits(const GemmArgs& a, int u);
-int tri_launch(const GemmArgs& a, float* data, GMeta* meta, cudaStream_t s, int sms);
+int tri_launch(const GemmArgs& a, float* data, GMeta* meta, cudaStream_t s, int sms,
+               bool* used_tma = nullptr);
 
 // GEMM_TILE: fold A', fold B' (when the side has small operands), tiled GEMM
 // (tensor-copy staging when a.use_tma and the blocks allow it: *used_tma);

@@ -31,3 +31,36 @@ def test_tma_staging_matches_oracle(qt, case):
     for tma in (0, 1):
         assert rel_err(amps[tma], ref) <= 1e-5, (tma, amps[tma], ref)
     assert abs(amps[0] - amps[1]) <= 1e-12 * abs(ref)
+
+
+TRI_CASES = [(36, 2, 7, 0, 1), (30, 3, 7, -2, 2), (50, 2, 2, -4, 3), (56, 2, 4, -2, 2),
+             (44, 3, 1, -2, 1), (80, 2, 1002, 26 - 35, 4)]
+
+
+@pytest.mark.parametrize("case", TRI_CASES)
+def test_tma_triangle_matches_oracle(qt, case):
+    """Triangle-form launches with tensor-copy staging (the default) and with the
+    cp.async kernel: both within the complex64 bar of the oracle; the bench workload's
+    launch (NX = 4, NY = 2) takes the tensor-copy kernel."""
+    n, p, seed, off, batch = case
+    edges, gammas, betas, z, tensors, nv, norm, adj = oracle_problem(n, p, seed)
+    amps, launches = {}, {}
+    for tma in (0, 1):
+        net = qt.Network(edges, n, p, gammas, betas, z)
+        qt.qt_set_option(net.handle, qt.QT_OPT_TRIANGLE, 1)
+        qt.qt_set_option(net.handle, qt.QT_OPT_TMA, tma)
+        w = net.order(0)
+        if off:
+            net.slice(w + off, 6, 1)
+        net.prepare(0, batch=batch)
+        amps[tma] = net.contract(0)
+        st = net.stats()
+        assert st["tri_groups"] >= 1
+        launches[tma] = st["tma_gemm_launches"]
+    plan = oracle_plan(adj, 0, w + off, 6, 1) if off else oracle_plan(adj, 0)
+    ref, _ = oracle_amplitude(tensors, norm, plan)
+    for tma in (0, 1):
+        assert rel_err(amps[tma], ref) <= 1e-5, (tma, amps[tma], ref)
+    assert launches[0] == 0
+    if n == 80:
+        assert launches[1] > 0
