@@ -316,10 +316,12 @@ void qt_mlp_free(qt_mlp* mlp);
  *                  kernels + GEMM); 0 (default): there only the autotuner may
  *                  pick it. Discards the prepared schedule.
  *   QT_OPT_SEGMENTS 1 (default): two or more consecutive small launches (union
- *                  of at most 13 indices) run as one segment launch, one block
+ *                  of at most 12 indices) run as one segment launch, one block
  *                  per slice stepping through them with block barriers; results
- *                  read only inside the run stay in shared memory. 0: one
- *                  launch each. Discards the prepared schedule.
+ *                  read only inside the run stay in shared memory. 2..13: the
+ *                  same with launches of at most that many union indices. 0: one
+ *                  launch each. Values outside 0..13: QT_EINVAL. Discards the
+ *                  prepared schedule.
  *   QT_OPT_TRIANGLE 1: launches in triangle form run it by default (complex64
  *                  precisions): three large tensors A, B, C with every summed
  *                  index in exactly two of them (K: A and B, X: A and C, Y: B

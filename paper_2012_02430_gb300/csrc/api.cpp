@@ -531,7 +531,9 @@ qt_status qt_set_option(qt_net* net, int32_t option, int64_t value) {
       net->sched = qt::Schedule();  // prepare again
       break;
     case QT_OPT_SEGMENTS:
+      if (value < 0 || value > 13) return fail(QT_EINVAL, "qt_set_option: QT_OPT_SEGMENTS takes 0..13");
       net->segments = value != 0;
+      net->seg_max_u = value >= 2 ? (int)value : 12;
       net->sched = qt::Schedule();  // prepare again
       break;
     case QT_OPT_TRIANGLE:

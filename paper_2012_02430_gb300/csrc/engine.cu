@@ -1531,7 +1531,8 @@ static bool build_cache(qt_net* net, EngineCache& c, std::string& err) {
     };
     for (size_t i = 0; i < list->size();) {
       size_t j = i;
-      auto small = [&](const LaunchDesc& d) { return d.kind == 0 && d.k.u <= SEG_MAX_U; };
+      const int max_u = std::min(net->seg_max_u, SEG_MAX_U);
+      auto small = [&](const LaunchDesc& d) { return d.kind == 0 && d.k.u <= max_u; };
       while (j < list->size() && small((*list)[j]) && j - i < (size_t)SEG_MAX_STEPS) ++j;
       LaunchDesc d;
       std::vector<KStep> recs;

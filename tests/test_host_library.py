@@ -411,3 +411,14 @@ def test_mlp_forward_host_matches_oracle(qt):
                                          batch, y.ctypes.data_as(fp)))
     ref, _ = mlp.forward(p.astype(np.float64), x.astype(np.float64), nf, hidden)
     assert np.max(np.abs(y - ref)) <= 1e-5 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_segment_option_range(qt):
+    """QT_OPT_SEGMENTS takes 0 (off), 1 (on, default limit) or a limit of 2..13 union
+    indices; other values are refused."""
+    net = qt.Network([(0, 1), (1, 2), (2, 0)], 3, 1, [0.3], [0.2], [0, 1, 0])
+    for v in (0, 1, 2, 12, 13):
+        qt.qt_set_option(net.handle, qt.QT_OPT_SEGMENTS, v)
+    for v in (-1, 14, 1 << 40):
+        with pytest.raises(qt.QtError):
+            qt.qt_set_option(net.handle, qt.QT_OPT_SEGMENTS, v)
