@@ -313,8 +313,11 @@ void qt_mlp_free(qt_mlp* mlp);
  *                  (CUDA-core GEMM: when every summed index is in both large
  *                  tensors, a shared-memory tiled kernel over the lowest U bits
  *                  after folding the small tensors into their side; else pack
- *                  kernels + GEMM); 0 (default): there only the autotuner may
- *                  pick it. Discards the prepared schedule.
+ *                  kernels + GEMM); 2: the same, with the streaming kernel
+ *                  (one thread per row of the large tensor, the small one
+ *                  staged whole) where it applies; 0 (default): there only the
+ *                  autotuner may pick them. Other values: QT_EINVAL. Discards
+ *                  the prepared schedule.
  *   QT_OPT_SEGMENTS 1 (default): two or more consecutive small launches (union
  *                  of at most 12 indices) run as one segment launch, one block
  *                  per slice stepping through them with block barriers; results

@@ -313,6 +313,7 @@ qt_status qt_prepare(qt_net* net, int32_t precision, int32_t batch, size_t* work
                   "qt_prepare: " + err);
     }
     net->sched.force_gemm = net->force_gemm;
+    net->sched.force_stream = net->force_stream;
     net->sched.force_tri = net->force_tri;
   } catch (const std::bad_alloc&) {
     net->sched = qt::Schedule();
@@ -329,7 +330,8 @@ qt_status qt_stats(const qt_net* net, char* buf, size_t cap, size_t* needed) {
   std::string s = qt::schedule_json(net->sched, net->plan);
   s.pop_back();
   s += ",\"launches\":" + std::to_string(net->launches) +
-       ",\"tma_gemm_launches\":" + std::to_string(net->tma_launches) + "}";
+       ",\"tma_gemm_launches\":" + std::to_string(net->tma_launches) +
+       ",\"stream_gemm_launches\":" + std::to_string(net->stream_launches) + "}";
   if (needed) *needed = s.size() + 1;
   if (buf && cap > 0) {
     size_t n = std::min(cap - 1, s.size());
@@ -527,7 +529,9 @@ qt_status qt_set_option(qt_net* net, int32_t option, int64_t value) {
       net->graphs = value != 0;
       break;
     case QT_OPT_GEMM:
+      if (value < 0 || value > 2) return fail(QT_EINVAL, "qt_set_option: QT_OPT_GEMM takes 0..2");
       net->force_gemm = value != 0;
+      net->force_stream = value == 2;
       net->sched = qt::Schedule();  // prepare again
       break;
     case QT_OPT_SEGMENTS:

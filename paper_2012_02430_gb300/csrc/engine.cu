@@ -1095,7 +1095,8 @@ struct LaunchDesc {
 constexpr int VARIANT_GEMM = 3;
 constexpr int VARIANT_TRI = 4;
 constexpr int VARIANT_FLAT = 5;  // the flat kernel for a launch the tiled kernel takes
-constexpr int N_ALL_VARIANTS = 6;
+constexpr int VARIANT_STREAM = 6;  // the GEMM form's streaming kernel
+constexpr int N_ALL_VARIANTS = 7;
 
 // GEMM flavour of a GEMM-form launch in a precision mode
 static int gemm_mode_for(const Schedule& S, const SGroup& g) {
@@ -1299,7 +1300,7 @@ static bool make_desc(const Schedule& S, int gi, long long nslices, LaunchDesc& 
   const SGroup& st = S.groups[gi];
   if (variant < 0)
     variant = st.gemm && (tc_precision(S.precision) || S.force_gemm)
-                  ? VARIANT_GEMM
+                  ? (S.force_stream && !tc_precision(S.precision) ? VARIANT_STREAM : VARIANT_GEMM)
                   : (st.tri && S.force_tri ? VARIANT_TRI : 1);
   KStep& k = d.k;
   k = KStep{};
@@ -1341,6 +1342,17 @@ static bool make_desc(const Schedule& S, int gi, long long nslices, LaunchDesc& 
   d.kind = tiled ? 1 : 0;
   d.variant = variant;
   d.gemm_mode = -1;
+  if (variant == VARIANT_STREAM && st.gemm && sizeof(R) == 4 && !tc_precision(S.precision)) {
+    fill_gemm(S, st, nslices, d.ga);
+    if (gemm_stream_ok(d.ga)) {
+      d.ga.use_stream = 1;
+      d.kind = 4;
+      d.gemm_mode = GEMM_TILE;
+      d.grid = 0;
+      return true;
+    }
+    variant = VARIANT_GEMM;  // the streaming kernel does not apply: the tiled GEMM
+  }
   if (variant == VARIANT_GEMM && st.gemm && sizeof(R) == 4) {
     d.kind = 3;
     d.gemm_mode = gemm_mode_for(S, st);
@@ -1352,6 +1364,7 @@ static bool make_desc(const Schedule& S, int gi, long long nslices, LaunchDesc& 
     d.grid = 0;
     return true;
   }
+
   if (variant == VARIANT_TRI && st.tri && sizeof(R) == 4) {
     fill_tri(S, st, nslices, d.ga);
     if (d.ga.tb > 0) {
@@ -1644,6 +1657,7 @@ static void launch_desc(qt_net* net, const LaunchDesc& d0, long long nslices, lo
     net->launches += gemm_launch(ga, d0.gemm_mode, reinterpret_cast<float*>(base),
                                  reinterpret_cast<GMeta*>(meta), s, num_sms(), &tma);
     if (tma) net->tma_launches++;
+    if (ga.use_stream) net->stream_launches++;
     if (net->prof) prof_end(net, s, pr);
     return;
   }
@@ -1741,6 +1755,11 @@ static qt_status autotune_impl(qt_net* net, char* base, cudaStream_t s, std::str
       std::vector<int> cands;
       for (int v = 0; v < N_VARIANTS; ++v) cands.push_back(v);
       if (can_gemm) cands.push_back(VARIANT_GEMM);
+      if (can_gemm) {
+        GemmArgs ga;
+        fill_gemm(S, grp, d.k.nslices, ga);
+        if (gemm_stream_ok(ga)) cands.push_back(VARIANT_STREAM);
+      }
       if (can_tri) cands.push_back(VARIANT_TRI);
       if (grp.u <= 20) cands.push_back(VARIANT_FLAT);  // small launches: one pair per thread
       const int nv = (int)cands.size();
@@ -1795,10 +1814,10 @@ static qt_status autotune_impl(qt_net* net, char* base, cudaStream_t s, std::str
       char buf[200];
       auto half = [](float x) { return x >= 1e29f ? -1.0 : x / 2.0; };
       std::snprintf(buf, sizeof buf,
-                    "%s{\"step\":%d,\"variant\":%d,\"ms\":[%.4f,%.4f,%.4f,%.4f,%.4f,%.4f]}",
+                    "%s{\"step\":%d,\"variant\":%d,\"ms\":[%.4f,%.4f,%.4f,%.4f,%.4f,%.4f,%.4f]}",
                     first ? "" : ",", S.groups[d.group].first, bv, half(kv.second[0]),
                     half(kv.second[1]), half(kv.second[2]), half(kv.second[3]),
-                    half(kv.second[4]), half(kv.second[5]));
+                    half(kv.second[4]), half(kv.second[5]), half(kv.second[6]));
       report += buf;
       first = false;
     }

@@ -619,6 +619,107 @@ __global__ void __launch_bounds__(256, 4) k_gemm_tile(const GemmArgs a, int u, f
   if (cur >= 0) flush_max(a, meta, cur, mx);
 }
 
+// GEMM form, streaming: for launches whose small side S (at most 12 indices) fits
+// in shared memory whole and whose large side G has no operand folded into it.
+// One thread per row of G (its K summed values, contiguous), loaded once with
+// 16-byte streaming loads and multiplied with every row of S' that shares its
+// batch indices (S' = S times its folded operands, staged per slice); the outputs
+// of consecutive rows of G are consecutive when G holds the lowest output indices.
+// The bit deposit of a row's output position and the extract of its S row use
+// byte tables in shared memory.
+// rows per thread and pass of the streaming kernel: up to 4 row loads in flight
+__host__ __device__ constexpr int stream_rows(int nsum) { return nsum <= 1 ? 4 : (nsum == 2 ? 2 : 1); }
+
+template <int NSUM>
+__global__ void __launch_bounds__(256) k_gemm_stream(const GemmArgs a, float* data, GMeta* meta) {
+  constexpr int K = 1 << NSUM, kStreamRows = stream_rows(NSUM);
+  extern __shared__ float4 stm[];
+  __shared__ PdepLut Lg;               // pdep over G's output indices
+  __shared__ unsigned int Ps[4][256];  // pext over S's output indices
+  const int gside = a.stay;            // 0: A is the large side G
+  const GOp& OG = a.op[gside ? a.gB : a.gA];
+  const GOp& OS = a.op[gside ? a.gA : a.gB];
+  const int fold_s = gside ? a.fold_a : a.fold_b;
+  const long long scr_s = gside ? a.scratch_a : a.scratch_b;
+  const unsigned int Gm = OG.umask >> NSUM, Sm = OS.umask >> NSUM, Nm = Sm & ~Gm;
+  const int rbits = __popc(Gm), nS = __popc(OS.umask), nN = __popc(Nm);
+  float2* sS = reinterpret_cast<float2*>(stm);                             // 2^nS complex
+  unsigned int* nTab = reinterpret_cast<unsigned int*>(sS + (1 << nS));  // S row part of nb
+  unsigned int* oTab = nTab + (1 << nN);                                   // output part of nb
+  build_pdep(Lg, Gm);
+  build_pext(Ps, Sm);
+  for (int e = threadIdx.x; e < (1 << nN); e += blockDim.x) {
+    const unsigned int on = pdep32g((unsigned)e, Nm);
+    oTab[e] = on;
+    nTab[e] = pext32g(on, Sm);
+  }
+  const long long rows = 1ll << rbits;  // rows of G per slice (a multiple of the block)
+  const long long total = a.nslices << rbits;
+  const float2* d2 = reinterpret_cast<const float2*>(data);
+  long long cur = -1;
+  float sc = 1.f, mx = 0.f;
+  // kStreamRows rows per thread per pass (consecutive runs of the block's rows), so
+  // that several row loads are in flight
+  const long long span = (long long)blockDim.x * kStreamRows;
+  for (long long base = (long long)blockIdx.x * span; base < total; base += (long long)gridDim.x * span) {
+    const long long i = base >> rbits;  // the same for the whole block (rows is a multiple of span)
+    const unsigned long long sid = (unsigned long long)(a.slice_first + i);
+    if (i != cur) {
+      if (cur >= 0) flush_max(a, meta, cur, mx);
+      mx = 0.f;
+      __syncthreads();  // the tables are built; the last slice's S' is no longer read
+      const long long sb = fold_s ? scr_s + i * a.scratch_stride : op_slice_base(OS, i, sid);
+      const float ss = fold_s ? 1.f
+          : pow2_neg_g(scale_exp_g(meta[OS.meta + (OS.meta_per_slice ? i : 0)].maxabs));
+      for (int e = threadIdx.x; e < (1 << nS); e += blockDim.x) {
+        const float2 v = d2[sb + e];
+        sS[e] = make_float2(v.x * ss, v.y * ss);
+      }
+      sc = pow2_neg_g(scale_exp_g(meta[OG.meta + (OG.meta_per_slice ? i : 0)].maxabs));
+      if ((base & (rows - 1)) == 0 && threadIdx.x == 0) write_meta_e(a, meta, i);
+      cur = i;
+      __syncthreads();
+    }
+    const float2* gbase = d2 + op_slice_base(OG, i, sid);
+    float2* out = reinterpret_cast<float2*>(data) + a.out_base + i * a.out_slice_stride;
+    float4 gv[kStreamRows][K / 2];
+#pragma unroll
+    for (int r = 0; r < kStreamRows; ++r) {
+      const unsigned int rG = (unsigned int)((base + threadIdx.x + r * blockDim.x) & (rows - 1));
+      const float4* gp = reinterpret_cast<const float4*>(gbase + (long long)rG * K);
+#pragma unroll
+      for (int q = 0; q < K / 2; ++q) gv[r][q] = __ldcs(gp + q);
+    }
+#pragma unroll
+    for (int r = 0; r < kStreamRows; ++r) {
+      const unsigned int rG = (unsigned int)((base + threadIdx.x + r * blockDim.x) & (rows - 1));
+      const unsigned int oG = pdep_lut(Lg, rG);
+      const unsigned int sG = pext_lut(Ps, oG);
+      for (int nb = 0; nb < (1 << nN); ++nb) {
+        const float4* sp = reinterpret_cast<const float4*>(sS + (size_t)(sG + nTab[nb]) * K);
+        float cr = 0.f, ci = 0.f;
+#pragma unroll
+        for (int q = 0; q < K / 2; ++q) {
+          const float4 x = gv[r][q], y = sp[q];
+          cr = fmaf(x.x, y.x, cr);
+          cr = fmaf(-x.y, y.y, cr);
+          ci = fmaf(x.x, y.y, ci);
+          ci = fmaf(x.y, y.x, ci);
+          cr = fmaf(x.z, y.z, cr);
+          cr = fmaf(-x.w, y.w, cr);
+          ci = fmaf(x.z, y.w, ci);
+          ci = fmaf(x.w, y.z, ci);
+        }
+        cr *= sc;
+        ci *= sc;
+        __stcs(out + (oG | oTab[nb]), make_float2(cr, ci));
+        mx = fmaxf(mx, absmax_g(cr, ci));
+      }
+    }
+  }
+  if (cur >= 0) flush_max(a, meta, cur, mx);
+}
+
 // GEMM_TILE with tensor-copy (TMA) staging and a producer warp: the same tiles,
 // tile numbering, block ranges, register blocking and arithmetic (so the same
 // results, bit for bit) as k_gemm_tile, with the summed-index count a
@@ -2031,9 +2132,57 @@ static TmaFn tma_fn(int nsum) {
   }
 }
 
+bool gemm_stream_ok(const GemmArgs& a) {
+  if (a.mSA || a.mSB || a.gA < 0 || a.gB < 0 || a.nsum < 1 || a.nsum > 5) return false;
+  const int gs = gemm_tile_stay(a);
+  const GOp& G = a.op[gs ? a.gB : a.gA];
+  const GOp& S = a.op[gs ? a.gA : a.gB];
+  if (gs ? a.fold_b : a.fold_a) return false;  // nothing folded into the large side
+  const unsigned int Gm = G.umask >> a.nsum, Sm = S.umask >> a.nsum;
+  // (the row's output position comes from 3 byte tables: at most 24 row indices)
+  return __builtin_popcount(S.umask) <= 12 && __builtin_popcount(Gm) >= 10 &&
+         __builtin_popcount(Gm) <= 24 && __builtin_popcount(Sm & ~Gm) <= 10;
+}
+
+typedef void (*StreamFn)(const GemmArgs, float*, GMeta*);
+
+static StreamFn stream_fn(int nsum) {
+  switch (nsum) {
+    case 1: return k_gemm_stream<1>;
+    case 2: return k_gemm_stream<2>;
+    case 3: return k_gemm_stream<3>;
+    case 4: return k_gemm_stream<4>;
+    case 5: return k_gemm_stream<5>;
+    default: return nullptr;
+  }
+}
+
 int gemm_launch(const GemmArgs& a, int mode, float* data, GMeta* meta, cudaStream_t s, int sms,
                 bool* used_tma) {
   if (used_tma) *used_tma = false;
+  if (mode == GEMM_TILE && a.use_stream) {
+    int n = 0;
+    const int gs = gemm_tile_stay(a);
+    if (gs ? a.fold_a : a.fold_b) {  // fold the small side into its scratch
+      const int side = gs ? 0 : 1;
+      const long long work = a.nslices << __builtin_popcount(a.op[side ? a.gB : a.gA].umask);
+      const long long g = std::min<long long>((work + 255) / 256, (long long)sms * 16);
+      k_gemm_fold<<<(unsigned)std::max<long long>(1, g), 256, 0, s>>>(a, side, data, meta);
+      ++n;
+    }
+    const GOp& G = a.op[gs ? a.gB : a.gA];
+    const GOp& S = a.op[gs ? a.gA : a.gB];
+    const unsigned int Gm = G.umask >> a.nsum, Sm = S.umask >> a.nsum;
+    const size_t smem = ((size_t)8 << __builtin_popcount(S.umask)) +
+                        ((size_t)8 << __builtin_popcount(Sm & ~Gm));
+    const long long total = a.nslices << __builtin_popcount(Gm);
+    StreamFn fn = stream_fn(a.nsum);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    const unsigned grid = (unsigned)std::max<long long>(
+        1, std::min<long long>(total / (256 * stream_rows(a.nsum)), (long long)sms * 8));
+    fn<<<grid, 256, smem, s>>>(a, data, meta);
+    return n + 1;
+  }
   if (mode == GEMM_TILE) {
     int n = 0;
     for (int side = 0; side < 2; ++side) {

@@ -40,6 +40,7 @@ struct GemmArgs {
   unsigned int tK, tX, tY;  // triangle form: summed bits of each class
   int use_tma;              // GEMM_TILE: stage the blocks with tensor copies (TMA)
   int stay;                 // GEMM_TILE: 0 the tiles of a group share A's block, 1 B's
+  int use_stream;           // GEMM_TILE: the streaming kernel (gemm_stream_ok) instead
   long long ws_elems;       // workspace size (complex): the extent of the tensor maps
   int* err;                 // device status word: set to 1 when a bounded wait gives up
   GOp op[GEMM_MAXOP];
@@ -53,6 +54,9 @@ int gemm_tile_bits(const GemmArgs& a, int u);
 // and the side whose block the tiles differing only in them share (0 A, 1 B).
 unsigned int gemm_tile_inner(const GemmArgs& a, int u);
 int gemm_tile_stay(const GemmArgs& a);
+// The streaming GEMM kernel applies: the smaller operand (at most 12 indices, nothing
+// folded into the larger one) is staged whole per slice, one thread per row of the other.
+bool gemm_stream_ok(const GemmArgs& a);
 // Register-blocking bits of the GEMM_TILE kernel: an A-only and a B-only output
 // bit inside the tile, or -1, -1.
 void gemm_tile_regs(const GemmArgs& a, int& reg_a, int& reg_b);

@@ -549,9 +549,11 @@ std::string schedule_json(const Schedule& S, const SlicePlan& plan) {
         if (std::find(t.labels.begin(), t.labels.end(), g.ulabels[b]) != t.labels.end())
           um[s] |= 1u << b;
     }
+    int na = 0, nb = 0;  // operands folded into A', into B' (the large ones included)
+    for (size_t j = 0; j < g.ops.size(); ++j) (g.side[j] ? nb : na)++;
     o << (first ? "" : ",") << "[" << g.first << "," << g.u << "," << g.mK << "," << g.mSA << ","
       << g.mSB << "," << g.mM << "," << g.mN << "," << g.mBt << "," << um[0] << "," << um[1]
-      << "]";
+      << "," << na << "," << nb << "]";
     first = false;
   }
   // triangle-form launches: first step, U, the summed bits of each class (K, X, Y)

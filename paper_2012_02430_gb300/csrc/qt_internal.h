@@ -135,6 +135,7 @@ struct SGroup {
 struct Schedule {
   bool valid = false;
   bool force_gemm = false;       // copy of the network option at compile time
+  bool force_stream = false;     // copy of the network option at compile time
   bool force_tri = false;        // copy of the network option at compile time
   bool fused = true;             // steps grouped into fused launches
   uint64_t generation = 0;      // changes with every compile
@@ -222,11 +223,13 @@ struct qt_net {
   bool graphs = true;            // replay runs as captured CUDA graphs
   bool fuse = true;              // fuse bucket steps whose summed indices die together
   bool force_gemm = false;       // GEMM-form launches by default also in FP32 mode
+  bool force_stream = false;     // ... with the streaming kernel where it applies
   bool segments = true;          // runs of small launches as one segment launch
   int seg_max_u = 12;            // union indices of a step a segment may hold (at most 13)
   bool force_tri = false;        // triangle-form launches by default where they apply
   bool tma = true;               // tiled GEMM stages its blocks with tensor copies (TMA)
   int64_t tma_launches = 0;      // tiled GEMM launches that took the tensor-copy staging
+  int64_t stream_launches = 0;   // GEMM-form launches by the streaming kernel
   void* engine = nullptr;        // engine.cu: launch descriptors and graph cache
   ~qt_net();
 };

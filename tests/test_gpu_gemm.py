@@ -14,15 +14,15 @@ TOL = {"fp32gemm": 1e-5, 3: 1e-5, 1: 1e-2, 2: 5e-2}
 CASES = [(44, 2, 14, -4), (60, 2, 18, -4), (24, 3, 15, -4)]
 
 
-def _amp(qt, n, p, seed, off, prec, force_gemm=False, profile=False):
+def _amp(qt, n, p, seed, off, prec, force_gemm=False, profile=False, batch=3):
     edges, gammas, betas, z, tensors, nv, norm, adj = oracle_problem(n, p, seed)
     net = qt.Network(edges, n, p, gammas, betas, z)
     if force_gemm:
-        qt.qt_set_option(net.handle, qt.QT_OPT_GEMM, 1)
+        qt.qt_set_option(net.handle, qt.QT_OPT_GEMM, int(force_gemm))
     w = net.order(0)
     net.slice(w + off, 6, 1)
     plan = oracle_plan(adj, 0, w + off, 6, 1)
-    net.prepare(prec, batch=3)
+    net.prepare(prec, batch=batch)
     st = net.stats()
     kinds = set()
     if profile:
@@ -33,6 +33,7 @@ def _amp(qt, n, p, seed, off, prec, force_gemm=False, profile=False):
         kinds = {r["kernel"] for r in qt.qt_profile_read(net.handle)}
         qt.qt_profile(net.handle, 0)
     amp = net.contract(prec)
+    st = net.stats()
     ref, _ = oracle_amplitude(tensors, norm, plan)
     return amp, ref, st, kinds
 
@@ -51,6 +52,22 @@ def test_gemm_tile_bench_workload(qt):
     GEMM kernel runs and the amplitude meets the complex64 bar."""
     amp, ref, st, kinds = _amp(qt, 80, 2, 1002, 26 - 35, 0, force_gemm=True, profile=True)
     assert 4 in kinds
+    assert rel_err(amp, ref) <= TOL["fp32gemm"], (amp, ref)
+
+
+STREAM_CASES = [(44, 2, 14, -4, 3), (60, 2, 18, -4, 3), (80, 2, 1002, 26 - 35, 4),
+                (50, 3, 1003, -4, 2)]
+
+
+@pytest.mark.parametrize("case", STREAM_CASES)
+def test_gemm_stream_kernel(qt, case):
+    """GEMM form with the streaming kernel forced where it applies (QT_OPT_GEMM = 2: the
+    small operand staged whole per slice, one thread per row of the large one), the
+    tiled GEMM elsewhere: the amplitude meets the complex64 bar and the streaming
+    kernel really ran."""
+    n, p, seed, off, batch = case
+    amp, ref, st, kinds = _amp(qt, n, p, seed, off, 0, force_gemm=2, batch=batch)
+    assert st["stream_gemm_launches"] > 0
     assert rel_err(amp, ref) <= TOL["fp32gemm"], (amp, ref)
 
 

@@ -422,3 +422,14 @@ def test_segment_option_range(qt):
     for v in (-1, 14, 1 << 40):
         with pytest.raises(qt.QtError):
             qt.qt_set_option(net.handle, qt.QT_OPT_SEGMENTS, v)
+
+
+def test_gemm_option_range(qt):
+    """QT_OPT_GEMM takes 0, 1 (the GEMM form by default) or 2 (with the streaming kernel
+    where it applies); other values are refused."""
+    net = qt.Network([(0, 1), (1, 2), (2, 0)], 3, 1, [0.3], [0.2], [0, 1, 0])
+    for v in (0, 1, 2):
+        qt.qt_set_option(net.handle, qt.QT_OPT_GEMM, v)
+    for v in (-1, 3):
+        with pytest.raises(qt.QtError):
+            qt.qt_set_option(net.handle, qt.QT_OPT_GEMM, v)
