@@ -1166,7 +1166,7 @@ static void fill_gemm(const Schedule& S, const SGroup& g, long long nslices, Gem
   a.tile_inner = gemm_tile_inner(a, g.u);
   a.stay = gemm_tile_stay(a);
   a.ws_elems = (long long)(S.total_bytes / 8);
-  gemm_tile_regs(a, a.reg_a, a.reg_b);
+  gemm_tile_regs(a);
 }
 
 // Triangle form of a launch (three large operands; see gemm.cu k_tri_tile).
@@ -1184,7 +1184,7 @@ static void fill_tri(const Schedule& S, const SGroup& g, long long nslices, Gemm
   a.out_meta_per_slice = per_slice ? 1 : 0;
   a.out_meta = out.meta;
   a.gA = a.gB = -1;
-  a.reg_a = a.reg_b = -1;
+  a.reg_a = a.reg_b = a.reg_a2 = a.reg_b2 = -1;
   for (int j = 0; j < a.m; ++j) {
     KOp o;
     fill_op(S, g, j, o);

@@ -759,7 +759,7 @@ struct TmaSlot {
   int first;         // the slice's first tile (tau = 0)
 };
 
-template <int NSUM>
+template <int NSUM, int WIDE>
 __global__ void __launch_bounds__(kTmaThreads, 3) k_gemm_tma(
     const GemmArgs a, const __grid_constant__ CUtensorMap mapA,
     const __grid_constant__ CUtensorMap mapB, int u, int nmove, float* data, GMeta* meta) {
@@ -918,26 +918,39 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gemm_tma(
     }
   } else {
     // ---- consumer warps ----
+    // register block: NA rows of A x NB rows of B (the wide side's two bits reg_x, reg_x2)
+    constexpr int NA = WIDE == 2 ? 4 : 2, NB = WIDE == 1 ? 4 : 2;
+    constexpr int kItems = NA * NB == 4 ? kTileQuads : 1;  // tiles of up to 2^11 outputs
     const unsigned int ma = (OA.umask & L) >> NSUM, mb = (OB.umask & L) >> NSUM;
     const int T = 1 << t;
     const bool blocked = a.reg_a >= 0;
-    const unsigned int rmask = blocked ? ((1u << a.reg_a) | (1u << a.reg_b)) : 0u;
-    const int items = blocked ? (T >> 2) : T;
-    int nmine = 0;
-    unsigned int o_of[kTileQuads];
-    int ra0[kTileQuads], ra1[kTileQuads], rb0[kTileQuads], rb1[kTileQuads];
+    const unsigned int amask = (blocked ? 1u << a.reg_a : 0u) | (WIDE == 2 ? 1u << a.reg_a2 : 0u);
+    const unsigned int bmask = (blocked ? 1u << a.reg_b : 0u) | (WIDE == 1 ? 1u << a.reg_b2 : 0u);
+    const unsigned int rmask = amask | bmask;
+    const int items = blocked ? (T / (NA * NB)) : T;
+    unsigned int aoff[NA], boff[NB];
 #pragma unroll
-    for (int r = 0; r < kTileQuads; ++r) {
+    for (int x = 0; x < NA; ++x) aoff[x] = pdep32g((unsigned)x, amask);
+#pragma unroll
+    for (int y = 0; y < NB; ++y) boff[y] = pdep32g((unsigned)y, bmask);
+    int nmine = 0;
+    unsigned int o_of[kItems];
+    int ra[kItems][NA], rb[kItems][NB];
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
       const int q = threadIdx.x + r * kTmaConsumers;
       o_of[r] = 0u;
-      ra0[r] = ra1[r] = rb0[r] = rb1[r] = 0;
+#pragma unroll
+      for (int x = 0; x < NA; ++x) ra[r][x] = 0;
+#pragma unroll
+      for (int y = 0; y < NB; ++y) rb[r][y] = 0;
       if (blocked && q < items) {
         const unsigned int o00 = pdep32g((unsigned)q, (unsigned)(T - 1) & ~rmask);
         o_of[r] = o00;
-        ra0[r] = (int)pext32g(o00, ma) * RS;
-        ra1[r] = (int)pext32g(o00 | (1u << a.reg_a), ma) * RS;
-        rb0[r] = (int)pext32g(o00, mb) * RS;
-        rb1[r] = (int)pext32g(o00 | (1u << a.reg_b), mb) * RS;
+#pragma unroll
+        for (int x = 0; x < NA; ++x) ra[r][x] = (int)pext32g(o00 | aoff[x], ma) * RS;
+#pragma unroll
+        for (int y = 0; y < NB; ++y) rb[r][y] = (int)pext32g(o00 | boff[y], mb) * RS;
         nmine = r + 1;
       }
     }
@@ -970,34 +983,44 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gemm_tma(
       float2* out = reinterpret_cast<float2*>(data) + s_slot[ms].out;
       if (blocked) {
 #pragma unroll
-        for (int r = 0; r < kTileQuads; ++r) {
+        for (int r = 0; r < kItems; ++r) {
           if (r >= nmine) break;
-          const float4* pa0 = reinterpret_cast<const float4*>(sA + ra0[r]);
-          const float4* pa1 = reinterpret_cast<const float4*>(sA + ra1[r]);
-          const float4* pb0 = reinterpret_cast<const float4*>(sB + rb0[r]);
-          const float4* pb1 = reinterpret_cast<const float4*>(sB + rb1[r]);
-          float c00r = 0.f, c00i = 0.f, c01r = 0.f, c01i = 0.f, c10r = 0.f, c10i = 0.f,
-                c11r = 0.f, c11i = 0.f;
+          float cr[NA][NB], ci[NA][NB];
+#pragma unroll
+          for (int x = 0; x < NA; ++x)
+#pragma unroll
+            for (int y = 0; y < NB; ++y) cr[x][y] = ci[x][y] = 0.f;
 #pragma unroll
           for (int k2 = 0; k2 < KC; ++k2) {
-            const float4 x0 = pa0[k2], x1 = pa1[k2], y0 = pb0[k2], y1 = pb1[k2];
-#define QT_CMAC2(CR, CI, P, Q)                                                          \
-  CR = fmaf(P.x, Q.x, CR); CR = fmaf(-P.y, Q.y, CR); CI = fmaf(P.x, Q.y, CI);          \
-  CI = fmaf(P.y, Q.x, CI); CR = fmaf(P.z, Q.z, CR); CR = fmaf(-P.w, Q.w, CR);          \
-  CI = fmaf(P.z, Q.w, CI); CI = fmaf(P.w, Q.z, CI);
-            QT_CMAC2(c00r, c00i, x0, y0)
-            QT_CMAC2(c01r, c01i, x0, y1)
-            QT_CMAC2(c10r, c10i, x1, y0)
-            QT_CMAC2(c11r, c11i, x1, y1)
-#undef QT_CMAC2
+            float4 xv[NA], yv[NB];
+#pragma unroll
+            for (int x = 0; x < NA; ++x) xv[x] = reinterpret_cast<const float4*>(sA + ra[r][x])[k2];
+#pragma unroll
+            for (int y = 0; y < NB; ++y) yv[y] = reinterpret_cast<const float4*>(sB + rb[r][y])[k2];
+#pragma unroll
+            for (int x = 0; x < NA; ++x)
+#pragma unroll
+              for (int y = 0; y < NB; ++y) {
+                const float4 P = xv[x], Q = yv[y];
+                cr[x][y] = fmaf(P.x, Q.x, cr[x][y]);
+                cr[x][y] = fmaf(-P.y, Q.y, cr[x][y]);
+                ci[x][y] = fmaf(P.x, Q.y, ci[x][y]);
+                ci[x][y] = fmaf(P.y, Q.x, ci[x][y]);
+                cr[x][y] = fmaf(P.z, Q.z, cr[x][y]);
+                cr[x][y] = fmaf(-P.w, Q.w, cr[x][y]);
+                ci[x][y] = fmaf(P.z, Q.w, ci[x][y]);
+                ci[x][y] = fmaf(P.w, Q.z, ci[x][y]);
+              }
           }
           const unsigned int o00 = o_of[r];
-          out[o00] = make_float2(c00r * sc, c00i * sc);
-          out[o00 | (1u << a.reg_b)] = make_float2(c01r * sc, c01i * sc);
-          out[o00 | (1u << a.reg_a)] = make_float2(c10r * sc, c10i * sc);
-          out[o00 | rmask] = make_float2(c11r * sc, c11i * sc);
-          mx = fmaxf(mx, fmaxf(fmaxf(absmax_g(c00r, c00i), absmax_g(c01r, c01i)),
-                               fmaxf(absmax_g(c10r, c10i), absmax_g(c11r, c11i))) * sc);
+#pragma unroll
+          for (int x = 0; x < NA; ++x)
+#pragma unroll
+            for (int y = 0; y < NB; ++y) {
+              const float vr = cr[x][y] * sc, vi = ci[x][y] * sc;
+              out[o00 | aoff[x] | boff[y]] = make_float2(vr, vi);
+              mx = fmaxf(mx, absmax_g(vr, vi));
+            }
         }
       } else {
         for (int o = threadIdx.x; o < T; o += kTmaConsumers) {
@@ -1914,14 +1937,58 @@ int gemm_tile_bits(const GemmArgs& a, int u) {
   return 0;
 }
 
-void gemm_tile_regs(const GemmArgs& a, int& reg_a, int& reg_b) {
-  // the highest A-only and B-only output bits inside the tile (-1: none)
-  reg_a = reg_b = -1;
+void gemm_tile_regs(GemmArgs& a) {
+  // the highest (reg_x) and second highest (reg_x2) A-only and B-only output bits
+  // inside the tile (-1: none)
+  a.reg_a = a.reg_b = a.reg_a2 = a.reg_b2 = -1;
+  a.wide = 0;
   for (int b = 0; b < a.tb; ++b) {
-    if ((a.mM >> (a.nsum + b)) & 1u) reg_a = b;
-    if ((a.mN >> (a.nsum + b)) & 1u) reg_b = b;
+    if ((a.mM >> (a.nsum + b)) & 1u) {
+      a.reg_a2 = a.reg_a;
+      a.reg_a = b;
+    }
+    if ((a.mN >> (a.nsum + b)) & 1u) {
+      a.reg_b2 = a.reg_b;
+      a.reg_b = b;
+    }
   }
-  if (reg_a < 0 || reg_b < 0 || a.tb < 3) reg_a = reg_b = -1;
+  if (a.reg_a < 0 || a.reg_b < 0 || a.tb < 3) {
+    a.reg_a = a.reg_b = a.reg_a2 = a.reg_b2 = -1;
+    return;
+  }
+  // a 2 x 4 (or 4 x 2) block when the wide side's rows are shared by more lanes of a
+  // warp: a warp's lanes take the five lowest tile bits outside the block's bits, and
+  // a shared-memory wavefront serves 8 distinct 16-byte rows
+  auto wavefronts = [&](unsigned int rmask, unsigned int side) {
+    int n = 0, seen = 0;
+    for (int b = 0; b < a.tb && seen < 5; ++b) {
+      if ((rmask >> b) & 1u) continue;
+      ++seen;
+      n += (side >> (a.nsum + b)) & 1u;
+    }
+    return std::max(1, (1 << n) / 8);
+  };
+  const unsigned int uA = a.op[a.gA].umask, uB = a.op[a.gB].umask;
+  const unsigned int r2 = (1u << a.reg_a) | (1u << a.reg_b);
+  // (a wider block costs registers: taken only for a quarter fewer wavefronts or more)
+  const int cost22 = 2 * wavefronts(r2, uA) + 2 * wavefronts(r2, uB);  // per 4 outputs
+  int best = 3 * cost22 / 2;  // per 8 outputs, x 3/4
+  if (a.reg_b2 >= 0 && a.tb >= 4) {
+    const unsigned int rm = r2 | (1u << a.reg_b2);
+    const int c = 2 * wavefronts(rm, uA) + 4 * wavefronts(rm, uB);
+    if (c < best) {
+      best = c;
+      a.wide = 1;
+    }
+  }
+  if (a.reg_a2 >= 0 && a.tb >= 4) {
+    const unsigned int rm = r2 | (1u << a.reg_a2);
+    const int c = 4 * wavefronts(rm, uA) + 2 * wavefronts(rm, uB);
+    if (c < best) {
+      best = c;
+      a.wide = 2;
+    }
+  }
 }
 
 unsigned int gemm_tile_inner(const GemmArgs& a, int u) {
@@ -2120,16 +2187,21 @@ static size_t tma_smem(const GemmArgs& a, int nmove) {
 typedef void (*TmaFn)(const GemmArgs, const CUtensorMap, const CUtensorMap, int, int, float*,
                       GMeta*);
 
-static TmaFn tma_fn(int nsum) {
+template <int WIDE>
+static TmaFn tma_fn_w(int nsum) {
   switch (nsum) {
-    case 1: return k_gemm_tma<1>;
-    case 2: return k_gemm_tma<2>;
-    case 3: return k_gemm_tma<3>;
-    case 4: return k_gemm_tma<4>;
-    case 5: return k_gemm_tma<5>;
-    case 6: return k_gemm_tma<6>;
+    case 1: return k_gemm_tma<1, WIDE>;
+    case 2: return k_gemm_tma<2, WIDE>;
+    case 3: return k_gemm_tma<3, WIDE>;
+    case 4: return k_gemm_tma<4, WIDE>;
+    case 5: return k_gemm_tma<5, WIDE>;
+    case 6: return k_gemm_tma<6, WIDE>;
     default: return nullptr;
   }
+}
+
+static TmaFn tma_fn(int nsum, int wide) {
+  return wide == 1 ? tma_fn_w<1>(nsum) : (wide == 2 ? tma_fn_w<2>(nsum) : tma_fn_w<0>(nsum));
 }
 
 bool gemm_stream_ok(const GemmArgs& a) {
@@ -2206,7 +2278,7 @@ int gemm_launch(const GemmArgs& a, int mode, float* data, GMeta* meta, cudaStrea
     };
     // tensor-copy staging when the rows line up and the maps encode; the ring as
     // deep as it can be without fewer resident blocks than a ring of 2
-    TmaFn fn = tma_fn(a.nsum);
+    TmaFn fn = tma_fn(a.nsum, a.wide);
     if (a.use_tma && a.err && fn && tma_smem(a, 2) <= kTileSmemMax && rows_aligned(a)) {
       const unsigned int L = (a.nsum + a.tb >= 32) ? 0xffffffffu : ((1u << (a.nsum + a.tb)) - 1u);
       const int ra = 1 << (__builtin_popcount(a.op[a.gA].umask & L) - a.nsum);

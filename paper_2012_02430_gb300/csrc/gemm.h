@@ -36,6 +36,8 @@ struct GemmArgs {
   int gA, gB, tb, fold_a, fold_b;
   unsigned int tile_inner;  // high output indices (above tb) visited innermost
   int reg_a, reg_b;         // register-blocking bits of the tile (-1: none)
+  int reg_a2, reg_b2;       // second A-only / B-only bits (-1: none)
+  int wide;                 // k_gemm_tma block: 0 2 x 2, 1 2 x 4 (reg_b2), 2 4 x 2 (reg_a2)
   int tA, tB, tC;           // triangle form: the large operands
   unsigned int tK, tX, tY;  // triangle form: summed bits of each class
   int use_tma;              // GEMM_TILE: stage the blocks with tensor copies (TMA)
@@ -57,9 +59,10 @@ int gemm_tile_stay(const GemmArgs& a);
 // The streaming GEMM kernel applies: the smaller operand (at most 12 indices, nothing
 // folded into the larger one) is staged whole per slice, one thread per row of the other.
 bool gemm_stream_ok(const GemmArgs& a);
-// Register-blocking bits of the GEMM_TILE kernel: an A-only and a B-only output
-// bit inside the tile, or -1, -1.
-void gemm_tile_regs(const GemmArgs& a, int& reg_a, int& reg_b);
+// Register-blocking bits of the GEMM_TILE kernels (an A-only and a B-only output bit
+// inside the tile, or -1, -1; second bits for the wider blocks) and the block shape
+// of k_gemm_tma (fewest shared-memory wavefronts per output).
+void gemm_tile_regs(GemmArgs& a);
 
 // Triangle form (three large operands): output indices per tile (0: not taken)
 // and the launch (one kernel).
