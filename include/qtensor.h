@@ -338,9 +338,15 @@ void qt_mlp_free(qt_mlp* mlp);
  *                  bounded waits raise QT_ETIMEOUT in qt_contract), when every
  *                  block starts on a whole row; 0: 16-byte cp.async copies by
  *                  every thread. Both give the same results, bit for bit.
+ *   QT_OPT_CONCURRENT 1 (default): in a captured graph the slice-phase launches
+ *                  that touch disjoint workspace ranges (results, operands and
+ *                  scratch, compared as element ranges since the arena reuses
+ *                  memory) run on up to 4 streams at once, joined by events;
+ *                  0: one stream. Results are the same either way. Discards the
+ *                  prepared schedule.
  * Errors: QT_EINVAL for a null network or an unknown option. */
 enum { QT_OPT_FUSION = 1, QT_OPT_GRAPHS = 2, QT_OPT_GEMM = 3, QT_OPT_SEGMENTS = 4,
-       QT_OPT_TRIANGLE = 5, QT_OPT_TMA = 6 };
+       QT_OPT_TRIANGLE = 5, QT_OPT_TMA = 6, QT_OPT_CONCURRENT = 7 };
 qt_status qt_set_option(qt_net* net, int32_t option, int64_t value);
 
 /*
@@ -363,8 +369,10 @@ qt_status qt_autotune(qt_net* net, void* workspace, size_t workspace_bytes, void
  * cost per launch); qt_profile(net, 0) stops. Either call drops the records.
  * qt_profile_read waits for the recorded events and writes a JSON array, one
  * object per launch: {"step", "kernel" (0 flat bucket, 1 tiled bucket,
- * 2 slice finalize + reduce), "slices", "bytes", "flops" (the ledger's
- * algorithmic counts for that launch), "ms"} into buf (as qt_stats).
+ * 2 slice finalize + reduce, 3 GEMM form by pack + GEMM kernels, 4 tiled GEMM
+ * form, 5 segment run, 6 triangle form, 7 streaming GEMM form), "slices",
+ * "bytes", "flops" (the ledger's algorithmic counts for that launch), "ms"}
+ * into buf (as qt_stats).
  * Errors: QT_EINVAL for a null network; QT_ECUDA if an event fails.
  */
 qt_status qt_profile(qt_net* net, int32_t enable);

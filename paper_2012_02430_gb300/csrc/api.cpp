@@ -540,6 +540,10 @@ qt_status qt_set_option(qt_net* net, int32_t option, int64_t value) {
       net->seg_max_u = value >= 2 ? (int)value : 12;
       net->sched = qt::Schedule();  // prepare again
       break;
+    case QT_OPT_CONCURRENT:
+      net->concurrent = value != 0;
+      net->sched = qt::Schedule();  // prepare again
+      break;
     case QT_OPT_TRIANGLE:
       net->force_tri = value != 0;
       net->sched = qt::Schedule();  // prepare again

@@ -1090,6 +1090,7 @@ struct LaunchDesc {
   long long seg_off = 0;             // kind 5: byte offset of its records in the segment table
   int seg_count = 0, stage_count = 0, level_count = 0;
   long long seg_arena = 0;           // kind 5: shared-arena elements per block
+  int g_last = -1;                   // last schedule group the launch covers (kind 5: a run)
 };
 
 constexpr int VARIANT_GEMM = 3;
@@ -1231,9 +1232,23 @@ static void fill_tri(const Schedule& S, const SGroup& g, long long nslices, Gemm
     if (!((AB >> (g.nsum + a.tb + b)) & 1u)) a.tile_inner |= 1u << b;
 }
 
+// Concurrency of the slice-phase launches inside a captured graph: per launch, the
+// stream it goes to (0: the capturing stream) and the launches on other streams it
+// waits for; a launch whose event someone waits for records it.
+constexpr int kStreams = 4;
+struct LaunchPlan {
+  std::vector<int> stream;
+  std::vector<std::vector<int>> wait;
+  std::vector<char> record;
+};
+
 struct EngineCache {
   uint64_t generation = 0;
   std::vector<LaunchDesc> prefix, slice;
+  LaunchPlan plan;
+  cudaStream_t aux[kStreams] = {};       // aux[1..] join the capture by a fork event
+  std::vector<cudaEvent_t> events;       // one per slice-phase launch
+  cudaEvent_t fork = nullptr, join[kStreams] = {};
   std::vector<unsigned char> segtab;  // per segment launch: step records, stage records, levels
   const void* seg_ws = nullptr;    // workspace the table was last copied to
   uint64_t seg_gen = 0;
@@ -1246,6 +1261,12 @@ struct EngineCache {
   ~EngineCache() {
     if (exec) cudaGraphExecDestroy(exec);
     if (capture) cudaStreamDestroy(capture);
+    for (int k = 1; k < kStreams; ++k) {
+      if (aux[k]) cudaStreamDestroy(aux[k]);
+      if (join[k]) cudaEventDestroy(join[k]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
   }
 };
 
@@ -1389,6 +1410,76 @@ static bool make_desc(const Schedule& S, int gi, long long nslices, LaunchDesc& 
     d.grid = (unsigned)std::max<long long>(1, std::min<long long>(blocks, (long long)num_sms() * 16));
   }
   return true;
+}
+
+// Which slice-phase launches may run at the same time. A launch reads its groups'
+// per-slice operands and writes their results and their GEMM / triangle scratch
+// (counted whatever kernel the autotuner picks); two launches conflict when one
+// writes arena elements the other reads or writes (the arena reuses memory by
+// liveness, so tensors are compared as element ranges). A launch goes to the stream
+// whose last launch is its latest conflict, else to the least recently used stream,
+// and waits for its latest conflict on every other stream.
+static void plan_streams(const Schedule& S, const std::vector<LaunchDesc>& list, LaunchPlan& P) {
+  struct Span {
+    int64_t lo, hi;
+  };
+  auto span = [](int64_t off, int64_t n) { return Span{off, off + (n + 63) / 64 * 64}; };
+  const size_t n = list.size();
+  std::vector<std::vector<Span>> rd(n), wr(n);
+  for (size_t x = 0; x < n; ++x) {
+    const LaunchDesc& d = list[x];
+    const int last = d.g_last >= 0 ? d.g_last : d.group;
+    for (int gi = d.group; gi <= last; ++gi) {
+      const SGroup& g = S.groups[gi];
+      for (int32_t tid : g.ops) {
+        const STensor& t = S.tensors[tid];
+        if (t.kind == TK_SLICE && !t.virt) rd[x].push_back(span(t.offset, (int64_t)1 << t.rank));
+      }
+      const STensor& o = S.tensors[g.out];
+      if (o.kind == TK_SLICE) wr[x].push_back(span(o.offset, (int64_t)1 << o.rank));
+      if (g.region == 1 && g.gemm) {
+        const int kb = __builtin_popcount(g.mK), bt = __builtin_popcount(g.mBt);
+        wr[x].push_back(span(g.scratch_a, (int64_t)1 << (bt + __builtin_popcount(g.mM) + kb)));
+        wr[x].push_back(span(g.scratch_b, (int64_t)1 << (bt + __builtin_popcount(g.mN) + kb)));
+      }
+      if (g.region == 1 && g.tri) wr[x].push_back(span(g.scratch_t, (int64_t)1 << g.tCbits));
+    }
+  }
+  auto meet = [](const std::vector<Span>& a, const std::vector<Span>& b) {
+    for (const Span& p : a)
+      for (const Span& q : b)
+        if (p.lo < q.hi && q.lo < p.hi) return true;
+    return false;
+  };
+  P.stream.assign(n, 0);
+  P.wait.assign(n, {});
+  P.record.assign(n, 0);
+  int lastl[kStreams];
+  for (int k = 0; k < kStreams; ++k) lastl[k] = -1;
+  for (size_t m = 0; m < n; ++m) {
+    int latest[kStreams];  // latest conflicting launch on each stream
+    for (int k = 0; k < kStreams; ++k) latest[k] = -1;
+    int top = -1;
+    for (size_t l = 0; l < m; ++l)
+      if (meet(wr[l], rd[m]) || meet(wr[l], wr[m]) || meet(rd[l], wr[m])) {
+        latest[P.stream[l]] = std::max(latest[P.stream[l]], (int)l);
+        top = std::max(top, (int)l);
+      }
+    int st = -1;
+    if (top >= 0 && lastl[P.stream[top]] == top) st = P.stream[top];
+    if (st < 0) {
+      st = 0;
+      for (int k = 1; k < kStreams; ++k)
+        if (lastl[k] < lastl[st]) st = k;
+    }
+    P.stream[m] = st;
+    for (int k = 0; k < kStreams; ++k)
+      if (k != st && latest[k] >= 0) {
+        P.wait[m].push_back(latest[k]);
+        P.record[latest[k]] = 1;
+      }
+    lastl[st] = (int)m;
+  }
 }
 
 template <typename R>
@@ -1571,6 +1662,7 @@ static bool build_cache(qt_net* net, EngineCache& c, std::string& err) {
       append(recs.data(), recs.size() * sizeof(KStep));
       append(stages.data(), stages.size() * sizeof(SegStage));
       append(levels.data(), levels.size() * sizeof(SegLevel));
+      d.g_last = (*list)[j - 1].group;
       merged.push_back(d);
       i = j;
     }
@@ -1580,6 +1672,7 @@ static bool build_cache(qt_net* net, EngineCache& c, std::string& err) {
     err = "segment tables exceed their workspace region";
     return false;
   }
+  plan_streams(S, c.slice, c.plan);
   c.seg_ws = nullptr;
   if (c.exec) cudaGraphExecDestroy(c.exec);
   c.exec = nullptr;
@@ -1631,7 +1724,9 @@ static void launch_desc(qt_net* net, const LaunchDesc& d0, long long nslices, lo
   }
   R* data = reinterpret_cast<R*>(base);
   Meta* meta = reinterpret_cast<Meta*>(base + S.off_meta);
-  ProfRec pr{S.groups[d0.group].first, d0.kind, nslices, d0.bytes * nslices, d0.flops * nslices,
+  // (profile class 7: the GEMM form's streaming kernel)
+  ProfRec pr{S.groups[d0.group].first, d0.kind == 4 && d0.ga.use_stream ? 7 : d0.kind, nslices,
+             d0.bytes * nslices, d0.flops * nslices,
              nullptr, nullptr};
   if (net->prof) prof_begin(net, s, pr);
   if (d0.kind == 6) {
@@ -1672,7 +1767,8 @@ static void launch_desc(qt_net* net, const LaunchDesc& d0, long long nslices, lo
 
 template <typename R>
 static qt_status enqueue_run(qt_net* net, EngineCache& c, long long first, long long count,
-                             char* base, cudaStream_t s, double* d_out, std::string& err) {
+                             char* base, cudaStream_t s, double* d_out, std::string& err,
+                             bool fork = false) {
   const Schedule& S = net->sched;
   const size_t ngm = n_gate_meta(S);
   Meta* meta = reinterpret_cast<Meta*>(base + S.off_meta);
@@ -1696,7 +1792,23 @@ static qt_status enqueue_run(qt_net* net, EngineCache& c, long long first, long 
                                  (size_t)(S.n_slice_meta_tensors * S.batch) * sizeof(Meta), s),
                  "reset slice meta", err))
       return QT_ECUDA;
-    for (const LaunchDesc& d : c.slice) launch_desc<R>(net, d, nb, b0, base, s);
+    if (fork) {
+      // fork: the other streams join the capture behind everything issued so far
+      cudaEventRecord(c.fork, s);
+      for (int k = 1; k < kStreams; ++k) cudaStreamWaitEvent(c.aux[k], c.fork, 0);
+      for (size_t x = 0; x < c.slice.size(); ++x) {
+        cudaStream_t st = c.plan.stream[x] ? c.aux[c.plan.stream[x]] : s;
+        for (int w : c.plan.wait[x]) cudaStreamWaitEvent(st, c.events[w], 0);
+        launch_desc<R>(net, c.slice[x], nb, b0, base, st);
+        if (c.plan.record[x]) cudaEventRecord(c.events[x], st);
+      }
+      for (int k = 1; k < kStreams; ++k) {  // join
+        cudaEventRecord(c.join[k], c.aux[k]);
+        cudaStreamWaitEvent(s, c.join[k], 0);
+      }
+    } else {
+      for (const LaunchDesc& d : c.slice) launch_desc<R>(net, d, nb, b0, base, s);
+    }
     ProfRec pr{-1, 2, nb, 0, 0, nullptr, nullptr};
     if (net->prof) prof_begin(net, s, pr);
     net->launches += 2;
@@ -1866,11 +1978,31 @@ static qt_status run_impl(qt_net* net, long long first, long long count, char* b
     if (!c.capture &&
         !cuda_ok(cudaStreamCreateWithFlags(&c.capture, cudaStreamNonBlocking), "capture stream", err))
       return QT_ECUDA;
+    // streams and events of the concurrent slice phase (fork / join inside the capture)
+    const bool fork = net->concurrent && c.slice.size() > 1;
+    if (fork) {
+      for (int k = 1; k < kStreams; ++k) {
+        if (!c.aux[k] && !cuda_ok(cudaStreamCreateWithFlags(&c.aux[k], cudaStreamNonBlocking),
+                                  "aux stream", err))
+          return QT_ECUDA;
+        if (!c.join[k] &&
+            !cuda_ok(cudaEventCreateWithFlags(&c.join[k], cudaEventDisableTiming), "event", err))
+          return QT_ECUDA;
+      }
+      if (!c.fork && !cuda_ok(cudaEventCreateWithFlags(&c.fork, cudaEventDisableTiming), "event", err))
+        return QT_ECUDA;
+      while (c.events.size() < c.slice.size()) {
+        cudaEvent_t e = nullptr;
+        if (!cuda_ok(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event", err))
+          return QT_ECUDA;
+        c.events.push_back(e);
+      }
+    }
     if (!cuda_ok(cudaStreamBeginCapture(c.capture, cudaStreamCaptureModeThreadLocal),
                  "begin capture", err))
       return QT_ECUDA;
     const int64_t launches0 = net->launches;
-    qt_status r = enqueue_run<R>(net, c, first, count, base, c.capture, d_out, err);
+    qt_status r = enqueue_run<R>(net, c, first, count, base, c.capture, d_out, err, fork);
     net->launches = launches0;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(c.capture, &g);

@@ -226,6 +226,7 @@ struct qt_net {
   bool force_stream = false;     // ... with the streaming kernel where it applies
   bool segments = true;          // runs of small launches as one segment launch
   int seg_max_u = 12;            // union indices of a step a segment may hold (at most 13)
+  bool concurrent = true;        // captured graphs run independent slice launches concurrently
   bool force_tri = false;        // triangle-form launches by default where they apply
   bool tma = true;               // tiled GEMM stages its blocks with tensor copies (TMA)
   int64_t tma_launches = 0;      // tiled GEMM launches that took the tensor-copy staging
