@@ -658,16 +658,41 @@ __global__ void __launch_bounds__(256) k_gemm_stream(const GemmArgs a, float* da
   const float2* d2 = reinterpret_cast<const float2*>(data);
   long long cur = -1;
   float sc = 1.f, mx = 0.f;
-  // kStreamRows rows per thread per pass (consecutive runs of the block's rows), so
-  // that several row loads are in flight
+  // kStreamRows rows per thread per pass (consecutive runs of the block's rows), the
+  // next pass's rows loaded before this pass's products (two register sets). Output
+  // position and S row split into this thread's low 8 row bits (once) and the
+  // block-uniform high bits (pdep and pext add over disjoint bit sets).
   const long long span = (long long)blockDim.x * kStreamRows;
-  for (long long base = (long long)blockIdx.x * span; base < total; base += (long long)gridDim.x * span) {
+  const long long step = (long long)gridDim.x * span;
+  __syncthreads();  // the byte tables and nTab / oTab are complete
+  const unsigned int oLo = pdep_lut(Lg, threadIdx.x & 255u);
+  const unsigned int sLo = pext_lut(Ps, oLo);
+  float4 gv[kStreamRows][K / 2], gn[kStreamRows][K / 2];
+  auto load_pass = [&](long long b, float4 (&dst)[kStreamRows][K / 2]) {
+    const long long ib = b >> rbits;
+    const float2* gb = d2 + op_slice_base(OG, ib, (unsigned long long)(a.slice_first + ib));
+#pragma unroll
+    for (int r = 0; r < kStreamRows; ++r) {
+      const unsigned int rG = (unsigned int)((b + threadIdx.x + r * blockDim.x) & (rows - 1));
+      const float4* gp = reinterpret_cast<const float4*>(gb + (long long)rG * K);
+#pragma unroll
+      for (int q = 0; q < K / 2; ++q) dst[r][q] = __ldcs(gp + q);
+    }
+  };
+  long long base = (long long)blockIdx.x * span;
+  if (base < total) load_pass(base, gn);
+  for (; base < total; base += step) {
+#pragma unroll
+    for (int r = 0; r < kStreamRows; ++r)
+#pragma unroll
+      for (int q = 0; q < K / 2; ++q) gv[r][q] = gn[r][q];
+    if (base + step < total) load_pass(base + step, gn);
     const long long i = base >> rbits;  // the same for the whole block (rows is a multiple of span)
-    const unsigned long long sid = (unsigned long long)(a.slice_first + i);
     if (i != cur) {
       if (cur >= 0) flush_max(a, meta, cur, mx);
       mx = 0.f;
       __syncthreads();  // the tables are built; the last slice's S' is no longer read
+      const unsigned long long sid = (unsigned long long)(a.slice_first + i);
       const long long sb = fold_s ? scr_s + i * a.scratch_stride : op_slice_base(OS, i, sid);
       const float ss = fold_s ? 1.f
           : pow2_neg_g(scale_exp_g(meta[OS.meta + (OS.meta_per_slice ? i : 0)].maxabs));
@@ -680,21 +705,13 @@ __global__ void __launch_bounds__(256) k_gemm_stream(const GemmArgs a, float* da
       cur = i;
       __syncthreads();
     }
-    const float2* gbase = d2 + op_slice_base(OG, i, sid);
     float2* out = reinterpret_cast<float2*>(data) + a.out_base + i * a.out_slice_stride;
-    float4 gv[kStreamRows][K / 2];
 #pragma unroll
     for (int r = 0; r < kStreamRows; ++r) {
-      const unsigned int rG = (unsigned int)((base + threadIdx.x + r * blockDim.x) & (rows - 1));
-      const float4* gp = reinterpret_cast<const float4*>(gbase + (long long)rG * K);
-#pragma unroll
-      for (int q = 0; q < K / 2; ++q) gv[r][q] = __ldcs(gp + q);
-    }
-#pragma unroll
-    for (int r = 0; r < kStreamRows; ++r) {
-      const unsigned int rG = (unsigned int)((base + threadIdx.x + r * blockDim.x) & (rows - 1));
-      const unsigned int oG = pdep_lut(Lg, rG);
-      const unsigned int sG = pext_lut(Ps, oG);
+      // high row bits: the same for the whole block in this pass
+      const unsigned int rHi = (unsigned int)((base + r * blockDim.x) & (rows - 1)) & ~255u;
+      const unsigned int oG = oLo | pdep_lut(Lg, rHi);
+      const unsigned int sG = sLo + pext_lut(Ps, oG & ~oLo);
       for (int nb = 0; nb < (1 << nN); ++nb) {
         const float4* sp = reinterpret_cast<const float4*>(sS + (size_t)(sG + nTab[nb]) * K);
         float cr = 0.f, ci = 0.f;
