@@ -108,6 +108,22 @@ __device__ __forceinline__ unsigned long long pext64(unsigned long long x, unsig
   return r;
 }
 
+// pext over a 32-bit mask for 32-bit x, one run of adjacent mask bits at a time (the
+// union index of the flat and segment kernels fits 32 bits)
+__device__ __forceinline__ unsigned int pext32r(unsigned int x, unsigned int m) {
+  unsigned int r = 0;
+  int k = 0;
+  while (m) {
+    const int b = __ffs(m) - 1;
+    const unsigned int next = m + (m & (0u - m));  // the lowest run cleared, a carry above it
+    const int len = __popc(m & ~next);
+    r |= ((x >> b) & (0xffffffffu >> (32 - len))) << k;
+    k += len;
+    m &= next;
+  }
+  return r;
+}
+
 // binary exponent s with maxabs * 2^-s in [0.5, 1); 0 for a zero tensor
 __device__ __forceinline__ int scale_exp(unsigned int maxabs_bits) {
   if (maxabs_bits == 0u) return 0;
@@ -194,7 +210,7 @@ __global__ void __launch_bounds__(256) k_bucket_flat(const KStep st, R* data, Me
         const int s = scale_exp(mt.maxabs);
         Eout += mt.E + s;
         if (o.level != 0) continue;
-        long long off = o.base + i * o.slice_stride + (long long)pext64(I, o.umask);
+        long long off = o.base + i * o.slice_stride + (long long)pext32r((unsigned int)I, o.umask);
         if (o.smask) off += (long long)(pext64(sid, o.smask) << o.sshift);
         const R sc = pow2_neg<R>(s);
         R r0, i0, r1, i1;
@@ -209,7 +225,7 @@ __global__ void __launch_bounds__(256) k_bucket_flat(const KStep st, R* data, Me
         for (int j = 0; j < st.m; ++j) {
           const KOp& o = st.op[j];
           if (o.level != l) continue;
-          long long off = o.base + i * o.slice_stride + (long long)pext64(I, o.umask);
+          long long off = o.base + i * o.slice_stride + (long long)pext32r((unsigned int)I, o.umask);
           if (o.smask) off += (long long)(pext64(sid, o.smask) << o.sshift);
           const R sc = pow2_neg<R>(scale_exp(meta[o.meta + (o.meta_per_slice ? i : 0)].maxabs));
           using C2 = typename CT<R>::c2;
@@ -310,7 +326,7 @@ __device__ __forceinline__ void seg_pair(const KStep& st, const R* sc, bool acti
     vr0[j] = vi0[j] = vr1[j] = vi1[j] = R(0);
     if (active) {
       const KOp& o = st.op[j];
-      const long long loc = (long long)pext64(I, o.umask);
+      const long long loc = (long long)pext32r((unsigned int)I, o.umask);
       if (o.soff >= 0) {
         const R* p = arena + 2 * (o.soff + loc);
         vr0[j] = p[0];
