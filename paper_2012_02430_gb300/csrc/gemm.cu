@@ -667,6 +667,14 @@ __global__ void __launch_bounds__(256) k_gemm_stream(const GemmArgs a, float* da
   __syncthreads();  // the byte tables and nTab / oTab are complete
   const unsigned int oLo = pdep_lut(Lg, threadIdx.x & 255u);
   const unsigned int sLo = pext_lut(Ps, oLo);
+  // a row's index is (pass base) + r * 256 + (thread): three disjoint bit ranges, so its
+  // output position and S row are sums of three parts; the r parts are constants
+  unsigned int oR[kStreamRows], sR[kStreamRows];
+#pragma unroll
+  for (int r = 0; r < kStreamRows; ++r) {
+    oR[r] = pdep_lut(Lg, (unsigned int)(r * 256));
+    sR[r] = pext_lut(Ps, oR[r]);
+  }
   float4 gv[kStreamRows][K / 2], gn[kStreamRows][K / 2];
   auto load_pass = [&](long long b, float4 (&dst)[kStreamRows][K / 2]) {
     const long long ib = b >> rbits;
@@ -706,12 +714,12 @@ __global__ void __launch_bounds__(256) k_gemm_stream(const GemmArgs a, float* da
       __syncthreads();
     }
     float2* out = reinterpret_cast<float2*>(data) + a.out_base + i * a.out_slice_stride;
+    const unsigned int oB = pdep_lut(Lg, (unsigned int)(base & (rows - 1)));  // pass base
+    const unsigned int sB = pext_lut(Ps, oB);
 #pragma unroll
     for (int r = 0; r < kStreamRows; ++r) {
-      // high row bits: the same for the whole block in this pass
-      const unsigned int rHi = (unsigned int)((base + r * blockDim.x) & (rows - 1)) & ~255u;
-      const unsigned int oG = oLo | pdep_lut(Lg, rHi);
-      const unsigned int sG = sLo + pext_lut(Ps, oG & ~oLo);
+      const unsigned int oG = oLo | oR[r] | oB;
+      const unsigned int sG = sLo + sR[r] + sB;
       for (int nb = 0; nb < (1 << nN); ++nb) {
         const float4* sp = reinterpret_cast<const float4*>(sS + (size_t)(sG + nTab[nb]) * K);
         float cr = 0.f, ci = 0.f;
