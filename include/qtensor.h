@@ -332,12 +332,16 @@ void qt_mlp_free(qt_mlp* mlp);
  *                  out = sum_k w(k) sum_x A[k,x] sum_y B[k,y] C'[x,y], tiled over
  *                  the lowest U bits in shared memory. 0 (default): only the
  *                  autotuner may pick it. Discards the prepared schedule.
- *   QT_OPT_TMA     1 (default): the FP32 tiled GEMM stages its operand blocks
- *                  with tensor copies (cp.async.bulk.tensor over 2-D tensor maps
- *                  of the workspace, completing on shared-memory mbarriers;
- *                  bounded waits raise QT_ETIMEOUT in qt_contract), when every
- *                  block starts on a whole row; 0: 16-byte cp.async copies by
- *                  every thread. Both give the same results, bit for bit.
+ *   QT_OPT_TMA     1 (default): the FP32 tiled GEMM and the triangle form
+ *                  stage their operand blocks with tensor copies
+ *                  (cp.async.bulk.tensor over 2-D tensor maps of the workspace,
+ *                  completing on shared-memory mbarriers; bounded waits raise
+ *                  QT_ETIMEOUT in qt_contract), when every block starts on a
+ *                  whole row; 0: cp.async copies by every thread. 2, 3, 4: as
+ *                  1 with the tiled GEMM's register block fixed instead of
+ *                  chosen by shared-memory wavefronts: 2 x 2 (2), 2 x 4 where
+ *                  a second B-only index exists (3), 4 x 2 where a second
+ *                  A-only index exists (4). Other values: QT_EINVAL.
  *   QT_OPT_CONCURRENT 1 (default): in a captured graph the slice-phase launches
  *                  that touch disjoint workspace ranges (results, operands and
  *                  scratch, compared as element ranges since the arena reuses

@@ -1183,7 +1183,7 @@ static void fill_gemm(const Schedule& S, const SGroup& g, long long nslices, Gem
   a.tile_inner = gemm_tile_inner(a, g.u);
   a.stay = gemm_tile_stay(a);
   a.ws_elems = (long long)(S.total_bytes / 8);
-  gemm_tile_regs(a);
+  gemm_tile_regs(a, S.tma_block);
 }
 
 // Triangle form of a launch (three large operands; see gemm.cu k_tri_tile).

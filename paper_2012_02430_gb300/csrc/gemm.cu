@@ -1962,7 +1962,7 @@ int gemm_tile_bits(const GemmArgs& a, int u) {
   return 0;
 }
 
-void gemm_tile_regs(GemmArgs& a) {
+void gemm_tile_regs(GemmArgs& a, int block_mode) {
   // the highest (reg_x) and second highest (reg_x2) A-only and B-only output bits
   // inside the tile (-1: none)
   a.reg_a = a.reg_b = a.reg_a2 = a.reg_b2 = -1;
@@ -1993,6 +1993,13 @@ void gemm_tile_regs(GemmArgs& a) {
     }
     return std::max(1, (1 << n) / 8);
   };
+  if (block_mode == 1) return;
+  if (block_mode == 2 || block_mode == 3) {  // a wide block whenever a second bit exists
+    const bool b_ok = a.reg_b2 >= 0 && a.tb >= 4, a_ok = a.reg_a2 >= 0 && a.tb >= 4;
+    if (block_mode == 2) a.wide = b_ok ? 1 : (a_ok ? 2 : 0);
+    else a.wide = a_ok ? 2 : (b_ok ? 1 : 0);
+    return;
+  }
   const unsigned int uA = a.op[a.gA].umask, uB = a.op[a.gB].umask;
   const unsigned int r2 = (1u << a.reg_a) | (1u << a.reg_b);
   // (a wider block costs registers: taken only for a quarter fewer wavefronts or more)

@@ -62,7 +62,9 @@ bool gemm_stream_ok(const GemmArgs& a);
 // Register-blocking bits of the GEMM_TILE kernels (an A-only and a B-only output bit
 // inside the tile, or -1, -1; second bits for the wider blocks) and the block shape
 // of k_gemm_tma (fewest shared-memory wavefronts per output).
-void gemm_tile_regs(GemmArgs& a);
+// block_mode: 0 chosen by shared-memory wavefronts, 1 always 2 x 2, 2 (3) 2 x 4 (4 x 2)
+// whenever that side has a second bit, else the other wide block, else 2 x 2.
+void gemm_tile_regs(GemmArgs& a, int block_mode = 0);
 
 // Triangle form (three large operands): output indices per tile (0: not taken)
 // and the launch (one kernel).

@@ -137,6 +137,7 @@ struct Schedule {
   bool force_gemm = false;       // copy of the network option at compile time
   bool force_stream = false;     // copy of the network option at compile time
   bool force_tri = false;        // copy of the network option at compile time
+  int tma_block = 0;             // copy of the network option at compile time
   bool fused = true;             // steps grouped into fused launches
   uint64_t generation = 0;      // changes with every compile
   int precision = QT_FP32_SIMT;
@@ -230,6 +231,7 @@ struct qt_net {
   bool force_tri = false;        // triangle-form launches by default where they apply
   bool tma = true;               // tiled GEMM stages its blocks with tensor copies (TMA)
   int64_t tma_launches = 0;      // tiled GEMM launches that took the tensor-copy staging
+  int tma_block = 0;             // tiled GEMM register block: 0 chosen, 1 2 x 2, 2 / 3 wide
   int64_t stream_launches = 0;   // GEMM-form launches by the streaming kernel
   void* engine = nullptr;        // engine.cu: launch descriptors and graph cache
   ~qt_net();

@@ -64,3 +64,25 @@ def test_tma_triangle_matches_oracle(qt, case):
     assert launches[0] == 0
     if n == 80:
         assert launches[1] > 0
+
+
+BLOCK_CASES = [(44, 2, 14, -4), (60, 2, 18, -4), (24, 3, 15, -4), (80, 2, 1002, 26 - 35)]
+
+
+@pytest.mark.parametrize("mode", [2, 3, 4])
+@pytest.mark.parametrize("case", BLOCK_CASES)
+def test_tma_register_blocks(qt, case, mode):
+    """Every register-block shape of the tensor-copy GEMM (2 x 2, 2 x 4, 4 x 2, forced by
+    QT_OPT_TMA = 2, 3, 4 wherever the tile allows it) against the FP64 oracle."""
+    n, p, seed, off = case
+    edges, gammas, betas, z, tensors, nv, norm, adj = oracle_problem(n, p, seed)
+    net = qt.Network(edges, n, p, gammas, betas, z)
+    qt.qt_set_option(net.handle, qt.QT_OPT_GEMM, 1)
+    qt.qt_set_option(net.handle, qt.QT_OPT_TMA, mode)
+    w = net.order(0)
+    net.slice(w + off, 6, 1)
+    net.prepare(0, batch=4)
+    amp = net.contract(0)
+    assert net.stats()["tma_gemm_launches"] > 0
+    ref, _ = oracle_amplitude(tensors, norm, oracle_plan(adj, 0, w + off, 6, 1))
+    assert rel_err(amp, ref) <= 1e-5, (mode, amp, ref)

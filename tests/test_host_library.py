@@ -433,3 +433,14 @@ def test_gemm_option_range(qt):
     for v in (-1, 3):
         with pytest.raises(qt.QtError):
             qt.qt_set_option(net.handle, qt.QT_OPT_GEMM, v)
+
+
+def test_tma_option_range(qt):
+    """QT_OPT_TMA takes 0..4 (off, on, and on with a fixed register block); other values
+    are refused."""
+    net = qt.Network([(0, 1), (1, 2), (2, 0)], 3, 1, [0.3], [0.2], [0, 1, 0])
+    for v in range(5):
+        qt.qt_set_option(net.handle, qt.QT_OPT_TMA, v)
+    for v in (-1, 5):
+        with pytest.raises(qt.QtError):
+            qt.qt_set_option(net.handle, qt.QT_OPT_TMA, v)
