@@ -1240,12 +1240,7 @@ static void fill_tri(const Schedule& S, const SGroup& g, long long nslices, Gemm
   a.tY = g.tY;
   a.tb = tri_tile_bits(a, g.u);
   a.ws_elems = (long long)(S.total_bytes / 8);
-  // consecutive tiles share A's or B's block: high output bits missing from A or B innermost
-  const int hb = g.u - g.nsum - a.tb;
-  const unsigned int AB = a.op[g.tA].umask & a.op[g.tB].umask;
-  a.tile_inner = 0;
-  for (int b = 0; b < hb && a.tb > 0; ++b)
-    if (!((AB >> (g.nsum + a.tb + b)) & 1u)) a.tile_inner |= 1u << b;
+  a.tile_inner = tri_tile_inner(a, g.u);
 }
 
 // Concurrency of the slice-phase launches inside a captured graph: per launch, the

@@ -2096,6 +2096,17 @@ static bool tri_rows_aligned(const GemmArgs& a) {
   return true;
 }
 
+unsigned int tri_tile_inner(const GemmArgs& a, int u) {
+  // consecutive tiles share A's or B's block: the high output bits missing from A or B
+  // are visited innermost
+  const int hb = u - a.nsum - a.tb;
+  const unsigned int AB = a.op[a.tA].umask & a.op[a.tB].umask;
+  unsigned int inner = 0;
+  for (int b = 0; b < hb && a.tb > 0; ++b)
+    if (!((AB >> (a.nsum + a.tb + b)) & 1u)) inner |= 1u << b;
+  return inner;
+}
+
 int tri_launch(const GemmArgs& a, float* data, GMeta* meta, cudaStream_t s, int sms,
                bool* used_tma) {
   if (used_tma) *used_tma = false;
@@ -2116,34 +2127,45 @@ int tri_launch(const GemmArgs& a, float* data, GMeta* meta, cudaStream_t s, int 
     k_tri_fold<<<(unsigned)std::max<long long>(1, g), 256, 0, s>>>(a, data, meta);
     ++n;
   }
-  const long long ntiles = a.nslices << (u - a.nsum - a.tb);
-  // tensor-copy staging when the kernel exists for the shape and the rows line up
+  // tensor-copy staging when the kernel exists for the shape and the rows line up, with
+  // its own tile: the largest of 2^9 .. 2^7 outputs whose two-stage ring fits
   TriTmaFn tfn = tri_tma_fn(nx, ny);
-  const size_t tsm = tfn ? tri_tma_smem(a) : 0;
-  if (a.use_tma && a.err && tfn && tsm && tsm <= kTriTmaSmemMax && a.tK &&
-      (1 << a.tb) <= kTriOutsPerThread * kTmaConsumers && tri_rows_aligned(a)) {
-    const unsigned int L = (a.nsum + a.tb >= 32) ? 0xffffffffu : ((1u << (a.nsum + a.tb)) - 1u);
-    const unsigned int Sm = (1u << a.nsum) - 1u;
-    CUtensorMap mp[3];
-    const int ops[3] = {a.tA, a.tB, a.tC};
-    bool ok = true;
-    for (int q = 0; q < 3 && ok; ++q) {
-      const unsigned int m = a.op[ops[q]].umask;
-      const int sq = __builtin_popcount(m & Sm), la = __builtin_popcount(m & L);
-      ok = cols_map(mp[q], data, a.ws_elems, sq, std::min(1 << (la - sq), 256));
+  if (a.use_tma && a.err && tfn && a.tK && tri_rows_aligned(a)) {
+    GemmArgs b = a;
+    size_t tsm = 0;
+    for (int t = std::min(9, u - a.nsum); t >= 7 && !tsm; --t) {
+      b.tb = t;
+      const size_t z = tri_tma_smem(b);
+      if (z && z <= kTriTmaSmemMax) tsm = z;
     }
-    if (ok) {
-      cudaFuncSetAttribute(tfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriTmaSmemMax);
-      int per_sm = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tfn, kTmaThreads, tsm) != cudaSuccess)
-        per_sm = 1;
-      const unsigned grid = (unsigned)std::max<long long>(
-          1, std::min<long long>(ntiles, (long long)sms * std::max(1, per_sm)));
-      tfn<<<grid, kTmaThreads, tsm, s>>>(a, mp[0], mp[1], mp[2], u, data, meta);
-      if (used_tma) *used_tma = true;
-      return n + 1;
+    if (tsm) {
+      b.tile_inner = tri_tile_inner(b, u);
+      const unsigned int L = (b.nsum + b.tb >= 32) ? 0xffffffffu : ((1u << (b.nsum + b.tb)) - 1u);
+      const unsigned int Sm = (1u << b.nsum) - 1u;
+      CUtensorMap mp[3];
+      const int ops[3] = {b.tA, b.tB, b.tC};
+      bool ok = true;
+      for (int q = 0; q < 3 && ok; ++q) {
+        const unsigned int m = b.op[ops[q]].umask;
+        const int sq = __builtin_popcount(m & Sm), la = __builtin_popcount(m & L);
+        ok = cols_map(mp[q], data, b.ws_elems, sq, std::min(1 << (la - sq), 256));
+      }
+      if (ok) {
+        cudaFuncSetAttribute(tfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriTmaSmemMax);
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tfn, kTmaThreads, tsm) !=
+            cudaSuccess)
+          per_sm = 1;
+        const long long nt = b.nslices << (u - b.nsum - b.tb);
+        const unsigned grid = (unsigned)std::max<long long>(
+            1, std::min<long long>(nt, (long long)sms * std::max(1, per_sm)));
+        tfn<<<grid, kTmaThreads, tsm, s>>>(b, mp[0], mp[1], mp[2], u, data, meta);
+        if (used_tma) *used_tma = true;
+        return n + 1;
+      }
     }
   }
+  const long long ntiles = a.nslices << (u - a.nsum - a.tb);
   const TriLayout l = tri_layout(a, a.tb);
   const int threads = std::min(256, 1 << a.tb);
   const int per_sm = std::max<int>(1, std::min<int>(8, (int)((220 * 1024) / (l.bytes + 2048))));

@@ -69,6 +69,8 @@ void gemm_tile_regs(GemmArgs& a, int block_mode = 0);
 // Triangle form (three large operands): output indices per tile (0: not taken)
 // and the launch (one kernel).
 int tri_tile_bits(const GemmArgs& a, int u);
+// Tile visiting order of the triangle form for tiles of a.tb bits.
+unsigned int tri_tile_inner(const GemmArgs& a, int u);
 int tri_launch(const GemmArgs& a, float* data, GMeta* meta, cudaStream_t s, int sms,
                bool* used_tma = nullptr);
 
