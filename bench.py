@@ -374,6 +374,22 @@ def ours(args):
            "includes": "qt_set_angles (host tensors) + qt_contract (H2D gates, all slices, D2H amplitude, stream sync)"}
     del gstage
 
+    # angle sweep of the amplitude: 16 sets through one qt_contract_sweep call
+    n_sw = 16
+    sw_sets = [random_angles(WORKLOAD["p"], 6000 + i) for i in range(n_sw)]
+    sw_g = [list(g2) for g2, _ in sw_sets]
+    sw_b = [list(b2) for _, b2 in sw_sets]
+    net.contract_sweep(sw_g, sw_b, prec)  # warm: workspace, graph capture
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    net.contract_sweep(sw_g, sw_b, prec)
+    t_sw = time.perf_counter() - t0
+    amp_sweep_line = {"workload": f"{n_sw} angle sets of the same amplitude, one qt_contract_sweep",
+                      "ms_per_sweep": 1e3 * t_sw, "amplitudes_per_s": n_sw / t_sw,
+                      "slices_per_s": n_sw * nslices / t_sw,
+                      "includes": "host gate images of every set, one H2D, per set: gate copy "
+                                  "+ graph replay, one D2H of the amplitudes"}
+
     line = {
         "metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -394,6 +410,7 @@ def ours(args):
         "batched_energy": energy_line,
         "batched_amplitudes": batch_line,
         "angle_sweep": sweep_line,
+        "amplitude_sweep": amp_sweep_line,
         "orderings": order_line,
         "precision_modes": modes_line,
         "amplitude": [amp.real, amp.imag],

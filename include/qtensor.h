@@ -229,6 +229,26 @@ qt_status qt_contract(qt_net* net, int32_t precision, void* workspace, size_t wo
 qt_status qt_contract_batch(qt_net* net, int32_t precision, void* workspace,
                             size_t workspace_bytes, void* stream, double* amps);
 
+/*
+ * Angle sweep of the amplitude: n_sets >= 1 angle sets (gammas, betas: n_sets * p
+ * doubles each, set s at gammas[s p .. s p + p - 1]) contracted with one order,
+ * one slicing and one schedule, the reuse that makes parameter scans cheap
+ * (Sec. VIII). Every set's gate tensors are built on the host and uploaded in one
+ * copy; then, with no host wait in between, each set's gates are copied over the
+ * workspace's gate region and all slices run (the captured graph replayed). The
+ * n_sets amplitudes go to the HOST array amps (2 n_sets doubles, set s at
+ * amps[2s], amps[2s+1]); `stream` is synchronised once at the end. The
+ * workspace must also hold the sets' gate images: prepares (batch = all slices
+ * that fit beside them) when the precision differs or they do not fit. The
+ * network keeps the last set's angles. Errors: QT_EINVAL for null arguments,
+ * n_sets < 1 or an angle that is not finite; QT_ESTATE before qt_order or with
+ * open qubits; QT_ENOMEM when one batch and the images do not fit; as
+ * qt_contract otherwise.
+ */
+qt_status qt_contract_sweep(qt_net* net, int32_t precision, int32_t n_sets, const double* gammas,
+                            const double* betas, void* workspace, size_t workspace_bytes,
+                            void* stream, double* amps);
+
 /* Plan bookkeeping: greedy ordering runs made by the last qt_order/qt_slice/
  * qt_slice_learned and the plan's cost sum over its steps of 2^width. */
 qt_status qt_plan_info(const qt_net* net, int64_t* greedy_runs, double* plan_cost);

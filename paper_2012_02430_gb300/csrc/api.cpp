@@ -15,6 +15,9 @@ void build_stage(qt_net* net);
 qt_status upload(qt_net* net, void* ws, size_t bytes, void* stream, std::string& err);
 qt_status run(qt_net* net, long long first, long long count, void* ws, void* stream,
               double* d_out, std::string& err);
+size_t stage_image_bytes(const qt_net* net);
+qt_status sweep_run(qt_net* net, void* ws, void* stream, int n_sets, const void* images,
+                    size_t staging_off, size_t stride, size_t results_off, std::string& err);
 qt_status download_result(const double* d_out, double* host, int64_t n_doubles, void* stream,
                           std::string& err);
 qt_status read_status(const qt_net* net, const void* ws, void* stream, int* status,
@@ -433,6 +436,76 @@ qt_status qt_contract_batch(qt_net* net, int32_t precision, void* workspace,
   if (!check_net(net) || !amps) return fail(QT_EINVAL, "qt_contract_batch: null argument");
   return contract_impl(net, precision, workspace, workspace_bytes, stream, amps,
                        "qt_contract_batch");
+}
+
+qt_status qt_contract_sweep(qt_net* net, int32_t precision, int32_t n_sets, const double* gammas,
+                            const double* betas, void* workspace, size_t workspace_bytes,
+                            void* stream, double* amps) {
+  const char* who = "qt_contract_sweep";
+  if (!check_net(net) || !gammas || !betas || !amps)
+    return fail(QT_EINVAL, std::string(who) + ": null argument");
+  if (n_sets < 1) return fail(QT_EINVAL, std::string(who) + ": need n_sets >= 1");
+  if (!net->ordered) return fail(QT_ESTATE, std::string(who) + ": call qt_order first");
+  if (!net->open.empty())
+    return fail(QT_ESTATE, std::string(who) + ": the network has open qubits");
+  for (int64_t e = 0; e < (int64_t)n_sets * net->p; ++e)
+    if (!std::isfinite(gammas[e]) || !std::isfinite(betas[e]))
+      return fail(QT_EINVAL, std::string(who) + ": angle not finite");
+  auto align256 = [](size_t x) { return (x + 255) / 256 * 256; };
+  // room after the schedule's workspace: one gate + gate-meta image per set, the amplitudes
+  auto reserve = [&]() {
+    return align256(qt::stage_image_bytes(net)) * (size_t)n_sets +
+           align256((size_t)16 * (size_t)n_sets);
+  };
+  if (!net->sched.valid || net->sched.precision != precision ||
+      net->sched.total_bytes + reserve() > workspace_bytes) {
+    size_t need = 0;
+    qt_status s = qt_prepare(net, precision, 1, &need);
+    if (s != QT_OK) return s;
+    const size_t room = reserve();
+    if (workspace_bytes < room + need)
+      return fail(QT_ENOMEM, std::string(who) + ": workspace too small for one batch and the images");
+    int64_t lo = 1, hi = net->sched.nslices;
+    while (lo < hi) {
+      int64_t mid = (lo + hi + 1) / 2;
+      s = qt_prepare(net, precision, (int32_t)std::min<int64_t>(mid, 1 << 30), &need);
+      if (s != QT_OK) return s;
+      if (need + room <= workspace_bytes) lo = mid;
+      else hi = mid - 1;
+    }
+    s = qt_prepare(net, precision, (int32_t)lo, &need);
+    if (s != QT_OK) return s;
+  }
+  qt_status s = check_ws(net, workspace, workspace_bytes - reserve(), who);
+  if (s != QT_OK) return s;
+  const qt::Schedule& S = net->sched;
+  const size_t img = qt::stage_image_bytes(net);
+  const size_t stride = align256(img);
+  const size_t staging_off = align256(S.total_bytes);
+  const size_t results_off = staging_off + stride * (size_t)n_sets;
+  // host: every set's gate and gate-meta image (the order, slices and schedule are reused)
+  std::vector<unsigned char> images(stride * (size_t)n_sets);
+  for (int k = 0; k < n_sets; ++k) {
+    s = qt_set_angles(net, gammas + (size_t)k * net->p, betas + (size_t)k * net->p);
+    if (s != QT_OK) return s;
+    qt::build_stage(net);
+    net->stage_dirty = false;
+    std::memcpy(images.data() + (size_t)k * stride, net->gate_stage.data(), img);
+  }
+  std::string err;
+  s = qt::upload(net, workspace, workspace_bytes, stream, err);  // scalar table, last set's gates
+  if (s != QT_OK) return fail(s, std::string(who) + ": " + err);
+  s = qt::sweep_run(net, workspace, stream, n_sets, images.data(), staging_off, stride,
+                    results_off, err);
+  if (s != QT_OK) return fail(s, std::string(who) + ": " + err);
+  s = qt::download_result(reinterpret_cast<const double*>((char*)workspace + results_off), amps,
+                          2 * (int64_t)n_sets, stream, err);
+  if (s != QT_OK) return fail(s, std::string(who) + ": " + err);
+  int status = 0;
+  s = qt::read_status(net, workspace, stream, &status, err);
+  if (s != QT_OK) return fail(s, std::string(who) + ": " + err);
+  if (status) return fail(QT_ETIMEOUT, std::string(who) + ": a bounded device wait gave up");
+  return ok();
 }
 
 qt_status qt_profile(qt_net* net, int32_t enable) {

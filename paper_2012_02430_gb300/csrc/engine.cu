@@ -2058,6 +2058,50 @@ qt_status read_status(const qt_net* net, const void* ws, void* stream, int* stat
   return QT_OK;
 }
 
+// Angle sweep of the amplitude (the reuse of one plan for many angles): the gate and
+// gate-meta images of n_sets angle sets (host, stride bytes apart) are copied to
+// ws + staging_off.
+// Each is copied in turn over the workspace's gate and meta regions and followed by a run
+// of all slices (the captured graph replayed); the run's amplitudes (2 n_amps doubles) are
+// copied to ws + results_off + s * 16 n_amps. Nothing waits on the host in between.
+size_t stage_image_bytes(const qt_net* net) {
+  const Schedule& S = net->sched;
+  return (size_t)S.gate_elems * (size_t)S.elem_bytes + (size_t)S.n_shared_meta * sizeof(Meta);
+}
+
+qt_status sweep_run(qt_net* net, void* ws, void* stream, int n_sets, const void* images,
+                    size_t staging_off, size_t stride, size_t results_off, std::string& err) {
+  const Schedule& S = net->sched;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* base = (char*)ws;
+  const size_t gate_bytes = (size_t)S.gate_elems * (size_t)S.elem_bytes;
+  const size_t meta_bytes = (size_t)S.n_shared_meta * sizeof(Meta);
+  const size_t out_bytes = (size_t)16 * (size_t)S.n_amps;
+  if (!cuda_ok(cudaMemcpyAsync(base + staging_off, images, stride * (size_t)n_sets,
+                               cudaMemcpyHostToDevice, s),
+               "upload of the angle sets", err))
+    return QT_ECUDA;
+  double* d_out = reinterpret_cast<double*>(base + S.off_acc + out_bytes);
+  for (int k = 0; k < n_sets; ++k) {
+    const char* img = base + staging_off + (size_t)k * stride;
+    if (gate_bytes && !cuda_ok(cudaMemcpyAsync(base + S.off_gates, img, gate_bytes,
+                                               cudaMemcpyDeviceToDevice, s),
+                               "install gates", err))
+      return QT_ECUDA;
+    if (meta_bytes && !cuda_ok(cudaMemcpyAsync(base + S.off_meta, img + gate_bytes, meta_bytes,
+                                               cudaMemcpyDeviceToDevice, s),
+                               "install gate meta", err))
+      return QT_ECUDA;
+    qt_status r = run(net, 0, S.nslices, ws, stream, d_out, err);
+    if (r != QT_OK) return r;
+    if (!cuda_ok(cudaMemcpyAsync(base + results_off + (size_t)k * out_bytes, d_out, out_bytes,
+                                 cudaMemcpyDeviceToDevice, s),
+                 "collect amplitude", err))
+      return QT_ECUDA;
+  }
+  return QT_OK;
+}
+
 qt_status download_result(const double* d_out, double* host, int64_t n_doubles, void* stream,
                           std::string& err) {
   cudaStream_t s = (cudaStream_t)stream;

@@ -50,6 +50,7 @@ _SIGS = {
     "qt_set_bitstring": [_vp, _u8p],
     "qt_set_open": [_vp, _i32p, C.c_int32],
     "qt_contract_batch": [_vp, C.c_int32, _vp, C.c_size_t, _vp, _f64p],
+    "qt_contract_sweep": [_vp, C.c_int32, C.c_int32, _f64p, _f64p, _vp, C.c_size_t, _vp, _f64p],
     "qt_order": [_vp, C.c_int32, C.c_uint64, _i32p],
     "qt_order_rgreedy": [_vp, C.c_double, C.c_int32, C.c_uint64, _i32p],
     "qt_slice": [_vp, C.c_int32, C.c_int32, C.c_int32, _i32p, _i32p],
@@ -238,6 +239,20 @@ def qt_contract_batch(net, precision, workspace_ptr, workspace_bytes, stream_ptr
     _check(lib.qt_contract_batch(net, int(precision), _vp(workspace_ptr), int(workspace_bytes),
                                  _vp(stream_ptr), buf))
     return [complex(buf[2 * b], buf[2 * b + 1]) for b in range(1 << a)]
+
+
+def qt_contract_sweep(net, precision, gammas, betas, workspace_ptr, workspace_bytes, stream_ptr):
+    """Amplitudes for n angle sets (gammas, betas: n lists of p angles) with one plan."""
+    n = len(gammas)
+    if n != len(betas):
+        raise ValueError("gammas and betas need the same number of sets")
+    flat_g = [float(x) for row in gammas for x in row]
+    flat_b = [float(x) for row in betas for x in row]
+    buf = (C.c_double * (2 * max(n, 1)))()
+    _check(lib.qt_contract_sweep(net, int(precision), int(n), _arr(C.c_double, flat_g),
+                                 _arr(C.c_double, flat_b), _vp(workspace_ptr), int(workspace_bytes),
+                                 _vp(stream_ptr), buf))
+    return [complex(buf[2 * s], buf[2 * s + 1]) for s in range(n)]
 
 
 def qt_contract_static(net, precision, stream_ptr):
@@ -478,6 +493,19 @@ class Network:
     def contract(self, precision=QT_FP32_SIMT):
         return qt_contract(self.handle, precision, self.workspace.data_ptr(),
                            self.workspace.numel(), self._stream())
+
+    def contract_sweep(self, gammas, betas, precision=QT_FP32_SIMT):
+        """Amplitudes for several angle sets with this network's order and slicing. The
+        workspace grows to hold every set's gate image beside the prepared schedule."""
+        import torch
+        st = self.stats()
+        need = st["workspace_bytes"] + len(gammas) * (st["upload_bytes"] + 512) + 1024
+        if self.workspace.numel() < need:
+            dev = self.workspace.device
+            self.workspace = None
+            self.workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+        return qt_contract_sweep(self.handle, precision, gammas, betas, self.workspace.data_ptr(),
+                                 self.workspace.numel(), self._stream())
 
     def contract_batch(self, precision=QT_FP32_SIMT):
         return qt_contract_batch(self.handle, precision, self.workspace.data_ptr(),

@@ -444,3 +444,22 @@ def test_tma_option_range(qt):
     for v in (-1, 5):
         with pytest.raises(qt.QtError):
             qt.qt_set_option(net.handle, qt.QT_OPT_TMA, v)
+
+
+def test_contract_sweep_errors(qt):
+    """qt_contract_sweep refuses bad arguments before any device work: no sets, a non-finite
+    angle, a network that is not ordered, or one with open qubits."""
+    import ctypes as C
+    lib = qt.lib
+    net = qt.Network([(0, 1), (1, 2), (2, 0)], 3, 1, [0.3], [0.2], [0, 1, 0])
+    out = (C.c_double * 4)()
+    g = (C.c_double * 2)(0.1, 0.2)
+    b = (C.c_double * 2)(0.3, 0.4)
+    assert lib.qt_contract_sweep(net.handle, 0, 2, g, b, None, 0, None, out) == qt.QT_ESTATE
+    net.order(0)
+    assert lib.qt_contract_sweep(net.handle, 0, 0, g, b, None, 0, None, out) == qt.QT_EINVAL
+    assert lib.qt_contract_sweep(net.handle, 0, 2, None, b, None, 0, None, out) == qt.QT_EINVAL
+    bad = (C.c_double * 2)(0.1, float("nan"))
+    assert lib.qt_contract_sweep(net.handle, 0, 2, bad, b, None, 0, None, out) == qt.QT_EINVAL
+    net.set_open([0])
+    assert lib.qt_contract_sweep(net.handle, 0, 2, g, b, None, 0, None, out) == qt.QT_ESTATE
