@@ -264,7 +264,7 @@ qt_status qt_plan_info(const qt_net* net, int64_t* greedy_runs, double* plan_cos
  * run (positions, widths, degrees, fill-in and density, normalised by the
  * current width). A 2-hidden-layer ReLU MLP scores them; only the `topm`
  * best-scored candidates are ordered greedily and the best verified plan by
- * (width, sum of 2^w, s, rank) is kept, so greedy stays the judge.
+ * (width, sum of 2^w, s, rank) is kept, so greedy ordering decides.
  * ------------------------------------------------------------------------- */
 enum { QT_PROPOSAL_FEATURES = 16 };
 

@@ -8,7 +8,7 @@
 // gets a feature vector read off the graph at step s without any ordering run;
 // a small MLP (trained on the GPU by the kernels in mlp.cu, on candidates whose
 // true width this code measured) predicts the plan width, and only the `topm`
-// best-scored candidates are re-ordered greedily. Greedy stays the judge: the
+// best-scored candidates are re-ordered greedily. Greedy ordering decides: the
 // chosen candidate is the best verified one by (width, sum of 2^w, s, rank).
 #include <algorithm>
 #include <cmath>
@@ -121,7 +121,7 @@ struct Eval {
 };
 
 // Plan of one candidate: eliminate order[:s], slice v, then r-1 more vertices of
-// largest degree, re-order greedily (the judge's ordering run).
+// largest degree, re-order greedily (the deciding ordering run).
 static Eval evaluate(const BitGraph& g, const std::vector<int32_t>& order,
                      const std::vector<int32_t>& widths, const std::vector<int32_t>& done_widths,
                      int s, int v, int r, int algo) {
