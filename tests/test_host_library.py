@@ -463,3 +463,44 @@ def test_contract_sweep_errors(qt):
     assert lib.qt_contract_sweep(net.handle, 0, 2, bad, b, None, 0, None, out) == qt.QT_EINVAL
     net.set_open([0])
     assert lib.qt_contract_sweep(net.handle, 0, 2, g, b, None, 0, None, out) == qt.QT_ESTATE
+
+
+@pytest.mark.parametrize("case", [(80, 2, 1002, 26, 20), (50, 3, 1003, 28, 20), (32, 3, 25, 0, 0)])
+def test_launch_form_masks(qt, case):
+    """The schedule's GEMM-form and triangle-form classifications are exact set relations
+    over each launch's union U: GEMM form -- summed-in-both (K) and batch indices lie in
+    A and B, A-only outputs in A and not B, B-only outputs in B and not A, one-sided summed
+    indices in one side only, the six classes disjoint and covering U; triangle form --
+    K in A and B only, X in A and C only, Y in B and C only, and every summed index of U
+    in exactly one class."""
+    n, p, seed, wl, mv = case
+    from paper_2012_02430_gb300.inputs import qaoa_instance
+    edges, g, b, z = qaoa_instance(n, p, seed)
+    net = qt.Network(edges, n, p, g, b, z)
+    qt.qt_set_option(net.handle, qt.QT_OPT_TRIANGLE, 1)
+    net.order(0)
+    if wl:
+        net.slice(wl, mv, 1)
+    qt.qt_prepare(net.handle, 0, 1)
+    st = net.stats()
+    assert st["gemm_masks"] and (st["tri_masks"] or n == 50)  # both forms are exercised
+    for first, u, mK, mSA, mSB, mM, mN, mBt, uA, uB, na, nb in st["gemm_masks"]:
+        full = (1 << u) - 1
+        classes = [mK, mSA, mSB, mM, mN, mBt]
+        assert sum(bin(c).count("1") for c in classes) == u, first
+        acc = 0
+        for c in classes:
+            assert c & acc == 0, first
+            acc |= c
+        assert acc == full, first
+        assert mK & ~(uA & uB) == 0 and mBt & ~(uA & uB) == 0, first
+        assert mM & ~(uA & ~uB) == 0 and mSA & ~(uA & ~uB) == 0, first
+        assert mN & ~(uB & ~uA) == 0 and mSB & ~(uB & ~uA) == 0, first
+        assert na >= 1 and nb >= 1, first
+    for first, u, tK, tX, tY, uA, uB, uC in st["tri_masks"]:
+        assert tK & tX == 0 and tK & tY == 0 and tX & tY == 0, first
+        assert tK & ~(uA & uB & ~uC) == 0, first
+        assert tX & ~(uA & uC & ~uB) == 0, first
+        assert tY & ~(uB & uC & ~uA) == 0, first
+        nsum = bin(tK | tX | tY).count("1")
+        assert tK | tX | tY == (1 << nsum) - 1, first  # the summed indices are U's lowest
