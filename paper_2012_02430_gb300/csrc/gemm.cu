@@ -2304,8 +2304,14 @@ int gemm_launch(const GemmArgs& a, int mode, float* data, GMeta* meta, cudaStrea
     const long long total = a.nslices << __builtin_popcount(Gm);
     StreamFn fn = stream_fn(a.nsum);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    // one block per resident slot: a single wave, so the next-pass prefetch never restarts
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, 256, smem) !=
+        cudaSuccess)
+      per_sm = 4;
     const unsigned grid = (unsigned)std::max<long long>(
-        1, std::min<long long>(total / (256 * stream_rows(a.nsum)), (long long)sms * 8));
+        1, std::min<long long>(total / (256 * stream_rows(a.nsum)),
+                               (long long)sms * std::max(1, per_sm)));
     fn<<<grid, 256, smem, s>>>(a, data, meta);
     return n + 1;
   }
