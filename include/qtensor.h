@@ -182,12 +182,25 @@ qt_status qt_num_tensors(const qt_net* net, int32_t* count, int32_t* n_vars);
 qt_status qt_prepare(qt_net* net, int32_t precision, int32_t batch, size_t* workspace_bytes);
 
 /*
- * Integer ledger of the prepared schedule (per-step FLOPs/bytes as in
- * Alg. 1; see the DESIGN notes for the formulas), written as one JSON object
- * into buf (NUL-terminated, truncated to cap). *needed receives the full length
- * + 1. Errors: QT_ESTATE before qt_prepare.
+ * Integer ledger of the prepared schedule (per Alg. 1 step over complex
+ * elements of e bytes: bytes = e (sum over operands of 2^rank + 2^c), flops =
+ * 6 (m - 1) 2^u + 2 (2^u - 2^c) for m operands over union rank u), written as
+ * one JSON object into buf (NUL-terminated, truncated to cap). *needed receives
+ * the full length + 1. Errors: QT_ESTATE before qt_prepare.
  */
 qt_status qt_stats(const qt_net* net, char* buf, size_t cap, size_t* needed);
+
+/*
+ * The prepared schedule's slice-phase launches as a captured run orders them,
+ * as one JSON object into buf (as qt_stats): {"streams": S, "launches": [{"group",
+ * "g_last" (the schedule groups it covers), "kind", "stream" (0 .. S-1), "wait"
+ * (earlier launches on other streams it waits for), "reads", "writes" (per-slice
+ * arena element ranges [lo, hi))}, ...]}. Launches on one stream run in order.
+ * Two launches that write what the other reads or writes are ordered by their
+ * stream or by a chain of waits. Host work only. Errors: QT_ESTATE before
+ * qt_prepare; QT_ERANGE if the schedule's launches cannot be built.
+ */
+qt_status qt_launch_plan(qt_net* net, char* buf, size_t cap, size_t* needed);
 
 /*
  * Copies the gate tensors (in the prepared precision and canonical layout) into

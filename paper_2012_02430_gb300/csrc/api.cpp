@@ -16,6 +16,7 @@ qt_status upload(qt_net* net, void* ws, size_t bytes, void* stream, std::string&
 qt_status run(qt_net* net, long long first, long long count, void* ws, void* stream,
               double* d_out, std::string& err);
 size_t stage_image_bytes(const qt_net* net);
+qt_status launch_plan(qt_net* net, std::string& out, std::string& err);
 qt_status sweep_run(qt_net* net, void* ws, void* stream, int n_sets, const void* images,
                     size_t staging_off, size_t stride, size_t results_off, std::string& err);
 qt_status download_result(const double* d_out, double* host, int64_t n_doubles, void* stream,
@@ -505,6 +506,21 @@ qt_status qt_contract_sweep(qt_net* net, int32_t precision, int32_t n_sets, cons
   s = qt::read_status(net, workspace, stream, &status, err);
   if (s != QT_OK) return fail(s, std::string(who) + ": " + err);
   if (status) return fail(QT_ETIMEOUT, std::string(who) + ": a bounded device wait gave up");
+  return ok();
+}
+
+qt_status qt_launch_plan(qt_net* net, char* buf, size_t cap, size_t* needed) {
+  if (!check_net(net)) return fail(QT_EINVAL, "qt_launch_plan: null network");
+  if (!net->sched.valid) return fail(QT_ESTATE, "qt_launch_plan: call qt_prepare first");
+  std::string s, err;
+  qt_status r = qt::launch_plan(net, s, err);
+  if (r != QT_OK) return fail(r, "qt_launch_plan: " + err);
+  if (needed) *needed = s.size() + 1;
+  if (buf && cap > 0) {
+    size_t n = std::min(cap - 1, s.size());
+    std::memcpy(buf, s.data(), n);
+    buf[n] = 0;
+  }
   return ok();
 }
 

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <sstream>
 #include <map>
 #include <cmath>
 #include <cstdio>
@@ -1430,10 +1431,13 @@ static bool make_desc(const Schedule& S, int gi, long long nslices, LaunchDesc& 
 // liveness, so tensors are compared as element ranges). A launch goes to the stream
 // whose last launch is its latest conflict, else to the least recently used stream,
 // and waits for its latest conflict on every other stream.
-static void plan_streams(const Schedule& S, const std::vector<LaunchDesc>& list, LaunchPlan& P) {
-  struct Span {
-    int64_t lo, hi;
-  };
+struct Span {
+  int64_t lo, hi;  // per-slice arena elements [lo, hi)
+};
+
+static void plan_streams(const Schedule& S, const std::vector<LaunchDesc>& list, LaunchPlan& P,
+                         std::vector<std::vector<Span>>* reads = nullptr,
+                         std::vector<std::vector<Span>>* writes = nullptr) {
   auto span = [](int64_t off, int64_t n) { return Span{off, off + (n + 63) / 64 * 64}; };
   const size_t n = list.size();
   std::vector<std::vector<Span>> rd(n), wr(n);
@@ -1491,6 +1495,8 @@ static void plan_streams(const Schedule& S, const std::vector<LaunchDesc>& list,
       }
     lastl[st] = (int)m;
   }
+  if (reads) *reads = rd;
+  if (writes) *writes = wr;
 }
 
 template <typename R>
@@ -2047,6 +2053,46 @@ qt_status run(qt_net* net, long long first, long long count, void* ws, void* str
 }
 
 // the device status word of a run: nonzero when a bounded wait gave up
+// The slice phase's launches as the engine would capture them: per launch its first and
+// last schedule group, kernel class, stream, the launches it waits for, and the per-slice
+// arena ranges it reads and writes. Host work only.
+template <typename R>
+static bool launch_plan_impl(qt_net* net, std::string& out, std::string& err) {
+  EngineCache tmp;
+  if (!build_cache<R>(net, tmp, err)) return false;
+  std::vector<std::vector<Span>> rd, wr;
+  LaunchPlan P;
+  plan_streams(net->sched, tmp.slice, P, &rd, &wr);
+  std::ostringstream o;
+  o << "{\"streams\":" << kStreams << ",\"launches\":[";
+  auto spans = [&](const std::vector<Span>& v) {
+    o << "[";
+    for (size_t q = 0; q < v.size(); ++q) o << (q ? "," : "") << "[" << v[q].lo << "," << v[q].hi << "]";
+    o << "]";
+  };
+  for (size_t x = 0; x < tmp.slice.size(); ++x) {
+    const LaunchDesc& d = tmp.slice[x];
+    o << (x ? "," : "") << "{\"group\":" << d.group << ",\"g_last\":"
+      << (d.g_last >= 0 ? d.g_last : d.group) << ",\"kind\":" << d.kind
+      << ",\"stream\":" << P.stream[x] << ",\"wait\":[";
+    for (size_t q = 0; q < P.wait[x].size(); ++q) o << (q ? "," : "") << P.wait[x][q];
+    o << "],\"reads\":";
+    spans(rd[x]);
+    o << ",\"writes\":";
+    spans(wr[x]);
+    o << "}";
+  }
+  o << "]}";
+  out = o.str();
+  return true;
+}
+
+qt_status launch_plan(qt_net* net, std::string& out, std::string& err) {
+  const bool ok = net->sched.precision == QT_FP64 ? launch_plan_impl<double>(net, out, err)
+                                                  : launch_plan_impl<float>(net, out, err);
+  return ok ? QT_OK : QT_ERANGE;
+}
+
 qt_status read_status(const qt_net* net, const void* ws, void* stream, int* status,
                       std::string& err) {
   cudaStream_t s = (cudaStream_t)stream;

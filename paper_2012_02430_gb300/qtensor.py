@@ -61,6 +61,7 @@ _SIGS = {
     "qt_num_tensors": [_vp, _i32p, _i32p],
     "qt_prepare": [_vp, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)],
     "qt_stats": [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)],
+    "qt_launch_plan": [_vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)],
     "qt_upload": [_vp, _vp, C.c_size_t, _vp],
     "qt_run": [_vp, C.c_int64, C.c_int64, _vp, C.c_size_t, _vp, _vp],
     "qt_contract": [_vp, C.c_int32, _vp, C.c_size_t, _vp, _f64p, _f64p],
@@ -214,6 +215,15 @@ def qt_stats(net):
     _check(lib.qt_stats(net, None, 0, C.byref(n)))
     buf = C.create_string_buffer(n.value)
     _check(lib.qt_stats(net, buf, n.value, C.byref(n)))
+    return json.loads(buf.value.decode())
+
+
+def qt_launch_plan(net):
+    """The slice-phase launches' streams, waits and workspace ranges (a dict)."""
+    n = C.c_size_t()
+    _check(lib.qt_launch_plan(net, None, 0, C.byref(n)))
+    buf = C.create_string_buffer(n.value)
+    _check(lib.qt_launch_plan(net, buf, n.value, C.byref(n)))
     return json.loads(buf.value.decode())
 
 

@@ -504,3 +504,61 @@ def test_launch_form_masks(qt, case):
         assert tY & ~(uB & uC & ~uA) == 0, first
         nsum = bin(tK | tX | tY).count("1")
         assert tK | tX | tY == (1 << nsum) - 1, first  # the summed indices are U's lowest
+
+
+def _plan_reaches(plan):
+    """reach[m] = the set of launches that launch m is ordered after: the earlier launches
+    on its stream and, through waits, everything those and the waited-for launches follow."""
+    launches = plan["launches"]
+    reach = []
+    last_on = {}
+    for m, d in enumerate(launches):
+        before = set()
+        prev = last_on.get(d["stream"])
+        if prev is not None:
+            before |= {prev} | reach[prev]
+        for w in d["wait"]:
+            assert 0 <= w < m and launches[w]["stream"] != d["stream"]
+            before |= {w} | reach[w]
+        reach.append(before)
+        last_on[d["stream"]] = m
+    return reach
+
+
+@pytest.mark.parametrize("case", [(80, 2, 1002, 26, 20, 4), (44, 2, 14, 0, 0, 1),
+                                  (60, 2, 18, 23, 6, 4), (50, 3, 1003, 28, 20, 2)])
+def test_launch_plan_orders_every_conflict(qt, case):
+    """The concurrent plan of the slice phase: any two launches where one writes arena
+    elements the other reads or writes are ordered (same stream, or a chain of waits),
+    streams are in range, and every launch's ranges are well formed."""
+    n, p, seed, wl, mv, batch = case
+    from paper_2012_02430_gb300.inputs import qaoa_instance
+    edges, g, b, z = qaoa_instance(n, p, seed)
+    net = qt.Network(edges, n, p, g, b, z)
+    net.order(0)
+    if wl:
+        net.slice(wl, mv, 1)
+    qt.qt_prepare(net.handle, 0, batch)
+    plan = qt.qt_launch_plan(net.handle)
+    launches = plan["launches"]
+    assert launches and all(0 <= d["stream"] < plan["streams"] for d in launches)
+    for d in launches:
+        for lo, hi in d["reads"] + d["writes"]:
+            assert 0 <= lo < hi
+    reach = _plan_reaches(plan)
+
+    def meet(xs, ys):
+        return any(a < d and c < b for a, b in xs for c, d in ys)
+
+    conflicts = 0
+    for m, dm in enumerate(launches):
+        for l in range(m):
+            dl = launches[l]
+            if (meet(dl["writes"], dm["reads"]) or meet(dl["writes"], dm["writes"])
+                    or meet(dl["reads"], dm["writes"])):
+                conflicts += 1
+                assert l in reach[m], (l, m)
+    assert conflicts > 0
+    # more than one stream carries work on the larger plans
+    if n >= 60:
+        assert len({d["stream"] for d in launches}) > 1
