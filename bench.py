@@ -35,6 +35,20 @@ L2_FLUSH_BYTES = 512 << 20
 PRECISIONS = {"fp32": 0, "tf32": 1, "bf16": 2, "3xtf32": 3, "fp64": 4}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 
+# DRAM bytes (read + write) per launch of each kernel class on this workload, from one ncu
+# capture of the profiled pass (GB300, 1 GPU):
+#   ncu --nvtx --nvtx-include "qt_pass/" --clock-control none --csv --log-file dram.csv
+#       --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+#       python bench.py --profile-pass
+# averaged over the class's launches in the pass (its fold launches included). The roofline
+# line reports it as `traffic` when that class dominates; an entry must be dropped when its
+# kernel changes.
+CLASS_DRAM_BYTES = {
+    "gemm_stream (k_gemm_fold + k_gemm_stream)": 394.8e6,  # steps 120, 121, 131
+    "gemm_tile (k_gemm_fold + k_gemm_tma)": 179.5e6,       # steps 117, 127
+    "k_tri_tma": 440.2e6,                                  # step 132
+}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -316,7 +330,11 @@ def ours(args):
         roofline = {"bound": "hbm", "kernel": kind_names[dom], "achieved": achieved,
                     "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                     "peak_source": f"{peak_src} hbm_gbs"}
-    roofline.update({"traffic": None, "launches": d["n"], "flop_per_byte": intensity,
+    per_launch_bytes = d["bytes"] / max(1, d["n"])
+    roofline.update({"traffic": CLASS_DRAM_BYTES.get(kind_names[dom]),
+                     "traffic_unit": "bytes per launch (ncu dram read + write)",
+                     "algorithmic_bytes_per_launch": per_launch_bytes,
+                     "launches": d["n"], "flop_per_byte": intensity,
                      "ridge_flop_per_byte": ridge,
                      "share": {kind_names[kk]: by_kind[kk]["ms"] / tot_ms for kk in by_kind}})
 
