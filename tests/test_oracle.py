@@ -333,16 +333,27 @@ def test_replay_matches_greedy_profile():
 
 # ----------------------------- slicing ---------------------------------------
 
+RULES = {"min-degree": ordering.MIN_DEGREE, "min-fill": ordering.MIN_FILL}
+
+
 def test_slicing_hand_examples():
-    for c in load("slicing_hand.json")["cases"]:
+    """Step-dependent slicing worked by hand: min-degree and min-fill, r = 1 and r = 2,
+    one and two rounds (rounds at s = 0 and s > 0, widths of earlier rounds counted)."""
+    cases = load("slicing_hand.json")["cases"]
+    assert {c["algo"] for c in cases} == set(RULES) and {c["r"] for c in cases} == {1, 2}
+    for c in cases:
         a = adj_of(c["n"], c["edges"])
-        plan = slicing.step_dependent_slicing(a, ordering.MIN_DEGREE, c["width_limit"],
-                                              c["max_vars"], 1)
+        plan = slicing.step_dependent_slicing(a, RULES[c["algo"]], c["width_limit"],
+                                              c["max_vars"], c["r"])
         e = c["expect"]
         assert plan["sliced"] == e["sliced"], c["name"]
         assert plan["slice_step"] == e["slice_step"], c["name"]
         assert plan["order"] == e["order"], c["name"]
         assert plan["width"] == e["width"], c["name"]
+        if "widths" in e:
+            assert plan["widths"] == e["widths"], c["name"]
+        if "rounds" in e:
+            assert [[s, list(v)] for s, v in plan["rounds"]] == e["rounds"], c["name"]
 
 
 def test_slicing_plan_widths_replay():
@@ -483,3 +494,65 @@ def test_proposal_candidate_counts():
     assert all(c[2] == i % 3 for i, c in enumerate(cands))
     F, L, M = proposal.dataset(adj, ordering.MIN_FILL, 3)
     assert F.shape == (3 * (peak + 1), 16) and np.all(L > 0) and np.all(L <= 1.0 + 1e-12)
+
+
+# ------------------------ launch groups (fusion rule) -------------------------
+
+def test_launch_groups_hand_examples():
+    """The fusion rule's grouping worked by hand: joins, and launches cut by union
+    containment, by max_nsum, by max_ops, by a bucket without the previous result, and
+    by the slice boundary (sliced indices dropped from per-slice tensors)."""
+    for c in load("launch_groups_hand.json")["cases"]:
+        got = ledger.launch_groups(c["tensors"], c["order"], c["sliced"], c["slice_step"],
+                                   max_nsum=c["max_nsum"], max_ops=c["max_ops"])
+        assert got == c["expect"], c["name"]
+
+
+# ----------------------------- proposal features -------------------------------
+
+def _feature_value(f):
+    if isinstance(f, str):  # "log2(k)/d"
+        num, den = f.split("/")
+        return math.log2(float(num[len("log2("):-1])) / float(den)
+    return f[0] / f[1]
+
+
+def test_proposal_features_hand_example():
+    """Every one of the 16 features of four candidates, and their labels, worked by hand
+    on a five-vertex graph."""
+    from oracle import proposal
+    g = load("proposal_hand.json")
+    a = adj_of(g["n"], g["edges"])
+    order, widths = ordering.greedy_order(a, None, ordering.MIN_DEGREE)
+    assert order == g["order"] and widths == g["widths"]
+    base = proposal.round_candidates(a, order, widths, g["n"], g["topv"])
+    assert len(base) == g["n_candidates"]
+    for c in g["candidates"]:
+        cands = base if "topv" not in c else proposal.round_candidates(a, order, widths, g["n"],
+                                                                       c["topv"])
+        hit = [f for s, v, j, f in cands if (s, v, j) == (c["s"], c["v"], c["j"])]
+        assert len(hit) == 1, c
+        want = [_feature_value(x) for x in c["features"]]
+        assert len(want) == 16
+        assert np.allclose(hit[0], want, rtol=0, atol=1e-12), (c["s"], c["v"], hit[0], want)
+        w = proposal.candidate_width(a, order, widths, c["s"], c["v"], ordering.MIN_DEGREE)
+        assert w == c["label_width"], (c["s"], c["v"], w)
+
+
+# ------------------------------ MLP forward ------------------------------------
+
+def test_mlp_forward_hand_example():
+    """Forward values, loss and two gradients of the proposal MLP worked by hand."""
+    from oracle import mlp
+    g = load("mlp_hand.json")
+    params = np.concatenate([np.ravel(g["W1"]), g["b1"], np.ravel(g["W2"]), g["b2"], g["w3"],
+                             [g["b3"]]])
+    assert len(params) == mlp.n_params(g["nf"], g["hidden"])
+    y, _ = mlp.forward(params, g["x"], g["nf"], g["hidden"])
+    assert np.array_equal(y, np.array(g["y"]))  # exact in binary floating point
+    L = mlp.loss(params, g["x"], g["t"], g["nf"], g["hidden"])
+    assert abs(L - g["loss"][0] / g["loss"][1]) <= 1e-15
+    grad = mlp.gradients(params, g["x"], g["t"], g["nf"], g["hidden"])
+    assert abs(grad[-1] - g["grad_b3"]) <= 1e-15
+    gw3 = [_feature_value(x) if isinstance(x, list) else x for x in g["grad_w3"]]
+    assert np.allclose(grad[-1 - g["hidden"]:-1], gw3, rtol=0, atol=1e-15)
