@@ -218,8 +218,12 @@ qt_status qt_upload(qt_net* net, void* workspace, size_t workspace_bytes, void* 
  * to the DEVICE pointer d_out, asynchronously on `stream`; no host copy, no
  * synchronisation. With a open qubits (qt_set_open) d_out receives 2^a such
  * pairs, amplitude b at d_out[2b], d_out[2b+1]. The unsliced prefix (contract_first) is recomputed by every
- * call. Errors: QT_ESTATE before qt_prepare; QT_EINVAL for a range outside
- * [0, 2^k) or a null d_out; QT_ENOMEM for a small workspace; QT_ECUDA.
+ * call. The workspace must hold the upload of the current schedule: QT_ESTATE
+ * when qt_upload has not been called on this workspace since the last
+ * qt_prepare (or since qt_set_angles / qt_set_bitstring), so a stale layout is
+ * never read. Errors: QT_ESTATE before qt_prepare or as above; QT_EINVAL for a
+ * range outside [0, 2^k) or a null d_out; QT_ENOMEM for a small workspace;
+ * QT_ECUDA.
  */
 qt_status qt_run(qt_net* net, int64_t first, int64_t count, void* workspace, size_t workspace_bytes,
                  void* stream, double* d_out);
@@ -394,7 +398,8 @@ qt_status qt_set_option(qt_net* net, int32_t option, int64_t value);
  * per step for later qt_run / qt_contract calls until the next qt_prepare.
  * Synchronises `stream`. The choice per step is written as a JSON array
  * [{"step", "variant", "ms": [per variant]}] into buf (as qt_stats; buf may be
- * NULL). Errors: QT_ESTATE before qt_prepare; workspace errors as qt_run;
+ * NULL). Errors: QT_ESTATE before qt_prepare or without a current qt_upload
+ * (as qt_run); workspace errors as qt_run;
  * QT_ECUDA.
  */
 qt_status qt_autotune(qt_net* net, void* workspace, size_t workspace_bytes, void* stream, char* buf,
@@ -424,18 +429,22 @@ qt_status qt_profile_read(qt_net* net, char* buf, size_t cap, size_t* needed);
  * All device scratch (gate copies, intermediate tensors, bookkeeping) lives in
  * one static device array of 64 MiB inside the library; every GPU on which the
  * library's module is loaded holds it until the process exits. The largest
- * slice batch whose schedule fits the array is used (a schedule the caller had
- * prepared with qt_prepare is restored before the call returns); a network whose schedule
- * needs more than 64 MiB even one slice at a time is rejected with QT_ENOMEM
- * and a message giving both sizes. It calls no cudaMalloc/cudaFree and creates
- * no CUDA objects (tracing is skipped on this path).
- * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture. All calls
- * on a device share the array, which keeps the last call's contents (the call
- * re-uploads and re-zeroes everything it reads): calls that may overlap on the
- * GPU (different streams or threads) race and must be serialised by the caller.
+ * slice batch whose schedule fits the array is used. The caller's own planning
+ * state is left exactly as it was: a schedule prepared with qt_prepare, its
+ * upload to the caller's workspace and its autotuned kernel choices stay valid
+ * for later qt_run calls. A network whose schedule needs more than 64 MiB even
+ * one slice at a time is rejected with QT_ENOMEM and a message giving both
+ * sizes. It calls no cudaMalloc/cudaFree and creates no CUDA objects (tracing
+ * and graph capture are skipped on this path).
+ * Every call looks up the array's device address on the current device; the
+ * first call on a device also loads the library's module there, so make that
+ * first call before any stream capture. All calls on a device share the array,
+ * which keeps the last call's contents (the call re-uploads and re-zeroes
+ * everything it reads): calls that may overlap on the GPU (different streams
+ * or threads) race and must be serialised by the caller.
  * The call synchronises `stream`. Errors: QT_EINVAL for a null argument;
- * QT_ESTATE before qt_order; QT_ENOMEM as above; QT_ECUDA; others as qt_prepare.
+ * QT_ESTATE before qt_order; QT_ENOMEM as above; QT_ETIMEOUT when a bounded
+ * device wait gave up (as qt_contract); QT_ECUDA; others as qt_prepare.
  */
 qt_status qt_contract_static(qt_net* net, int32_t precision, void* stream, double* amp_re,
                              double* amp_im);

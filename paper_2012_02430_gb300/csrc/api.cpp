@@ -81,8 +81,43 @@ bool check_net(const qt_net* net) { return net != nullptr; }
 
 }  // namespace
 
+extern "C" qt_status qt_prepare(qt_net* net, int32_t precision, int32_t batch,
+                                size_t* workspace_bytes);
+
 namespace qt {
 void set_last_error(const std::string& msg) { g_err = msg; }
+
+qt_status prepare_fitting(qt_net* net, int32_t precision, size_t budget,
+                          size_t (*room)(const qt_net*, const void*), const void* room_arg,
+                          std::string& err) {
+  size_t need = 0;
+  qt_status s = qt_prepare(net, precision, 1, &need);
+  if (s != QT_OK) {
+    err = g_err;
+    return s;
+  }
+  const size_t extra = room ? room(net, room_arg) : 0;
+  if (need + extra > budget) {
+    err = "one slice needs " + std::to_string(need + extra) + " bytes of workspace; " +
+          std::to_string(budget) + " are available";
+    return QT_ENOMEM;
+  }
+  // the batch-1 schedule fits; the workspace grows with the batch
+  int64_t lo = 1, hi = net->sched.nslices;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) / 2;
+    s = qt_prepare(net, precision, (int32_t)std::min<int64_t>(mid, 1 << 30), &need);
+    if (s != QT_OK) {
+      err = g_err;
+      return s;
+    }
+    if (need + extra <= budget) lo = mid;
+    else hi = mid - 1;
+  }
+  s = qt_prepare(net, precision, (int32_t)lo, &need);
+  if (s != QT_OK) err = g_err;
+  return s;
+}
 bool slice_dataset(const qt_net* net, int topv, std::vector<float>& feats,
                    std::vector<float>& labels, std::vector<int32_t>& meta);
 SlicePlan learned_slicing(const qt_net* net, const float* params, int hidden, int width_limit,
@@ -150,6 +185,7 @@ qt_status qt_set_angles(qt_net* net, const double* gammas, const double* betas) 
   net->betas.assign(betas, betas + net->p);
   make_tensors(net);
   net->stage_dirty = true;
+  net->data_version++;
   return ok();
 }
 
@@ -160,6 +196,7 @@ qt_status qt_set_bitstring(qt_net* net, const uint8_t* bitstring) {
   net->z.assign(bitstring, bitstring + net->n);
   make_tensors(net);
   net->stage_dirty = true;
+  net->data_version++;
   return ok();
 }
 
@@ -375,6 +412,11 @@ qt_status qt_run(qt_net* net, int64_t first, int64_t count, void* workspace, siz
     return fail(QT_EINVAL, "qt_run: slice range outside [0, 2^k)");
   qt_status s = check_ws(net, workspace, workspace_bytes, "qt_run");
   if (s != QT_OK) return s;
+  if (net->uploaded_gen != net->sched.generation || net->uploaded_ws != workspace)
+    return fail(QT_ESTATE, "qt_run: this workspace does not hold the prepared schedule's upload; "
+                           "call qt_upload after qt_prepare");
+  if (net->uploaded_data != net->data_version)
+    return fail(QT_ESTATE, "qt_run: angles or bitstring changed since qt_upload; call qt_upload");
   std::string err;
   s = qt::run(net, first, count, workspace, stream, d_out, err);
   if (s != QT_OK) return fail(s, "qt_run: " + err);
@@ -385,25 +427,14 @@ static qt_status contract_impl(qt_net* net, int32_t precision, void* workspace,
                                size_t workspace_bytes, void* stream, double* host_out,
                                const char* who) {
   if (!net->ordered) return fail(QT_ESTATE, std::string(who) + ": call qt_order first");
+  std::string err;
   if (!net->sched.valid || net->sched.precision != precision) {
     // the largest batch whose workspace fits
-    size_t need = 0;
-    qt_status s = qt_prepare(net, precision, 1, &need);
-    if (s != QT_OK) return s;
-    int64_t lo = 1, hi = net->sched.nslices;
-    while (lo < hi) {
-      int64_t mid = (lo + hi + 1) / 2;
-      s = qt_prepare(net, precision, (int32_t)std::min<int64_t>(mid, 1 << 30), &need);
-      if (s != QT_OK) return s;
-      if (need <= workspace_bytes) lo = mid;
-      else hi = mid - 1;
-    }
-    s = qt_prepare(net, precision, (int32_t)lo, &need);
-    if (s != QT_OK) return s;
+    qt_status s = qt::prepare_fitting(net, precision, workspace_bytes, nullptr, nullptr, err);
+    if (s != QT_OK) return fail(s, std::string(who) + ": " + err);
   }
   qt_status s = check_ws(net, workspace, workspace_bytes, who);
   if (s != QT_OK) return s;
-  std::string err;
   s = qt::upload(net, workspace, workspace_bytes, stream, err);
   if (s != QT_OK) return fail(s, std::string(who) + ": " + err);
   const int64_t A = net->sched.n_amps;
@@ -454,28 +485,17 @@ qt_status qt_contract_sweep(qt_net* net, int32_t precision, int32_t n_sets, cons
       return fail(QT_EINVAL, std::string(who) + ": angle not finite");
   auto align256 = [](size_t x) { return (x + 255) / 256 * 256; };
   // room after the schedule's workspace: one gate + gate-meta image per set, the amplitudes
-  auto reserve = [&]() {
-    return align256(qt::stage_image_bytes(net)) * (size_t)n_sets +
-           align256((size_t)16 * (size_t)n_sets);
+  // (the gate image does not depend on the batch)
+  auto room = [](const qt_net* nt, const void* arg) {
+    const size_t sets = (size_t)*static_cast<const int32_t*>(arg);
+    return (qt::stage_image_bytes(nt) + 255) / 256 * 256 * sets + (16 * sets + 255) / 256 * 256;
   };
+  auto reserve = [&]() { return room(net, &n_sets); };
   if (!net->sched.valid || net->sched.precision != precision ||
       net->sched.total_bytes + reserve() > workspace_bytes) {
-    size_t need = 0;
-    qt_status s = qt_prepare(net, precision, 1, &need);
-    if (s != QT_OK) return s;
-    const size_t room = reserve();
-    if (workspace_bytes < room + need)
-      return fail(QT_ENOMEM, std::string(who) + ": workspace too small for one batch and the images");
-    int64_t lo = 1, hi = net->sched.nslices;
-    while (lo < hi) {
-      int64_t mid = (lo + hi + 1) / 2;
-      s = qt_prepare(net, precision, (int32_t)std::min<int64_t>(mid, 1 << 30), &need);
-      if (s != QT_OK) return s;
-      if (need + room <= workspace_bytes) lo = mid;
-      else hi = mid - 1;
-    }
-    s = qt_prepare(net, precision, (int32_t)lo, &need);
-    if (s != QT_OK) return s;
+    std::string perr;
+    qt_status s = qt::prepare_fitting(net, precision, workspace_bytes, room, &n_sets, perr);
+    if (s != QT_OK) return fail(s, std::string(who) + ": " + perr);
   }
   qt_status s = check_ws(net, workspace, workspace_bytes - reserve(), who);
   if (s != QT_OK) return s;
@@ -656,6 +676,9 @@ qt_status qt_autotune(qt_net* net, void* workspace, size_t workspace_bytes, void
   if (!net->sched.valid) return fail(QT_ESTATE, "qt_autotune: call qt_prepare first");
   qt_status s = check_ws(net, workspace, workspace_bytes, "qt_autotune");
   if (s != QT_OK) return s;
+  if (net->uploaded_gen != net->sched.generation || net->uploaded_ws != workspace ||
+      net->uploaded_data != net->data_version)
+    return fail(QT_ESTATE, "qt_autotune: call qt_upload after qt_prepare or new angles");
   std::string report, err;
   s = qt::autotune(net, workspace, stream, report, err);
   if (s != QT_OK) return fail(s, "qt_autotune: " + err);

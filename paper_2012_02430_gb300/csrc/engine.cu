@@ -1061,6 +1061,9 @@ qt_status upload(qt_net* net, void* ws, size_t bytes, void* stream, std::string&
                              "upload scalar table", err))
     return QT_ECUDA;
   (void)bytes;
+  net->uploaded_gen = S.generation;
+  net->uploaded_data = net->data_version;
+  net->uploaded_ws = ws;
   return QT_OK;
 }
 
@@ -2159,6 +2162,19 @@ qt_status download_result(const double* d_out, double* host, int64_t n_doubles, 
   return QT_OK;
 }
 
+}  // namespace qt
+
+namespace qt {
+void* engine_detach(qt_net* net) {
+  void* e = net->engine;
+  net->engine = nullptr;
+  return e;
+}
+
+void engine_restore(qt_net* net, void* saved) {
+  delete static_cast<EngineCache*>(net->engine);
+  net->engine = saved;
+}
 }  // namespace qt
 
 qt_net::~qt_net() {

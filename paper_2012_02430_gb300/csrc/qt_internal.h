@@ -216,6 +216,11 @@ struct qt_net {
   std::vector<unsigned char> gate_stage;
   std::vector<unsigned char> meta_stage;
   bool stage_dirty = true;
+  // what qt_upload last copied: the schedule generation, the gate data version (bumped
+  // by every change of angles or bitstring) and the workspace it went to
+  uint64_t data_version = 1;
+  uint64_t uploaded_gen = 0, uploaded_data = 0;
+  const void* uploaded_ws = nullptr;
   // tracing: CUDA events around every launch when enabled
   bool prof = false;
   std::vector<qt::ProfRec> prof_recs;
@@ -238,6 +243,17 @@ struct qt_net {
 };
 
 namespace qt {
+// Prepares `net` in `precision` with the largest slice batch whose workspace size plus
+// room() bytes is at most `budget` (room() is evaluated on the batch-1 schedule). Returns
+// QT_ENOMEM, with both sizes in `err`, when one slice does not fit; prepare errors as
+// qt_prepare (message in qt_last_error()).
+qt_status prepare_fitting(qt_net* net, int32_t precision, size_t budget, size_t (*room)(const qt_net*, const void*),
+                          const void* room_arg, std::string& err);
+// The engine's launch descriptors, autotuned choices and captured graph: taken out of the
+// network (which then builds a fresh cache on its next run) and put back, the fresh one
+// deleted.
+void* engine_detach(qt_net* net);
+void engine_restore(qt_net* net, void* saved);
 // Line graph of the network plus the clique on its open indices (Sec. VII: the
 // result tensor over them), those indices marked as kept.
 BitGraph network_graph(const qt_net* net);

@@ -213,3 +213,44 @@ def test_bench_workload_full(qt):
         net.prepare(prec, batch=batch)
         amp = net.contract(prec)
         assert rel_err(amp, ref) <= TOL[prec], (prec, amp, ref)
+
+
+def test_run_requires_current_upload(qt):
+    """qt_run reads only an upload of the current schedule and angles: after qt_prepare,
+    after new angles, or on another workspace it returns QT_ESTATE until qt_upload."""
+    from paper_2012_02430_gb300.inputs import random_angles
+    n, p, seed = 14, 2, 7
+    edges, gammas, betas, z, tensors, nv, norm, adj = oracle_problem(n, p, seed)
+    net = qt.Network(edges, n, p, gammas, betas, z)
+    w = net.order(0)
+    k, _ = net.slice(w - 3, 4, 1)
+    plan = oracle_plan(adj, 0, w - 3, 4, 1)
+    ref, _ = oracle_amplitude(tensors, norm, plan)
+    net.prepare(0, batch=2)
+    with pytest.raises(qt.QtError) as e:
+        run_device(qt, net, 0, 1 << k)
+    assert e.value.status == qt.QT_ESTATE
+    net.upload()
+    assert rel_err(run_device(qt, net, 0, 1 << k), ref) <= 1e-5
+    net.prepare(0, batch=1)  # a new layout: the old upload no longer matches it
+    with pytest.raises(qt.QtError) as e:
+        run_device(qt, net, 0, 1 << k)
+    assert e.value.status == qt.QT_ESTATE
+    net.upload()
+    assert rel_err(run_device(qt, net, 0, 1 << k), ref) <= 1e-5
+    g2, b2 = random_angles(p, 99)
+    qt.qt_set_angles(net.handle, g2, b2)
+    with pytest.raises(qt.QtError) as e:
+        run_device(qt, net, 0, 1 << k)
+    assert e.value.status == qt.QT_ESTATE
+    net.upload()
+    from oracle import network
+    t2, _, norm2 = network.build_network(n, edges, p, g2, b2, z)
+    ref2, _ = oracle_amplitude(t2, norm2, plan)
+    assert rel_err(run_device(qt, net, 0, 1 << k), ref2) <= 1e-5
+    other = torch.empty_like(net.workspace)
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    with pytest.raises(qt.QtError) as e:
+        qt.qt_run(net.handle, 0, 1 << k, other.data_ptr(), other.numel(),
+                  torch.cuda.current_stream().cuda_stream, out.data_ptr())
+    assert e.value.status == qt.QT_ESTATE

@@ -160,6 +160,15 @@ def test_errors(qt):
         with pytest.raises(QtError) as e:
             qt.qt_run(h, 0, 1, 256, need - 1, 0, 256)
         assert e.value.status == qt.QT_ENOMEM
+        # a workspace that never received qt_upload for this schedule: refused before any
+        # CUDA call, so a stale layout is never read
+        with pytest.raises(QtError) as e:
+            qt.qt_run(h, 0, 1, 256, need, 0, 256)
+        assert e.value.status == qt.QT_ESTATE
+        assert "qt_upload" in str(e.value)
+        with pytest.raises(QtError) as e:
+            qt.qt_autotune(h, 256, need, 0)
+        assert e.value.status == qt.QT_ESTATE
     finally:
         qt.qt_free(h)
 
@@ -411,6 +420,23 @@ def test_mlp_forward_host_matches_oracle(qt):
                                          batch, y.ctypes.data_as(fp)))
     ref, _ = mlp.forward(p.astype(np.float64), x.astype(np.float64), nf, hidden)
     assert np.max(np.abs(y - ref)) <= 1e-5 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_mlp_forward_host_hand_example(qt):
+    """The library's host forward on the hand-worked 2-3-3-1 example (values exact in FP32)."""
+    import ctypes as C
+    import json
+    import numpy as np
+    with open(os.path.join(ROOT, "tests", "golden", "mlp_hand.json")) as f:
+        g = json.load(f)
+    p = np.concatenate([np.ravel(g["W1"]), g["b1"], np.ravel(g["W2"]), g["b2"], g["w3"],
+                        [g["b3"]]]).astype(np.float32)
+    x = np.array(g["x"], dtype=np.float32)
+    y = np.zeros(len(x), dtype=np.float32)
+    fp = C.POINTER(C.c_float)
+    qt._check(qt.lib.qt_mlp_forward_host(p.ctypes.data_as(fp), g["nf"], g["hidden"],
+                                         x.ctypes.data_as(fp), len(x), y.ctypes.data_as(fp)))
+    assert y.tolist() == g["y"]
 
 
 def test_segment_option_range(qt):

@@ -2,10 +2,13 @@
 
 Such a caller (a plugin inside an application that owns the CUDA allocator, or a
 path that must not allocate) passes only inputs and outputs; the library keeps its
-device scratch in one static array. This test calls the entry point through the C
-ABI twice in a row and checks each result against the workspace-based qt_contract
-on the same network, within the tolerances of the other parity tests. It is in a
-file of its own so that it runs last.
+device scratch in one static array. These tests call the entry point through the C
+ABI twice in a row and check each result against the workspace-based qt_contract on
+the same network, within the tolerances of the other parity tests: with the default
+kernels, and with the tensor-copy (TMA) GEMM and triangle kernels forced, whose
+tensor maps then describe the static array. They also check that the caller's own
+prepared schedule, upload and autotuned choices survive the static calls. The file
+is named to run last.
 """
 
 import pytest
@@ -18,6 +21,13 @@ pytestmark = pytest.mark.gpu
 TOL = {0: 1e-5, 4: 1e-10}
 
 
+def _static_twice(qt, net, prec):
+    stream = torch.cuda.current_stream().cuda_stream
+    first = qt.qt_contract_static(net.handle, prec, stream)
+    second = qt.qt_contract_static(net.handle, prec, stream)
+    return first, second
+
+
 @pytest.mark.parametrize("prec", [0, 4])
 def test_static_matches_workspace_contract(qt, prec):
     n, p, seed = 24, 3, 15
@@ -28,14 +38,38 @@ def test_static_matches_workspace_contract(qt, prec):
     assert k >= 1
     net.prepare(prec, batch=2)
     ref = net.contract(prec)
-    stream = torch.cuda.current_stream().cuda_stream
-    first = qt.qt_contract_static(net.handle, prec, stream)
-    second = qt.qt_contract_static(net.handle, prec, stream)
+    net.autotune()
+    first, second = _static_twice(qt, net, prec)
     assert rel_err(first, ref) <= TOL[prec], (first, ref)
     assert rel_err(second, ref) <= TOL[prec], (second, ref)
-    # the workspace path still works after the static one re-planned the batch
-    again = net.contract(prec)
+    # the caller's schedule, its upload to the caller's workspace and the autotuned
+    # choices are untouched: a device-resident run needs no new qt_upload
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    net.run(0, 1 << k, out)
+    torch.cuda.synchronize()
+    again = complex(out[0].item(), out[1].item())
     assert rel_err(again, ref) <= TOL[prec]
+    assert net.stats()["batch"] == 2
+
+
+@pytest.mark.parametrize("form", ["gemm", "triangle"])
+def test_static_tensor_copy_kernels(qt, form):
+    """The TMA-staged GEMM (forced GEMM form) and triangle kernels on the static array."""
+    n, p, seed, off = (44, 2, 14, -4) if form == "gemm" else (32, 3, 25, 0)
+    edges, gammas, betas, z, *_ = oracle_problem(n, p, seed)
+    net = qt.Network(edges, n, p, gammas, betas, z)
+    qt.qt_set_option(net.handle, qt.QT_OPT_GEMM if form == "gemm" else qt.QT_OPT_TRIANGLE, 1)
+    qt.qt_set_option(net.handle, qt.QT_OPT_TMA, 1)
+    w = net.order(0)
+    if off:
+        net.slice(w + off, 6, 1)
+    net.prepare(0, batch=2)
+    ref = net.contract(0)
+    before = net.stats()["tma_gemm_launches"]
+    first, second = _static_twice(qt, net, 0)
+    assert net.stats()["tma_gemm_launches"] > before  # the static calls took the TMA kernels
+    assert rel_err(first, ref) <= 1e-5, (first, ref)
+    assert rel_err(second, ref) <= 1e-5, (second, ref)
 
 
 def test_static_rejects_oversized_network(qt):
