@@ -309,7 +309,8 @@ def ours(args):
     kind_names = {0: "k_bucket_flat", 1: "k_bucket_tiled", 2: "k_finalize+k_reduce",
                   3: "gemm_form (k_gemm_pack x2 + k_gemm_tc/simt)",
                   4: "gemm_tile (k_gemm_fold + k_gemm_tma)", 5: "k_segment",
-                  6: "k_tri_tma", 7: "gemm_stream (k_gemm_fold + k_gemm_stream)"}
+                  6: "k_tri_tma", 7: "gemm_stream (k_gemm_fold + k_gemm_stream)",
+                  8: "gemm_tcgen05 (k_gemm_fold + k_gemm_umma)"}
     tot_ms = sum(d["ms"] for d in by_kind.values()) or 1.0
     dom = max(by_kind, key=lambda kk: by_kind[kk]["ms"])
     d = by_kind[dom]

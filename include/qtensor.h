@@ -385,9 +385,26 @@ void qt_mlp_free(qt_mlp* mlp);
  *                  memory) run on up to 4 streams at once, joined by events;
  *                  0: one stream. Results are the same either way. Discards the
  *                  prepared schedule.
+ *   QT_OPT_TCGEN05 In QT_TF32 and QT_3XTF32 modes, GEMM-form launches whose
+ *                  shape allows it run on the tcgen05 tensor cores (operand rows
+ *                  gathered by TMA tensor copies, split into TF32 planes in
+ *                  shared memory, products accumulated in tensor memory; the
+ *                  complex product as one real product of doubled size).
+ *                  0 (default): that kernel is the launch's default and one of
+ *                  the autotuner's candidates beside the FP32 kernels (which are
+ *                  at least as accurate); other GEMM-form launches run the FP32
+ *                  GEMM. Its tiles take as many output columns per product as
+ *                  tensor memory allows (two accumulator buffers of 512 columns).
+ *                  1: it is used wherever it applies, also after qt_autotune.
+ *                  2: never; GEMM-form launches use the warp-level mma.sync
+ *                  kernels as in QT_BF16 mode. 3: as 1, with tiles that instead
+ *                  cover the longest run of lowest output indices (up to 16
+ *                  batch values side by side, contiguous output runs, narrower
+ *                  products). Other values: QT_EINVAL. Discards the prepared
+ *                  schedule.
  * Errors: QT_EINVAL for a null network or an unknown option. */
 enum { QT_OPT_FUSION = 1, QT_OPT_GRAPHS = 2, QT_OPT_GEMM = 3, QT_OPT_SEGMENTS = 4,
-       QT_OPT_TRIANGLE = 5, QT_OPT_TMA = 6, QT_OPT_CONCURRENT = 7 };
+       QT_OPT_TRIANGLE = 5, QT_OPT_TMA = 6, QT_OPT_CONCURRENT = 7, QT_OPT_TCGEN05 = 8 };
 qt_status qt_set_option(qt_net* net, int32_t option, int64_t value);
 
 /*

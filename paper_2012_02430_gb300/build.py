@@ -20,7 +20,7 @@ LIB = os.path.join(LIBDIR, "libqtensor.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["api.cpp", "host_graph.cpp", "host_schedule.cpp", "engine.cu", "noalloc.cu",
-           "energy_host.cpp", "energy.cu", "learn.cpp", "mlp.cu", "gemm.cu"]
+           "energy_host.cpp", "energy.cu", "learn.cpp", "mlp.cu", "gemm.cu", "umma.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -357,6 +357,7 @@ qt_status qt_prepare(qt_net* net, int32_t precision, int32_t batch, size_t* work
     net->sched.force_stream = net->force_stream;
     net->sched.force_tri = net->force_tri;
     net->sched.tma_block = net->tma_block;
+    net->sched.tcgen05 = net->tcgen05;
   } catch (const std::bad_alloc&) {
     net->sched = qt::Schedule();
     return fail(QT_ENOMEM, "qt_prepare: out of host memory");
@@ -373,7 +374,8 @@ qt_status qt_stats(const qt_net* net, char* buf, size_t cap, size_t* needed) {
   s.pop_back();
   s += ",\"launches\":" + std::to_string(net->launches) +
        ",\"tma_gemm_launches\":" + std::to_string(net->tma_launches) +
-       ",\"stream_gemm_launches\":" + std::to_string(net->stream_launches) + "}";
+       ",\"stream_gemm_launches\":" + std::to_string(net->stream_launches) +
+       ",\"tcgen05_gemm_launches\":" + std::to_string(net->umma_launches) + "}";
   if (needed) *needed = s.size() + 1;
   if (buf && cap > 0) {
     size_t n = std::min(cap - 1, s.size());
@@ -662,6 +664,11 @@ qt_status qt_set_option(qt_net* net, int32_t option, int64_t value) {
       if (value < 0 || value > 4) return fail(QT_EINVAL, "qt_set_option: QT_OPT_TMA takes 0..4");
       net->tma = value != 0;
       net->tma_block = value >= 2 ? (int)value - 1 : 0;
+      net->sched = qt::Schedule();  // prepare again
+      break;
+    case QT_OPT_TCGEN05:
+      if (value < 0 || value > 3) return fail(QT_EINVAL, "qt_set_option: QT_OPT_TCGEN05 takes 0..3");
+      net->tcgen05 = (int)value;
       net->sched = qt::Schedule();  // prepare again
       break;
     default:

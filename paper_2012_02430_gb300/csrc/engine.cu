@@ -1117,12 +1117,27 @@ constexpr int VARIANT_GEMM = 3;
 constexpr int VARIANT_TRI = 4;
 constexpr int VARIANT_FLAT = 5;  // the flat kernel for a launch the tiled kernel takes
 constexpr int VARIANT_STREAM = 6;  // the GEMM form's streaming kernel
-constexpr int N_ALL_VARIANTS = 7;
+constexpr int VARIANT_UMMA = 7;    // the GEMM form on the tcgen05 tensor cores
+constexpr int N_ALL_VARIANTS = 8;
+
+static bool tc_precision(int p) { return p == QT_TF32 || p == QT_BF16 || p == QT_3XTF32; }
+
+// GEMM-form launches use the warp-level mma.sync kernels (BF16 mode, or tcgen05 off)
+static bool legacy_tc(const Schedule& S) {
+  return S.precision == QT_BF16 || (tc_precision(S.precision) && S.tcgen05 == 2);
+}
+
+// products per input pair of the tcgen05 kernel in this mode (0: the mode does not use it)
+static int umma_passes(const Schedule& S) {
+  if (S.tcgen05 == 2) return 0;
+  return S.precision == QT_TF32 ? 1 : (S.precision == QT_3XTF32 ? 3 : 0);
+}
 
 // GEMM flavour of a GEMM-form launch in a precision mode
 static int gemm_mode_for(const Schedule& S, const SGroup& g) {
   const int mb = __builtin_popcount(g.mM), nb = __builtin_popcount(g.mN);
   const bool tc_shape = mb >= 4 && nb >= 3;  // at least one full 16 x 8 tile
+  if (!legacy_tc(S)) return GEMM_SIMT;  // the FP32 GEMM (the tiled kernel where it applies)
   switch (S.precision) {
     case QT_TF32: return tc_shape ? GEMM_TC_TF32 : GEMM_SIMT;
     case QT_BF16: return tc_shape ? GEMM_TC_BF16 : GEMM_SIMT;
@@ -1130,8 +1145,6 @@ static int gemm_mode_for(const Schedule& S, const SGroup& g) {
     default: return GEMM_SIMT;
   }
 }
-
-static bool tc_precision(int p) { return p == QT_TF32 || p == QT_BF16 || p == QT_3XTF32; }
 
 static void fill_gemm(const Schedule& S, const SGroup& g, long long nslices, GemmArgs& a) {
   a = GemmArgs{};
@@ -1187,7 +1200,18 @@ static void fill_gemm(const Schedule& S, const SGroup& g, long long nslices, Gem
   a.tile_inner = gemm_tile_inner(a, g.u);
   a.stay = gemm_tile_stay(a);
   a.ws_elems = (long long)(S.total_bytes / 8);
+  a.umma_shape = S.tcgen05 == 3 ? 0 : 1;  // wide products unless the long-run tiles are asked for
   gemm_tile_regs(a, S.tma_block);
+}
+
+// the tcgen05 kernel takes this GEMM-form launch in the schedule's mode
+static bool umma_applies(const Schedule& S, const SGroup& g, long long nslices) {
+  const int np = umma_passes(S);
+  if (!g.gemm || !np) return false;
+  GemmArgs a;
+  fill_gemm(S, g, nslices, a);
+  UmmaPlan p;
+  return umma_plan(a, np, p);
 }
 
 // Triangle form of a launch (three large operands; see gemm.cu k_tri_tile).
@@ -1334,10 +1358,13 @@ template <typename R>
 static bool make_desc(const Schedule& S, int gi, long long nslices, LaunchDesc& d,
                       std::string& err, int variant = -1) {
   const SGroup& st = S.groups[gi];
-  if (variant < 0)
+  if (variant < 0) {
     variant = st.gemm && (tc_precision(S.precision) || S.force_gemm)
                   ? (S.force_stream && !tc_precision(S.precision) ? VARIANT_STREAM : VARIANT_GEMM)
                   : (st.tri && S.force_tri ? VARIANT_TRI : 1);
+    if (st.gemm && sizeof(R) == 4 && umma_passes(S) && umma_applies(S, st, nslices))
+      variant = VARIANT_UMMA;
+  }
   KStep& k = d.k;
   k = KStep{};
   k.m = (int)st.ops.size();
@@ -1378,7 +1405,19 @@ static bool make_desc(const Schedule& S, int gi, long long nslices, LaunchDesc& 
   d.kind = tiled ? 1 : 0;
   d.variant = variant;
   d.gemm_mode = -1;
-  if (variant == VARIANT_STREAM && st.gemm && sizeof(R) == 4 && !tc_precision(S.precision)) {
+  if (variant == VARIANT_UMMA && st.gemm && sizeof(R) == 4) {
+    fill_gemm(S, st, nslices, d.ga);
+    UmmaPlan up;
+    const int np = umma_passes(S);
+    if (np && umma_plan(d.ga, np, up)) {
+      d.kind = 3;
+      d.gemm_mode = np == 1 ? GEMM_UMMA_TF32 : GEMM_UMMA_3XTF32;
+      d.grid = 0;
+      return true;
+    }
+    variant = VARIANT_GEMM;  // the tensor-core kernel does not apply: the FP32 GEMM
+  }
+  if (variant == VARIANT_STREAM && st.gemm && sizeof(R) == 4 && !legacy_tc(S)) {
     fill_gemm(S, st, nslices, d.ga);
     if (gemm_stream_ok(d.ga)) {
       d.ga.use_stream = 1;
@@ -1745,9 +1784,12 @@ static void launch_desc(qt_net* net, const LaunchDesc& d0, long long nslices, lo
   R* data = reinterpret_cast<R*>(base);
   Meta* meta = reinterpret_cast<Meta*>(base + S.off_meta);
   // (profile class 7: the GEMM form's streaming kernel)
-  ProfRec pr{S.groups[d0.group].first, d0.kind == 4 && d0.ga.use_stream ? 7 : d0.kind, nslices,
-             d0.bytes * nslices, d0.flops * nslices,
-             nullptr, nullptr};
+  // (profile class 7: the GEMM form's streaming kernel; 8: the tcgen05 GEMM)
+  const bool umma = d0.kind == 3 &&
+                    (d0.gemm_mode == GEMM_UMMA_TF32 || d0.gemm_mode == GEMM_UMMA_3XTF32);
+  ProfRec pr{S.groups[d0.group].first,
+             umma ? 8 : (d0.kind == 4 && d0.ga.use_stream ? 7 : d0.kind), nslices,
+             d0.bytes * nslices, d0.flops * nslices, nullptr, nullptr};
   if (net->prof) prof_begin(net, s, pr);
   if (d0.kind == 6) {
     GemmArgs ga = d0.ga;
@@ -1771,7 +1813,8 @@ static void launch_desc(qt_net* net, const LaunchDesc& d0, long long nslices, lo
     bool tma = false;
     net->launches += gemm_launch(ga, d0.gemm_mode, reinterpret_cast<float*>(base),
                                  reinterpret_cast<GMeta*>(meta), s, num_sms(), &tma);
-    if (tma) net->tma_launches++;
+    if (tma && umma) net->umma_launches++;
+    else if (tma) net->tma_launches++;
     if (ga.use_stream) net->stream_launches++;
     if (net->prof) prof_end(net, s, pr);
     return;
@@ -1876,16 +1919,20 @@ static qt_status autotune_impl(qt_net* net, char* base, cudaStream_t s, std::str
     for (size_t i = 0; i < list.size(); ++i) {
       LaunchDesc& d = list[i];
       const SGroup& grp = S.groups[d.group];
-      const bool can_gemm = grp.gemm && !tc_precision(S.precision) && sizeof(R) == 4;
-      const bool can_tri = grp.tri && !tc_precision(S.precision) && sizeof(R) == 4;
+      // the FP32 GEMM, streaming and triangle kernels are candidates in every mode but
+      // the legacy tensor-core one (they are at least as accurate as TF32 products)
+      const bool can_gemm = grp.gemm && !legacy_tc(S) && sizeof(R) == 4;
+      const bool can_tri = grp.tri && !legacy_tc(S) && sizeof(R) == 4;
+      const bool can_umma = grp.gemm && sizeof(R) == 4 && umma_applies(S, grp, d.k.nslices);
       if (d.kind == 0 || d.kind == 5 ||
-          ((d.kind == 3 || d.kind == 4) && (tc_precision(S.precision) || S.force_gemm)) ||
-          (d.kind == 6 && S.force_tri)) {
+          ((d.kind == 3 || d.kind == 4) && (legacy_tc(S) || S.force_gemm)) ||
+          (d.kind == 6 && S.force_tri) || (can_umma && (S.tcgen05 == 1 || S.tcgen05 == 3))) {
         launch_desc<R>(net, d, nb, b0, base, s);
         continue;
       }
       std::vector<int> cands;
       for (int v = 0; v < N_VARIANTS; ++v) cands.push_back(v);
+      if (can_umma) cands.push_back(VARIANT_UMMA);
       if (can_gemm) cands.push_back(VARIANT_GEMM);
       if (can_gemm) {
         GemmArgs ga;
@@ -1946,10 +1993,11 @@ static qt_status autotune_impl(qt_net* net, char* base, cudaStream_t s, std::str
       char buf[200];
       auto half = [](float x) { return x >= 1e29f ? -1.0 : x / 2.0; };
       std::snprintf(buf, sizeof buf,
-                    "%s{\"step\":%d,\"variant\":%d,\"ms\":[%.4f,%.4f,%.4f,%.4f,%.4f,%.4f,%.4f]}",
+                    "%s{\"step\":%d,\"variant\":%d,\"ms\":[%.4f,%.4f,%.4f,%.4f,%.4f,%.4f,%.4f,%.4f]}",
                     first ? "" : ",", S.groups[d.group].first, bv, half(kv.second[0]),
                     half(kv.second[1]), half(kv.second[2]), half(kv.second[3]),
-                    half(kv.second[4]), half(kv.second[5]), half(kv.second[6]));
+                    half(kv.second[4]), half(kv.second[5]), half(kv.second[6]),
+                    half(kv.second[7]));
       report += buf;
       first = false;
     }
@@ -2083,6 +2131,27 @@ static bool launch_plan_impl(qt_net* net, std::string& out, std::string& err) {
     spans(rd[x]);
     o << ",\"writes\":";
     spans(wr[x]);
+    UmmaPlan up;
+    if (d.kind == 3 && (d.gemm_mode == GEMM_UMMA_TF32 || d.gemm_mode == GEMM_UMMA_3XTF32) &&
+        umma_plan(d.ga, d.gemm_mode == GEMM_UMMA_TF32 ? 1 : 3, up)) {
+      // the tcgen05 tiling: masks over the launch's U bits, sizes, tile order
+      o << ",\"umma\":{\"lside\":" << up.lside << ",\"nsum\":" << up.nsum << ",\"cb\":" << up.cb
+        << ",\"gb\":" << up.gb << ",\"passes\":" << up.passes << ",\"sraw\":" << up.sraw
+        << ",\"splane\":" << up.splane << ",\"tmem_cols\":" << up.tmem_cols
+        << ",\"smem\":" << umma_smem(up) << ",\"mlane\":" << up.mlane << ",\"mcol\":" << up.mcol
+        << ",\"mgrp\":" << up.mgrp << ",\"mM\":" << d.ga.mM << ",\"mN\":" << d.ga.mN
+        << ",\"mBt\":" << d.ga.mBt << ",\"mK\":" << d.ga.mK << ",\"cwb\":" << up.cwb
+        << ",\"rb\":" << up.rb << ",\"chunk_out\":" << up.chunk_out << ",\"prefix\":" << up.prefix
+        << ",\"lruns\":[";
+      for (int q = 0; q < up.nlrun; ++q)
+        o << (q ? "," : "") << "[" << up.lrun_start[q] << "," << up.lrun_len[q] << "]";
+      o << "],\"cruns\":[";
+      for (int q = 0; q < up.ncrun; ++q)
+        o << (q ? "," : "") << "[" << up.crun_start[q] << "," << up.crun_len[q] << "]";
+      o << "],\"rest\":[";
+      for (int q = 0; q < up.nrest; ++q) o << (q ? "," : "") << up.rest[q];
+      o << "]}";
+    }
     o << "}";
   }
   o << "]}";

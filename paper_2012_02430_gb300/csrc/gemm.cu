@@ -2283,9 +2283,31 @@ static StreamFn stream_fn(int nsum) {
   }
 }
 
-int gemm_launch(const GemmArgs& a, int mode, float* data, GMeta* meta, cudaStream_t s, int sms,
+int gemm_launch(const GemmArgs& a, int mode_in, float* data, GMeta* meta, cudaStream_t s, int sms,
                 bool* used_tma) {
   if (used_tma) *used_tma = false;
+  int mode = mode_in;
+  if (mode == GEMM_UMMA_TF32 || mode == GEMM_UMMA_3XTF32) {
+    // tcgen05 tensor cores: the folds of A' and B', then one launch; a launch the
+    // kernel cannot take (alignment, tensor maps) runs as the FP32 tiled GEMM
+    UmmaPlan p;
+    if (umma_plan(a, mode == GEMM_UMMA_TF32 ? 1 : 3, p)) {
+      int n = 0;
+      for (int side = 0; side < 2; ++side) {
+        if (!(side ? a.fold_b : a.fold_a)) continue;
+        const long long work = a.nslices << __builtin_popcount(a.op[side ? a.gB : a.gA].umask);
+        const long long g = std::min<long long>((work + 255) / 256, (long long)sms * 16);
+        k_gemm_fold<<<(unsigned)std::max<long long>(1, g), 256, 0, s>>>(a, side, data, meta);
+        ++n;
+      }
+      if (umma_launch(a, p, data, meta, s, sms)) {
+        if (used_tma) *used_tma = true;
+        return n + 1;
+      }
+      // the folds already ran; the tiled kernel below folds again (same values)
+    }
+    mode = a.tb > 0 ? GEMM_TILE : GEMM_SIMT;
+  }
   if (mode == GEMM_TILE && a.use_stream) {
     int n = 0;
     const int gs = gemm_tile_stay(a);

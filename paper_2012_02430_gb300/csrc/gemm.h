@@ -8,7 +8,8 @@
 
 namespace qt {
 
-enum { GEMM_SIMT = 0, GEMM_TC_TF32 = 1, GEMM_TC_BF16 = 2, GEMM_TC_3XTF32 = 3, GEMM_TILE = 4 };
+enum { GEMM_SIMT = 0, GEMM_TC_TF32 = 1, GEMM_TC_BF16 = 2, GEMM_TC_3XTF32 = 3, GEMM_TILE = 4,
+       GEMM_UMMA_TF32 = 5, GEMM_UMMA_3XTF32 = 6 };
 
 constexpr int GEMM_MAXOP = 12;
 
@@ -44,6 +45,7 @@ struct GemmArgs {
   int stay;                 // GEMM_TILE: 0 the tiles of a group share A's block, 1 B's
   int use_stream;           // GEMM_TILE: the streaming kernel (gemm_stream_ok) instead
   long long ws_elems;       // workspace size (complex): the extent of the tensor maps
+  int umma_shape;           // tcgen05 tiles: 0 the longest output runs, 1 the widest products (default)
   int* err;                 // device status word: set to 1 when a bounded wait gives up
   GOp op[GEMM_MAXOP];
 };
@@ -79,5 +81,37 @@ int tri_launch(const GemmArgs& a, float* data, GMeta* meta, cudaStream_t s, int 
 // other modes: pack A', pack B', GEMM. Returns the number of kernels launched.
 int gemm_launch(const GemmArgs& a, int mode, float* data, GMeta* meta, cudaStream_t s, int sms,
                 bool* used_tma = nullptr);
+
+// GEMM form on the tcgen05 tensor cores (umma.cu). A tile: one slice, 128 rows of
+// the lane side (its 7 lowest only-indices: the MMA's M), 2^cb rows of the column side
+// (the MMA's N is twice that: re and im rows) and 2^gb values of batch indices, all
+// chosen by walking the output indices from the lowest so that the tile covers as
+// long a prefix of them as tensor memory allows (contiguous output runs). A work unit
+// is one group value: its lane-side and column-side rows, one TMA box each. Masks are
+// over the launch's U bits.
+struct UmmaPlan {
+  int lside;                 // 0: A gives the lanes (M), B the columns; 1: the reverse
+  int nsum, cb, gb;          // summed indices; column bits (Nt = 2^cb); group bits (G = 2^gb)
+  int passes;                // 1 TF32, 3 split TF32 (hi.hi + hi.lo + lo.hi)
+  int sraw, splane;          // units of raw rows and of split planes in shared memory
+  int tmem_cols;             // tensor-memory columns allocated per block
+  unsigned int mlane, mcol, mgrp;
+  int nrest;                 // U bits that enumerate the tiles, in tile order
+  int rest[32];
+  // a unit's rows in each operand's row index: runs of consecutive row bits
+  int nlrun, lrun_start[3], lrun_len[3];
+  int ncrun, crun_start[3], crun_len[3];
+  int cwb;                   // epilogue chunk: 2^cwb columns x G groups x 32 lanes of a warp
+  int rb;                    // contiguous output runs of 2^rb complex inside a chunk
+  unsigned int chunk_out;    // the chunk's output bits (the run index takes those above rb)
+  int prefix;                // output indices from the lowest that the tile covers
+};
+// The launch takes the form (false: it does not; the caller keeps another kernel).
+bool umma_plan(const GemmArgs& a, int passes, UmmaPlan& p);
+size_t umma_smem(const UmmaPlan& p);
+// Launches k_gemm_umma (the folds of A', B' must have run); false if the operand rows
+// or the output are not aligned as the kernel needs, or a tensor map does not encode.
+bool umma_launch(const GemmArgs& a, const UmmaPlan& p, float* data, GMeta* meta, cudaStream_t s,
+                 int sms);
 
 }  // namespace qt

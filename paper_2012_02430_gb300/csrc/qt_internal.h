@@ -138,6 +138,7 @@ struct Schedule {
   bool force_stream = false;     // copy of the network option at compile time
   bool force_tri = false;        // copy of the network option at compile time
   int tma_block = 0;             // copy of the network option at compile time
+  int tcgen05 = 0;               // copy of the network option at compile time
   bool fused = true;             // steps grouped into fused launches
   uint64_t generation = 0;      // changes with every compile
   int precision = QT_FP32_SIMT;
@@ -238,6 +239,8 @@ struct qt_net {
   int64_t tma_launches = 0;      // tiled GEMM launches that took the tensor-copy staging
   int tma_block = 0;             // tiled GEMM register block: 0 chosen, 1 2 x 2, 2 / 3 wide
   int64_t stream_launches = 0;   // GEMM-form launches by the streaming kernel
+  int tcgen05 = 0;               // GEMM form on tcgen05: 0 default + autotuned, 1 forced, 2 never
+  int64_t umma_launches = 0;     // GEMM-form launches by the tcgen05 kernel
   void* engine = nullptr;        // engine.cu: launch descriptors and graph cache
   ~qt_net();
 };

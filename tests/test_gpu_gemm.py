@@ -74,9 +74,28 @@ def test_gemm_stream_kernel(qt, case):
 @pytest.mark.parametrize("prec", [3, 1, 2])
 @pytest.mark.parametrize("case", CASES)
 def test_gemm_form_tensor_cores(qt, case, prec):
+    """TF32 and split-TF32 modes: GEMM-form launches on the tcgen05 kernel where it
+    applies (profile class 8), the FP32 GEMM elsewhere; BF16: the warp-level mma.sync
+    kernel (pack + GEMM, class 3)."""
     amp, ref, st, kinds = _amp(qt, *case, prec, profile=True)
-    assert st["gemm_groups"] >= 1 and 3 in kinds
+    assert st["gemm_groups"] >= 1 and kinds & ({3} if prec == 2 else {3, 4, 8})
     assert rel_err(amp, ref) <= TOL[prec], (prec, amp, ref, rel_err(amp, ref))
+
+
+@pytest.mark.parametrize("prec", [3, 1])
+@pytest.mark.parametrize("case", CASES)
+def test_gemm_form_legacy_mma_sync(qt, case, prec):
+    """QT_OPT_TCGEN05 = 2: TF32 modes on the warp-level mma.sync kernels."""
+    edges, gammas, betas, z, tensors, nv, norm, adj = oracle_problem(case[0], case[1], case[2])
+    net = qt.Network(edges, case[0], case[1], gammas, betas, z)
+    qt.qt_set_option(net.handle, qt.QT_OPT_TCGEN05, 2)
+    w = net.order(0)
+    net.slice(w + case[3], 6, 1)
+    net.prepare(prec, batch=3)
+    amp = net.contract(prec)
+    assert net.stats()["tcgen05_gemm_launches"] == 0
+    ref, _ = oracle_amplitude(tensors, norm, oracle_plan(adj, 0, w + case[3], 6, 1))
+    assert rel_err(amp, ref) <= TOL[prec], (prec, rel_err(amp, ref))
 
 
 @pytest.mark.parametrize("prec", [3, 1, 2])

@@ -588,3 +588,62 @@ def test_launch_plan_orders_every_conflict(qt, case):
     # more than one stream carries work on the larger plans
     if n >= 60:
         assert len({d["stream"] for d in launches}) > 1
+
+
+UMMA_PLAN_CASES = [(30, 3, 5, -4), (44, 2, 3, -2), (60, 2, 19, -4), (50, 2, 7, -2),
+                   (48, 2, 5, 0), (44, 3, 15, -2), (50, 2, 22, -4), (24, 3, 21, 0),
+                   (80, 2, 1002, 26 - 35)]
+
+
+@pytest.mark.parametrize("case", UMMA_PLAN_CASES)
+def test_tcgen05_plan_invariants(qt, case):
+    """The tcgen05 GEMM's tiling of each launch it takes (host planning, no GPU): 128 lanes
+    from the 7 lowest only-indices of one side, at least 8 columns from the other side,
+    group indices among the batch indices, every output index in exactly one of lanes,
+    columns, group and tile indices; the tile covers a prefix of the output indices as
+    long as tensor memory allows; an epilogue chunk's runs start at output bit 0; the
+    unit boxes' row runs add up to the lanes and columns; tensor and shared memory in
+    range."""
+    n, p, seed, off = case
+    edges, gammas, betas, z, *_ = oracle_problem(n, p, seed)
+    h = qt.qt_build_network(edges, n, p, gammas, betas, z)
+    try:
+        qt.qt_set_option(h, qt.QT_OPT_TCGEN05, 1)
+        w = qt.qt_order(h, 0)
+        if off:
+            qt.qt_slice(h, w + off, 20 if n == 80 else 6, 1)
+        qt.qt_prepare(h, 3, 2)
+        plans = [L["umma"] for L in qt.qt_launch_plan(h)["launches"] if "umma" in L]
+    finally:
+        qt.qt_free(h)
+    assert plans
+    pop = lambda m: bin(m).count("1")
+    for u in plans:
+        ns = u["nsum"]
+        assert u["mK"] == (1 << ns) - 1 and 2 <= ns <= 6
+        lonly, conly = (u["mM"], u["mN"]) if u["lside"] == 0 else (u["mN"], u["mM"])
+        lowest = lambda m, k: sum(1 << b for b in sorted(b for b in range(32) if m >> b & 1)[:k])
+        assert pop(u["mlane"]) == 7 and u["mlane"] == lowest(lonly, 7)
+        assert u["mcol"] & ~conly == 0 and pop(u["mcol"]) == u["cb"] and 3 <= u["cb"] <= 7
+        assert u["mgrp"] & ~u["mBt"] == 0 and pop(u["mgrp"]) == u["gb"] <= 4
+        out_bits = (u["mM"] | u["mN"] | u["mBt"]) & ~((1 << ns) - 1)
+        rest = sum(1 << b for b in u["rest"])
+        parts = [u["mlane"], u["mcol"], u["mgrp"], rest]
+        assert sum(pop(x) for x in parts) == pop(out_bits)
+        assert parts[0] | parts[1] | parts[2] | parts[3] == out_bits
+        tile = u["mlane"] | u["mcol"] | u["mgrp"]
+        # the covered prefix: output bits ns .. ns + prefix - 1 all belong to the tile
+        assert u["prefix"] >= 1 and all(tile >> b & 1 for b in range(ns, ns + u["prefix"]))
+        G, Nt = 1 << u["gb"], 1 << u["cb"]
+        assert G * Nt <= 128
+        cols = u["tmem_cols"]
+        assert cols & (cols - 1) == 0 and 4 * G * Nt <= cols <= 512
+        # epilogue chunk: lanes 0-4, the groups and the lowest 2^cwb columns, in output bits
+        chunk = (lowest(u["mlane"], 5) | u["mgrp"] | lowest(u["mcol"], u["cwb"])) >> ns
+        assert u["chunk_out"] == chunk and pop(chunk) == 5 + u["gb"] + u["cwb"] <= 10
+        assert u["rb"] >= 1 and chunk & ((1 << u["rb"]) - 1) == (1 << u["rb"]) - 1
+        assert not (chunk >> u["rb"]) & 1
+        assert sum(l for _, l in u["lruns"]) == 7 and sum(l for _, l in u["cruns"]) == u["cb"]
+        assert 1 <= len(u["lruns"]) <= 3 and 1 <= len(u["cruns"]) <= 3
+        assert u["smem"] <= 225 * 1024 and u["passes"] == 3
+        assert 2 <= u["sraw"] <= 8 and 1 <= u["splane"] <= 4
