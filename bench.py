@@ -41,13 +41,24 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max
 #       --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
 #       python bench.py --profile-pass
 # averaged over the class's launches in the pass (its fold launches included). The roofline
-# line reports it as `traffic` when that class dominates; an entry must be dropped when its
-# kernel changes.
+# line reports it as `traffic` when that class dominates, and only while the kernel sources
+# hash to CLASS_DRAM_SOURCES (the sources the capture ran); after any change it is null.
 CLASS_DRAM_BYTES = {
-    "gemm_stream (k_gemm_fold + k_gemm_stream)": 394.8e6,  # steps 120, 121, 131
-    "gemm_tile (k_gemm_fold + k_gemm_tma)": 179.5e6,       # steps 117, 127
-    "k_tri_tma": 440.2e6,                                  # step 132
+    "gemm_stream (k_gemm_fold + k_gemm_stream)": None,  # steps 120, 121, 131
+    "gemm_tile (k_gemm_fold + k_gemm_tma)": None,       # steps 117, 127
+    "k_tri_tma": None,                                  # step 132
 }
+CLASS_DRAM_SOURCES = None
+KERNEL_SOURCES = ("engine.cu", "gemm.cu", "umma.cu", "gemm.h", "qt_internal.h")
+
+
+def kernel_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2012_02430_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -63,6 +74,8 @@ def parse():
     ap.add_argument("--no-modes", action="store_true", help="skip the precision-mode table")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-slices", type=int, default=1)
+    ap.add_argument("--no-all-cores", action="store_true",
+                    help="skip the oracle timed over all host cores")
     ap.add_argument("--profile-pass", action="store_true",
                     help="for ncu: plan, autotune and warm the amplitude path, then run one pass "
                          "inside the NVTX range 'qt_pass' (direct launches) and print its launch list")
@@ -105,6 +118,74 @@ def oracle_sample(n_slices, rank=0):
 def cpu_threads_used():
     # numpy.einsum (the oracle's contraction primitive) runs on one thread
     return 1
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+_WORKER_PLAN = None
+
+
+def _oracle_worker_init(plan):
+    global _WORKER_PLAN
+    _WORKER_PLAN = plan
+
+
+def _oracle_slice_worker(sid):
+    """One slice of the workload on the oracle, in a spawned process (plan from the parent;
+    sid < 0: start-up only)."""
+    import time as _t
+    from oracle import contract
+    tensors, order, sliced, step = _WORKER_PLAN
+    if sid < 0:
+        return 0j, 0.0
+    t0 = _t.perf_counter()
+    total, _ = contract.contract_amplitude(tensors, order, sliced, step, [sid])
+    return complex(total), _t.perf_counter() - t0
+
+
+def oracle_all_cores():
+    """Every slice of the workload at once, one spawned process per slice up to the host's
+    cores (the paper's slice-level parallelism), the partial sums added in slice order.
+    Timed from the first slice's start to the last one's end inside the workers."""
+    import multiprocessing as mp
+    ncpu = os.cpu_count() or 1
+    from oracle import network, ordering, slicing
+    edges, gammas, betas, z = instance(0)
+    tensors, nv, norm = network.build_network(WORKLOAD["n"], edges, WORKLOAD["p"], gammas, betas, z)
+    adj = ordering.adjacency_matrix(network.line_graph(tensors, nv), nv)
+    plan = slicing.step_dependent_slicing(adj, ordering.MIN_FILL, WORKLOAD["width_limit"],
+                                          WORKLOAD["max_vars"], WORKLOAD["r"])
+    nsl = 1 << len(plan["sliced"])
+    procs = min(ncpu, nsl)
+    ctx = mp.get_context("spawn")
+    wplan = (tensors, plan["order"], plan["sliced"], plan["slice_step"])
+    with ctx.Pool(procs, initializer=_oracle_worker_init, initargs=(wplan,)) as pool:
+        pool.map(_oracle_slice_worker, [-1] * procs)  # start-up and imports, untimed
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_slice_worker, list(range(nsl)))
+        wall = time.perf_counter() - t0
+    amp = sum((r[0] for r in res), 0j) * norm
+    return {"value": nsl / wall, "unit": "slices/s", "cores": procs, "host_cores": ncpu,
+            "cpu_model": cpu_model(), "kind": "oracle",
+            "sample": f"all {nsl} slices, one process per slice ({procs} processes of "
+                      f"{ncpu} cores), FP64 numpy.einsum, partial sums added in slice order",
+            "seconds": wall, "amplitude": [amp.real, amp.imag]}
 
 
 def reference_arm(args):
@@ -332,8 +413,11 @@ def ours(args):
                     "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                     "peak_source": f"{peak_src} hbm_gbs"}
     per_launch_bytes = d["bytes"] / max(1, d["n"])
-    roofline.update({"traffic": CLASS_DRAM_BYTES.get(kind_names[dom]),
+    src_hash = kernel_sources_hash()
+    traffic = CLASS_DRAM_BYTES.get(kind_names[dom]) if src_hash == CLASS_DRAM_SOURCES else None
+    roofline.update({"traffic": traffic,
                      "traffic_unit": "bytes per launch (ncu dram read + write)",
+                     "traffic_sources": {"measured_on": CLASS_DRAM_SOURCES, "now": src_hash},
                      "algorithmic_bytes_per_launch": per_launch_bytes,
                      "launches": d["n"], "flop_per_byte": intensity,
                      "ridge_flop_per_byte": ridge,
@@ -436,12 +520,23 @@ def ours(args):
         "gpu_launches": launches,
         "roofline": roofline, "clocks": clk, "e2e": e2e,
     }
+    # the whole pass against HBM: the fused launches' algorithmic bytes over the step time
+    pass_bytes = line["launch_bytes_per_step"]
+    hbm_peak, peak_src = measured_peaks()
+    line["pass_roofline"] = {"bound": "hbm", "algorithmic_bytes": pass_bytes,
+                             "achieved": pass_bytes / (total_ms / args.steps / 1e3) / 1e9,
+                             "peak": hbm_peak, "unit": "GB/s",
+                             "frac": pass_bytes / (total_ms / args.steps / 1e3) / 1e9 / hbm_peak,
+                             "peak_source": f"{peak_src} hbm_gbs"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ns, dt, _ = oracle_sample(args.cpu_sample_slices)
         line["cpu_baseline"] = {"value": ns / dt, "unit": "slices/s", "cores": cpu_threads_used(),
+                                "host_cores": os.cpu_count(), "cpu_model": cpu_model(),
                                 "kind": "oracle",
                                 "sample": f"{ns} slice(s) of the same workload, FP64 oracle "
                                           f"(numpy.einsum bucket elimination), {dt:.1f} s"}
+        if not args.no_all_cores:
+            line["cpu_baseline_all_cores"] = oracle_all_cores()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

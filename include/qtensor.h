@@ -402,9 +402,16 @@ void qt_mlp_free(qt_mlp* mlp);
  *                  batch values side by side, contiguous output runs, narrower
  *                  products). Other values: QT_EINVAL. Discards the prepared
  *                  schedule.
+ *   QT_OPT_SCALED  1: the tiled bucket kernel multiplies every operand by its
+ *                  exact power-of-two scale 2^-s (result exponent sum of E_j + s_j)
+ *                  in every slice, the path it otherwise takes only for a slice
+ *                  with an extreme exponent (|s_j| > 30, or |sum s_j| > 60);
+ *                  0 (default): that choice per slice. Values agree within
+ *                  FP32 rounding. Discards the prepared schedule.
  * Errors: QT_EINVAL for a null network or an unknown option. */
 enum { QT_OPT_FUSION = 1, QT_OPT_GRAPHS = 2, QT_OPT_GEMM = 3, QT_OPT_SEGMENTS = 4,
-       QT_OPT_TRIANGLE = 5, QT_OPT_TMA = 6, QT_OPT_CONCURRENT = 7, QT_OPT_TCGEN05 = 8 };
+       QT_OPT_TRIANGLE = 5, QT_OPT_TMA = 6, QT_OPT_CONCURRENT = 7, QT_OPT_TCGEN05 = 8,
+       QT_OPT_SCALED = 9 };
 qt_status qt_set_option(qt_net* net, int32_t option, int64_t value);
 
 /*

@@ -358,6 +358,7 @@ qt_status qt_prepare(qt_net* net, int32_t precision, int32_t batch, size_t* work
     net->sched.force_tri = net->force_tri;
     net->sched.tma_block = net->tma_block;
     net->sched.tcgen05 = net->tcgen05;
+    net->sched.force_scaled = net->force_scaled;
   } catch (const std::bad_alloc&) {
     net->sched = qt::Schedule();
     return fail(QT_ENOMEM, "qt_prepare: out of host memory");
@@ -664,6 +665,10 @@ qt_status qt_set_option(qt_net* net, int32_t option, int64_t value) {
       if (value < 0 || value > 4) return fail(QT_EINVAL, "qt_set_option: QT_OPT_TMA takes 0..4");
       net->tma = value != 0;
       net->tma_block = value >= 2 ? (int)value - 1 : 0;
+      net->sched = qt::Schedule();  // prepare again
+      break;
+    case QT_OPT_SCALED:
+      net->force_scaled = value != 0;
       net->sched = qt::Schedule();  // prepare again
       break;
     case QT_OPT_TCGEN05:

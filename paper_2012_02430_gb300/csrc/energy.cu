@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -255,8 +256,54 @@ void layout_sweep(qt_energy* E, int nsets) {
   off = a256(off + 64);
   E->sw_off_arenas = off;
   off = a256(off + (size_t)E->blocks * (size_t)E->arena_elems * eb);
+  // device assembly of the gate images: template, slots, codes, per-set table
+  if (E->sw_template.empty()) qt::energy_sweep_template(E);
+  E->sw_off_tmpl = off;
+  off = a256(off + E->sw_template.size());
+  E->sw_off_slots = off;
+  off = a256(off + E->sw_slots.size() * sizeof(uint32_t) + 4);
+  E->sw_off_codes = off;
+  off = a256(off + E->sw_codes.size() * sizeof(uint32_t) + 4);
+  E->sw_off_table = off;
+  off = a256(off + (size_t)nsets * E->p * 8 * eb);
   E->sw_total = off;
   E->sweep_sets = nsets;
+  E->sw_tmpl_ws = nullptr;
+}
+
+// Every set's gate image: the template copied, then the angle-dependent gates written
+// from the set's table (phase {1, e, e, 1} with e = exp(-i g) or its conjugate; mixer
+// {c, -i s, -i s, c}). One thread per complex element of the images, then one per gate.
+template <typename R>
+__global__ void k_sweep_copy(const R* __restrict__ tmpl, long long img_c, int nsets, R* images) {
+  using C2 = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+  const C2* src = reinterpret_cast<const C2*>(tmpl);
+  C2* dst = reinterpret_cast<C2*>(images);
+  const long long total = img_c * nsets;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    dst[e] = src[e % img_c];
+}
+
+template <typename R>
+__global__ void k_sweep_gates(const uint32_t* __restrict__ slots, const uint32_t* __restrict__ codes,
+                              int nslots, const R* __restrict__ table, int p, int nsets,
+                              long long img_c, R* images) {
+  const long long total = (long long)nslots * nsets;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(e / nslots), j = (int)(e - (long long)q * nslots);
+    const uint32_t code = codes[j];
+    const int kind = code & 15, k = (code >> 4) & 255, side = code >> 12;
+    const R* t = table + ((size_t)q * p + (k - 1)) * 8 + (kind - 1) * 4 + (side - 1) * 2;
+    const R a = t[0], b = t[1];
+    R* g = images + 2 * ((long long)q * img_c + slots[j]);
+    if (kind == 1) {
+      g[0] = R(1); g[1] = R(0); g[2] = a; g[3] = b; g[4] = a; g[5] = b; g[6] = R(1); g[7] = R(0);
+    } else {
+      g[0] = a; g[1] = R(0); g[2] = R(0); g[3] = -b; g[4] = R(0); g[5] = -b; g[6] = a; g[7] = R(0);
+    }
+  }
 }
 
 template <typename R>
@@ -628,29 +675,63 @@ qt_status qt_energy_sweep_upload(qt_energy* E, int32_t n_sets, const double* gam
   for (int64_t q = 0; q < (int64_t)n_sets * E->p; ++q)
     if (!std::isfinite(gammas[q]) || !std::isfinite(betas[q]))
       return fail(QT_EINVAL, "qt_energy_sweep_upload: angle not finite");
-  const size_t img = (size_t)E->gate_elems * (size_t)E->elem_bytes;
   try {
-    E->sweep_stage.assign((size_t)n_sets * img, 0);
+    if (E->sw_template.empty()) {  // recompiled since qt_energy_sweep_prepare: lay out again
+      layout_sweep(E, E->sweep_sets);
+      if (bytes < E->sw_total) return fail(QT_ENOMEM, "qt_energy_sweep_upload: workspace too small");
+    }
+    qt::energy_sweep_table(E, n_sets, gammas, betas);
   } catch (const std::bad_alloc&) {
     return fail(QT_ENOMEM, "qt_energy_sweep_upload: out of host memory");
   }
-  for (int q = 0; q < n_sets; ++q)
-    qt::energy_gate_image(E, gammas + (size_t)q * E->p, betas + (size_t)q * E->p,
-                          E->sweep_stage.data() + (size_t)q * img);
   std::string err;
   char* base = (char*)ws;
   cudaStream_t st = (cudaStream_t)stream;
   struct Part { size_t off; const void* src; size_t n; };
+  // structure tables and the template once per workspace; the angle table every call
+  const bool fresh = E->sw_tmpl_ws != ws;
   const Part parts[] = {
-      {E->sw_off_gates, E->sweep_stage.data(), E->sweep_stage.size()},
-      {E->sw_off_ops, E->h_ops.data(), E->h_ops.size() * sizeof(qt::EOp)},
-      {E->sw_off_steps, E->h_steps.data(), E->h_steps.size() * sizeof(qt::EStep)},
-      {E->sw_off_nets, E->h_nets.data(), E->h_nets.size() * sizeof(qt::ENet)},
-      {E->sw_off_scalars, E->h_scalars.data(), E->h_scalars.size() * sizeof(uint32_t)}};
+      {E->sw_off_ops, E->h_ops.data(), fresh ? E->h_ops.size() * sizeof(qt::EOp) : 0},
+      {E->sw_off_steps, E->h_steps.data(), fresh ? E->h_steps.size() * sizeof(qt::EStep) : 0},
+      {E->sw_off_nets, E->h_nets.data(), fresh ? E->h_nets.size() * sizeof(qt::ENet) : 0},
+      {E->sw_off_scalars, E->h_scalars.data(),
+       fresh ? E->h_scalars.size() * sizeof(uint32_t) : 0},
+      {E->sw_off_tmpl, E->sw_template.data(), fresh ? E->sw_template.size() : 0},
+      {E->sw_off_slots, E->sw_slots.data(), fresh ? E->sw_slots.size() * sizeof(uint32_t) : 0},
+      {E->sw_off_codes, E->sw_codes.data(), fresh ? E->sw_codes.size() * sizeof(uint32_t) : 0},
+      {E->sw_off_table, E->sw_table.data(), E->sw_table.size()}};
   for (const Part& p : parts)
     if (p.n && !cuda_ok(cudaMemcpyAsync(base + p.off, p.src, p.n, cudaMemcpyHostToDevice, st),
                         "sweep upload", err))
       return fail(QT_ECUDA, "qt_energy_sweep_upload: " + err);
+  E->sw_tmpl_ws = ws;
+  const long long img_c = (long long)E->gate_elems;
+  const int nslots = (int)E->sw_slots.size();
+  const unsigned gcopy = (unsigned)std::max<long long>(
+      1, std::min<long long>((img_c * n_sets + 255) / 256, 152ll * 16));
+  const unsigned ggate = (unsigned)std::max<long long>(
+      1, std::min<long long>(((long long)nslots * n_sets + 255) / 256, 152ll * 16));
+  if (E->precision == QT_FP64) {
+    double* img = reinterpret_cast<double*>(base + E->sw_off_gates);
+    k_sweep_copy<double><<<gcopy, 256, 0, st>>>(
+        reinterpret_cast<const double*>(base + E->sw_off_tmpl), img_c, n_sets, img);
+    if (nslots)
+      k_sweep_gates<double><<<ggate, 256, 0, st>>>(
+          reinterpret_cast<const uint32_t*>(base + E->sw_off_slots),
+          reinterpret_cast<const uint32_t*>(base + E->sw_off_codes), nslots,
+          reinterpret_cast<const double*>(base + E->sw_off_table), E->p, n_sets, img_c, img);
+  } else {
+    float* img = reinterpret_cast<float*>(base + E->sw_off_gates);
+    k_sweep_copy<float><<<gcopy, 256, 0, st>>>(
+        reinterpret_cast<const float*>(base + E->sw_off_tmpl), img_c, n_sets, img);
+    if (nslots)
+      k_sweep_gates<float><<<ggate, 256, 0, st>>>(
+          reinterpret_cast<const uint32_t*>(base + E->sw_off_slots),
+          reinterpret_cast<const uint32_t*>(base + E->sw_off_codes), nslots,
+          reinterpret_cast<const float*>(base + E->sw_off_table), E->p, n_sets, img_c, img);
+  }
+  if (!cuda_ok(cudaGetLastError(), "sweep image kernels", err))
+    return fail(QT_ECUDA, "qt_energy_sweep_upload: " + err);
   qt::set_last_error("");
   return QT_OK;
 }

@@ -115,6 +115,8 @@ bool energy_build_networks(qt_energy* E, std::string& err) {
 }
 
 bool energy_compile(qt_energy* E, int precision, std::string& err) {
+  E->sw_template.clear();  // the sweep's template follows the compiled layout
+  E->sw_tmpl_ws = nullptr;
   const int ne = (int)E->nets.size();
   E->precision = precision;
   E->elem_bytes = precision == QT_FP64 ? 16 : 8;
@@ -262,6 +264,64 @@ void energy_gate_image(const qt_energy* E, const double* gammas, const double* b
     }
     base += S.gate_elems;
   }
+}
+
+void energy_sweep_template(qt_energy* E) {
+  const bool f64 = E->precision == QT_FP64;
+  const size_t eb = f64 ? sizeof(double) : sizeof(float);
+  E->sw_template.assign((size_t)E->gate_elems * 2 * eb, 0);
+  E->sw_slots.clear();
+  E->sw_codes.clear();
+  unsigned char* dst = E->sw_template.data();
+  auto put = [&](size_t at, double v) {
+    if (f64) std::memcpy(dst + at * sizeof(double), &v, sizeof(double));
+    else {
+      const float x = (float)v;
+      std::memcpy(dst + at * sizeof(float), &x, sizeof(float));
+    }
+  };
+  int64_t base = 0;
+  for (const EnergyNet& N : E->nets) {
+    const Schedule& S = N.sched;
+    for (const STensor& t : S.tensors) {
+      if (t.kind != TK_GATE) continue;
+      const int tag = N.tags[t.gate];
+      const int kind = tag & 15;
+      if (kind == 0) {
+        const std::vector<double> dd = canonical_data(N.tensors[t.gate], t.labels);
+        const size_t at = (size_t)(base + t.offset) * 2;
+        for (size_t q = 0; q < dd.size(); ++q) put(at + q, dd[q]);
+      } else {
+        // (the phase and mixer matrices are symmetric: their element order is canonical)
+        E->sw_slots.push_back((uint32_t)(base + t.offset));
+        E->sw_codes.push_back((uint32_t)tag);
+      }
+    }
+    base += S.gate_elems;
+  }
+}
+
+void energy_sweep_table(qt_energy* E, int n_sets, const double* gammas, const double* betas) {
+  const bool f64 = E->precision == QT_FP64;
+  const size_t eb = f64 ? sizeof(double) : sizeof(float);
+  const int p = E->p;
+  E->sw_table.assign((size_t)n_sets * p * 8 * eb, 0);
+  unsigned char* dst = E->sw_table.data();
+  for (int q = 0; q < n_sets; ++q)
+    for (int k = 0; k < p; ++k) {
+      const double g = gammas[(size_t)q * p + k], b = betas[(size_t)q * p + k];
+      // [kind 1 phase, kind 2 mixer][side 1, 2][2]: exp(-i g) / its conjugate; cos, sin b
+      const double v[8] = {std::cos(g), -std::sin(g), std::cos(g), std::sin(g),
+                           std::cos(b), std::sin(b),  std::cos(b), -std::sin(b)};
+      for (int e = 0; e < 8; ++e) {
+        const size_t at = (((size_t)q * p + k) * 8 + e) * eb;
+        if (f64) std::memcpy(dst + at, &v[e], sizeof(double));
+        else {
+          const float x = (float)v[e];
+          std::memcpy(dst + at, &x, sizeof(float));
+        }
+      }
+    }
 }
 
 }  // namespace qt

@@ -71,7 +71,15 @@ struct qt_energy {
   int sweep_sets = 0;
   size_t sw_off_gates = 0, sw_off_ops = 0, sw_off_steps = 0, sw_off_nets = 0, sw_off_scalars = 0,
          sw_off_zz = 0, sw_off_energy = 0, sw_off_counter = 0, sw_off_arenas = 0, sw_total = 0;
-  std::vector<unsigned char> sweep_stage;
+  // the sweep's gate images are assembled on the device: one image with every
+  // angle-free tensor in place (the template), the angle-dependent gates' element
+  // offsets and codes (kind | layer << 4 | side << 12), and per set a table of their
+  // entries (cos and sin of the set's angles, FP64 on the host, cast)
+  std::vector<unsigned char> sw_template;
+  std::vector<uint32_t> sw_slots, sw_codes;
+  std::vector<unsigned char> sw_table;
+  size_t sw_off_tmpl = 0, sw_off_slots = 0, sw_off_codes = 0, sw_off_table = 0;
+  const void* sw_tmpl_ws = nullptr;  // workspace holding the template and slot lists
   ~qt_energy();
 };
 
@@ -81,4 +89,9 @@ bool energy_compile(qt_energy* E, int precision, std::string& err);
 // gate data of every network for one angle set, in the compiled precision and layout
 void energy_gate_image(const qt_energy* E, const double* gammas, const double* betas,
                        unsigned char* dst);
+// the sweep's template image and angle-dependent gate slots (see qt_energy)
+void energy_sweep_template(qt_energy* E);
+// per set, per layer k: phase (re, im) and mixer (cos, sin) for ket side 1 and bra side 2,
+// 8 values [kind][side][2] in the compiled precision
+void energy_sweep_table(qt_energy* E, int n_sets, const double* gammas, const double* betas);
 }  // namespace qt

@@ -57,6 +57,7 @@ struct KStep {
   int out_soff;        // segment launch: shared-arena offset of the result (-1: none)
   int out_global;      // segment launch: the result is also stored to global memory
   int out_mslot;       // segment launch: slot of the result's metadata in the block's cache
+  int flags;           // bit 0: the tiled kernel takes its scaled path in every slice
   KOp op[MAXOP];
 };
 
@@ -763,7 +764,8 @@ __global__ void __launch_bounds__(TILE_THREADS, variant_minb(V))
         __any_sync(0xffffffffu, lane < m && (mys > SCALE_FREE_EXP || mys < -SCALE_FREE_EXP));
     const int ssum = __reduce_add_sync(0xffffffffu, mys);
     const int Esum = __reduce_add_sync(0xffffffffu, myE);
-    const bool scaled = extreme || ssum > 2 * SCALE_FREE_EXP || ssum < -2 * SCALE_FREE_EXP;
+    const bool scaled =
+        (st.flags & 1) || extreme || ssum > 2 * SCALE_FREE_EXP || ssum < -2 * SCALE_FREE_EXP;
     if (Tl == 0 && tid == 0)
       meta[st.out_meta + (st.out_meta_per_slice ? i : 0)].E = Esum + (scaled ? ssum : 0);
     const R* base[MS];
@@ -1383,6 +1385,7 @@ static bool make_desc(const Schedule& S, int gi, long long nslices, LaunchDesc& 
     k.out_meta_per_slice = 0;
   }
   k.out_meta = out.meta;
+  k.flags = S.force_scaled ? 1 : 0;
   if (k.m > MAXOP) {
     err = "bucket with more operands than the kernels take";
     return false;

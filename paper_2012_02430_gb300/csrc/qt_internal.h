@@ -139,6 +139,7 @@ struct Schedule {
   bool force_tri = false;        // copy of the network option at compile time
   int tma_block = 0;             // copy of the network option at compile time
   int tcgen05 = 0;               // copy of the network option at compile time
+  bool force_scaled = false;     // copy of the network option at compile time
   bool fused = true;             // steps grouped into fused launches
   uint64_t generation = 0;      // changes with every compile
   int precision = QT_FP32_SIMT;
@@ -241,6 +242,7 @@ struct qt_net {
   int64_t stream_launches = 0;   // GEMM-form launches by the streaming kernel
   int tcgen05 = 0;               // GEMM form on tcgen05: 0 default + autotuned, 1 forced, 2 never
   int64_t umma_launches = 0;     // GEMM-form launches by the tcgen05 kernel
+  bool force_scaled = false;     // the tiled kernel always takes its scaled path
   void* engine = nullptr;        // engine.cu: launch descriptors and graph cache
   ~qt_net();
 };

@@ -22,6 +22,7 @@ QT_FP32_SIMT, QT_TF32, QT_BF16, QT_3XTF32, QT_FP64 = 0, 1, 2, 3, 4
 QT_OPT_FUSION, QT_OPT_GRAPHS, QT_OPT_GEMM, QT_OPT_SEGMENTS, QT_OPT_TRIANGLE, QT_OPT_TMA = 1, 2, 3, 4, 5, 6
 QT_OPT_CONCURRENT = 7
 QT_OPT_TCGEN05 = 8
+QT_OPT_SCALED = 9
 QT_PROPOSAL_FEATURES = 16
 QT_MAX_OPEN = 16
 
