@@ -147,7 +147,7 @@ qt_status qt_order_rgreedy(qt_net* net, double tau, int32_t q, uint64_t seed, in
  * (bit j of the id = value of the j-th sliced vertex).
  * k_out (number of sliced vertices) and width_out (plan width) may be NULL.
  * Errors: QT_ESTATE before qt_order; QT_EINVAL for width_limit < 1, r < 1,
- * max_vars < 0 or max_vars > 30.
+ * max_vars < 0 or max_vars > 62 (slice ids are 64-bit; 2^k slices).
  */
 qt_status qt_slice(qt_net* net, int32_t width_limit, int32_t max_vars, int32_t r, int32_t* k_out,
                    int32_t* width_out);

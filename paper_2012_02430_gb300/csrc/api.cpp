@@ -276,8 +276,8 @@ qt_status qt_slice(qt_net* net, int32_t width_limit, int32_t max_vars, int32_t r
                    int32_t* width_out) {
   if (!check_net(net)) return fail(QT_EINVAL, "qt_slice: null network");
   if (!net->ordered) return fail(QT_ESTATE, "qt_slice: call qt_order first");
-  if (width_limit < 1 || r < 1 || max_vars < 0 || max_vars > 30)
-    return fail(QT_EINVAL, "qt_slice: need width_limit >= 1, r >= 1, 0 <= max_vars <= 30");
+  if (width_limit < 1 || r < 1 || max_vars < 0 || max_vars > 62)
+    return fail(QT_EINVAL, "qt_slice: need width_limit >= 1, r >= 1, 0 <= max_vars <= 62");
   try {
     qt::BitGraph g = qt::network_graph(net);
     net->plan = qt::step_dependent_slicing(g, net->algo, width_limit, max_vars, r);
@@ -605,7 +605,7 @@ qt_status qt_slice_learned(qt_net* net, const float* params, int32_t hidden, int
                            int32_t* k_out, int32_t* width_out) {
   if (!check_net(net)) return fail(QT_EINVAL, "qt_slice_learned: null network");
   if (!net->ordered) return fail(QT_ESTATE, "qt_slice_learned: call qt_order first");
-  if (width_limit < 1 || r < 1 || max_vars < 0 || max_vars > 30 || topv < 1 || topm < 0 ||
+  if (width_limit < 1 || r < 1 || max_vars < 0 || max_vars > 62 || topv < 1 || topm < 0 ||
       spread < 0 || (!params && spread < 1) ||
       (params && (hidden < 1 || hidden > 1024)))
     return fail(QT_EINVAL, "qt_slice_learned: argument out of range");

@@ -39,8 +39,8 @@ struct KOp {
   long long base;          // element offset from the workspace base
   long long slice_stride;  // elements between slice-local copies (0 for shared tensors)
   long long meta;          // meta slot (shared) or first slot (per slice)
+  unsigned long long smask;  // slice-id bits fixed into the operand
   unsigned int umask;      // U bits present in the operand
-  unsigned int smask;      // slice-id bits fixed into the operand
   int sshift;              // position of the slice block (unsliced rank)
   int meta_per_slice;
   int level;               // nested-sum level at which the operand is multiplied in
@@ -65,12 +65,11 @@ struct KStep {
 // shared arena at the start of the launch (its block for the block's slice).
 struct SegStage {
   long long base, slice_stride;
-  unsigned int smask;
+  unsigned long long smask;
   int sshift;
   int n;     // elements
   int soff;  // arena offset
   int cum;   // elements staged by the records before this one
-  int pad;
 };
 
 // One dependency level of a segment launch: its steps read only results of
@@ -89,8 +88,9 @@ struct Meta {
 // and sliced (smask) indices only, stored (open bits, slice bits) from bit 0 up.
 struct ScalarTerm {
   long long base, slice_stride, meta;
-  unsigned int smask, omask;
-  int per_slice, pad;
+  unsigned long long smask;
+  unsigned int omask;
+  int per_slice;
 };
 static_assert(sizeof(ScalarTerm) == kScalarTermBytes, "scalar table record size");
 
@@ -98,11 +98,11 @@ template <typename R> struct CT;
 template <> struct CT<float> { using c2 = float2; using c4 = float4; };
 template <> struct CT<double> { using c2 = double2; struct c4 { double2 a, b; }; };
 
-__device__ __forceinline__ unsigned long long pext64(unsigned long long x, unsigned int m) {
+__device__ __forceinline__ unsigned long long pext64(unsigned long long x, unsigned long long m) {
   unsigned long long r = 0;
   int k = 0;
   while (m) {
-    int b = __ffs(m) - 1;
+    int b = __ffsll((long long)m) - 1;
     r |= ((x >> b) & 1ull) << k;
     ++k;
     m &= m - 1;
@@ -996,7 +996,7 @@ void build_stage(qt_net* net) {
     else st.base = (long long)(S.off_slices / eb) + t.offset;
     st.slice_stride = t.kind == TK_SLICE ? S.slice_elems : 0;
     st.per_slice = t.kind == TK_SLICE;
-    st.smask = t.kind == TK_SLICE ? 0u : t.smask;
+    st.smask = t.kind == TK_SLICE ? 0ull : t.smask;
     for (int32_t l : t.labels) {  // open indices are the pos range [n_order, n_order + n_open)
       const int j = S.pos[l] - (int)(S.pos.size() - S.k - S.n_open);
       if (j >= 0 && j < S.n_open) st.omask |= 1u << j;
@@ -1639,7 +1639,7 @@ static bool build_cache(qt_net* net, EngineCache& c, std::string& err) {
           if (off < 0) return false;
           slot[tid] = {off, cnt};
           stages.push_back(SegStage{k.op[o].base, k.op[o].slice_stride, k.op[o].smask,
-                                    k.op[o].sshift, (int)cnt, (int)off, cum, 0});
+                                    k.op[o].sshift, (int)cnt, (int)off, cum});
           cum += (int)cnt;
         }
       }

@@ -24,11 +24,11 @@ namespace qt {
 
 namespace {
 
-__device__ __forceinline__ unsigned long long pext64g(unsigned long long x, unsigned int m) {
+__device__ __forceinline__ unsigned long long pext64g(unsigned long long x, unsigned long long m) {
   unsigned long long r = 0;
   int k = 0;
   while (m) {
-    const int b = __ffs(m) - 1;
+    const int b = __ffsll((long long)m) - 1;
     r |= ((x >> b) & 1ull) << k;
     ++k;
     m &= m - 1;

@@ -20,10 +20,11 @@ struct GMeta {
 
 struct GOp {
   long long base, slice_stride, meta;
-  unsigned int umask, smask;
+  unsigned long long smask;  // slice-id bits fixed into the operand
+  unsigned int umask;
   int sshift, meta_per_slice, side;
   unsigned int xmask;  // GEMM_TILE: the operand's indices in the bit numbering of its side's big operand
-  int tfold, pad;      // triangle form: 0 large, 1 folded into C, 2 weight over K
+  int tfold;           // triangle form: 0 large, 1 folded into C, 2 weight over K
 };
 
 struct GemmArgs {

@@ -162,7 +162,7 @@ bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePla
     for (int32_t l : labels)
       if (slice_bit[l] >= 0) {
         t.nsliced++;
-        t.smask |= 1u << slice_bit[l];
+        t.smask |= 1ull << slice_bit[l];
       }
     S.tensors.push_back(t);
     return (int32_t)S.tensors.size() - 1;

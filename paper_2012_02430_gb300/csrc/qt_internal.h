@@ -77,7 +77,7 @@ struct STensor {
   std::vector<int32_t> labels;  // canonical: ascending position (sliced labels on top)
   int rank = 0;                 // number of labels (sliced included)
   int nsliced = 0;              // labels that are sliced vertices
-  uint32_t smask = 0;           // slice-id bits present (bit j: j-th sliced vertex)
+  uint64_t smask = 0;           // slice-id bits present (bit j: j-th sliced vertex)
   int64_t offset = 0;           // element offset inside its region
   int64_t meta = 0;             // meta slot (shared) or first slot (per slice)
   int producer = -1;            // step that writes it (-1 for gates)

@@ -50,11 +50,11 @@ namespace {
 
 // ------------------------------ device helpers ------------------------------
 
-__device__ __forceinline__ unsigned long long u_pext64(unsigned long long x, unsigned int m) {
+__device__ __forceinline__ unsigned long long u_pext64(unsigned long long x, unsigned long long m) {
   unsigned long long r = 0;
   int k = 0;
   while (m) {
-    const int b = __ffs(m) - 1;
+    const int b = __ffsll((long long)m) - 1;
     r |= ((x >> b) & 1ull) << k;
     ++k;
     m &= m - 1;

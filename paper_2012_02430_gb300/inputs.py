@@ -93,3 +93,10 @@ def qaoa_instance(n: int, p: int, seed: int, d: int = 3):
     gammas, betas = random_angles(p, seed)
     z = random_bitstring(n, seed)
     return edges, gammas, betas, z
+
+
+def random_slice_ids(k: int, count: int, seed: int):
+    """count slice ids uniform in [0, 2^k) (k <= 64), from SplitMix64."""
+    rng = SplitMix64(seed ^ 0x3C3C3C3C3C3C3C3C)
+    mask = (1 << k) - 1
+    return [rng.next_u64() & mask for _ in range(count)]
