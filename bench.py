@@ -458,6 +458,9 @@ def ours(args):
     order_line = orderings(Q, edges, gammas, betas, z)
     modes_line = None if args.no_modes else precision_modes(Q, torch, edges, gammas, betas, z,
                                                             flush, stream)
+    c3_line = None if args.no_modes else mixed_precision_c3(args, Q, torch, flush, stream)
+    paper_line = None if args.no_modes else paper_shape_amplitude(args, Q, torch, flush, stream)
+    c5_line = None if args.no_modes else planner_comparison(Q)
 
     # end to end: host inputs -> amplitude on the host, through qt_contract
     from paper_2012_02430_gb300.inputs import random_angles
@@ -516,6 +519,9 @@ def ours(args):
         "amplitude_sweep": amp_sweep_line,
         "orderings": order_line,
         "precision_modes": modes_line,
+        "mixed_precision_n120_p3": c3_line,
+        "paper_shape_n210_p1": paper_line,
+        "learned_vs_greedy_n210_p3": c5_line,
         "amplitude": [amp.real, amp.imag],
         "gpu_launches": launches,
         "roofline": roofline, "clocks": clk, "e2e": e2e,
@@ -545,6 +551,177 @@ def ours(args):
 
 
 ENERGY_WORKLOAD = dict(n=1000, p=2, seed=1004)
+# mixed precision: p=3 on a random 3-regular graph with N=120, sliced with 43 variables so
+# that every slice's widest step has 28 indices (each slice fixes all sliced indices after
+# the first round's step); accuracy on the N=50 p=3 stand-in over 64 seeded bitstrings
+C3_WORKLOAD = dict(n=120, p=3, seed=1003, width_limit=28, max_vars=43, r=1)
+C3_STAND_IN = dict(n=50, p=3, seed=1003, width_drop=6, max_vars=10, bitstrings=64)
+C3_SAMPLED = 1024
+
+
+PAPER_SHAPE = dict(n=210, p=1, seed=1005, width_limit=30, max_vars=12, r=1)
+C5_WORKLOAD = dict(n=210, p=3, seed=1005, width_limit=30, max_vars=12, r=1)
+
+
+def paper_shape_amplitude(args, Q, torch, flush, stream):
+    """The paper's own experiment shape (one amplitude of p=1 QAOA on a 210-vertex random
+    3-regular graph; Sec. VIII ran it on 1,024 Theta nodes): sliced to rank 30 and every
+    slice contracted on one GPU (FP32, autotuned, CUDA events, L2 flushed)."""
+    from paper_2012_02430_gb300.inputs import qaoa_instance
+    w = PAPER_SHAPE
+    edges, g, b, z = qaoa_instance(w["n"], w["p"], w["seed"])
+    net = Q.Network(edges, w["n"], w["p"], g, b, z)
+    width = net.order(Q.QT_GREEDY_MINFILL)
+    t0 = time.perf_counter()
+    k, planned = net.slice(w["width_limit"], w["max_vars"], w["r"])
+    t_plan = time.perf_counter() - t0
+    net.prepare(Q.QT_FP32_SIMT, batch=1)
+    need1 = net.stats()["workspace_bytes"]
+    batch = max(1, min(1 << k, int((96 << 30) // max(1, need1))))
+    net.prepare(Q.QT_FP32_SIMT, batch=batch)
+    st = net.stats()
+    net.upload()
+    net.autotune()
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    net.run(0, 1 << k, out)
+    times = []
+    for i in range(3):
+        flush.fill_(i & 0xFF)
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        net.run(0, 1 << k, out)
+        e.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(e))
+    ms = statistics.median(times)
+    flops = st["prefix_flops"] + st["slice_flops"] * (1 << k)
+    return {"workload": "amplitude of p=1 QAOA MaxCut, random 3-regular N=210 seed 1005, "
+                        "min-fill, sliced to rank 30, all slices",
+            "greedy_width": width, "k": k, "slices": 1 << k, "planned_width": planned,
+            "executed_slice_width": st["slice_width"], "batch": batch,
+            "workspace_gb": st["workspace_bytes"] / 1e9, "ms_per_amplitude": ms,
+            "slices_per_s": (1 << k) / (ms / 1e3), "complex_tflops": flops / (ms / 1e3) / 1e12,
+            "plan_seconds": t_plan, "amplitude": [out[0].item(), out[1].item()],
+            "context": "the paper: one amplitude of this shape (its decomposition: width 44) on "
+                       "1,024 nodes of Theta; widths differ with the gate decomposition"}
+
+
+def planner_comparison(Q):
+    """Slicing plans of N=210 p=3 QAOA (rank target 30, 12 sliced variables) by the
+    paper's search (every step up to the peak, max-degree vertex), the learned proposals
+    (the committed GPU-trained model's top 8 per round) and the same budget without a
+    model (8 candidates evenly spaced): plan width, log2 plan cost (sum of 2^w), greedy
+    ordering runs and seconds. Greedy (no slicing) for reference."""
+    import ctypes as C
+    import math
+    import numpy as np
+    from paper_2012_02430_gb300 import learn
+    from paper_2012_02430_gb300.inputs import qaoa_instance
+    params, hidden, _ = learn.load()
+    w = C5_WORKLOAD
+    edges, g, b, z = qaoa_instance(w["n"], w["p"], w["seed"])
+    res = {"workload": f"N={w['n']} p={w['p']} seed {w['seed']}, width target "
+                       f"{w['width_limit']}, {w['max_vars']} sliced variables"}
+    for mode in ("greedy", "paper_search", "learned_top8", "budget8_no_model"):
+        h = Q.qt_build_network(edges, w["n"], w["p"], g, b, z)
+        try:
+            w0 = Q.qt_order(h, Q.QT_GREEDY_MINFILL)
+            k, wd = C.c_int32(0), C.c_int32(w0)
+            t0 = time.perf_counter()
+            if mode == "paper_search":
+                Q._check(Q.lib.qt_slice(h, w["width_limit"], w["max_vars"], w["r"], C.byref(k),
+                                        C.byref(wd)))
+            elif mode != "greedy":
+                pa = np.ascontiguousarray(params, dtype=np.float32)
+                pp = pa.ctypes.data_as(C.POINTER(C.c_float)) if mode == "learned_top8" else None
+                Q._check(Q.lib.qt_slice_learned(h, pp, hidden, w["width_limit"], w["max_vars"],
+                                                w["r"], 3, 8 if pp is not None else 0,
+                                                0 if pp is not None else 8, C.byref(k),
+                                                C.byref(wd)))
+            dt = time.perf_counter() - t0
+            runs, cost = C.c_int64(), C.c_double()
+            Q._check(Q.lib.qt_plan_info(h, C.byref(runs), C.byref(cost)))
+            res[mode] = {"plan_width": wd.value, "k": k.value,
+                         "log2_plan_cost": math.log2(cost.value),
+                         "greedy_runs": runs.value, "seconds": dt}
+        finally:
+            Q.qt_free(h)
+    return res
+
+
+def mixed_precision_c3(args, Q, torch, flush, stream):
+    """Sampled-slice throughput of the N=120 p=3 schedule (1,024 consecutive slice ids
+    from a seeded offset; slices are independent units of the amplitude, Eq. 2) in FP32
+    and split TF32, with the projected time to the full amplitude; and each precision
+    mode's relative error on 64 seeded bitstrings of the N=50 p=3 stand-in against the
+    FP64 path (which the GPU tests hold within 1e-10 of the oracle)."""
+    import statistics as stats
+    from paper_2012_02430_gb300.inputs import qaoa_instance, random_bitstring, random_slice_ids
+    w = C3_WORKLOAD
+    edges, g, b, z = qaoa_instance(w["n"], w["p"], w["seed"])
+    sampled = {}
+    for name in ("fp32", "3xtf32"):
+        net = Q.Network(edges, w["n"], w["p"], g, b, z)
+        width = net.order(Q.QT_GREEDY_MINFILL)
+        t0 = time.perf_counter()
+        k, planned = net.slice(w["width_limit"], w["max_vars"], w["r"])
+        t_plan = time.perf_counter() - t0
+        net.prepare(PRECISIONS[name], batch=1)
+        st1 = net.stats()
+        batch = max(1, min(C3_SAMPLED, int((64 << 30) // max(1, st1["workspace_bytes"]))))
+        net.prepare(PRECISIONS[name], batch=batch)
+        st = net.stats()
+        net.upload()
+        net.autotune()
+        first = random_slice_ids(k, 1, 4242)[0] & ~(C3_SAMPLED - 1)
+        first = min(first, (1 << k) - C3_SAMPLED)
+        out = torch.zeros(2, dtype=torch.float64, device="cuda")
+        net.run(first, C3_SAMPLED, out)
+        torch.cuda.synchronize()
+        flush.fill_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        net.run(first, C3_SAMPLED, out)
+        e.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(e)
+        sps = C3_SAMPLED / (ms / 1e3)
+        sampled[name] = {"slices_per_s": sps,
+                         "complex_tflops": st["slice_flops"] * C3_SAMPLED / (ms / 1e3) / 1e12,
+                         "ms_per_1024_slices": ms, "batch": batch,
+                         "projected_seconds_to_amplitude": (2.0 ** k) / sps,
+                         "projected_years_to_amplitude": (2.0 ** k) / sps / 3.156e7}
+        sampled["schedule"] = {"n": w["n"], "p": w["p"], "seed": w["seed"], "greedy_width": width,
+                               "k": k, "executed_slice_width": st["slice_width"],
+                               "prefix_width": st["prefix_width"], "planned_width": planned,
+                               "slice_flops": st["slice_flops"], "first_slice_id": first,
+                               "plan_seconds": t_plan}
+        del net
+    # accuracy over 64 bitstrings of the stand-in
+    si = C3_STAND_IN
+    e2, g2, b2, z2 = qaoa_instance(si["n"], si["p"], si["seed"])
+    bits = [random_bitstring(si["n"], 9000 + q) for q in range(si["bitstrings"])]
+    amps = {}
+    for name in ("fp64", "fp32", "3xtf32", "tf32", "bf16"):
+        net = Q.Network(e2, si["n"], si["p"], g2, b2, z2)
+        wd = net.order(Q.QT_GREEDY_MINFILL)
+        k2, _ = net.slice(wd - si["width_drop"], si["max_vars"], 1)
+        net.prepare(PRECISIONS[name], batch=1 << k2)
+        res = []
+        for zq in bits:
+            Q.qt_set_bitstring(net.handle, zq)
+            res.append(net.contract(PRECISIONS[name]))
+        amps[name] = res
+        del net
+    acc = {"stand_in": f"N={si['n']} p={si['p']} seed {si['seed']}, greedy width - "
+                       f"{si['width_drop']}, {si['bitstrings']} seeded bitstrings",
+           "reference": "the FP64 path (held within 1e-10 of the oracle by the GPU tests)"}
+    for name in ("fp32", "3xtf32", "tf32", "bf16"):
+        errs = [abs(x - r) / abs(r) for x, r in zip(amps[name], amps["fp64"])]
+        acc[name] = {"max_rel_err": max(errs), "median_rel_err": stats.median(errs)}
+    return {"sampled_slices": sampled, "accuracy_64_bitstrings": acc}
 
 
 def precision_modes(Q, torch, edges, gammas, betas, z, flush, stream, reps=5):
