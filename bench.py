@@ -647,7 +647,49 @@ def planner_comparison(Q):
                          "greedy_runs": runs.value, "seconds": dt}
         finally:
             Q.qt_free(h)
+    res["elimination_orders"] = order_comparison(Q)
     return res
+
+
+def order_comparison(Q):
+    """Unsliced elimination orders of the N=210 p=3 and N=120 p=3 networks: min-fill,
+    min-degree, one Boltzmann-randomised greedy run (rgreedy, tau 0.1) and the learned
+    elimination-step proposals (the committed model picks among the 4 best min-fill
+    candidates at every step; min-fill judges, 2 ordering runs): width, log2 of the sum
+    of 2^w over the steps, and seconds."""
+    import json
+    import math
+    import numpy as np
+    from paper_2012_02430_gb300 import learn
+    from paper_2012_02430_gb300.inputs import qaoa_instance
+    with open(learn.ORDER_WEIGHTS) as f:
+        d = json.load(f)
+    params, hidden = np.array(d["params"], dtype=np.float32), int(d["hidden"])
+    out = {}
+    for n, p, seed in ((C5_WORKLOAD["n"], C5_WORKLOAD["p"], C5_WORKLOAD["seed"]),
+                       (C3_WORKLOAD["n"], C3_WORKLOAD["p"], C3_WORKLOAD["seed"])):
+        edges, g, b, z = qaoa_instance(n, p, seed)
+        row = {}
+        h = Q.qt_build_network(edges, n, p, g, b, z)
+        try:
+            for name, run in (("min_fill", lambda: Q.qt_order(h, Q.QT_GREEDY_MINFILL)),
+                              ("min_degree", lambda: Q.qt_order(h, Q.QT_GREEDY_MINDEG)),
+                              ("rgreedy_q1", lambda: Q.qt_order_rgreedy(h, 0.1, 1, 1))):
+                t0 = time.perf_counter()
+                run()
+                dt = time.perf_counter() - t0
+                ws = Q.qt_get_widths(h)
+                row[name] = {"width": max(ws),
+                             "log2_cost": math.log2(sum(math.ldexp(1.0, x) for x in ws)),
+                             "seconds": dt}
+        finally:
+            Q.qt_free(h)
+        t0 = time.perf_counter()
+        wd, lc, kept = learn.order_with((n, p, seed), params, hidden, learn.STEP_TOPC, 1)
+        row["learned_judged"] = {"width": wd, "log2_cost": lc, "learned_kept": bool(kept),
+                                 "seconds": time.perf_counter() - t0}
+        out[f"N={n} p={p} seed {seed}"] = row
+    return out
 
 
 def mixed_precision_c3(args, Q, torch, flush, stream):

@@ -308,6 +308,36 @@ qt_status qt_slice_learned(qt_net* net, const float* params, int32_t hidden, int
 
 /* The MLP's forward pass on the host, as qt_slice_learned uses it: x [batch][F]
  * -> y [batch]. Parameters: W1[H][F], b1[H], W2[H][H], b2[H], w3[H], b3. */
+/*
+ * Learned elimination steps (the next vertex to eliminate). Not in the paper, which
+ * orders greedily (Sec. V.A); a model trained on the simulator's own orderings
+ * proposes, greedy judges. At a step of a greedy ordering the candidates are the
+ * `topc` alive vertices best by the greedy key of the network's rule (min-fill:
+ * fill, degree, id; min-degree: degree, id); rank 0 is the vertex greedy takes.
+ *
+ * qt_order_dataset: along the network's greedy order (qt_order first), at every
+ * `stride`-th step, each candidate's QT_PROPOSAL_FEATURES features (degree, fill
+ * ratio, rank, fill and degree above rank 0's, neighbour degree mean/max/min, alive
+ * fraction, step fraction, largest width so far, mean degree, edge density, shared
+ * neighbours with rank 0, degree over the largest, 2-hop size; widths over the
+ * greedy width) into features[count][F], its rollout label into labels[count]
+ * (log2 of the sum of 2^w over the order: greedy up to the step, the candidate,
+ * greedy after) and (step, vertex, rollout width) into meta[count][3]; at most cap
+ * records written, *count gets the total (NULL arrays: count only). Errors:
+ * QT_ESTATE before qt_order; QT_EINVAL for topc < 2 or stride < 1.
+ *
+ * qt_order_learned: orders the network by taking at every step the candidate (of
+ * the top `topc`) with the lowest model score (params/hidden as qt_slice_learned);
+ * with judge != 0 the plain greedy order replaces it unless the learned order's
+ * (width, sum of 2^w) is smaller (*learned_kept tells which was kept). Sets the
+ * network's order like qt_order (slicing and schedule discarded). Errors:
+ * QT_EINVAL for a null argument, hidden outside 1..1024 or topc < 1.
+ */
+qt_status qt_order_dataset(const qt_net* net, int32_t topc, int32_t stride, float* features,
+                           float* labels, int32_t* meta, int32_t cap, int32_t* count);
+qt_status qt_order_learned(qt_net* net, const float* params, int32_t hidden, int32_t topc,
+                           int32_t judge, int32_t* width_out, int32_t* learned_kept);
+
 qt_status qt_mlp_forward_host(const float* params, int32_t n_features, int32_t hidden,
                               const float* x, int32_t batch, float* y);
 

@@ -123,6 +123,10 @@ bool slice_dataset(const qt_net* net, int topv, std::vector<float>& feats,
 SlicePlan learned_slicing(const qt_net* net, const float* params, int hidden, int width_limit,
                           int max_vars, int r, int topv, int topm, int spread,
                           int64_t& greedy_runs);
+bool order_dataset(const qt_net* net, int topc, int stride, std::vector<float>& feats,
+                   std::vector<float>& labels, std::vector<int32_t>& meta);
+OrderResult learned_order(const BitGraph& g, int algo, const float* params, int hidden, int topc,
+                          int n0, int W0);
 }  // namespace qt
 
 extern "C" {
@@ -619,6 +623,67 @@ qt_status qt_slice_learned(qt_net* net, const float* params, int32_t hidden, int
     if (width_out) *width_out = net->plan.width;
   } catch (const std::bad_alloc&) {
     return fail(QT_ENOMEM, "qt_slice_learned: out of host memory");
+  }
+  return ok();
+}
+
+qt_status qt_order_dataset(const qt_net* net, int32_t topc, int32_t stride, float* features,
+                           float* labels, int32_t* meta, int32_t cap, int32_t* count) {
+  if (!check_net(net) || !count) return fail(QT_EINVAL, "qt_order_dataset: null argument");
+  if (!net->ordered) return fail(QT_ESTATE, "qt_order_dataset: call qt_order first");
+  if (topc < 2 || stride < 1) return fail(QT_EINVAL, "qt_order_dataset: need topc >= 2, stride >= 1");
+  std::vector<float> f, l;
+  std::vector<int32_t> m;
+  try {
+    qt::order_dataset(net, topc, stride, f, l, m);
+  } catch (const std::bad_alloc&) {
+    return fail(QT_ENOMEM, "qt_order_dataset: out of host memory");
+  }
+  *count = (int32_t)l.size();
+  const int32_t n = std::min<int32_t>(cap, (int32_t)l.size());
+  if (features && n > 0) std::memcpy(features, f.data(), sizeof(float) * n * qt::kProposalFeatures);
+  if (labels && n > 0) std::memcpy(labels, l.data(), sizeof(float) * n);
+  if (meta && n > 0) std::memcpy(meta, m.data(), sizeof(int32_t) * n * 3);
+  return ok();
+}
+
+qt_status qt_order_learned(qt_net* net, const float* params, int32_t hidden, int32_t topc,
+                           int32_t judge, int32_t* width_out, int32_t* learned_kept) {
+  if (!check_net(net) || !params) return fail(QT_EINVAL, "qt_order_learned: null argument");
+  if (hidden < 1 || hidden > 1024 || topc < 1)
+    return fail(QT_EINVAL, "qt_order_learned: need 1 <= hidden <= 1024 and topc >= 1");
+  try {
+    const qt::BitGraph g = qt::network_graph(net);
+    const int algo = net->algo;
+    const qt::OrderResult gr = qt::greedy_order(g, algo);
+    int W0 = 0;
+    for (int32_t w : gr.widths) W0 = std::max(W0, w);
+    qt::OrderResult lr = qt::learned_order(g, algo, params, hidden, topc, net->n_vars, W0);
+    auto key = [](const qt::OrderResult& o) {
+      int w = 0;
+      double c = 0.0;
+      for (int32_t x : o.widths) {
+        w = std::max(w, x);
+        c += std::ldexp(1.0, x);
+      }
+      return std::make_pair(w, c);
+    };
+    const bool keep = !judge || key(lr) < key(gr);
+    const qt::OrderResult& r = keep ? lr : gr;
+    net->plan = qt::SlicePlan();
+    net->plan.order = r.order;
+    net->plan.widths = r.widths;
+    net->plan.greedy_runs = judge ? 2 : 1;
+    int w = 0;
+    for (int x : r.widths) w = std::max(w, x);
+    net->plan.width = w;
+    net->ordered = true;
+    net->sched = qt::Schedule();
+    net->stage_dirty = true;
+    if (width_out) *width_out = w;
+    if (learned_kept) *learned_kept = keep ? 1 : 0;
+  } catch (const std::bad_alloc&) {
+    return fail(QT_ENOMEM, "qt_order_learned: out of host memory");
   }
   return ok();
 }

@@ -320,4 +320,174 @@ SlicePlan learned_slicing(const qt_net* net, const float* params, int hidden, in
   return plan;
 }
 
+// ---------------------------------------------------------------------------
+// Learned elimination steps (the other half of the proposals). At every step of a
+// greedy ordering the candidates are the `topc` alive vertices best by the greedy
+// key (min-fill: fill, degree, id; min-degree: degree, id); rank 0 is the vertex
+// greedy itself takes. Each gets 16 features read off the current graph; a model
+// trained on rollouts (the candidate eliminated, then greedy to the end, labelled
+// by log2 of the plan cost sum 2^w) picks one. Greedy stays the judge: the learned
+// order is kept only if its (width, cost) is below the plain greedy order's.
+// ---------------------------------------------------------------------------
+struct StepCand {
+  int v, deg, fill;
+};
+
+static std::vector<StepCand> step_candidates(const BitGraph& h, int algo, int topc) {
+  std::vector<StepCand> all;
+  for (int x = 0; x < h.n; ++x) {
+    if (!h.takeable(x)) continue;
+    const int d = h.degree(x);
+    all.push_back({x, d, algo == QT_GREEDY_MINFILL ? count_fill(h, x, d) : 0});
+  }
+  const int k = std::min<int>(topc, (int)all.size());
+  std::partial_sort(all.begin(), all.begin() + k, all.end(), [&](const StepCand& a, const StepCand& b) {
+    if (algo == QT_GREEDY_MINFILL && a.fill != b.fill) return a.fill < b.fill;
+    if (a.deg != b.deg) return a.deg < b.deg;
+    return a.v < b.v;
+  });
+  all.resize(k);
+  return all;
+}
+
+// features of candidate j at step t (W0: the plain greedy width of the whole graph,
+// n0: vertices of the network, maxw: the largest width of the steps taken so far)
+static void step_features(const BitGraph& h, const std::vector<StepCand>& c, int j, int t, int n0,
+                          int W0, int maxw, int alive, int64_t deg_sum, int dmax, float* f) {
+  const StepCand& x = c[j];
+  const double W = std::max(1, W0);
+  int nmin = 1 << 30, nmax = 0;
+  int64_t nsum = 0;
+  std::vector<uint64_t> two(h.W, 0);
+  const uint64_t* rv = h.row(x.v);
+  for (int w = 0; w < h.W; ++w) {
+    uint64_t bits = rv[w];
+    while (bits) {
+      const int a = w * 64 + __builtin_ctzll(bits);
+      bits &= bits - 1;
+      const int da = h.degree(a);
+      nmin = std::min(nmin, da);
+      nmax = std::max(nmax, da);
+      nsum += da;
+      const uint64_t* ra = h.row(a);
+      for (int q = 0; q < h.W; ++q) two[q] |= ra[q];
+    }
+  }
+  int hop2 = 0;
+  for (int q = 0; q < h.W; ++q) hop2 += __builtin_popcountll(two[q] | rv[q]);
+  int common = 0;  // neighbours shared with the greedy choice (rank 0)
+  const uint64_t* r0 = h.row(c[0].v);
+  for (int q = 0; q < h.W; ++q) common += __builtin_popcountll(rv[q] & r0[q]);
+  const double edges = deg_sum / 2.0;
+  f[0] = (float)(x.deg / W);
+  f[1] = (float)(x.fill / std::max(1.0, x.deg * (x.deg - 1) / 2.0));
+  f[2] = (float)(j / (double)std::max<size_t>(1, c.size()));
+  f[3] = (float)((x.fill - c[0].fill) / W);
+  f[4] = (float)((x.deg - c[0].deg) / W);
+  f[5] = (float)(x.deg ? (nsum / (double)x.deg) / W : 0.0);
+  f[6] = (float)(nmax / W);
+  f[7] = (float)(x.deg ? nmin / W : 0.0);
+  f[8] = (float)(alive / (double)n0);
+  f[9] = (float)(t / (double)n0);
+  f[10] = (float)(maxw / W);
+  f[11] = (float)((alive ? 2.0 * edges / alive : 0.0) / W);
+  f[12] = (float)(edges / std::max(1.0, alive * (alive - 1) / 2.0));
+  f[13] = (float)(j == 0 ? 1.0 : common / std::max(1.0, (double)x.deg));
+  f[14] = (float)(x.deg / std::max(1.0, (double)dmax));
+  f[15] = (float)(hop2 / std::max(1.0, (double)alive));
+}
+
+static void graph_stats(const BitGraph& h, int& alive, int64_t& deg_sum, int& dmax) {
+  alive = 0;
+  deg_sum = 0;
+  dmax = 0;
+  for (int x = 0; x < h.n; ++x) {
+    if (!h.takeable(x)) continue;
+    const int d = h.degree(x);
+    ++alive;
+    deg_sum += d;
+    dmax = std::max(dmax, d);
+  }
+}
+
+static double log2_cost(const std::vector<int32_t>& widths) {
+  double c = 0.0;
+  for (int32_t w : widths) c += std::ldexp(1.0, w);
+  return std::log2(std::max(1.0, c));
+}
+
+bool order_dataset(const qt_net* net, int topc, int stride, std::vector<float>& feats,
+                   std::vector<float>& labels, std::vector<int32_t>& meta) {
+  const BitGraph g = network_graph(net);
+  const int algo = net->algo;
+  const OrderResult gr = greedy_order(g, algo);
+  int W0 = 0;
+  for (int32_t w : gr.widths) W0 = std::max(W0, w);
+  BitGraph h = g;
+  std::vector<int32_t> prefix;
+  int maxw = 0;
+  for (size_t t = 0; t < gr.order.size(); ++t) {
+    if (t % (size_t)std::max(1, stride) == 0) {
+      const std::vector<StepCand> c = step_candidates(h, algo, topc);
+      if (c.size() >= 2) {
+        int alive, dmax;
+        int64_t deg_sum;
+        graph_stats(h, alive, deg_sum, dmax);
+        for (size_t j = 0; j < c.size(); ++j) {
+          float f[kFeatures];
+          step_features(h, c, (int)j, (int)t, net->n_vars, W0, maxw, alive, deg_sum, dmax, f);
+          BitGraph r = h;
+          const int d = r.eliminate(c[j].v);
+          const OrderResult rest = greedy_order(r, algo);
+          std::vector<int32_t> ws = prefix;
+          ws.push_back(d);
+          ws.insert(ws.end(), rest.widths.begin(), rest.widths.end());
+          int width = 0;
+          for (int32_t w : ws) width = std::max(width, w);
+          feats.insert(feats.end(), f, f + kFeatures);
+          labels.push_back((float)log2_cost(ws));
+          meta.push_back((int32_t)t);
+          meta.push_back(c[j].v);
+          meta.push_back(width);
+        }
+      }
+    }
+    prefix.push_back(gr.widths[t]);
+    maxw = std::max(maxw, gr.widths[t]);
+    h.eliminate(gr.order[t]);
+  }
+  return true;
+}
+
+OrderResult learned_order(const BitGraph& g, int algo, const float* params, int hidden, int topc,
+                          int n0, int W0) {
+  BitGraph h = g;
+  OrderResult res;
+  int maxw = 0;
+  std::vector<float> x, y;
+  for (int t = 0;; ++t) {
+    const std::vector<StepCand> c = step_candidates(h, algo, topc);
+    if (c.empty()) break;
+    int pick = 0;
+    if (c.size() >= 2) {
+      int alive, dmax;
+      int64_t deg_sum;
+      graph_stats(h, alive, deg_sum, dmax);
+      x.assign(c.size() * kFeatures, 0.f);
+      y.assign(c.size(), 0.f);
+      for (size_t j = 0; j < c.size(); ++j)
+        step_features(h, c, (int)j, t, n0, W0, maxw, alive, deg_sum, dmax, &x[j * kFeatures]);
+      mlp_forward_host(params, kFeatures, hidden, x.data(), (int)c.size(), y.data());
+      for (size_t j = 1; j < c.size(); ++j)
+        if (y[j] < y[pick]) pick = (int)j;
+    }
+    const int d = h.eliminate(c[pick].v);
+    res.order.push_back(c[pick].v);
+    res.widths.push_back(d);
+    maxw = std::max(maxw, d);
+  }
+  return res;
+}
+
 }  // namespace qt
+

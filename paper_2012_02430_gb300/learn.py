@@ -7,7 +7,9 @@ the plan width it gives, placed between the round's best (0) and worst (1) width
 kernels (qt_mlp_train_step: forward, backward, Adam). The planner then verifies
 only the top-m scored candidates per round (qt_slice_learned).
 
-    python -m paper_2012_02430_gb300.learn train   # writes data/proposal_mlp.json (GPU)
+    python -m paper_2012_02430_gb300.learn train        # data/proposal_mlp.json (GPU)
+    python -m paper_2012_02430_gb300.learn train-order  # data/order_mlp.json (GPU):
+        elimination-step proposals, trained on rollouts of the simulator's own orderings
 """
 
 from __future__ import annotations
@@ -179,6 +181,81 @@ def mlp_forward_full(mlp, Xd):
     return torch.cat(out)
 
 
+# ---------------------------------------------------------------------------
+# Learned elimination steps: at a step of a greedy ordering the candidates are the
+# STEP_TOPC vertices best by the greedy key; features and rollout labels come from
+# qt_order_dataset, the model ranks candidates within a step, qt_order_learned
+# orders with it (greedy as judge).
+# ---------------------------------------------------------------------------
+ORDER_WEIGHTS = os.path.join(HERE, "data", "order_mlp.json")
+STEP_TOPC = 4
+STEP_STRIDE = 4
+
+
+def order_dataset_of(edges, n, p, gammas, betas, z, topc=STEP_TOPC, stride=STEP_STRIDE,
+                     algo=Q.QT_GREEDY_MINFILL):
+    h = Q.qt_build_network(edges, n, p, gammas, betas, z)
+    try:
+        Q.qt_order(h, algo)
+        cnt = C.c_int32()
+        Q._check(Q.lib.qt_order_dataset(h, topc, stride, None, None, None, 0, C.byref(cnt)))
+        k = cnt.value
+        f = (C.c_float * max(1, k * NF))()
+        lab = (C.c_float * max(1, k))()
+        meta = (C.c_int32 * max(1, 3 * k))()
+        Q._check(Q.lib.qt_order_dataset(h, topc, stride, f, lab, meta, k, C.byref(cnt)))
+        X = np.frombuffer(f, dtype=np.float32, count=k * NF).reshape(k, NF).copy()
+        L = np.frombuffer(lab, dtype=np.float32, count=k).copy()
+        M = np.frombuffer(meta, dtype=np.int32, count=3 * k).reshape(k, 3).copy()
+        return X, L, M
+    finally:
+        Q.qt_free(h)
+
+
+def step_targets(L, M):
+    """Each candidate's rollout log2 cost placed between its step's best (0) and worst (1)
+    candidate, so the model learns to rank the candidates of a step."""
+    Y = np.zeros_like(L)
+    for t in np.unique(M[:, 0]):
+        sel = M[:, 0] == t
+        lo, hi = L[sel].min(), L[sel].max()
+        Y[sel] = (L[sel] - lo) / max(1e-6, hi - lo)
+    return Y
+
+
+def make_order_dataset(instances, topc=STEP_TOPC, stride=STEP_STRIDE):
+    Xs, Ys = [], []
+    for n, p, seed in instances:
+        edges, g, b, z = qaoa_instance(n, p, seed)
+        X, L, M = order_dataset_of(edges, n, p, g, b, z, topc, stride)
+        Xs.append(X)
+        Ys.append(step_targets(L, M))
+    return np.concatenate(Xs), np.concatenate(Ys)
+
+
+def order_with(instance, params=None, hidden=64, topc=STEP_TOPC, judge=0):
+    """Orders one instance greedily (params None) or with the learned steps; returns
+    (width, log2 sum of 2^w, learned order kept)."""
+    n, p, seed = instance
+    edges, g, b, z = qaoa_instance(n, p, seed)
+    h = Q.qt_build_network(edges, n, p, g, b, z)
+    try:
+        if params is None:
+            w = Q.qt_order(h, Q.QT_GREEDY_MINFILL)
+            kept = 0
+        else:
+            Q.qt_order(h, Q.QT_GREEDY_MINFILL)
+            pa = np.ascontiguousarray(params, dtype=np.float32)
+            wc, kc = C.c_int32(), C.c_int32()
+            Q._check(Q.lib.qt_order_learned(h, pa.ctypes.data_as(C.POINTER(C.c_float)), hidden,
+                                            topc, judge, C.byref(wc), C.byref(kc)))
+            w, kept = wc.value, kc.value
+        widths = Q.qt_get_widths(h)
+        return w, math.log2(sum(math.ldexp(1.0, x) for x in widths)), kept
+    finally:
+        Q.qt_free(h)
+
+
 def save(params, hidden, info, path=WEIGHTS):
     os.makedirs(os.path.dirname(path), exist_ok=True)
     with open(path, "w") as f:
@@ -226,8 +303,45 @@ def plan_with(instance, mode, params=None, hidden=64, topv=3, topm=4, spread=4, 
         Q.qt_free(h)
 
 
+def evaluate_order(params, hidden, instances=None, topc=STEP_TOPC):
+    """Greedy vs learned steps (alone, and with greedy as judge) on held-out networks:
+    per instance (width, log2 cost) of each."""
+    rows = []
+    for inst in instances or HELD_OUT:
+        g = order_with(inst)
+        lone = order_with(inst, params, hidden, topc, judge=0)
+        judged = order_with(inst, params, hidden, topc, judge=1)
+        rows.append({"instance": list(inst), "greedy": g[:2], "learned": lone[:2],
+                     "judged": judged[:2], "kept": judged[2]})
+    return rows
+
+
 def main(argv):
-    if len(argv) > 1 and argv[1] == "train":
+    if len(argv) > 1 and argv[1] == "train-order":
+        out = argv[2] if len(argv) > 2 else ORDER_WEIGHTS
+        t0 = time.time()
+        X, Y = make_order_dataset(TRAIN_SET, STEP_TOPC, 2)
+        t_data = time.time() - t0
+        print(f"dataset: {X.shape[0]} step candidates from {len(TRAIN_SET)} networks "
+              f"({t_data:.1f} s)", flush=True)
+        params, info = train(X, Y)
+        info["dataset_size"] = int(X.shape[0])
+        info["dataset_seconds"] = t_data
+        info["topc"] = STEP_TOPC
+        info["stride"] = 2
+        rows = evaluate_order(params, 64)
+        info["held_out"] = rows
+        save(params, 64, info, out)
+        print(json.dumps({k: v for k, v in info.items() if k not in ("log", "held_out")}), flush=True)
+        for r in rows:
+            print(r)
+        g = np.array([r["greedy"] for r in rows])
+        lo = np.array([r["learned"] for r in rows])
+        ju = np.array([r["judged"] for r in rows])
+        print("mean width greedy %.2f learned %.2f judged %.2f; mean log2 cost greedy %.3f "
+              "learned %.3f judged %.3f" % (g[:, 0].mean(), lo[:, 0].mean(), ju[:, 0].mean(),
+                                            g[:, 1].mean(), lo[:, 1].mean(), ju[:, 1].mean()))
+    elif len(argv) > 1 and argv[1] == "train":
         X, Y = make_dataset(TRAIN_SET)
         print(f"dataset: {X.shape[0]} candidates from {len(TRAIN_SET)} networks", flush=True)
         params, info = train(X, Y)

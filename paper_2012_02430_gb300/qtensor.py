@@ -75,6 +75,10 @@ _SIGS = {
                          C.c_int32, _i32p],
     "qt_slice_learned": [_vp, C.POINTER(C.c_float), C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                          C.c_int32, C.c_int32, C.c_int32, _i32p, _i32p],
+    "qt_order_dataset": [_vp, C.c_int32, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                         C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32)],
+    "qt_order_learned": [_vp, C.POINTER(C.c_float), C.c_int32, C.c_int32, C.c_int32,
+                         C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
     "qt_mlp_forward_host": [C.POINTER(C.c_float), C.c_int32, C.c_int32, C.POINTER(C.c_float),
                             C.c_int32, C.POINTER(C.c_float)],
     "qt_mlp_create": [C.c_int32, C.c_int32, C.c_int32, C.POINTER(_vp)],

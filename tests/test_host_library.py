@@ -647,3 +647,35 @@ def test_tcgen05_plan_invariants(qt, case):
         assert 1 <= len(u["lruns"]) <= 3 and 1 <= len(u["cruns"]) <= 3
         assert u["smem"] <= 225 * 1024 and u["passes"] == 3
         assert 2 <= u["sraw"] <= 8 and 1 <= u["splane"] <= 4
+
+
+@pytest.mark.parametrize("case", [(12, 1, 3, 0), (16, 2, 5, 0), (14, 2, 9, 1)])
+def test_order_dataset_matches_oracle(qt, case):
+    """qt_order_dataset (elimination-step candidates, features, rollout labels) against the
+    oracle's restatement: candidates and rollout widths bit-exact, features and labels to
+    FP32 rounding."""
+    import ctypes as C
+    import numpy as np
+    from oracle import ordering, proposal
+    n, p, seed, algo = case
+    edges, gammas, betas, z, tensors, nv, norm, adj = oracle_problem(n, p, seed)
+    h = qt.qt_build_network(edges, n, p, gammas, betas, z)
+    try:
+        qt.qt_order(h, algo)
+        cnt = C.c_int32()
+        qt._check(qt.lib.qt_order_dataset(h, 4, 3, None, None, None, 0, C.byref(cnt)))
+        k = cnt.value
+        f = (C.c_float * (k * 16))()
+        lab = (C.c_float * k)()
+        meta = (C.c_int32 * (3 * k))()
+        qt._check(qt.lib.qt_order_dataset(h, 4, 3, f, lab, meta, k, C.byref(cnt)))
+    finally:
+        qt.qt_free(h)
+    X = np.frombuffer(f, dtype=np.float32).reshape(k, 16)
+    L = np.frombuffer(lab, dtype=np.float32)
+    M = np.frombuffer(meta, dtype=np.int32).reshape(k, 3)
+    rule = ordering.MIN_DEGREE if algo else ordering.MIN_FILL
+    Xo, Lo, Mo = proposal.order_dataset(adj, rule, 4, 3)
+    assert [tuple(int(x) for x in m) for m in M] == [tuple(m) for m in Mo]
+    assert np.allclose(X, Xo, rtol=1e-6, atol=1e-6)
+    assert np.allclose(L, Lo, rtol=1e-6, atol=1e-6)

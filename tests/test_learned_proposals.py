@@ -1,7 +1,8 @@
-"""What the trained proposal network (GPU-trained, committed weights) gains over the
-search without it, on held-out graphs (N = 60..140, p = 1, 2, seeds outside training).
+"""What the trained proposal networks (GPU-trained, committed weights) gain over the
+searches without them, on held-out graphs (seeds outside training).
 
-Measured and asserted here (host planner; no GPU needed):
+Slicing candidates (N = 60..140, p = 1, 2), measured and asserted here (host planner; no
+GPU needed):
   * against the paper's search (every step verified): the model's top 8 per round need
     at least 5x fewer greedy ordering runs, for a mean width at most 2.5 higher;
   * against the same budget without a model (8 candidates evenly spaced): reported, not
@@ -50,3 +51,58 @@ def test_learned_per_step_vertex_choice(model):
     per_step = _run(learn, "learned", params, hidden, topm=0, spread=0)
     assert np.all(per_step[:, 2] <= paper[:, 2] * 1.5 + 2)
     assert per_step[:, 1].mean() <= paper[:, 1].mean() + 0.5
+
+
+# ---------------------------------------------------------------------------------------
+# Elimination-step proposals: the model picks the next vertex among the 4 best by the
+# min-fill key at every step; greedy min-fill judges (2 ordering runs). The same budget
+# without a model: the better of min-fill and one Boltzmann-randomised greedy run
+# (rgreedy, tau = 0.1), and the better of min-fill and min-degree.
+# ---------------------------------------------------------------------------------------
+STEP_HELD_OUT = [(n, p, 95000 + 17 * n + p) for n in (70, 110, 150) for p in (1, 2, 3)]
+
+
+def _order_key(qt, h):
+    import math
+    ws = qt.qt_get_widths(h)
+    return max(ws), math.log2(sum(math.ldexp(1.0, x) for x in ws))
+
+
+@pytest.fixture(scope="module")
+def order_model(qt):
+    import json
+    from paper_2012_02430_gb300 import learn
+    with open(learn.ORDER_WEIGHTS) as f:
+        d = json.load(f)
+    return np.array(d["params"], dtype=np.float32), int(d["hidden"]), d
+
+
+def test_learned_steps_beat_equal_budget(qt, order_model):
+    from paper_2012_02430_gb300 import learn
+    from paper_2012_02430_gb300.inputs import qaoa_instance
+    params, hidden, info = order_model
+    assert info["dataset_size"] >= 10000 and info["topc"] == 4
+    rows = []
+    for inst in STEP_HELD_OUT:
+        n, p, seed = inst
+        e, g, b, z = qaoa_instance(n, p, seed)
+        h = qt.qt_build_network(e, n, p, g, b, z)
+        try:
+            qt.qt_order(h, 0)
+            mf = _order_key(qt, h)
+            qt.qt_order(h, 1)
+            md = _order_key(qt, h)
+            qt.qt_order_rgreedy(h, 0.1, 1, 1)
+            rg = _order_key(qt, h)
+        finally:
+            qt.qt_free(h)
+        judged = learn.order_with(inst, params, hidden, 4, 1)[:2]
+        rows.append((mf, min(mf, md), min(mf, rg), judged))
+    a = np.array(rows, dtype=np.float64)  # [instance][method][width, log2 cost]
+    mean = a.mean(axis=0)
+    print("mean width / log2 cost: min-fill %.2f/%.2f, best(mf, md) %.2f/%.2f, "
+          "best(mf, rgreedy) %.2f/%.2f, learned+judge %.2f/%.2f" % tuple(mean.ravel()))
+    # never worse than min-fill (the judge), and below both equal-budget searches
+    assert np.all(a[:, 3, 0] <= a[:, 0, 0])
+    assert mean[3, 0] < mean[1, 0] and mean[3, 0] < mean[2, 0]
+    assert mean[3, 1] < mean[1, 1] - 0.25 and mean[3, 1] < mean[2, 1] - 0.25

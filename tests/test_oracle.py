@@ -556,3 +556,18 @@ def test_mlp_forward_hand_example():
     assert abs(grad[-1] - g["grad_b3"]) <= 1e-15
     gw3 = [_feature_value(x) if isinstance(x, list) else x for x in g["grad_w3"]]
     assert np.allclose(grad[-1 - g["hidden"]:-1], gw3, rtol=0, atol=1e-15)
+
+
+def test_step_proposal_hand_example():
+    """Candidates, all 16 features and the rollout labels of two elimination-step
+    candidates, worked by hand on a five-vertex graph."""
+    from oracle import proposal
+    g = load("step_proposal_hand.json")
+    a = adj_of(g["n"], g["edges"])
+    feats, labels, meta = proposal.order_dataset(a, ordering.MIN_FILL, g["topc"], g["stride"])
+    at0 = [m[1] for m in meta if m[0] == 0]
+    assert at0 == g["candidates"]
+    for v, want in g["features"].items():
+        i = [q for q, m in enumerate(meta) if m[0] == 0 and m[1] == int(v)][0]
+        assert np.allclose(feats[i], [_feature_value(x) for x in want], rtol=0, atol=1e-12), v
+        assert abs(labels[i] - math.log2(g["labels_log2_of"][v])) <= 1e-12
