@@ -386,9 +386,10 @@ void qt_mlp_free(qt_mlp* mlp);
  *                  autotuner may pick them. Other values: QT_EINVAL. Discards
  *                  the prepared schedule.
  *   QT_OPT_SEGMENTS 1 (default): two or more consecutive small launches (union
- *                  of at most 12 indices) run as one segment launch, one block
- *                  per slice stepping through them with block barriers; results
- *                  read only inside the run stay in shared memory. 2..13: the
+ *                  of at most 12 indices) run as one segment launch, a block (or
+ *                  a cluster of blocks, QT_OPT_SEG_CLUSTER) per slice stepping
+ *                  through them level by level with barriers; results read only
+ *                  inside the run stay in shared memory. 2..13: the
  *                  same with launches of at most that many union indices. 0: one
  *                  launch each. Values outside 0..13: QT_EINVAL. Discards the
  *                  prepared schedule.
@@ -438,10 +439,19 @@ void qt_mlp_free(qt_mlp* mlp);
  *                  with an extreme exponent (|s_j| > 30, or |sum s_j| > 60);
  *                  0 (default): that choice per slice. Values agree within
  *                  FP32 rounding. Discards the prepared schedule.
+ *   QT_OPT_SEG_CLUSTER blocks per slice of a segment launch (a thread-block
+ *                  cluster: each dependency level's work spread over its blocks,
+ *                  every result written into each block's shared memory, one
+ *                  cluster barrier per level). 0 (default): the largest of 8, 4,
+ *                  2 whose clusters fill at most two blocks per SM, 1 when the
+ *                  batch already fills the device; 1, 2, 4, 8: that size (lowered
+ *                  to what the device can co-schedule). Other values: QT_EINVAL.
+ *                  Results are the same bits for every size. Discards the
+ *                  prepared schedule.
  * Errors: QT_EINVAL for a null network or an unknown option. */
 enum { QT_OPT_FUSION = 1, QT_OPT_GRAPHS = 2, QT_OPT_GEMM = 3, QT_OPT_SEGMENTS = 4,
        QT_OPT_TRIANGLE = 5, QT_OPT_TMA = 6, QT_OPT_CONCURRENT = 7, QT_OPT_TCGEN05 = 8,
-       QT_OPT_SCALED = 9 };
+       QT_OPT_SCALED = 9, QT_OPT_SEG_CLUSTER = 10 };
 qt_status qt_set_option(qt_net* net, int32_t option, int64_t value);
 
 /*

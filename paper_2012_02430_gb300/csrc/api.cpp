@@ -736,6 +736,12 @@ qt_status qt_set_option(qt_net* net, int32_t option, int64_t value) {
       net->force_scaled = value != 0;
       net->sched = qt::Schedule();  // prepare again
       break;
+    case QT_OPT_SEG_CLUSTER:
+      if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8)
+        return fail(QT_EINVAL, "qt_set_option: QT_OPT_SEG_CLUSTER takes 0, 1, 2, 4 or 8");
+      net->seg_cluster = (int)value;
+      net->sched = qt::Schedule();  // prepare again
+      break;
     case QT_OPT_TCGEN05:
       if (value < 0 || value > 3) return fail(QT_EINVAL, "qt_set_option: QT_OPT_TCGEN05 takes 0..3");
       net->tcgen05 = (int)value;

@@ -58,6 +58,7 @@ struct KStep {
   int out_global;      // segment launch: the result is also stored to global memory
   int out_mslot;       // segment launch: slot of the result's metadata in the block's cache
   int flags;           // bit 0: the tiled kernel takes its scaled path in every slice
+  int item0;           // segment launch: the step's first work item within its level
   KOp op[MAXOP];
 };
 
@@ -74,9 +75,11 @@ struct SegStage {
 
 // One dependency level of a segment launch: its steps read only results of
 // earlier levels. Steps [first, first + nwarp) are small (at most 32 value
-// pairs) and run one per warp, concurrently; the next nblock steps use the block.
+// pairs), the next nblock larger. Every step is cut into work items of 32 value
+// pairs (one warp each); the level's `items` items run concurrently over all warps
+// of the slice's block or cluster.
 struct SegLevel {
-  int first, nwarp, nblock, pad;
+  int first, nwarp, nblock, items;
 };
 
 struct Meta {
@@ -255,6 +258,11 @@ __global__ void __launch_bounds__(256) k_bucket_flat(const KStep st, R* data, Me
 }
 
 static_assert(sizeof(KStep) <= kStepRecordBytes, "step record size");
+// a segment block's shared layout keeps every part 8-byte aligned (16 at part starts):
+// the cluster path stores metadata words and complex values remotely
+static_assert(sizeof(KStep) % 16 == 0 && sizeof(SegStage) % 8 == 0 && sizeof(SegLevel) % 8 == 0 &&
+                  sizeof(Meta) == 8,
+              "segment shared layout alignment");
 
 // Segment kernel: a run of consecutive small launches as one launch. Block b
 // handles slice b of the batch and runs the run's steps one after another with
@@ -373,13 +381,88 @@ __device__ __forceinline__ void seg_pair(const KStep& st, const R* sc, bool acti
   }
 }
 
+// Shared layout of a segment block: records (steps, stages, levels), the metadata
+// cache and the arena, each part starting on a 16-byte boundary (the records are
+// copied in 16-byte chunks, the arena in 8- or 16-byte values).
+struct SegLayout {
+  int meta, arena;  // byte offsets
+};
+__host__ __device__ __forceinline__ SegLayout seg_layout(int nsteps, int nstages, int nlevels,
+                                                         int nmeta) {
+  const int rec = nsteps * (int)sizeof(KStep) + nstages * (int)sizeof(SegStage) +
+                  nlevels * (int)sizeof(SegLevel);
+  SegLayout l;
+  l.meta = (rec + 15) & ~15;
+  l.arena = (l.meta + nmeta * (int)sizeof(Meta) + 15) & ~15;
+  return l;
+}
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::
+                   "r"((unsigned int)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::
+                   "r"((unsigned int)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Thread-block clusters: a segment launch may give each slice a cluster of C blocks
+// (C = %cluster_nctarank; 1 without a cluster launch). Every block of the cluster
+// keeps a full copy of the arena and of the metadata cache; a level's work items are
+// spread over all C blocks, and each result is written into every block's copy
+// through distributed shared memory, so all reads stay local. One cluster barrier
+// (release / acquire) per dependency level makes a level's results visible.
+__device__ __forceinline__ unsigned int cl_rank() {
+  unsigned int r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned int cl_size() {
+  unsigned int r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+               ::: "memory");
+}
+// the address of local shared variable p in block `rank` of the cluster
+__device__ __forceinline__ unsigned int cl_map(const void* p, unsigned int rank) {
+  const unsigned int a = (unsigned int)__cvta_generic_to_shared(p);
+  unsigned int r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cl_st2(unsigned int a, float x, float y) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" :: "r"(a), "f"(x), "f"(y) : "memory");
+}
+// (a complex128 value is stored as two 8-byte words: only 8-byte alignment is needed)
+__device__ __forceinline__ void cl_st2(unsigned int a, double x, double y) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;\n\tst.shared::cluster.f64 [%0+8], %2;"
+               :: "r"(a), "d"(x), "d"(y) : "memory");
+}
+__device__ __forceinline__ void cl_st_s32(unsigned int a, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" :: "r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cl_max(unsigned int a, unsigned int v) {
+  asm volatile("red.shared::cluster.max.u32 [%0], %1;" :: "r"(a), "r"(v) : "memory");
+}
+
 template <typename R>
 __device__ __forceinline__ void seg_store(const KStep& st, long long i, unsigned long long I,
-                                          R sr, R si, R* data, R* arena) {
+                                          R sr, R si, R* data, R* arena, unsigned int ncl) {
   const long long oi = (long long)(I >> st.nsum);
   if (st.out_soff >= 0) {
-    arena[2 * (st.out_soff + oi)] = sr;
-    arena[2 * (st.out_soff + oi) + 1] = si;
+    R* p = arena + 2 * (st.out_soff + oi);
+    if (ncl == 1) {
+      p[0] = sr;
+      p[1] = si;
+    } else {
+      for (unsigned int r = 0; r < ncl; ++r) cl_st2(cl_map(p, r), sr, si);
+    }
   }
   if (st.out_global) store_out<R>(data, st.out_base + i * st.out_slice_stride + oi, sr, si);
 }
@@ -390,53 +473,62 @@ __global__ void __launch_bounds__(seg_threads<R>()) k_segment(const KStep* steps
                                                         const SegLevel* levels, int nlevels,
                                                         R* data, Meta* meta, long long slice_first,
                                                         int n_shared, int n_slice_t, long long batch) {
-  extern __shared__ KStep seg_steps[];
-  __shared__ unsigned int s_max;
-  const long long i = blockIdx.x;
+  extern __shared__ __align__(16) KStep seg_steps[];
+  const unsigned int ncl = cl_size(), rank = ncl > 1 ? cl_rank() : 0u;
+  const long long i = blockIdx.x / ncl;  // the slice of this block's cluster
   const unsigned long long sid = (unsigned long long)(slice_first + i);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   SegStage* sst = reinterpret_cast<SegStage*>(seg_steps + nsteps);
   SegLevel* slv = reinterpret_cast<SegLevel*>(sst + nstages);
-  Meta* mc = reinterpret_cast<Meta*>(slv + nlevels);
-  R* arena = reinterpret_cast<R*>(mc + ((n_shared + n_slice_t + 1) & ~1));
-  using C2 = typename CT<R>::c2;
+  const int nmeta = n_shared + n_slice_t;
+  const SegLayout lay = seg_layout(nsteps, nstages, nlevels, nmeta);
+  char* sbase = reinterpret_cast<char*>(seg_steps);
+  Meta* mc = reinterpret_cast<Meta*>(sbase + lay.meta);
+  R* arena = reinterpret_cast<R*>(sbase + lay.arena);
+  // the records (16-byte chunks) and the metadata cache: asynchronous copies, all in flight
   {
-    const int* src = reinterpret_cast<const int*>(steps);
-    int* dst = reinterpret_cast<int*>(seg_steps);
-    const int words = (nsteps * (int)sizeof(KStep) + nstages * (int)sizeof(SegStage) +
-                       nlevels * (int)sizeof(SegLevel)) / 4;
-    for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = __ldcg(src + w);
-    for (int q = threadIdx.x; q < n_shared + n_slice_t; q += blockDim.x) {
+    const char* src = reinterpret_cast<const char*>(steps);
+    for (int w = threadIdx.x; w < lay.meta / 16; w += blockDim.x)
+      cp_async16(sbase + 16 * w, src + 16 * w);
+    for (int q = threadIdx.x; q < nmeta; q += blockDim.x) {
       const long long g = q < n_shared ? q : n_shared + (long long)(q - n_shared) * batch + i;
-      mc[q] = ld_meta_cg(meta + g);
+      cp_async8(mc + q, meta + g);
     }
-    if (threadIdx.x == 0) s_max = 0u;
+    cp_async_wait_all();
   }
   __syncthreads();
-  // inputs from outside the run: one parallel copy into the arena
-  if (nstages > 0) {
-    const int total = sst[nstages - 1].cum + sst[nstages - 1].n;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-      int lo = 0, hi = nstages - 1;  // last record with cum <= e
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (sst[mid].cum <= e) lo = mid;
-        else hi = mid - 1;
-      }
-      const SegStage& sg = sst[lo];
-      long long src = sg.base + i * sg.slice_stride + (e - sg.cum);
-      if (sg.smask) src += (long long)(pext64(sid, sg.smask) << sg.sshift);
-      const C2 v = __ldcg(reinterpret_cast<const C2*>(data + 2 * src));
-      arena[2 * (sg.soff + e - sg.cum)] = v.x;
-      arena[2 * (sg.soff + e - sg.cum) + 1] = v.y;
+  // the launch's results start at max-abs 0 (every work item raises it)
+  for (int q = threadIdx.x; q < nsteps; q += blockDim.x) mc[seg_steps[q].out_mslot].maxabs = 0u;
+  // inputs from outside the run: one stage record per warp, asynchronous copies into the
+  // arena (every block of a cluster its own copy)
+  for (int q = warp; q < nstages; q += nwarps) {
+    const SegStage sg = sst[q];
+    long long src = sg.base + i * sg.slice_stride;
+    if (sg.smask) src += (long long)(pext64(sid, sg.smask) << sg.sshift);
+    for (int e = lane; e < sg.n; e += 32) {
+      if constexpr (sizeof(R) == 4) cp_async8(arena + 2 * (sg.soff + e), data + 2 * (src + e));
+      else cp_async16(arena + 2 * (sg.soff + e), data + 2 * (src + e));
     }
   }
-  __syncthreads();
+  cp_async_wait_all();
+  // every block of the cluster has started and reset its slots before any remote write
+  if (ncl > 1) cl_sync();
+  else __syncthreads();
+  const int cl_warp = (int)rank * nwarps + warp, cl_warps = (int)ncl * nwarps;
   for (int L = 0; L < nlevels; ++L) {
     const SegLevel lv = slv[L];
-    // small steps: one warp each
-    for (int ws = warp; ws < lv.nwarp; ws += nwarps) {
-      const KStep& st = seg_steps[lv.first + ws];
+    const int nst = lv.nwarp + lv.nblock;
+    // work items of 32 value pairs over the cluster's warps; no barrier inside a level
+    // (a level's steps read only earlier levels)
+    for (int it = cl_warp; it < lv.items; it += cl_warps) {
+      int lo = lv.first, hi = lv.first + nst - 1;  // the step: last with item0 <= it
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (seg_steps[mid].item0 <= it) lo = mid;
+        else hi = mid - 1;
+      }
+      const KStep& st = seg_steps[lo];
+      const int chunk = it - st.item0;
       R scj = R(1);
       int e = 0;
       if (lane < st.m) {
@@ -450,62 +542,39 @@ __global__ void __launch_bounds__(seg_threads<R>()) k_segment(const KStep* steps
 #pragma unroll
       for (int j = 0; j < MAXOP; ++j) sc[j] = __shfl_sync(0xffffffffu, scj, j);
       const long long npairs = 1ll << (st.u - 1);
-      const bool active = lane < npairs;
-      const unsigned long long I = (unsigned long long)(active ? lane : 0) << 1;
+      const long long g = (long long)chunk * 32 + lane;
+      const bool active = g < npairs;
+      const unsigned long long I = (unsigned long long)(active ? g : 0) << 1;
       R sr, si;
       seg_pair<R>(st, sc, active, I, i, sid, data, arena, sr, si);
       float mx = 0.f;
       if (active && (lane & ((1 << (st.nsum - 1)) - 1)) == 0) {
-        seg_store<R>(st, i, I, sr, si, data, arena);
+        seg_store<R>(st, i, I, sr, si, data, arena, ncl);
         mx = absmax(sr, si);
       }
       const unsigned int red = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+      // the result's metadata: max-abs raised by every item, the exponent set by item 0
       if (lane == 0) {
-        const Meta mo{red, e};
-        mc[st.out_mslot] = mo;
-        meta[st.out_meta + (st.out_meta_per_slice ? i : 0)] = mo;
-      }
-    }
-    // larger steps: the whole block
-    for (int bs = 0; bs < lv.nblock; ++bs) {
-      const KStep& st = seg_steps[lv.first + lv.nwarp + bs];
-      R sc[MAXOP];
-      int e = 0;
-#pragma unroll
-      for (int j = 0; j < MAXOP; ++j) {
-        if (j >= st.m) break;
-        const Meta mt = mc[st.op[j].mslot];
-        const int sj = scale_exp(mt.maxabs);
-        sc[j] = pow2_neg<R>(sj);
-        e += mt.E + sj;
-      }
-      const long long npairs = 1ll << (st.u - 1);
-      float mx = 0.f;
-      for (long long b0 = 0; b0 < npairs; b0 += blockDim.x) {
-        if (b0 + (threadIdx.x & ~31) >= npairs) break;
-        const long long g = b0 + threadIdx.x;
-        const bool active = g < npairs;
-        const unsigned long long I = (unsigned long long)(active ? g : 0) << 1;
-        R sr, si;
-        seg_pair<R>(st, sc, active, I, i, sid, data, arena, sr, si);
-        if (active && (lane & ((1 << (st.nsum - 1)) - 1)) == 0) {
-          seg_store<R>(st, i, I, sr, si, data, arena);
-          mx = fmaxf(mx, absmax(sr, si));
+        if (ncl == 1) {
+          if (red != 0u) atomicMax(&mc[st.out_mslot].maxabs, red);
+          if (chunk == 0) mc[st.out_mslot].E = e;
+        } else {
+          for (unsigned int r = 0; r < ncl; ++r) {
+            if (red != 0u) cl_max(cl_map(&mc[st.out_mslot].maxabs, r), red);
+            if (chunk == 0) cl_st_s32(cl_map(&mc[st.out_mslot].E, r), e);
+          }
         }
       }
-      const unsigned int red = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
-      if (lane == 0 && red != 0u) atomicMax(&s_max, red);
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        const Meta mo{s_max, e};
-        mc[st.out_mslot] = mo;
-        meta[st.out_meta + (st.out_meta_per_slice ? i : 0)] = mo;
-        s_max = 0u;
-      }
-      __syncthreads();
     }
-    __syncthreads();
+    if (ncl > 1) cl_sync();
+    else __syncthreads();
   }
+  // the launch's result metadata, from the (identical) cache of the cluster's first block
+  if (rank == 0)
+    for (int q = threadIdx.x; q < nsteps; q += blockDim.x) {
+      const KStep& st = seg_steps[q];
+      meta[st.out_meta + (st.out_meta_per_slice ? i : 0)] = mc[st.out_mslot];
+    }
 }
 
 // Tiled kernel. Per slice, the U index space is cut into tiles of 2^TILE_UBITS
@@ -1112,6 +1181,7 @@ struct LaunchDesc {
   long long seg_off = 0;             // kind 5: byte offset of its records in the segment table
   int seg_count = 0, stage_count = 0, level_count = 0;
   long long seg_arena = 0;           // kind 5: shared-arena elements per block
+  int seg_cl_max = 1;                // kind 5: largest cluster the device co-schedules (1..8)
   int g_last = -1;                   // last schedule group the launch covers (kind 5: a run)
 };
 
@@ -1544,6 +1614,61 @@ static void plan_streams(const Schedule& S, const std::vector<LaunchDesc>& list,
   if (writes) *writes = wr;
 }
 
+// Segment launches: dynamic shared memory of a block and the largest cluster size (8,
+// 4, 2, else 1) the device can co-schedule with it, asked once when the launch is
+// planned (never during stream capture).
+template <typename R>
+static void seg_set_attr() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(k_segment<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(220 * 1024));
+    done = true;
+  }
+}
+
+template <typename R>
+static size_t seg_smem(const Schedule& S, const LaunchDesc& d) {
+  const SegLayout l = seg_layout(d.seg_count, d.stage_count, d.level_count,
+                                 (int)(S.n_shared_meta + S.n_slice_meta_tensors));
+  return (size_t)l.arena + (size_t)d.seg_arena * 2 * sizeof(R);
+}
+
+template <typename R>
+static int seg_cluster_max(size_t smem) {
+  seg_set_attr<R>();
+  for (int c = 8; c > 1; c >>= 1) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)c);
+    cfg.blockDim = dim3(seg_threads<R>());
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)c;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_segment<R>, &cfg) == cudaSuccess && n > 0) return c;
+    cudaGetLastError();
+  }
+  return 1;
+}
+
+// Blocks per slice of a segment launch: the network's setting (QT_OPT_SEG_CLUSTER), or
+// the largest of 8, 4, 2 whose clusters fill at most two blocks per SM, so that small
+// slice batches spread each slice's work over several SMs; 1 for large batches. Never
+// above what the device co-schedules.
+static int seg_cluster_size(const qt_net* net, const LaunchDesc& d, long long nslices) {
+  int c = net->seg_cluster;
+  if (c == 0) {
+    c = 8;
+    while (c > 1 && nslices * c > 2ll * num_sms()) c >>= 1;
+  }
+  return std::min(c, d.seg_cl_max);
+}
+
 template <typename R>
 static bool build_cache(qt_net* net, EngineCache& c, std::string& err) {
   const Schedule& S = net->sched;
@@ -1658,6 +1783,7 @@ static bool build_cache(qt_net* net, EngineCache& c, std::string& err) {
           }
         }
         SegLevel sl{(int)recs.size(), 0, 0, 0};
+        int items = 0;
         for (int pass = 0; pass < 2; ++pass)  // warp steps, then block steps
           for (int q = 0; q < n; ++q) {
             if (lev[q] != L) continue;
@@ -1682,11 +1808,14 @@ static bool build_cache(qt_net* net, EngineCache& c, std::string& err) {
               slot[out] = {off, cnt};
             }
             k.out_global = (ot.last_use > gi_last || k.out_soff < 0) ? 1 : 0;
+            k.item0 = items;
+            items += (int)std::max(1ll, (1ll << (k.u - 1)) / 32);
             recs.push_back(k);
             (pass == 0 ? sl.nwarp : sl.nblock)++;
             d.bytes += (*list)[i + q].bytes;
             d.flops += (*list)[i + q].flops;
           }
+        sl.items = items;
         levels.push_back(sl);
       }
       d.seg_count = n;
@@ -1716,6 +1845,9 @@ static bool build_cache(qt_net* net, EngineCache& c, std::string& err) {
         ++i;
         continue;
       }
+      d.seg_cl_max = seg_cluster_max<R>(seg_smem<R>(S, d));
+      // records start on 16 bytes and are read in 16-byte chunks
+      c.segtab.resize((c.segtab.size() + 15) & ~(size_t)15, 0);
       d.seg_off = (long long)c.segtab.size();
       auto append = [&](const void* p, size_t bytes) {
         const unsigned char* b = static_cast<const unsigned char*>(p);
@@ -1724,6 +1856,7 @@ static bool build_cache(qt_net* net, EngineCache& c, std::string& err) {
       append(recs.data(), recs.size() * sizeof(KStep));
       append(stages.data(), stages.size() * sizeof(SegStage));
       append(levels.data(), levels.size() * sizeof(SegLevel));
+      c.segtab.resize((c.segtab.size() + 15) & ~(size_t)15, 0);
       d.g_last = (*list)[j - 1].group;
       merged.push_back(d);
       i = j;
@@ -1757,20 +1890,24 @@ static void launch_desc(qt_net* net, const LaunchDesc& d0, long long nslices, lo
     const KStep* tab = reinterpret_cast<const KStep*>(base + S.off_segtab + d0.seg_off);
     const SegStage* stab = reinterpret_cast<const SegStage*>(tab + d0.seg_count);
     const SegLevel* ltab = reinterpret_cast<const SegLevel*>(stab + d0.stage_count);
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_segment<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(220 * 1024));
-      attr = true;
-    }
+    seg_set_attr<R>();
     const int nsh = (int)S.n_shared_meta, nst = (int)S.n_slice_meta_tensors;
-    const size_t smem = d0.seg_count * sizeof(KStep) + d0.stage_count * sizeof(SegStage) +
-                        d0.level_count * sizeof(SegLevel) +
-                        (size_t)((nsh + nst + 1) & ~1) * sizeof(Meta) +
-                        (size_t)d0.seg_arena * 2 * sizeof(R);
-    k_segment<R><<<(unsigned)nslices, seg_threads<R>(), smem, s>>>(
-        tab, d0.seg_count, stab, d0.stage_count, ltab, d0.level_count, data, meta, slice_first,
-        nsh, nst, (long long)S.batch);
+    const size_t smem = seg_smem<R>(S, d0);
+    const int ncl = seg_cluster_size(net, d0, nslices);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nslices * ncl));
+    cfg.blockDim = dim3(seg_threads<R>());
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)ncl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = ncl > 1 ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k_segment<R>, tab, d0.seg_count, stab, d0.stage_count, ltab,
+                       d0.level_count, data, meta, slice_first, nsh, nst, (long long)S.batch);
     if (net->prof) prof_end(net, s, pr);
     return;
   }
@@ -2134,6 +2271,23 @@ static bool launch_plan_impl(qt_net* net, std::string& out, std::string& err) {
     spans(rd[x]);
     o << ",\"writes\":";
     spans(wr[x]);
+    if (d.kind == 5) {
+      // the segment's dependency levels (warp steps, block steps) and per step its
+      // operand count, union indices and summed indices
+      const KStep* ks = reinterpret_cast<const KStep*>(tmp.segtab.data() + d.seg_off);
+      const SegLevel* lv =
+          reinterpret_cast<const SegLevel*>(reinterpret_cast<const SegStage*>(ks + d.seg_count) +
+                                            d.stage_count);
+      o << ",\"segment\":{\"arena\":" << d.seg_arena << ",\"stages\":" << d.stage_count
+        << ",\"cluster_max\":" << d.seg_cl_max << ",\"levels\":[";
+      for (int q = 0; q < d.level_count; ++q)
+        o << (q ? "," : "") << "[" << lv[q].nwarp << "," << lv[q].nblock << "," << lv[q].items
+          << "]";
+      o << "],\"steps\":[";
+      for (int q = 0; q < d.seg_count; ++q)
+        o << (q ? "," : "") << "[" << ks[q].m << "," << ks[q].u << "," << ks[q].nsum << "]";
+      o << "]}";
+    }
     UmmaPlan up;
     if (d.kind == 3 && (d.gemm_mode == GEMM_UMMA_TF32 || d.gemm_mode == GEMM_UMMA_3XTF32) &&
         umma_plan(d.ga, d.gemm_mode == GEMM_UMMA_TF32 ? 1 : 3, up)) {

@@ -234,6 +234,7 @@ struct qt_net {
   bool force_stream = false;     // ... with the streaming kernel where it applies
   bool segments = true;          // runs of small launches as one segment launch
   int seg_max_u = 12;            // union indices of a step a segment may hold (at most 13)
+  int seg_cluster = 0;           // blocks per slice of a segment launch: 0 chosen, 1, 2, 4, 8
   bool concurrent = true;        // captured graphs run independent slice launches concurrently
   bool force_tri = false;        // triangle-form launches by default where they apply
   bool tma = true;               // tiled GEMM stages its blocks with tensor copies (TMA)

@@ -23,6 +23,7 @@ QT_OPT_FUSION, QT_OPT_GRAPHS, QT_OPT_GEMM, QT_OPT_SEGMENTS, QT_OPT_TRIANGLE, QT_
 QT_OPT_CONCURRENT = 7
 QT_OPT_TCGEN05 = 8
 QT_OPT_SCALED = 9
+QT_OPT_SEG_CLUSTER = 10
 QT_PROPOSAL_FEATURES = 16
 QT_MAX_OPEN = 16
 
