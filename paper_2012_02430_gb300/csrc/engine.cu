@@ -274,9 +274,10 @@ static_assert(sizeof(KStep) % 16 == 0 && sizeof(SegStage) % 8 == 0 && sizeof(Seg
 // (ld.global.cg): neither the read-only path nor L1 may hold a stale copy of an
 // arena slot that an earlier step of the launch rewrote.
 template <typename R>
-constexpr int seg_threads() { return sizeof(R) == 4 ? 384 : 256; }
+constexpr int seg_threads() { return sizeof(R) == 4 ? 512 : 256; }
 constexpr int SEG_MAX_U = 13;
 constexpr int SEG_MAX_STEPS = 64;  // step records per segment launch (shared memory)
+constexpr int SEG_SMEM_MAX = 220 * 1024;  // dynamic shared memory of a segment block
 
 template <typename R>
 __device__ __forceinline__ void load_pair_cg(const R* data, long long off, bool has_bit0, R& r0,
@@ -319,15 +320,17 @@ constexpr size_t SEG_ARENA_BYTES = 96 * 1024;  // shared arena for results that 
 // read only earlier levels): small steps one per warp, concurrently, larger ones
 // with the whole block; one block barrier per level.
 
-// the pair index I of one value pair of a step: loads every operand, multiplies
-// level by level (levels >= 1 summed across lanes by shuffles over the lanes that
-// share the pair's higher bits), returns the lane's partial result
+// One value pair of a step inside a segment work item. The pair index is
+// I = 2 (32 chunk + lane): an operand's element offset pext(I, umask) is its arena
+// offset plus the chunk's high bits (obase[j], computed once per item by lane j)
+// plus the lane's six low bits, looked up in the block's table lt[umask & 63][lane].
+// Loads every operand, multiplies level by level (levels >= 1 summed across lanes by
+// shuffles over the lanes that share the pair's higher bits), returns the lane's
+// partial result.
 template <typename R>
-__device__ __forceinline__ void seg_pair(const KStep& st, const R* sc, bool active,
-                                         unsigned long long I, long long i,
-                                         unsigned long long sid, const R* data, const R* arena,
-                                         R& sr, R& si) {
-  using C2 = typename CT<R>::c2;
+__device__ __forceinline__ void seg_pair(const KStep& st, const R* sc, const int* obase,
+                                         const unsigned char* lt, bool active, int lane,
+                                         const R* arena, R& sr, R& si) {
   const int m = st.m;
   R vr0[MAXOP], vi0[MAXOP], vr1[MAXOP], vi1[MAXOP];
 #pragma unroll
@@ -335,26 +338,29 @@ __device__ __forceinline__ void seg_pair(const KStep& st, const R* sc, bool acti
     if (j >= m) break;
     vr0[j] = vi0[j] = vr1[j] = vi1[j] = R(0);
     if (active) {
+      using C2 = typename CT<R>::c2;
       const KOp& o = st.op[j];
-      const long long loc = (long long)pext32r((unsigned int)I, o.umask);
-      if (o.soff >= 0) {
-        const R* p = arena + 2 * (o.soff + loc);
-        vr0[j] = p[0];
-        vi0[j] = p[1];
-        if (o.level == 0) {
-          const int d = (o.umask & 1u) ? 2 : 0;
-          vr1[j] = p[d];
-          vi1[j] = p[d + 1];
+      const unsigned int um = o.umask;
+      // the element and, for a level-0 operand holding U bit 0, its neighbour (the
+      // offset is then even: one 16-byte load for complex64)
+      const R* p = arena + 2 * (obase[j] + lt[((um & 63u) << 5) | (unsigned int)lane]);
+      if constexpr (sizeof(R) == 4) {
+        if (o.level == 0 && (um & 1u)) {
+          const float4 v = *reinterpret_cast<const float4*>(p);
+          vr0[j] = v.x; vi0[j] = v.y; vr1[j] = v.z; vi1[j] = v.w;
+        } else {
+          const float2 v = *reinterpret_cast<const float2*>(p);
+          vr0[j] = vr1[j] = v.x;
+          vi0[j] = vi1[j] = v.y;
         }
       } else {
-        long long off = o.base + i * o.slice_stride + loc;
-        if (o.smask) off += (long long)(pext64(sid, o.smask) << o.sshift);
-        if (o.level == 0) {
-          load_pair_cg<R>(data, off, o.umask & 1u, vr0[j], vi0[j], vr1[j], vi1[j]);
-        } else {
-          const C2 a = __ldcg(reinterpret_cast<const C2*>(data + 2 * off));
-          vr0[j] = a.x;
-          vi0[j] = a.y;
+        const C2 a = *reinterpret_cast<const C2*>(p);
+        vr0[j] = vr1[j] = a.x;
+        vi0[j] = vi1[j] = a.y;
+        if (o.level == 0 && (um & 1u)) {
+          const C2 b = *reinterpret_cast<const C2*>(p + 2);
+          vr1[j] = b.x;
+          vi1[j] = b.y;
         }
       }
     }
@@ -384,15 +390,19 @@ __device__ __forceinline__ void seg_pair(const KStep& st, const R* sc, bool acti
 // Shared layout of a segment block: records (steps, stages, levels), the metadata
 // cache and the arena, each part starting on a 16-byte boundary (the records are
 // copied in 16-byte chunks, the arena in 8- or 16-byte values).
+// After the level records come the item map (one byte per work item: its step) and,
+// past the records, the lane table lt[mask][lane] = pext(2 lane, mask) for 6-bit masks.
 struct SegLayout {
-  int meta, arena;  // byte offsets
+  int table, meta, arena;  // byte offsets
 };
+constexpr int SEG_TABLE_BYTES = 64 * 32;
 __host__ __device__ __forceinline__ SegLayout seg_layout(int nsteps, int nstages, int nlevels,
-                                                         int nmeta) {
+                                                         int nitems, int nmeta) {
   const int rec = nsteps * (int)sizeof(KStep) + nstages * (int)sizeof(SegStage) +
-                  nlevels * (int)sizeof(SegLevel);
+                  nlevels * (int)sizeof(SegLevel) + nitems;
   SegLayout l;
-  l.meta = (rec + 15) & ~15;
+  l.table = (rec + 15) & ~15;
+  l.meta = l.table + SEG_TABLE_BYTES;
   l.arena = (l.meta + nmeta * (int)sizeof(Meta) + 15) & ~15;
   return l;
 }
@@ -458,8 +468,11 @@ __device__ __forceinline__ void seg_store(const KStep& st, long long i, unsigned
   if (st.out_soff >= 0) {
     R* p = arena + 2 * (st.out_soff + oi);
     if (ncl == 1) {
-      p[0] = sr;
-      p[1] = si;
+      using C2 = typename CT<R>::c2;
+      C2 v;
+      v.x = sr;
+      v.y = si;
+      *reinterpret_cast<C2*>(p) = v;
     } else {
       for (unsigned int r = 0; r < ncl; ++r) cl_st2(cl_map(p, r), sr, si);
     }
@@ -471,8 +484,9 @@ template <typename R>
 __global__ void __launch_bounds__(seg_threads<R>()) k_segment(const KStep* steps, int nsteps,
                                                         const SegStage* stages, int nstages,
                                                         const SegLevel* levels, int nlevels,
-                                                        R* data, Meta* meta, long long slice_first,
-                                                        int n_shared, int n_slice_t, long long batch) {
+                                                        int nitems, R* data, Meta* meta,
+                                                        long long slice_first, int n_shared,
+                                                        int n_slice_t, long long batch) {
   extern __shared__ __align__(16) KStep seg_steps[];
   const unsigned int ncl = cl_size(), rank = ncl > 1 ? cl_rank() : 0u;
   const long long i = blockIdx.x / ncl;  // the slice of this block's cluster
@@ -481,18 +495,28 @@ __global__ void __launch_bounds__(seg_threads<R>()) k_segment(const KStep* steps
   SegStage* sst = reinterpret_cast<SegStage*>(seg_steps + nsteps);
   SegLevel* slv = reinterpret_cast<SegLevel*>(sst + nstages);
   const int nmeta = n_shared + n_slice_t;
-  const SegLayout lay = seg_layout(nsteps, nstages, nlevels, nmeta);
+  const SegLayout lay = seg_layout(nsteps, nstages, nlevels, nitems, nmeta);
   char* sbase = reinterpret_cast<char*>(seg_steps);
+  const unsigned char* imap = reinterpret_cast<const unsigned char*>(slv + nlevels);
+  unsigned char* lt = reinterpret_cast<unsigned char*>(sbase + lay.table);
   Meta* mc = reinterpret_cast<Meta*>(sbase + lay.meta);
   R* arena = reinterpret_cast<R*>(sbase + lay.arena);
-  // the records (16-byte chunks) and the metadata cache: asynchronous copies, all in flight
+  // the records (16-byte chunks) and the metadata cache: asynchronous copies, all in
+  // flight; meanwhile the lane table
   {
     const char* src = reinterpret_cast<const char*>(steps);
-    for (int w = threadIdx.x; w < lay.meta / 16; w += blockDim.x)
+    for (int w = threadIdx.x; w < lay.table / 16; w += blockDim.x)
       cp_async16(sbase + 16 * w, src + 16 * w);
     for (int q = threadIdx.x; q < nmeta; q += blockDim.x) {
       const long long g = q < n_shared ? q : n_shared + (long long)(q - n_shared) * batch + i;
       cp_async8(mc + q, meta + g);
+    }
+    for (int q = threadIdx.x; q < SEG_TABLE_BYTES; q += blockDim.x) {
+      const unsigned int mask = (unsigned int)q >> 5, x = ((unsigned int)q & 31u) << 1;
+      unsigned int r = 0, k = 0;
+      for (int bit = 0; bit < 6; ++bit)
+        if ((mask >> bit) & 1u) r |= ((x >> bit) & 1u) << k++;
+      lt[q] = (unsigned char)r;
     }
     cp_async_wait_all();
   }
@@ -515,38 +539,41 @@ __global__ void __launch_bounds__(seg_threads<R>()) k_segment(const KStep* steps
   if (ncl > 1) cl_sync();
   else __syncthreads();
   const int cl_warp = (int)rank * nwarps + warp, cl_warps = (int)ncl * nwarps;
+  int ibase = 0;  // the level's first entry in the item map
   for (int L = 0; L < nlevels; ++L) {
     const SegLevel lv = slv[L];
-    const int nst = lv.nwarp + lv.nblock;
     // work items of 32 value pairs over the cluster's warps; no barrier inside a level
     // (a level's steps read only earlier levels)
     for (int it = cl_warp; it < lv.items; it += cl_warps) {
-      int lo = lv.first, hi = lv.first + nst - 1;  // the step: last with item0 <= it
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (seg_steps[mid].item0 <= it) lo = mid;
-        else hi = mid - 1;
-      }
-      const KStep& st = seg_steps[lo];
+      const KStep& st = seg_steps[imap[ibase + it]];
       const int chunk = it - st.item0;
+      // lane j < m: operand j's scale and its arena offset for this chunk
       R scj = R(1);
-      int e = 0;
+      int e = 0, bj = 0;
       if (lane < st.m) {
-        const Meta mt = mc[st.op[lane].mslot];
+        const KOp& o = st.op[lane];
+        const Meta mt = mc[o.mslot];
         const int sj = scale_exp(mt.maxabs);
         scj = pow2_neg<R>(sj);
         e = mt.E + sj;
+        const unsigned int um = o.umask;
+        bj = o.soff + (int)(pext32r((unsigned int)chunk, um >> 6) << __popc(um & 63u));
       }
-      for (int d = 16; d > 0; d >>= 1) e += __shfl_xor_sync(0xffffffffu, e, d);
+      e = __reduce_add_sync(0xffffffffu, e);
       R sc[MAXOP];
+      int obase[MAXOP];
 #pragma unroll
-      for (int j = 0; j < MAXOP; ++j) sc[j] = __shfl_sync(0xffffffffu, scj, j);
+      for (int j = 0; j < MAXOP; ++j) {  // m is the same in every lane
+        if (j >= st.m) break;
+        sc[j] = __shfl_sync(0xffffffffu, scj, j);
+        obase[j] = __shfl_sync(0xffffffffu, bj, j);
+      }
       const long long npairs = 1ll << (st.u - 1);
       const long long g = (long long)chunk * 32 + lane;
       const bool active = g < npairs;
       const unsigned long long I = (unsigned long long)(active ? g : 0) << 1;
       R sr, si;
-      seg_pair<R>(st, sc, active, I, i, sid, data, arena, sr, si);
+      seg_pair<R>(st, sc, obase, lt, active, lane, arena, sr, si);
       float mx = 0.f;
       if (active && (lane & ((1 << (st.nsum - 1)) - 1)) == 0) {
         seg_store<R>(st, i, I, sr, si, data, arena, ncl);
@@ -554,18 +581,18 @@ __global__ void __launch_bounds__(seg_threads<R>()) k_segment(const KStep* steps
       }
       const unsigned int red = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
       // the result's metadata: max-abs raised by every item, the exponent set by item 0
-      if (lane == 0) {
-        if (ncl == 1) {
+      // (in a cluster, lane r updates block r's copy)
+      if (ncl == 1) {
+        if (lane == 0) {
           if (red != 0u) atomicMax(&mc[st.out_mslot].maxabs, red);
           if (chunk == 0) mc[st.out_mslot].E = e;
-        } else {
-          for (unsigned int r = 0; r < ncl; ++r) {
-            if (red != 0u) cl_max(cl_map(&mc[st.out_mslot].maxabs, r), red);
-            if (chunk == 0) cl_st_s32(cl_map(&mc[st.out_mslot].E, r), e);
-          }
         }
+      } else if ((unsigned int)lane < ncl) {
+        if (red != 0u) cl_max(cl_map(&mc[st.out_mslot].maxabs, (unsigned int)lane), red);
+        if (chunk == 0) cl_st_s32(cl_map(&mc[st.out_mslot].E, (unsigned int)lane), e);
       }
     }
+    ibase += lv.items;
     if (ncl > 1) cl_sync();
     else __syncthreads();
   }
@@ -1182,6 +1209,7 @@ struct LaunchDesc {
   int seg_count = 0, stage_count = 0, level_count = 0;
   long long seg_arena = 0;           // kind 5: shared-arena elements per block
   int seg_cl_max = 1;                // kind 5: largest cluster the device co-schedules (1..8)
+  int seg_items = 0;                 // kind 5: work items over all levels (item-map bytes)
   int g_last = -1;                   // last schedule group the launch covers (kind 5: a run)
 };
 
@@ -1622,14 +1650,14 @@ static void seg_set_attr() {
   static bool done = false;
   if (!done) {
     cudaFuncSetAttribute(k_segment<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(220 * 1024));
+                         SEG_SMEM_MAX);
     done = true;
   }
 }
 
 template <typename R>
 static size_t seg_smem(const Schedule& S, const LaunchDesc& d) {
-  const SegLayout l = seg_layout(d.seg_count, d.stage_count, d.level_count,
+  const SegLayout l = seg_layout(d.seg_count, d.stage_count, d.level_count, d.seg_items,
                                  (int)(S.n_shared_meta + S.n_slice_meta_tensors));
   return (size_t)l.arena + (size_t)d.seg_arena * 2 * sizeof(R);
 }
@@ -1693,7 +1721,8 @@ static bool build_cache(qt_net* net, EngineCache& c, std::string& err) {
     // already have reused the global slot of a tensor that dies in the run); returns
     // false when some input or internal result does not fit.
     auto plan = [&](size_t i, size_t j, LaunchDesc& d, std::vector<KStep>& recs,
-                    std::vector<SegStage>& stages, std::vector<SegLevel>& levels) -> bool {
+                    std::vector<SegStage>& stages, std::vector<SegLevel>& levels,
+                    std::vector<unsigned char>& imap) -> bool {
       const int n = (int)(j - i);
       const int gi_last = (*list)[j - 1].group;
       std::map<int, int> producer;  // tid -> step index in the run
@@ -1750,6 +1779,7 @@ static bool build_cache(qt_net* net, EngineCache& c, std::string& err) {
       recs.clear();
       stages.clear();
       levels.clear();
+      imap.clear();
       // inputs produced before the run: staged at the start, kept for the whole run
       int cum = 0;
       for (int q = 0; q < n; ++q) {
@@ -1809,7 +1839,9 @@ static bool build_cache(qt_net* net, EngineCache& c, std::string& err) {
             }
             k.out_global = (ot.last_use > gi_last || k.out_soff < 0) ? 1 : 0;
             k.item0 = items;
-            items += (int)std::max(1ll, (1ll << (k.u - 1)) / 32);
+            const int nit = (int)std::max(1ll, (1ll << (k.u - 1)) / 32);
+            items += nit;
+            imap.insert(imap.end(), (size_t)nit, (unsigned char)recs.size());
             recs.push_back(k);
             (pass == 0 ? sl.nwarp : sl.nblock)++;
             d.bytes += (*list)[i + q].bytes;
@@ -1819,10 +1851,11 @@ static bool build_cache(qt_net* net, EngineCache& c, std::string& err) {
         levels.push_back(sl);
       }
       d.seg_count = n;
+      d.seg_items = (int)imap.size();
       d.stage_count = (int)stages.size();
       d.level_count = nlev;
       d.seg_arena = peak;
-      return true;
+      return seg_smem<R>(S, d) <= (size_t)SEG_SMEM_MAX;
     };
     for (size_t i = 0; i < list->size();) {
       size_t j = i;
@@ -1833,10 +1866,11 @@ static bool build_cache(qt_net* net, EngineCache& c, std::string& err) {
       std::vector<KStep> recs;
       std::vector<SegStage> stages;
       std::vector<SegLevel> levels;
+      std::vector<unsigned char> imap;
       bool ok = false;
       if (net->segments && S.n_shared_meta + S.n_slice_meta_tensors <= SEG_META_MAX)
         for (; j - i >= 2; --j)
-          if (plan(i, j, d, recs, stages, levels)) {
+          if (plan(i, j, d, recs, stages, levels, imap)) {
             ok = true;
             break;
           }
@@ -1856,6 +1890,7 @@ static bool build_cache(qt_net* net, EngineCache& c, std::string& err) {
       append(recs.data(), recs.size() * sizeof(KStep));
       append(stages.data(), stages.size() * sizeof(SegStage));
       append(levels.data(), levels.size() * sizeof(SegLevel));
+      append(imap.data(), imap.size());
       c.segtab.resize((c.segtab.size() + 15) & ~(size_t)15, 0);
       d.g_last = (*list)[j - 1].group;
       merged.push_back(d);
@@ -1907,7 +1942,8 @@ static void launch_desc(qt_net* net, const LaunchDesc& d0, long long nslices, lo
     cfg.attrs = at;
     cfg.numAttrs = ncl > 1 ? 1 : 0;
     cudaLaunchKernelEx(&cfg, k_segment<R>, tab, d0.seg_count, stab, d0.stage_count, ltab,
-                       d0.level_count, data, meta, slice_first, nsh, nst, (long long)S.batch);
+                       d0.level_count, d0.seg_items, data, meta, slice_first, nsh, nst,
+                       (long long)S.batch);
     if (net->prof) prof_end(net, s, pr);
     return;
   }
