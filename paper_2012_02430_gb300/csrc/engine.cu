@@ -2307,6 +2307,19 @@ static bool launch_plan_impl(qt_net* net, std::string& out, std::string& err) {
     spans(rd[x]);
     o << ",\"writes\":";
     spans(wr[x]);
+    if (d.kind != 5 && d.group >= 0 && net->sched.groups[d.group].gemm) {
+      // a group with a GEMM form (whichever kernel runs it): summed indices, the U-bit
+      // masks of each index class, the two large operands' index masks, the tiled
+      // kernels' tile bits and staying side
+      GemmArgs ga;
+      fill_gemm(net->sched, net->sched.groups[d.group], d.k.nslices, ga);
+      o << ",\"gemm\":{\"step\":" << net->sched.groups[d.group].first << ",\"nsum\":" << ga.nsum << ",\"mK\":" << ga.mK << ",\"mM\":" << ga.mM
+        << ",\"mN\":" << ga.mN << ",\"mBt\":" << ga.mBt << ",\"mSA\":" << ga.mSA
+        << ",\"mSB\":" << ga.mSB << ",\"umA\":" << (ga.gA >= 0 ? ga.op[ga.gA].umask : 0u)
+        << ",\"umB\":" << (ga.gB >= 0 ? ga.op[ga.gB].umask : 0u) << ",\"tb\":" << ga.tb
+        << ",\"stay\":" << ga.stay << ",\"fold_a\":" << ga.fold_a << ",\"fold_b\":"
+        << ga.fold_b << "}";
+    }
     if (d.kind == 5) {
       // the segment's dependency levels (warp steps, block steps) and per step its
       // operand count, union indices and summed indices

@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(256, 4) k_gemm_tile(const GemmArgs a, int u, f
 __host__ __device__ constexpr int stream_rows(int nsum) { return nsum <= 1 ? 4 : (nsum == 2 ? 2 : 1); }
 
 template <int NSUM>
-__global__ void __launch_bounds__(256) k_gemm_stream(const GemmArgs a, float* data, GMeta* meta) {
+__global__ void __launch_bounds__(256, NSUM <= 3 ? 4 : 2) k_gemm_stream(const GemmArgs a, float* data, GMeta* meta) {
   constexpr int K = 1 << NSUM, kStreamRows = stream_rows(NSUM);
   extern __shared__ float4 stm[];
   __shared__ PdepLut Lg;               // pdep over G's output indices
@@ -701,12 +701,38 @@ __global__ void __launch_bounds__(256) k_gemm_stream(const GemmArgs a, float* da
       mx = 0.f;
       __syncthreads();  // the tables are built; the last slice's S' is no longer read
       const unsigned long long sid = (unsigned long long)(a.slice_first + i);
-      const long long sb = fold_s ? scr_s + i * a.scratch_stride : op_slice_base(OS, i, sid);
-      const float ss = fold_s ? 1.f
-          : pow2_neg_g(scale_exp_g(meta[OS.meta + (OS.meta_per_slice ? i : 0)].maxabs));
-      for (int e = threadIdx.x; e < (1 << nS); e += blockDim.x) {
-        const float2 v = d2[sb + e];
-        sS[e] = make_float2(v.x * ss, v.y * ss);
+      if (fold_s && a.fold_in) {
+        // S' = the product of the S side's operands, each times its scale, in operand
+        // order (the arithmetic of k_gemm_fold, so the same values); a small S only
+        // (its rebuild, once per slice, stalls the block)
+        const int sside = gside ? 0 : 1;
+        const unsigned int xall = (unsigned int)((1ull << nS) - 1ull);
+        for (int e = threadIdx.x; e < (1 << nS); e += blockDim.x) {
+          float pr = 1.f, pi = 0.f;
+#pragma unroll 1
+          for (int j = 0; j < a.m; ++j) {
+            const GOp& o = a.op[j];
+            if (o.side != sside) continue;
+            const float fs =
+                pow2_neg_g(scale_exp_g(meta[o.meta + (o.meta_per_slice ? i : 0)].maxabs));
+            const unsigned int idx = o.xmask == xall ? (unsigned int)e : pext32g((unsigned int)e, o.xmask);
+            const float2 v = d2[op_slice_base(o, i, sid) + idx];
+            const float vr = v.x * fs, vi = v.y * fs;
+            const float nr = pr * vr - pi * vi, ni = pr * vi + pi * vr;
+            pr = nr;
+            pi = ni;
+          }
+          sS[e] = make_float2(pr, pi);
+        }
+      } else {
+        // S' from the fold kernel's scratch, or S itself times its scale
+        const long long sb = fold_s ? scr_s + i * a.scratch_stride : op_slice_base(OS, i, sid);
+        const float ss = fold_s ? 1.f
+            : pow2_neg_g(scale_exp_g(meta[OS.meta + (OS.meta_per_slice ? i : 0)].maxabs));
+        for (int e = threadIdx.x; e < (1 << nS); e += blockDim.x) {
+          const float2 v = d2[sb + e];
+          sS[e] = make_float2(v.x * ss, v.y * ss);
+        }
       }
       sc = pow2_neg_g(scale_exp_g(meta[OG.meta + (OG.meta_per_slice ? i : 0)].maxabs));
       if ((base & (rows - 1)) == 0 && threadIdx.x == 0) write_meta_e(a, meta, i);
@@ -2311,7 +2337,12 @@ int gemm_launch(const GemmArgs& a, int mode_in, float* data, GMeta* meta, cudaSt
   if (mode == GEMM_TILE && a.use_stream) {
     int n = 0;
     const int gs = gemm_tile_stay(a);
-    if (gs ? a.fold_a : a.fold_b) {  // fold the small side into its scratch
+    // a small side of at most 256 elements is folded inside the kernel (one element per
+    // thread); a larger one by the fold kernel into its scratch first
+    GemmArgs as = a;
+    const int s_bits = __builtin_popcount(a.op[gs ? a.gA : a.gB].umask);
+    as.fold_in = (gs ? a.fold_a : a.fold_b) && s_bits <= 8;
+    if ((gs ? a.fold_a : a.fold_b) && !as.fold_in) {
       const int side = gs ? 0 : 1;
       const long long work = a.nslices << __builtin_popcount(a.op[side ? a.gB : a.gA].umask);
       const long long g = std::min<long long>((work + 255) / 256, (long long)sms * 16);
@@ -2334,7 +2365,7 @@ int gemm_launch(const GemmArgs& a, int mode_in, float* data, GMeta* meta, cudaSt
     const unsigned grid = (unsigned)std::max<long long>(
         1, std::min<long long>(total / (256 * stream_rows(a.nsum)),
                                (long long)sms * std::max(1, per_sm)));
-    fn<<<grid, 256, smem, s>>>(a, data, meta);
+    fn<<<grid, 256, smem, s>>>(as, data, meta);
     return n + 1;
   }
   if (mode == GEMM_TILE) {

@@ -32,7 +32,8 @@ struct GemmArgs {
   unsigned int mK, mSA, mSB, mM, mN, mBt;
   long long nslices, slice_first;
   long long out_base, out_slice_stride, out_meta;
-  int out_meta_per_slice, pad;
+  int out_meta_per_slice;
+  int fold_in;              // streaming GEMM: the small side is folded inside the kernel
   long long scratch_a, scratch_b, scratch_stride;  // elements (complex64 units)
   // GEMM_TILE: big operands, output indices per tile, which sides are folded
   int gA, gB, tb, fold_a, fold_b;
