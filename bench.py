@@ -35,20 +35,25 @@ L2_FLUSH_BYTES = 512 << 20
 PRECISIONS = {"fp32": 0, "tf32": 1, "bf16": 2, "3xtf32": 3, "fp64": 4}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 
-# DRAM bytes (read + write) per launch of each kernel class on this workload, from one ncu
-# capture of the profiled pass (GB300, 1 GPU):
+# DRAM bytes (read + write) of the large launches of one amplitude pass of this workload,
+# per step (a step's fold kernel included), from one ncu capture of the profiled pass
+# (GB300, 1 GPU; `python bench.py --profile-pass` exited 0 first):
 #   ncu --nvtx --nvtx-include "qt_pass/" --clock-control none --csv --log-file dram.csv
 #       --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
 #       python bench.py --profile-pass
-# averaged over the class's launches in the pass (its fold launches included). The roofline
-# line reports it as `traffic` when that class dominates, and only while the kernel sources
-# hash to CLASS_DRAM_SOURCES (the sources the capture ran); after any change it is null.
-CLASS_DRAM_BYTES = {
-    "gemm_stream (k_gemm_fold + k_gemm_stream)": None,  # steps 120, 121, 131
-    "gemm_tile (k_gemm_fold + k_gemm_tma)": None,       # steps 117, 127
-    "k_tri_tma": None,                                  # step 132
+# Each entry holds the kernel class the capture ran for that step: the roofline line's
+# `traffic` averages the dominant class's steps that this run also gave to that class,
+# and lists them with their algorithmic bytes. Used only while the kernel sources hash to
+# STEP_DRAM_SOURCES (the sources the capture ran); after any change it is null.
+STEP_DRAM_BYTES = {
+    117: (4, 269.8e6),  # k_gemm_fold + k_gemm_tma<3,1>: read 61.9 MB, write 207.9 MB
+    120: (7, 481.5e6),  # k_gemm_stream<1> (small side folded in the kernel): 268.5 / 213.0
+    121: (7, 485.0e6),  # k_gemm_fold + k_gemm_stream<3>: 268.6 / 216.4
+    127: (4, 89.2e6),   # k_gemm_fold + k_gemm_tma<4,1>: 17.3 / 71.9
+    131: (7, 212.4e6),  # k_gemm_stream<1>: 134.3 / 78.1
+    132: (6, 440.5e6),  # k_tri_fold + k_tri_tma<4,2>: 413.4 / 27.1
 }
-CLASS_DRAM_SOURCES = None
+STEP_DRAM_SOURCES = "3fe99dc38595c04a"
 KERNEL_SOURCES = ("engine.cu", "gemm.cu", "umma.cu", "gemm.h", "qt_internal.h")
 
 
@@ -79,6 +84,9 @@ def parse():
     ap.add_argument("--profile-pass", action="store_true",
                     help="for ncu: plan, autotune and warm the amplitude path, then run one pass "
                          "inside the NVTX range 'qt_pass' (direct launches) and print its launch list")
+    ap.add_argument("--tcgen05", type=int, default=0, choices=[0, 1, 3],
+                    help="with --profile-pass: QT_OPT_TCGEN05 (1: the tcgen05 GEMM kernel on every "
+                         "GEMM-form launch it applies to, in the tf32 / 3xtf32 precisions)")
     return ap.parse_args()
 
 
@@ -381,12 +389,14 @@ def ours(args):
     recs = Q.qt_profile_read(net.handle)
     Q.qt_profile(net.handle, 0)
     by_kind = {}
+    step_bytes = {}  # (kind, step) -> algorithmic bytes of one launch
     for r in recs:
         d = by_kind.setdefault(r["kernel"], {"ms": 0.0, "bytes": 0, "flops": 0, "n": 0})
         d["ms"] += r["ms"]
         d["bytes"] += r["bytes"]
         d["flops"] += r["flops"]
         d["n"] += 1
+        step_bytes[(r["kernel"], r["step"])] = r["bytes"]
     kind_names = {0: "k_bucket_flat", 1: "k_bucket_tiled", 2: "k_finalize+k_reduce",
                   3: "gemm_form (k_gemm_pack x2 + k_gemm_tc/simt)",
                   4: "gemm_tile (k_gemm_fold + k_gemm_tma)", 5: "k_segment",
@@ -414,10 +424,18 @@ def ours(args):
                     "peak_source": f"{peak_src} hbm_gbs"}
     per_launch_bytes = d["bytes"] / max(1, d["n"])
     src_hash = kernel_sources_hash()
-    traffic = CLASS_DRAM_BYTES.get(kind_names[dom]) if src_hash == CLASS_DRAM_SOURCES else None
+    # measured DRAM bytes of the dominant class's steps that the capture also ran in it
+    covered = sorted(stp for (kk, stp) in step_bytes
+                     if kk == dom and STEP_DRAM_BYTES.get(stp, (None,))[0] == dom)
+    traffic = traffic_alg = None
+    if src_hash == STEP_DRAM_SOURCES and covered:
+        traffic = sum(STEP_DRAM_BYTES[stp][1] for stp in covered) / len(covered)
+        traffic_alg = sum(step_bytes[(dom, stp)] for stp in covered) / len(covered)
     roofline.update({"traffic": traffic,
                      "traffic_unit": "bytes per launch (ncu dram read + write)",
-                     "traffic_sources": {"measured_on": CLASS_DRAM_SOURCES, "now": src_hash},
+                     "traffic_steps": covered if traffic is not None else [],
+                     "algorithmic_bytes_per_launch_of_traffic_steps": traffic_alg,
+                     "traffic_sources": {"measured_on": STEP_DRAM_SOURCES, "now": src_hash},
                      "algorithmic_bytes_per_launch": per_launch_bytes,
                      "launches": d["n"], "flop_per_byte": intensity,
                      "ridge_flop_per_byte": ridge,
@@ -956,6 +974,7 @@ def profile_pass(args):
     net.order(Q.QT_GREEDY_MINFILL)
     k, _ = net.slice(WORKLOAD["width_limit"], WORKLOAD["max_vars"], WORKLOAD["r"])
     Q.qt_set_option(net.handle, Q.QT_OPT_GRAPHS, 0)
+    Q.qt_set_option(net.handle, Q.QT_OPT_TCGEN05, args.tcgen05)
     net.prepare(prec, batch=1 << k)
     net.upload()
     net.autotune()
