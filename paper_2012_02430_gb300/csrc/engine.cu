@@ -193,8 +193,11 @@ __device__ __forceinline__ void store_out(R* data, long long off, R re, R im) {
 // Level-0 operands multiply both values of the pair, the pair is summed, then
 // for level l = 1 .. nsum-1 the level-l operands multiply each lane's partial
 // sum before the lanes that differ in U bit l are added (a shuffle).
-template <typename R>
+// MO: operands the kernel is compiled for (st.m <= MO); every operand's metadata and
+// values are loaded first, all loads in flight at once, then multiplied in operand order
+template <typename R, int MO>
 __global__ void __launch_bounds__(256) k_bucket_flat(const KStep st, R* data, Meta* meta) {
+  using C2 = typename CT<R>::c2;
   const long long npairs = 1ll << (st.u - 1);
   const long long total = st.nslices * npairs;
   const int lane = threadIdx.x & 31;
@@ -208,34 +211,46 @@ __global__ void __launch_bounds__(256) k_bucket_flat(const KStep st, R* data, Me
     const unsigned long long sid = (unsigned long long)(st.slice_first + i);
     R p0r = 1, p0i = 0, p1r = 1, p1i = 0;
     int Eout = 0;
+    R vr0[MO], vi0[MO], vr1[MO], vi1[MO];
+    unsigned int mxb[MO];
     if (active) {
-      for (int j = 0; j < st.m; ++j) {
+#pragma unroll
+      for (int j = 0; j < MO; ++j) {
+        if (j >= st.m) break;
         const KOp& o = st.op[j];
         const Meta mt = meta[o.meta + (o.meta_per_slice ? i : 0)];
-        const int s = scale_exp(mt.maxabs);
-        Eout += mt.E + s;
-        if (o.level != 0) continue;
+        mxb[j] = mt.maxabs;
+        Eout += mt.E;
         long long off = o.base + i * o.slice_stride + (long long)pext32r((unsigned int)I, o.umask);
         if (o.smask) off += (long long)(pext64(sid, o.smask) << o.sshift);
+        if (o.level == 0) {
+          load_pair<R>(data, off, o.umask & 1u, vr0[j], vi0[j], vr1[j], vi1[j]);
+        } else {
+          const C2 v = __ldg(reinterpret_cast<const C2*>(data + 2 * off));
+          vr0[j] = v.x;
+          vi0[j] = v.y;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < MO; ++j) {
+        if (j >= st.m) break;
+        const int s = scale_exp(mxb[j]);
+        Eout += s;
+        if (st.op[j].level != 0) continue;
         const R sc = pow2_neg<R>(s);
-        R r0, i0, r1, i1;
-        load_pair<R>(data, off, o.umask & 1u, r0, i0, r1, i1);
-        cmul<R>(p0r, p0i, r0 * sc, i0 * sc);
-        cmul<R>(p1r, p1i, r1 * sc, i1 * sc);
+        cmul<R>(p0r, p0i, vr0[j] * sc, vi0[j] * sc);
+        cmul<R>(p1r, p1i, vr1[j] * sc, vi1[j] * sc);
       }
     }
     R sr = active ? p0r + p1r : R(0), si = active ? p0i + p1i : R(0);
     for (int l = 1; l < st.nsum; ++l) {
       if (active) {
-        for (int j = 0; j < st.m; ++j) {
-          const KOp& o = st.op[j];
-          if (o.level != l) continue;
-          long long off = o.base + i * o.slice_stride + (long long)pext32r((unsigned int)I, o.umask);
-          if (o.smask) off += (long long)(pext64(sid, o.smask) << o.sshift);
-          const R sc = pow2_neg<R>(scale_exp(meta[o.meta + (o.meta_per_slice ? i : 0)].maxabs));
-          using C2 = typename CT<R>::c2;
-          const C2 a = __ldg(reinterpret_cast<const C2*>(data + 2 * off));
-          cmul<R>(sr, si, a.x * sc, a.y * sc);
+#pragma unroll
+        for (int j = 0; j < MO; ++j) {
+          if (j >= st.m) break;
+          if (st.op[j].level != l) continue;
+          const R sc = pow2_neg<R>(scale_exp(mxb[j]));
+          cmul<R>(sr, si, vr0[j] * sc, vi0[j] * sc);
         }
       }
       sr += __shfl_xor_sync(0xffffffffu, sr, 1 << (l - 1));
@@ -1999,7 +2014,9 @@ static void launch_desc(qt_net* net, const LaunchDesc& d0, long long nslices, lo
   if (d0.kind == 1) {
     tiled_fn<R>(d0.variant, k.ms)<<<grid, TILE_THREADS, 0, s>>>(k, data, meta);
   } else {
-    k_bucket_flat<R><<<grid, 256, 0, s>>>(k, data, meta);
+    if (k.m <= 4) k_bucket_flat<R, 4><<<grid, 256, 0, s>>>(k, data, meta);
+    else if (k.m <= 8) k_bucket_flat<R, 8><<<grid, 256, 0, s>>>(k, data, meta);
+    else k_bucket_flat<R, MAXOP><<<grid, 256, 0, s>>>(k, data, meta);
   }
   if (net->prof) prof_end(net, s, pr);
 }
