@@ -484,6 +484,10 @@ def ours(args):
     from paper_2012_02430_gb300.inputs import random_angles
     e2e_steps = max(3, min(args.steps, 10))
     gstage = st.get("workspace_bytes", 0)
+    for i in range(max(3, args.warmup)):  # untimed: the first call re-captures the graph
+        g2, b2 = random_angles(WORKLOAD["p"], 4000 + i)
+        Q.qt_set_angles(net.handle, g2, b2)
+        net.contract(prec)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(e2e_steps):

@@ -23,6 +23,10 @@ qt_status download_result(const double* d_out, double* host, int64_t n_doubles, 
                           std::string& err);
 qt_status read_status(const qt_net* net, const void* ws, void* stream, int* status,
                       std::string& err);
+// the result and the status word, copied back with one stream synchronisation
+qt_status download_result_status(const qt_net* net, const void* ws, const double* d_out,
+                                 double* host, int64_t n_doubles, int* status, void* stream,
+                                 std::string& err);
 void prof_clear(qt_net* net);
 qt_status autotune(qt_net* net, void* ws, void* stream, std::string& report, std::string& err);
 qt_status prof_read(qt_net* net, std::string& out, std::string& err);
@@ -448,10 +452,9 @@ static qt_status contract_impl(qt_net* net, int32_t precision, void* workspace,
   double* d_out = reinterpret_cast<double*>((char*)workspace + net->sched.off_acc + 16 * A);
   s = qt::run(net, 0, net->sched.nslices, workspace, stream, d_out, err);
   if (s != QT_OK) return fail(s, std::string(who) + ": " + err);
-  s = qt::download_result(d_out, host_out, 2 * A, stream, err);
-  if (s != QT_OK) return fail(s, std::string(who) + ": " + err);
+  // the amplitudes and the status word read back together, one stream synchronisation
   int status = 0;
-  s = qt::read_status(net, workspace, stream, &status, err);
+  s = qt::download_result_status(net, workspace, d_out, host_out, 2 * A, &status, stream, err);
   if (s != QT_OK) return fail(s, std::string(who) + ": " + err);
   if (status) return fail(QT_ETIMEOUT, std::string(who) + ": a bounded device wait gave up");
   return ok();

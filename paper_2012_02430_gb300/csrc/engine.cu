@@ -2443,6 +2443,21 @@ qt_status sweep_run(qt_net* net, void* ws, void* stream, int n_sets, const void*
   return QT_OK;
 }
 
+qt_status download_result_status(const qt_net* net, const void* ws, const double* d_out,
+                                 double* host, int64_t n_doubles, int* status, void* stream,
+                                 std::string& err) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!cuda_ok(cudaMemcpyAsync(host, d_out, (size_t)n_doubles * sizeof(double),
+                               cudaMemcpyDeviceToHost, s),
+               "download result", err) ||
+      !cuda_ok(cudaMemcpyAsync(status, (const char*)ws + net->sched.off_err, sizeof(int),
+                               cudaMemcpyDeviceToHost, s),
+               "read status", err) ||
+      !cuda_ok(cudaStreamSynchronize(s), "stream synchronize", err))
+    return QT_ECUDA;
+  return QT_OK;
+}
+
 qt_status download_result(const double* d_out, double* host, int64_t n_doubles, void* stream,
                           std::string& err) {
   cudaStream_t s = (cudaStream_t)stream;
