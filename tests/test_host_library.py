@@ -590,6 +590,37 @@ def test_launch_plan_orders_every_conflict(qt, case):
         assert len({d["stream"] for d in launches}) > 1
 
 
+@pytest.mark.parametrize("case", [(80, 2, 1002, 26, 20, 4), (60, 2, 18, 23, 6, 4),
+                                  (50, 3, 1003, 28, 20, 2), (24, 3, 15, 0, 0, 4)])
+def test_segment_work_items(qt, case):
+    """Segment launches (host planning, no GPU): every step of a level is cut into work
+    items of 32 value pairs, max(1, 2^(u-1) / 32) of them, the level's item count is their
+    sum, the levels hold every step once, no step sums more than 6 indices (the shuffle
+    reduction stays inside a warp) or exceeds the segment's union limit, and the largest
+    cluster the device co-schedules is 1 without a GPU."""
+    n, p, seed, wl, mv, batch = case
+    from paper_2012_02430_gb300.inputs import qaoa_instance
+    edges, g, b, z = qaoa_instance(n, p, seed)
+    net = qt.Network(edges, n, p, g, b, z)
+    net.order(0)
+    if wl:
+        net.slice(wl, mv, 1)
+    qt.qt_prepare(net.handle, 0, batch)
+    segs = [L["segment"] for L in qt.qt_launch_plan(net.handle)["launches"] if "segment" in L]
+    assert segs
+    for sg in segs:
+        steps, levels = sg["steps"], sg["levels"]
+        assert sum(nw + nb for nw, nb, _ in levels) == len(steps) >= 2
+        first = 0
+        for nw, nb, items in levels:
+            lv = steps[first:first + nw + nb]
+            assert all(u <= 6 for _, u, _ in lv[:nw])  # warp steps: at most 32 value pairs
+            assert items == sum(max(1, (1 << (u - 1)) // 32) for _, u, _ in lv)
+            first += nw + nb
+        assert all(1 <= m <= 12 and 1 <= nsum <= 6 and nsum <= u <= 12 for m, u, nsum in steps)
+        assert sg["arena"] > 0 and sg["cluster_max"] in (1, 2, 4, 8)
+
+
 UMMA_PLAN_CASES = [(30, 3, 5, -4), (44, 2, 3, -2), (60, 2, 19, -4), (50, 2, 7, -2),
                    (48, 2, 5, 0), (44, 3, 15, -2), (50, 2, 22, -4), (24, 3, 21, 0),
                    (80, 2, 1002, 26 - 35)]
