@@ -46,14 +46,14 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max
 # and lists them with their algorithmic bytes. Used only while the kernel sources hash to
 # STEP_DRAM_SOURCES (the sources the capture ran); after any change it is null.
 STEP_DRAM_BYTES = {
-    117: (4, 269.8e6),  # k_gemm_fold + k_gemm_tma<3,1>: read 61.9 MB, write 207.9 MB
-    120: (7, 481.5e6),  # k_gemm_stream<1> (small side folded in the kernel): 268.5 / 213.0
-    121: (7, 485.0e6),  # k_gemm_fold + k_gemm_stream<3>: 268.6 / 216.4
-    127: (4, 89.2e6),   # k_gemm_fold + k_gemm_tma<4,1>: 17.3 / 71.9
-    131: (7, 212.4e6),  # k_gemm_stream<1>: 134.3 / 78.1
-    132: (6, 440.5e6),  # k_tri_fold + k_tri_tma<4,2>: 413.4 / 27.1
+    117: (4, 269.1e6),  # k_gemm_fold + k_gemm_tma<3,1>: read 61.5 MB, write 207.6 MB
+    120: (7, 481.4e6),  # k_gemm_stream<1> (small side folded in the kernel): 268.5 / 212.9
+    121: (7, 485.4e6),  # k_gemm_fold + k_gemm_stream<3>: 268.6 / 216.8
+    127: (4, 88.9e6),   # k_gemm_fold + k_gemm_tma<4,1>: 17.2 / 71.7
+    131: (7, 212.9e6),  # k_gemm_stream<1>: 134.3 / 78.6
+    132: (6, 440.4e6),  # k_tri_fold + k_tri_tma<4,2>: 413.4 / 27.0
 }
-STEP_DRAM_SOURCES = "3fe99dc38595c04a"
+STEP_DRAM_SOURCES = "46969563cb054597"
 KERNEL_SOURCES = ("engine.cu", "gemm.cu", "umma.cu", "gemm.h", "qt_internal.h")
 
 
