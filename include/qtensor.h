@@ -405,7 +405,9 @@ void qt_mlp_free(qt_mlp* mlp);
  *                  (cp.async.bulk.tensor over 2-D tensor maps of the workspace,
  *                  completing on shared-memory mbarriers; bounded waits raise
  *                  QT_ETIMEOUT in qt_contract), when every block starts on a
- *                  whole row; 0: cp.async copies by every thread. 2, 3, 4: as
+ *                  whole row (the tiled GEMM: rows of up to 32 summed values;
+ *                  rows of 64 use cp.async copies unless qt_autotune finds the
+ *                  tensor copies faster for the launch); 0: cp.async copies by every thread. 2, 3, 4: as
  *                  1 with the tiled GEMM's register block fixed instead of
  *                  chosen by shared-memory wavefronts: 2 x 2 (2), 2 x 4 where
  *                  a second B-only index exists (3), 4 x 2 where a second
@@ -420,7 +422,9 @@ void qt_mlp_free(qt_mlp* mlp);
  *                  shape allows it run on the tcgen05 tensor cores (operand rows
  *                  gathered by TMA tensor copies, split into TF32 planes in
  *                  shared memory, products accumulated in tensor memory; the
- *                  complex product as one real product of doubled size).
+ *                  complex product as one real product of doubled size; rows
+ *                  too long for shared memory are taken in chunks of the summed
+ *                  values that accumulate in the same tensor-memory columns).
  *                  0 (default): that kernel is the launch's default and one of
  *                  the autotuner's candidates beside the FP32 kernels (which are
  *                  at least as accurate); other GEMM-form launches run the FP32
@@ -431,8 +435,10 @@ void qt_mlp_free(qt_mlp* mlp);
  *                  kernels as in QT_BF16 mode. 3: as 1, with tiles that instead
  *                  cover the longest run of lowest output indices (up to 16
  *                  batch values side by side, contiguous output runs, narrower
- *                  products). Other values: QT_EINVAL. Discards the prepared
- *                  schedule.
+ *                  products). 4: as 1, with every work unit carrying at most 4
+ *                  of the summed values (the chunked accumulation, which longer
+ *                  rows need to fit shared memory, on every launch). Other
+ *                  values: QT_EINVAL. Discards the prepared schedule.
  *   QT_OPT_SCALED  1: the tiled bucket kernel multiplies every operand by its
  *                  exact power-of-two scale 2^-s (result exponent sum of E_j + s_j)
  *                  in every slice, the path it otherwise takes only for a slice

@@ -746,7 +746,7 @@ qt_status qt_set_option(qt_net* net, int32_t option, int64_t value) {
       net->sched = qt::Schedule();  // prepare again
       break;
     case QT_OPT_TCGEN05:
-      if (value < 0 || value > 3) return fail(QT_EINVAL, "qt_set_option: QT_OPT_TCGEN05 takes 0..3");
+      if (value < 0 || value > 4) return fail(QT_EINVAL, "qt_set_option: QT_OPT_TCGEN05 takes 0..4");
       net->tcgen05 = (int)value;
       net->sched = qt::Schedule();  // prepare again
       break;

@@ -1225,6 +1225,7 @@ struct LaunchDesc {
   long long seg_arena = 0;           // kind 5: shared-arena elements per block
   int seg_cl_max = 1;                // kind 5: largest cluster the device co-schedules (1..8)
   int seg_items = 0;                 // kind 5: work items over all levels (item-map bytes)
+  bool alt_staging = false;          // kind 4: the tiled GEMM's other staging (VARIANT_GEMM_ALT)
   int g_last = -1;                   // last schedule group the launch covers (kind 5: a run)
 };
 
@@ -1233,7 +1234,11 @@ constexpr int VARIANT_TRI = 4;
 constexpr int VARIANT_FLAT = 5;  // the flat kernel for a launch the tiled kernel takes
 constexpr int VARIANT_STREAM = 6;  // the GEMM form's streaming kernel
 constexpr int VARIANT_UMMA = 7;    // the GEMM form on the tcgen05 tensor cores
-constexpr int N_ALL_VARIANTS = 8;
+// the FP32 tiled GEMM with its other staging: by default it stages rows of up to 32
+// summed values with tensor copies and rows of 64 with cp.async (the tensor-copy ring of
+// long rows is 2x slower on some launches and 1.5x faster on others); this variant swaps
+constexpr int VARIANT_GEMM_ALT = 8;
+constexpr int N_ALL_VARIANTS = 9;
 
 static bool tc_precision(int p) { return p == QT_TF32 || p == QT_BF16 || p == QT_3XTF32; }
 
@@ -1316,6 +1321,7 @@ static void fill_gemm(const Schedule& S, const SGroup& g, long long nslices, Gem
   a.stay = gemm_tile_stay(a);
   a.ws_elems = (long long)(S.total_bytes / 8);
   a.umma_shape = S.tcgen05 == 3 ? 0 : 1;  // wide products unless the long-run tiles are asked for
+  a.umma_kc_max = S.tcgen05 == 4 ? 2 : 0;  // chunks of 4 summed values, to check the chunking
   gemm_tile_regs(a, S.tma_block);
 }
 
@@ -1544,8 +1550,9 @@ static bool make_desc(const Schedule& S, int gi, long long nslices, LaunchDesc& 
     }
     variant = VARIANT_GEMM;  // the streaming kernel does not apply: the tiled GEMM
   }
-  if (variant == VARIANT_GEMM && st.gemm && sizeof(R) == 4) {
+  if ((variant == VARIANT_GEMM || variant == VARIANT_GEMM_ALT) && st.gemm && sizeof(R) == 4) {
     d.kind = 3;
+    d.alt_staging = variant == VARIANT_GEMM_ALT;
     d.gemm_mode = gemm_mode_for(S, st);
     fill_gemm(S, st, nslices, d.ga);
     if (d.gemm_mode == GEMM_SIMT && d.ga.tb > 0) {
@@ -2000,7 +2007,8 @@ static void launch_desc(qt_net* net, const LaunchDesc& d0, long long nslices, lo
     ga.nslices = nslices;
     ga.slice_first = slice_first;
     ga.err = reinterpret_cast<int*>(base + S.off_err);
-    ga.use_tma = net->tma ? 1 : 0;
+    // default staging: tensor copies for rows of up to 32 summed values
+    ga.use_tma = (net->tma && ((ga.nsum <= 5) != d0.alt_staging)) ? 1 : 0;
     bool tma = false;
     net->launches += gemm_launch(ga, d0.gemm_mode, reinterpret_cast<float*>(base),
                                  reinterpret_cast<GMeta*>(meta), s, num_sms(), &tma);
@@ -2119,7 +2127,7 @@ static qt_status autotune_impl(qt_net* net, char* base, cudaStream_t s, std::str
       const bool can_umma = grp.gemm && sizeof(R) == 4 && umma_applies(S, grp, d.k.nslices);
       if (d.kind == 0 || d.kind == 5 ||
           ((d.kind == 3 || d.kind == 4) && (legacy_tc(S) || S.force_gemm)) ||
-          (d.kind == 6 && S.force_tri) || (can_umma && (S.tcgen05 == 1 || S.tcgen05 == 3))) {
+          (d.kind == 6 && S.force_tri) || (can_umma && (S.tcgen05 == 1 || S.tcgen05 == 3 || S.tcgen05 == 4))) {
         launch_desc<R>(net, d, nb, b0, base, s);
         continue;
       }
@@ -2127,6 +2135,7 @@ static qt_status autotune_impl(qt_net* net, char* base, cudaStream_t s, std::str
       for (int v = 0; v < N_VARIANTS; ++v) cands.push_back(v);
       if (can_umma) cands.push_back(VARIANT_UMMA);
       if (can_gemm) cands.push_back(VARIANT_GEMM);
+      if (can_gemm && net->tma) cands.push_back(VARIANT_GEMM_ALT);
       if (can_gemm) {
         GemmArgs ga;
         fill_gemm(S, grp, d.k.nslices, ga);
@@ -2183,14 +2192,14 @@ static qt_status autotune_impl(qt_net* net, char* base, cudaStream_t s, std::str
         if (kv.second[v] < kv.second[bv]) bv = v;
       std::string e2;
       make_desc<R>(S, d.group, d.k.nslices, d, e2, bv);
-      char buf[200];
+      char buf[256];
       auto half = [](float x) { return x >= 1e29f ? -1.0 : x / 2.0; };
       std::snprintf(buf, sizeof buf,
-                    "%s{\"step\":%d,\"variant\":%d,\"ms\":[%.4f,%.4f,%.4f,%.4f,%.4f,%.4f,%.4f,%.4f]}",
+                    "%s{\"step\":%d,\"variant\":%d,\"ms\":[%.4f,%.4f,%.4f,%.4f,%.4f,%.4f,%.4f,%.4f,%.4f]}",
                     first ? "" : ",", S.groups[d.group].first, bv, half(kv.second[0]),
                     half(kv.second[1]), half(kv.second[2]), half(kv.second[3]),
                     half(kv.second[4]), half(kv.second[5]), half(kv.second[6]),
-                    half(kv.second[7]));
+                    half(kv.second[7]), half(kv.second[8]));
       report += buf;
       first = false;
     }
@@ -2335,7 +2344,17 @@ static bool launch_plan_impl(qt_net* net, std::string& out, std::string& err) {
         << ",\"mSB\":" << ga.mSB << ",\"umA\":" << (ga.gA >= 0 ? ga.op[ga.gA].umask : 0u)
         << ",\"umB\":" << (ga.gB >= 0 ? ga.op[ga.gB].umask : 0u) << ",\"tb\":" << ga.tb
         << ",\"stay\":" << ga.stay << ",\"fold_a\":" << ga.fold_a << ",\"fold_b\":"
-        << ga.fold_b << "}";
+        << ga.fold_b << ",\"scratch\":[" << ga.scratch_a << "," << ga.scratch_b << ","
+        << ga.scratch_stride << "]";
+      // the two large operands' element offsets, slice strides and slice-bit placement
+      for (int side = 0; side < 2; ++side) {
+        const int gi2 = side ? ga.gB : ga.gA;
+        if (gi2 < 0) continue;
+        const GOp& op = ga.op[gi2];
+        o << (side ? ",\"B\":[" : ",\"A\":[") << op.base << "," << op.slice_stride << ","
+          << op.smask << "," << op.sshift << "]";
+      }
+      o << "}";
     }
     if (d.kind == 5) {
       // the segment's dependency levels (warp steps, block steps) and per step its
@@ -2359,7 +2378,7 @@ static bool launch_plan_impl(qt_net* net, std::string& out, std::string& err) {
         umma_plan(d.ga, d.gemm_mode == GEMM_UMMA_TF32 ? 1 : 3, up)) {
       // the tcgen05 tiling: masks over the launch's U bits, sizes, tile order
       o << ",\"umma\":{\"lside\":" << up.lside << ",\"nsum\":" << up.nsum << ",\"cb\":" << up.cb
-        << ",\"gb\":" << up.gb << ",\"passes\":" << up.passes << ",\"sraw\":" << up.sraw
+        << ",\"gb\":" << up.gb << ",\"kc\":" << up.kc << ",\"passes\":" << up.passes << ",\"sraw\":" << up.sraw
         << ",\"splane\":" << up.splane << ",\"tmem_cols\":" << up.tmem_cols
         << ",\"smem\":" << umma_smem(up) << ",\"mlane\":" << up.mlane << ",\"mcol\":" << up.mcol
         << ",\"mgrp\":" << up.mgrp << ",\"mM\":" << d.ga.mM << ",\"mN\":" << d.ga.mN

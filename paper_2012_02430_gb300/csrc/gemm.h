@@ -48,6 +48,7 @@ struct GemmArgs {
   int use_stream;           // GEMM_TILE: the streaming kernel (gemm_stream_ok) instead
   long long ws_elems;       // workspace size (complex): the extent of the tensor maps
   int umma_shape;           // tcgen05 tiles: 0 the longest output runs, 1 the widest products (default)
+  int umma_kc_max;          // tcgen05 work units: at most 2^this summed values (0: as many as fit)
   int* err;                 // device status word: set to 1 when a bounded wait gives up
   GOp op[GEMM_MAXOP];
 };
@@ -89,8 +90,10 @@ int gemm_launch(const GemmArgs& a, int mode, float* data, GMeta* meta, cudaStrea
 // (the MMA's N is twice that: re and im rows) and 2^gb values of batch indices, all
 // chosen by walking the output indices from the lowest so that the tile covers as
 // long a prefix of them as tensor memory allows (contiguous output runs). A work unit
-// is one group value: its lane-side and column-side rows, one TMA box each. Masks are
-// over the launch's U bits.
+// is one group value and one chunk of the summed values (all of them unless the rows do
+// not fit shared memory; the chunks of a group accumulate in the same tensor-memory
+// columns): its lane-side and column-side rows, one TMA box each. Masks are over the
+// launch's U bits.
 struct UmmaPlan {
   int lside;                 // 0: A gives the lanes (M), B the columns; 1: the reverse
   int nsum, cb, gb;          // summed indices; column bits (Nt = 2^cb); group bits (G = 2^gb)
@@ -107,6 +110,7 @@ struct UmmaPlan {
   int rb;                    // contiguous output runs of 2^rb complex inside a chunk
   unsigned int chunk_out;    // the chunk's output bits (the run index takes those above rb)
   int prefix;                // output indices from the lowest that the tile covers
+  int kc;                    // a work unit carries 2^kc of the 2^nsum summed values (kc <= nsum)
 };
 // The launch takes the form (false: it does not; the caller keeps another kernel).
 bool umma_plan(const GemmArgs& a, int passes, UmmaPlan& p);

@@ -462,10 +462,14 @@ bool compile_schedule(const std::vector<Tensor>& net, int n_vars, const SlicePla
   // workspace layout
   const size_t eb = (size_t)S.elem_bytes;
   size_t off = 0;
+  // the tensor regions start on 1024 bytes, so offsets aligned to kArenaAlign elements
+  // inside them are aligned in the workspace too (rows of up to 64 summed values start
+  // on a whole row, as the tensor-copy GEMM kernels need)
+  auto align1024 = [](size_t x) { return (x + 1023) / 1024 * 1024; };
   S.off_gates = off;
-  off = align256(off + (size_t)S.gate_elems * eb);
+  off = align1024(off + (size_t)S.gate_elems * eb);
   S.off_prefix = off;
-  off = align256(off + (size_t)S.prefix_elems * eb);
+  off = align1024(off + (size_t)S.prefix_elems * eb);
   S.off_slices = off;
   off = align256(off + (size_t)S.slice_elems * eb * (size_t)S.batch);
   S.off_meta = off;

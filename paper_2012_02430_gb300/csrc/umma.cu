@@ -142,26 +142,27 @@ __device__ __forceinline__ bool u_mbar_wait(unsigned long long* bar, unsigned in
 
 // one box of a 3- to 5-dimensional tensor map (coordinate 0 in every dimension but the
 // last, the row offset) into shared memory, completing on the mbarrier
-__device__ __forceinline__ void u_box(void* smem, const CUtensorMap* map, int rank, int row,
+// one unit's box: x (floats, a multiple of 4) selects the chunk of the summed values
+__device__ __forceinline__ void u_box(void* smem, const CUtensorMap* map, int rank, int x, int row,
                                       unsigned long long* bar) {
   const unsigned long long m = reinterpret_cast<unsigned long long>(map);
   if (rank == 3)
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %2, %3}], [%4];\n" ::"r"(u_smem(smem)),
-        "l"(m), "r"(0), "r"(row), "r"(u_smem(bar))
+        " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(u_smem(smem)),
+        "l"(m), "r"(x), "r"(0), "r"(row), "r"(u_smem(bar))
         : "memory");
   else if (rank == 4)
     asm volatile(
         "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %2, %2, %3}], [%4];\n" ::"r"(u_smem(smem)),
-        "l"(m), "r"(0), "r"(row), "r"(u_smem(bar))
+        " [%0], [%1, {%2, %3, %3, %4}], [%5];\n" ::"r"(u_smem(smem)),
+        "l"(m), "r"(x), "r"(0), "r"(row), "r"(u_smem(bar))
         : "memory");
   else
     asm volatile(
         "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %2, %2, %2, %3}], [%4];\n" ::"r"(u_smem(smem)),
-        "l"(m), "r"(0), "r"(row), "r"(u_smem(bar))
+        " [%0], [%1, {%2, %3, %3, %3, %4}], [%5];\n" ::"r"(u_smem(smem)),
+        "l"(m), "r"(x), "r"(0), "r"(row), "r"(u_smem(bar))
         : "memory");
 }
 
@@ -305,10 +306,11 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gemm_umma(
   // issuer's last commit on each plane slot (-1: none)
   __shared__ int s_fill_par[kMaxRaw], s_commit_par[kMaxPlane];
 
-  const int nsum = p.nsum, lq = nsum - 1;
-  const int Q = 1 << lq;              // 16-byte chunks per row (2 complex each)
+  const int nsum = p.nsum, kc = p.kc, lq = kc - 1;
+  const int NC = 1 << (nsum - kc);    // chunks of the summed values per group
+  const int Q = 1 << lq;              // 16-byte pieces per row chunk (2 complex each)
   const int Nt = 1 << p.cb, R2 = 2 * Nt;
-  const int rowB = 8 << nsum;         // bytes per row
+  const int rowB = 8 << kc;           // bytes per row chunk
   const int SR = p.sraw, SP = p.splane;
   const GOp& OL = a.op[p.lside ? a.gB : a.gA];
   const GOp& OC = a.op[p.lside ? a.gA : a.gB];
@@ -334,7 +336,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gemm_umma(
   const long long chunk = (ntiles + gridDim.x - 1) / gridDim.x;
   const long long w0 = (long long)blockIdx.x * chunk;
   const long long w1 = min(ntiles, w0 + chunk);
-  const long long nunits = w1 > w0 ? (w1 - w0) * G : 0;
+  const long long nunits = w1 > w0 ? (w1 - w0) * G * NC : 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
@@ -390,9 +392,11 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gemm_umma(
     long long rowL0 = 0, rowC0 = 0;
     for (long long u = 0; u < nunits; ++u) {
       const int slot = (int)(u % SR);
-      const int g = (int)(u & (G - 1));
-      if (g == 0) {
-        const long long w = w0 + (u / G);
+      const long long gu = u / NC;  // unit u: group gu % G of tile gu / G, chunk u % NC
+      const int c = (int)(u % NC);
+      const int g = (int)(gu & (G - 1));
+      if (g == 0 && c == 0) {
+        const long long w = w0 + (gu / G);
         const long long i = w >> p.nrest;
         const unsigned int tp = (unsigned int)(w & (per - 1));
         const unsigned int on = (tp >> lane) & 1u;
@@ -417,8 +421,8 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gemm_umma(
         char* dst = raw + slot * unit_b;
         u_mbar_expect_tx(&s_raw_full[slot], unitL + (unsigned int)Nt * rowB);
         s_fill_par[slot] = (int)((u / SR) & 1);
-        u_box(dst, &mapL, rankL, rl, &s_raw_full[slot]);
-        u_box(dst + unitL, &mapC, rankC, rc, &s_raw_full[slot]);
+        u_box(dst, &mapL, rankL, c << (kc + 1), rl, &s_raw_full[slot]);
+        u_box(dst + unitL, &mapC, rankC, c << (kc + 1), rc, &s_raw_full[slot]);
       }
       __syncwarp();
     }
@@ -486,13 +490,15 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gemm_umma(
     if (lane == 0) {
       const unsigned int idesc = u_idesc_tf32(128, R2);
       const unsigned int lboL = 128 * 16, lboC = (unsigned int)R2 * 16;
-      const int ksteps = (2 << nsum) / 8;  // the doubled K over 8 per tf32 MMA
+      const int ksteps = (2 << kc) / 8;  // the doubled chunk over 8 per tf32 MMA
       for (long long u = 0; u < nunits; ++u) {
         const int ps = (int)(u % SP);
-        const long long j = u / G;
-        const int g = (int)(u & (G - 1)), b = (int)(j & 1);
+        const long long gu = u / NC;
+        const long long j = gu / G;
+        const int c = (int)(u % NC);
+        const int g = (int)(gu & (G - 1)), b = (int)(j & 1);
         bool ok = !s_fail && u_mbar_wait(&s_op_full[ps], (unsigned)((u / SP) & 1), a.err);
-        if (ok && g == 0 && j >= 2)
+        if (ok && g == 0 && c == 0 && j >= 2)
           ok = u_mbar_wait(&s_acc_empty[b], (unsigned)(((j >> 1) - 1) & 1), a.err);
         if (!ok) {
           s_fail = 1;
@@ -502,7 +508,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gemm_umma(
         const unsigned int pL = u_smem(planes + ps * plane_b);
         const unsigned int aLhi = pL, aChi = pL + plL, aLlo = aChi + plC, aClo = aLlo + plL;
         const unsigned int d = tmem + (unsigned int)((b * G + g) * R2);
-        int acc = 0;
+        int acc = c > 0 ? 1 : 0;  // a group's later chunks add to its accumulator
         // (lo, hi), (hi, lo) first: the small terms accumulate before the large one
         for (int pass = (p.passes == 3 ? 0 : 2); pass < 3; ++pass) {
           const unsigned int la = pass == 0 ? aLlo : aLhi;
@@ -515,7 +521,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_gemm_umma(
         }
         u_mma_commit(&s_op_empty[ps]);
         s_commit_par[ps] = (int)((u / SP) & 1);
-        if (g == G - 1) u_mma_commit(&s_acc_full[b]);
+        if (g == G - 1 && c == NC - 1) u_mma_commit(&s_acc_full[b]);
       }
     }
     __syncwarp();
@@ -664,17 +670,19 @@ UEncodeFn u_encode() {
 // dimension per run of row bits (extent 2^len, stride 2^start rows) and a last
 // dimension of single rows (the box's origin row). The box: whole rows, every run,
 // one origin -- the rows of one unit, in the order of their row bits.
-bool u_unit_map(CUtensorMap& m, float* data, long long ws_elems, int nsum, int nrun,
+bool u_unit_map(CUtensorMap& m, float* data, long long ws_elems, int nsum, int kc, int nrun,
                 const int* start, const int* len) {
   UEncodeFn fn = u_encode();
   const long long K = 1ll << nsum;
   const long long rows = ws_elems / K;
-  if (!fn || rows < 1 || rows > 0x7fffffffll || 2 * K > 256 || nrun < 1 || nrun > 3) return false;
+  if (!fn || rows < 1 || rows > 0x7fffffffll || kc < 2 || kc > nsum || (2 << kc) > 256 ||
+      nrun < 1 || nrun > 3)
+    return false;
   const int rank = nrun + 2;
   cuuint64_t dims[5], strides[4];
   cuuint32_t box[5], estr[5];
   dims[0] = (cuuint64_t)(2 * K);
-  box[0] = (cuuint32_t)(2 * K);
+  box[0] = (cuuint32_t)(2 << kc);  // one chunk of the row
   for (int r = 0; r < nrun; ++r) {
     dims[1 + r] = (cuuint64_t)1 << len[r];
     strides[r] = (cuuint64_t)(K * 8) << start[r];
@@ -722,7 +730,7 @@ bool row_runs(unsigned int bits, unsigned int umask, int nsum, int& n, int* star
 
 size_t umma_smem(const UmmaPlan& p) {
   const int G = 1 << p.gb, Nt = 1 << p.cb;
-  const size_t rowB = (size_t)8 << p.nsum;
+  const size_t rowB = (size_t)8 << p.kc;
   const size_t unit = (((size_t)(128 + Nt) * rowB) + 1023) & ~(size_t)1023;
   const size_t plane = (((size_t)(128 + 2 * Nt) * rowB * (p.passes == 3 ? 2 : 1)) + 1023) & ~(size_t)1023;
   const int cw = 1 << p.cwb;
@@ -807,6 +815,20 @@ bool umma_plan(const GemmArgs& a, int passes, UmmaPlan& best) {
     // plane slots (converters ahead of the tensor cores)
     p.sraw = 2;
     p.splane = 1;
+    // the summed values in chunks (at least 4 complex: one tf32 MMA of K = 8) when the
+    // whole rows of two raw units and a plane slot do not fit
+    p.kc = a.umma_kc_max > 0 ? std::min(ns, std::max(2, a.umma_kc_max)) : ns;
+    while (p.kc > 2 && umma_smem(p) > kUmmaSmemMax) --p.kc;
+    if (p.kc < ns) {
+      // chunked anyway: smaller chunks for 4 raw units and 2 plane slots in flight
+      p.sraw = 4;
+      p.splane = 2;
+      while (p.kc > 2 && umma_smem(p) > kUmmaSmemMax) --p.kc;
+      if (umma_smem(p) > kUmmaSmemMax) {
+        p.sraw = 2;
+        p.splane = 1;
+      }
+    }
     if (umma_smem(p) > kUmmaSmemMax) continue;
     for (bool grew = true; grew;) {
       grew = false;
@@ -866,8 +888,8 @@ bool umma_launch(const GemmArgs& a, const UmmaPlan& p, float* data, GMeta* meta,
   // the epilogue's 16-byte stores start on 2-complex boundaries of the output
   if (a.out_base % 2 || a.out_slice_stride % 2) return false;
   CUtensorMap mL, mC;
-  if (!u_unit_map(mL, data, a.ws_elems, p.nsum, p.nlrun, p.lrun_start, p.lrun_len) ||
-      !u_unit_map(mC, data, a.ws_elems, p.nsum, p.ncrun, p.crun_start, p.crun_len))
+  if (!u_unit_map(mL, data, a.ws_elems, p.nsum, p.kc, p.nlrun, p.lrun_start, p.lrun_len) ||
+      !u_unit_map(mC, data, a.ws_elems, p.nsum, p.kc, p.ncrun, p.crun_start, p.crun_len))
     return false;
   const size_t smem = umma_smem(p);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=

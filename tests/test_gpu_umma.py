@@ -5,7 +5,9 @@ memory, products accumulated in tensor memory, outputs staged in shared memory a
 written as contiguous runs) is forced on every launch it applies to
 (QT_OPT_TCGEN05 = 1, and 3 for the other tile shape). The cases reach every way the
 two lowest output indices can fall on group and column indices, summed-index counts
-2 to 5, and both choices of the side that gives the 128 tensor-memory lanes. Split
+2 to 6, both choices of the side that gives the 128 tensor-memory lanes, and work units
+that carry a chunk of the summed values (rows too long for shared memory, or forced
+with QT_OPT_TCGEN05 = 4). Split
 TF32 (3 products per input pair) must meet the complex64 bar, 1e-5; plain TF32 (one
 product of 10-bit-mantissa inputs) is held to 1e-2.
 """
@@ -62,6 +64,39 @@ def test_umma_split_tf32_matches_oracle(qt, case, force):
     plans = _umma_launches(qt, net)
     assert plans, "no launch takes the tcgen05 kernel"
     amp = net.contract(3)  # QT_ETIMEOUT if a bounded wait gave up
+    assert net.stats()["tcgen05_gemm_launches"] > 0
+    ref, _ = oracle_amplitude(tensors, norm, plan)
+    assert rel_err(amp, ref) <= TOL[3], (case, amp, ref, rel_err(amp, ref))
+
+
+# rows too long for shared memory: the summed values in chunks accumulated in tensor memory
+CHUNK_CASES = [(36, 3, 14, 0),   # 6 summed indices (K = 64), chunks of 16
+               (30, 3, 7, 0)]    # 5 summed indices, chunks of 8
+
+
+@pytest.mark.parametrize("case", CHUNK_CASES)
+def test_umma_chunked_summed_values(qt, case):
+    """Launches whose whole rows do not fit: the plan takes chunks of the summed values
+    (kc < nsum), and the split-TF32 amplitude meets the complex64 bar."""
+    net, tensors, norm, plan = _net(qt, *case)
+    net.prepare(3, batch=2)
+    plans = _umma_launches(qt, net)
+    assert any(u["kc"] < u["nsum"] for u in plans), plans
+    amp = net.contract(3)
+    assert net.stats()["tcgen05_gemm_launches"] > 0
+    ref, _ = oracle_amplitude(tensors, norm, plan)
+    assert rel_err(amp, ref) <= TOL[3], (case, amp, ref, rel_err(amp, ref))
+
+
+@pytest.mark.parametrize("case", CASES[:6] + CHUNK_CASES)
+def test_umma_forced_small_chunks(qt, case):
+    """QT_OPT_TCGEN05 = 4: every work unit carries 4 summed values, so every launch
+    accumulates its products over several chunks; split TF32 within 1e-5."""
+    net, tensors, norm, plan = _net(qt, *case, force=4)
+    net.prepare(3, batch=2)
+    plans = _umma_launches(qt, net)
+    assert plans and all(u["kc"] == 2 for u in plans), plans
+    amp = net.contract(3)
     assert net.stats()["tcgen05_gemm_launches"] > 0
     ref, _ = oracle_amplitude(tensors, norm, plan)
     assert rel_err(amp, ref) <= TOL[3], (case, amp, ref, rel_err(amp, ref))

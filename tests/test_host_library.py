@@ -678,6 +678,27 @@ def test_tcgen05_plan_invariants(qt, case):
         assert 1 <= len(u["lruns"]) <= 3 and 1 <= len(u["cruns"]) <= 3
         assert u["smem"] <= 225 * 1024 and u["passes"] == 3
         assert 2 <= u["sraw"] <= 8 and 1 <= u["splane"] <= 4
+        assert 2 <= u["kc"] <= ns
+
+
+def test_tcgen05_chunks_long_rows(qt):
+    """N=120, p=3, seed 1003 sliced to rank 28 (the many-slice workload), split TF32:
+    the launches with 6 summed indices (rows of 64 complex) take the tcgen05 form with
+    chunks of the summed values, 4 raw units and 2 plane slots in flight; launches whose
+    rows fit whole keep them whole."""
+    from paper_2012_02430_gb300.inputs import qaoa_instance
+    edges, g, b, z = qaoa_instance(120, 3, 1003)
+    net = qt.Network(edges, 120, 3, g, b, z)
+    net.order(0)
+    net.slice(28, 43, 1)
+    qt.qt_prepare(net.handle, 3, 266)
+    plans = [L["umma"] for L in qt.qt_launch_plan(net.handle)["launches"] if "umma" in L]
+    deep = [u for u in plans if u["nsum"] == 6]
+    assert len(deep) >= 2
+    for u in deep:
+        assert 2 <= u["kc"] < 6 and u["sraw"] >= 4 and u["splane"] >= 2
+        assert u["smem"] <= 225 * 1024
+    assert all(u["kc"] == u["nsum"] for u in plans if u["nsum"] <= 3)
 
 
 @pytest.mark.parametrize("case", [(12, 1, 3, 0), (16, 2, 5, 0), (14, 2, 9, 1)])
