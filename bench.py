@@ -46,14 +46,13 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max
 # and lists them with their algorithmic bytes. Used only while the kernel sources hash to
 # STEP_DRAM_SOURCES (the sources the capture ran); after any change it is null.
 STEP_DRAM_BYTES = {
-    117: (4, 269.1e6),  # k_gemm_fold + k_gemm_tma<3,1>: read 61.5 MB, write 207.6 MB
-    120: (7, 481.4e6),  # k_gemm_stream<1> (small side folded in the kernel): 268.5 / 212.9
-    121: (7, 485.4e6),  # k_gemm_fold + k_gemm_stream<3>: 268.6 / 216.8
-    127: (4, 88.9e6),   # k_gemm_fold + k_gemm_tma<4,1>: 17.2 / 71.7
+    120: (7, 481.4e6),  # k_gemm_stream<1> (small side folded in the kernel): read 268.5 / write 212.9 MB
     131: (7, 212.9e6),  # k_gemm_stream<1>: 134.3 / 78.6
-    132: (6, 440.4e6),  # k_tri_fold + k_tri_tma<4,2>: 413.4 / 27.0
+    132: (6, 440.3e6),  # k_tri_fold + k_tri_tma<4,2>: 413.3 / 27.0
 }
-STEP_DRAM_SOURCES = "46969563cb054597"
+# (under ncu the autotuner gave steps 117, 121 and 127 to the tiled GEMM's cp.async staging,
+# which the timed run does not use there, so they have no entry)
+STEP_DRAM_SOURCES = "0297e3a862965203"
 KERNEL_SOURCES = ("engine.cu", "gemm.cu", "umma.cu", "gemm.h", "qt_internal.h")
 
 
@@ -84,7 +83,11 @@ def parse():
     ap.add_argument("--profile-pass", action="store_true",
                     help="for ncu: plan, autotune and warm the amplitude path, then run one pass "
                          "inside the NVTX range 'qt_pass' (direct launches) and print its launch list")
-    ap.add_argument("--tcgen05", type=int, default=0, choices=[0, 1, 3],
+    ap.add_argument("--profile-sampled", action="store_true",
+                    help="for ncu: a batch of 16 slices of the N=120 p=3 schedule (rank 28) in "
+                         "--precision, planned and uploaded, then one run inside the NVTX range "
+                         "'qt_sampled'")
+    ap.add_argument("--tcgen05", type=int, default=0, choices=[0, 1, 3, 4],
                     help="with --profile-pass: QT_OPT_TCGEN05 (1: the tcgen05 GEMM kernel on every "
                          "GEMM-form launch it applies to, in the tf32 / 3xtf32 precisions)")
     return ap.parse_args()
@@ -998,8 +1001,42 @@ def profile_pass(args):
                       "amplitude": [out[0].item(), out[1].item()]}))
 
 
+def profile_sampled(args):
+    """A 16-slice batch of the N=120 p=3 schedule (the many-slice workload's plan; 4 GB of
+    workspace) for ncu (--nvtx --nvtx-include qt_sampled/): no autotuning, so the kernel
+    choices are the defaults of --precision and --tcgen05."""
+    import torch
+
+    from paper_2012_02430_gb300 import qtensor as Q
+    from paper_2012_02430_gb300.inputs import qaoa_instance, random_slice_ids
+    w = C3_WORKLOAD
+    edges, g, b, z = qaoa_instance(w["n"], w["p"], w["seed"])
+    net = Q.Network(edges, w["n"], w["p"], g, b, z)
+    Q.qt_set_option(net.handle, Q.QT_OPT_GRAPHS, 0)
+    Q.qt_set_option(net.handle, Q.QT_OPT_TCGEN05, args.tcgen05)
+    net.order(Q.QT_GREEDY_MINFILL)
+    k, _ = net.slice(w["width_limit"], w["max_vars"], w["r"])
+    net.prepare(PRECISIONS[args.precision], batch=16)
+    net.upload()
+    first = random_slice_ids(k, 1, 4242)[0] & ~1023
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    net.run(first, 16, out)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("qt_sampled")
+    net.run(first, 16, out)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_sampled": {"k": k, "first_slice": first, "slices": 16,
+                                          "workspace_gb": net.stats()["workspace_bytes"] / 1e9,
+                                          "tcgen05_gemm_launches": net.stats()["tcgen05_gemm_launches"],
+                                          "sum": [out[0].item(), out[1].item()]}}))
+
+
 def main():
     args = parse()
+    if args.profile_sampled:
+        profile_sampled(args)
+        return
     if args.profile_pass:
         profile_pass(args)
         return
