@@ -472,6 +472,49 @@ def test_tma_option_range(qt):
             qt.qt_set_option(net.handle, qt.QT_OPT_TMA, v)
 
 
+def test_seg_cluster_and_tcgen05_option_ranges(qt):
+    """QT_OPT_SEG_CLUSTER takes 0 (chosen per launch) or a cluster size of 1, 2, 4 or 8;
+    QT_OPT_TCGEN05 takes 0..4 (4: every tcgen05 work unit carries 4 summed values); other
+    values are refused with QT_EINVAL."""
+    net = qt.Network([(0, 1), (1, 2), (2, 0)], 3, 1, [0.3], [0.2], [0, 1, 0])
+    for v in (0, 1, 2, 4, 8):
+        qt.qt_set_option(net.handle, qt.QT_OPT_SEG_CLUSTER, v)
+    for v in (-1, 3, 5, 16):
+        with pytest.raises(qt.QtError) as e:
+            qt.qt_set_option(net.handle, qt.QT_OPT_SEG_CLUSTER, v)
+        assert e.value.status == qt.QT_EINVAL
+    for v in range(5):
+        qt.qt_set_option(net.handle, qt.QT_OPT_TCGEN05, v)
+    for v in (-1, 5):
+        with pytest.raises(qt.QtError) as e:
+            qt.qt_set_option(net.handle, qt.QT_OPT_TCGEN05, v)
+        assert e.value.status == qt.QT_EINVAL
+
+
+def test_tensor_regions_aligned(qt):
+    """The prefix and slice regions of the workspace start on 1024 bytes, so tensor offsets
+    aligned to 64 elements inside them are aligned in the workspace: every per-slice operand
+    of a GEMM-form launch (the slice region) has its rows of up to 64 summed values start on
+    a row boundary. (Gates are packed two-element aligned and are not checked.)"""
+    from paper_2012_02430_gb300.inputs import qaoa_instance
+    for n, p, seed, wl, prec in ((120, 3, 1003, 28, 3), (80, 2, 1002, 26, 0), (30, 3, 7, 0, 4)):
+        edges, g, b, z = qaoa_instance(n, p, seed)
+        net = qt.Network(edges, n, p, g, b, z)
+        net.order(0)
+        if wl:
+            net.slice(wl, 43, 1)
+        qt.qt_prepare(net.handle, prec, 2)
+        for L in qt.qt_launch_plan(net.handle)["launches"]:
+            gm = L.get("gemm")
+            if not gm:
+                continue
+            K = 1 << gm["nsum"]
+            for side in ("A", "B"):
+                base, stride, smask, sshift = gm[side]
+                if stride:
+                    assert base % min(K, 64) == 0 and stride % min(K, 64) == 0, (n, gm["step"], side)
+
+
 def test_contract_sweep_errors(qt):
     """qt_contract_sweep refuses bad arguments before any device work: no sets, a non-finite
     angle, a network that is not ordered, or one with open qubits."""
