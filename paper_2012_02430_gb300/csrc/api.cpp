@@ -51,8 +51,19 @@ void make_tensors(qt_net* net) {
   const int n = net->n, p = net->p;
   auto var = [n](int v, int k) { return k * n + v; };
   std::vector<qt::Tensor>& T = net->tensors;
-  T.clear();
-  for (int v = 0; v < n; ++v) T.push_back({{var(v, 0)}, {1.0, 0.0, 1.0, 0.0}});
+  // the tensors are rewritten in place (new angles keep every label and size, so a call
+  // after the first allocates nothing); the list ends where this call's tensors end
+  size_t idx = 0;
+  auto emit = [&](std::initializer_list<int32_t> lab, std::initializer_list<double> dat) {
+    if (idx < T.size()) {
+      T[idx].labels.assign(lab);
+      T[idx].data.assign(dat);
+    } else {
+      T.push_back({std::vector<int32_t>(lab), std::vector<double>(dat)});
+    }
+    ++idx;
+  };
+  for (int v = 0; v < n; ++v) emit({var(v, 0)}, {1.0, 0.0, 1.0, 0.0});
   for (int k = 1; k <= p; ++k) {
     const double g = net->gammas[k - 1], b = net->betas[k - 1];
     // D(a, b) = exp(-i gamma [a != b]); M(a, a') = cos(beta) or -i sin(beta)
@@ -60,7 +71,7 @@ void make_tensors(qt_net* net) {
     const double c = std::cos(b), s = std::sin(b);
     for (int e = 0; e < net->n_edges; ++e) {
       const int u = net->edges[2 * e], w = net->edges[2 * e + 1];
-      T.push_back({{var(u, k - 1), var(w, k - 1)}, {1.0, 0.0, er, ei, er, ei, 1.0, 0.0}});
+      emit({var(u, k - 1), var(w, k - 1)}, {1.0, 0.0, er, ei, er, ei, 1.0, 0.0});
     }
     for (int v = 0; v < n; ++v) {
       int j = -1;  // open qubit number, Sec. VII
@@ -68,17 +79,18 @@ void make_tensors(qt_net* net) {
         for (size_t t = 0; t < net->open.size(); ++t)
           if (net->open[t] == v) j = (int)t;
       if (k < p) {
-        T.push_back({{var(v, k - 1), var(v, k)}, {c, 0.0, 0.0, -s, 0.0, -s, c, 0.0}});
+        emit({var(v, k - 1), var(v, k)}, {c, 0.0, 0.0, -s, 0.0, -s, c, 0.0});
       } else if (j >= 0) {
         // the whole mixer, its output index left open as variable n*p + j
-        T.push_back({{var(v, p - 1), n * p + j}, {c, 0.0, 0.0, -s, 0.0, -s, c, 0.0}});
+        emit({var(v, p - 1), n * p + j}, {c, 0.0, 0.0, -s, 0.0, -s, c, 0.0});
       } else {
         // row a' = z_v of M, as a function of a
-        if (net->z[v] == 0) T.push_back({{var(v, p - 1)}, {c, 0.0, 0.0, -s}});
-        else T.push_back({{var(v, p - 1)}, {0.0, -s, c, 0.0}});
+        if (net->z[v] == 0) emit({var(v, p - 1)}, {c, 0.0, 0.0, -s});
+        else emit({var(v, p - 1)}, {0.0, -s, c, 0.0});
       }
     }
   }
+  T.resize(idx);
 }
 
 bool check_net(const qt_net* net) { return net != nullptr; }

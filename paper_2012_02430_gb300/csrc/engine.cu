@@ -1121,17 +1121,30 @@ void build_stage(qt_net* net) {
   for (int64_t m = 0; m < S.n_shared_meta; ++m) gm[m] = Meta{0u, 0};
   for (const STensor& t : S.tensors) {
     if (t.kind != TK_GATE) continue;
-    std::vector<double> d = canonical_data(net->tensors[t.gate], t.labels);
+    // the gate's values in the canonical order of its schedule labels, written straight
+    // into the image (canonical bit b is the gate's axis axis_of[b]; no temporary copy)
+    const Tensor& gt = net->tensors[t.gate];
+    const int r = (int)gt.labels.size();
+    int axis_of[32] = {};
+    for (int b = 0; b < r; ++b)
+      for (int ax = 0; ax < r; ++ax)
+        if (gt.labels[ax] == t.labels[b]) axis_of[b] = ax;
     float mx = 0.f;
-    for (size_t e = 0; e < d.size(); ++e) {
-      if (S.precision == QT_FP64) {
-        double v = d[e];
-        std::memcpy(g + (t.offset * 2 + e) * sizeof(double), &v, sizeof(double));
-      } else {
-        float v = (float)d[e];
-        std::memcpy(g + (t.offset * 2 + e) * sizeof(float), &v, sizeof(float));
+    for (size_t e = 0; e < ((size_t)1 << r); ++e) {
+      size_t src = 0;
+      for (int b = 0; b < r; ++b)
+        if ((e >> b) & 1u) src |= (size_t)1 << axis_of[b];
+      for (int c = 0; c < 2; ++c) {
+        const double dv = gt.data[2 * src + c];
+        const size_t at = (size_t)t.offset * 2 + 2 * e + c;
+        if (S.precision == QT_FP64) {
+          std::memcpy(g + at * sizeof(double), &dv, sizeof(double));
+        } else {
+          const float fv = (float)dv;
+          std::memcpy(g + at * sizeof(float), &fv, sizeof(float));
+        }
+        mx = std::max(mx, (float)std::fabs(dv));
       }
-      mx = std::max(mx, (float)std::fabs(d[e]));
     }
     unsigned int bits;
     std::memcpy(&bits, &mx, 4);

@@ -472,6 +472,37 @@ def test_tma_option_range(qt):
             qt.qt_set_option(net.handle, qt.QT_OPT_TMA, v)
 
 
+def test_set_angles_rewrites_tensors_in_place(qt):
+    """qt_set_angles rewrites the network's tensors in place: after new angles (also with
+    open qubits, and after a new bitstring) every tensor's labels and values equal those of
+    a network built with those angles and that bitstring from the start, bit for bit."""
+    from paper_2012_02430_gb300.inputs import qaoa_instance, random_angles, random_bitstring
+    edges, g, b, z = qaoa_instance(20, 3, 77)
+    for open_q in ([], [3, 11]):
+        net = qt.qt_build_network(edges, 20, 3, g, b, z)
+        try:
+            if open_q:
+                qt.qt_set_open(net, open_q)
+            for i in range(3):
+                g2, b2 = random_angles(3, 900 + i)
+                z2 = random_bitstring(20, 950 + i) if i == 2 else z
+                if i == 2:
+                    qt.qt_set_bitstring(net, z2)
+                qt.qt_set_angles(net, g2, b2)
+                ref = qt.qt_build_network(edges, 20, 3, g2, b2, z2)
+                try:
+                    if open_q:
+                        qt.qt_set_open(ref, open_q)
+                    cnt, nv = qt.qt_num_tensors(net)
+                    assert (cnt, nv) == qt.qt_num_tensors(ref)
+                    for t in range(cnt):
+                        assert qt.qt_get_tensor(net, t) == qt.qt_get_tensor(ref, t), (open_q, i, t)
+                finally:
+                    qt.qt_free(ref)
+        finally:
+            qt.qt_free(net)
+
+
 def test_seg_cluster_and_tcgen05_option_ranges(qt):
     """QT_OPT_SEG_CLUSTER takes 0 (chosen per launch) or a cluster size of 1, 2, 4 or 8;
     QT_OPT_TCGEN05 takes 0..4 (4: every tcgen05 work unit carries 4 summed values); other
